@@ -1,0 +1,2 @@
+"""FP64 CPU oracle for subsampling SMC. Test infrastructure only: imported by tests/, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``, never by the library."""

@@ -1,0 +1,400 @@
+"""Python front end of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this module. It compiles ``smc_oracle.c`` with the host C compiler into ``oracle/_build`` and
+wraps it with ctypes; the SMC driver loop below follows Algorithm 2 of the paper step by step
+(reweight with an adaptive temperature, weighted moments and mass matrix, resample, R moves of
+Algorithm 1), calling the C routines for each step. Nothing here touches the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "smc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+FAMILIES = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3}
+TAG_INIT_THETA, TAG_INIT_U, TAG_UPM_BLOCK, TAG_UPM_IDX = 1, 2, 3, 4
+TAG_MOMENTUM, TAG_MH_THETA, TAG_MH_U, TAG_RESAMPLE = 5, 6, 7, 8
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C99 + OpenMP) into oracle/_build/liborc.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            c_i, c_i64, c_d, c_u32, c_u64 = (ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                             ctypes.c_uint32, ctypes.c_uint64)
+            L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            L.orc_r64.argtypes = [c_u64, c_u32, c_u32, c_u32, c_u64]
+            L.orc_r64.restype = c_u64
+            L.orc_index.argtypes = [c_u64, c_i64]
+            L.orc_index.restype = c_i64
+            L.orc_uniform.argtypes = [c_u64]
+            L.orc_uniform.restype = c_d
+            L.orc_normal.argtypes = [c_u64, c_u32, c_u32, c_u32, c_u64]
+            L.orc_normal.restype = c_d
+            L.orc_erfcx_cf.argtypes = [c_d]
+            L.orc_erfcx_cf.restype = c_d
+            L.orc_family.argtypes = [c_i, c_d, c_d, c_d, ctypes.POINTER(c_d),
+                                     ctypes.POINTER(c_d), ctypes.POINTER(c_d)]
+            L.orc_full_loglik.argtypes = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp,
+                                          ctypes.POINTER(c_d), ctypes.c_void_p]
+            L.orc_cv_moments.argtypes = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp,
+                                         ctypes.POINTER(c_d), _dp, _dp]
+            L.orc_log_prior.argtypes = [c_i, _dp, _dp, _dp, ctypes.c_void_p]
+            L.orc_log_prior.restype = c_d
+            prob = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp, c_d, _dp, _dp, _dp, _dp, c_i, c_i]
+            L.orc_loglik_batch.argtypes = prob + [c_i, _dp, _i64p, c_d, _dp, _dp,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_init.argtypes = [c_u64, c_i, c_i, c_i, c_i64, _dp, _dp, _dp, _i64p]
+            L.orc_upm_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, _dp, _i64p, _i32p]
+            L.orc_hmc_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, c_i, _dp, _dp, _dp,
+                                              _i64p, _i32p]
+            L.orc_ess_at.argtypes = [c_i, _dp, _dp, _dp, c_d, c_d]
+            L.orc_ess_at.restype = c_d
+            L.orc_reweight.argtypes = [c_i, _dp, _dp, _dp, _dp, c_d, c_d, c_i, c_i,
+                                       ctypes.POINTER(c_d), ctypes.POINTER(c_d)]
+            L.orc_reweight.restype = c_d
+            L.orc_cholesky.argtypes = [c_i, _dp, _dp]
+            L.orc_cholesky.restype = c_i
+            L.orc_moments.argtypes = [c_i, c_i, _dp, _dp, _dp, _dp, _dp]
+            L.orc_moments.restype = c_i
+            L.orc_resample.argtypes = [c_i, _dp, c_d, _i32p]
+            L.orc_num_threads.restype = c_i
+            _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------------------------
+# Random numbers (same published generator and counter layout as the CUDA side, separate code)
+# ----------------------------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(c, k, o)
+    return o
+
+
+def stage_move(stage: int, move: int) -> int:
+    return (stage << 8) | move
+
+
+def r64(seed, tag, sm, particle, j) -> int:
+    return int(lib().orc_r64(seed, tag, sm, particle, j))
+
+
+def index(r, n) -> int:
+    return int(lib().orc_index(r, n))
+
+
+def uniform(r) -> float:
+    return float(lib().orc_uniform(r))
+
+
+def normal(seed, tag, sm, particle, j) -> float:
+    return float(lib().orc_normal(seed, tag, sm, particle, j))
+
+
+# ----------------------------------------------------------------------------------------------
+# Model pieces
+# ----------------------------------------------------------------------------------------------
+def family(fam: str, eta: float, y: float, sigma: float = 1.0):
+    l, d1, d2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().orc_family(FAMILIES[fam], eta, y, sigma, ctypes.byref(l), ctypes.byref(d1),
+                     ctypes.byref(d2))
+    return l.value, d1.value, d2.value
+
+
+def full_loglik(fam, X, y, theta, sigma=1.0, grad=True):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n, p = X.shape
+    ell = ctypes.c_double()
+    g = np.zeros(p)
+    lib().orc_full_loglik(FAMILIES[fam], n, p, X, np.ascontiguousarray(y, np.float64), sigma,
+                          np.ascontiguousarray(theta, np.float64), ctypes.byref(ell),
+                          g.ctypes.data if grad else None)
+    return (ell.value, g) if grad else ell.value
+
+
+def cv_moments(fam, X, y, theta_bar, sigma=1.0):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n, p = X.shape
+    A = ctypes.c_double()
+    B = np.zeros(p)
+    C = np.zeros((p, p))
+    lib().orc_cv_moments(FAMILIES[fam], n, p, X, np.ascontiguousarray(y, np.float64), sigma,
+                         np.ascontiguousarray(theta_bar, np.float64), ctypes.byref(A), B, C)
+    return A.value, B, C
+
+
+def log_prior(theta, mu, var):
+    theta = np.ascontiguousarray(theta, np.float64)
+    g = np.zeros(theta.shape[0])
+    v = lib().orc_log_prior(theta.shape[0], theta, np.ascontiguousarray(mu, np.float64),
+                            np.ascontiguousarray(var, np.float64), g.ctypes.data)
+    return v, g
+
+
+@dataclass
+class Problem:
+    """A GLM posterior: data, family, prior, control-variate centre and its moments A, B, C."""
+    family: str
+    X: np.ndarray            # [n, p] float64 (the stored values, upcast)
+    y: np.ndarray            # [n] float64
+    prior_mean: np.ndarray   # [p]
+    prior_var: np.ndarray    # [p]
+    sigma: float = 1.0
+    theta_bar: np.ndarray | None = None
+    A: float = 0.0
+    B: np.ndarray | None = None
+    C: np.ndarray | None = None
+
+    def __post_init__(self):
+        self.X = np.ascontiguousarray(self.X, dtype=np.float64)
+        self.y = np.ascontiguousarray(self.y, dtype=np.float64)
+        self.prior_mean = np.ascontiguousarray(self.prior_mean, np.float64)
+        self.prior_var = np.ascontiguousarray(self.prior_var, np.float64)
+
+    @property
+    def n(self):
+        return self.X.shape[0]
+
+    @property
+    def p(self):
+        return self.X.shape[1]
+
+    def set_centre(self, theta_bar):
+        self.theta_bar = np.ascontiguousarray(theta_bar, np.float64)
+        self.A, self.B, self.C = cv_moments(self.family, self.X, self.y, self.theta_bar,
+                                            self.sigma)
+
+    def args(self, m, G):
+        return (FAMILIES[self.family], self.n, self.p, self.X, self.y, self.sigma,
+                self.theta_bar, self.A, self.B, self.C, self.prior_mean, self.prior_var, m, G)
+
+
+def newton_map(prob: Problem, iters: int = 50, tol: float = 1e-10):
+    """Posterior mode (full data + prior) by Newton's method with step halving; the
+    control-variate centre of the workloads (a fixed reading of Sec. 3.2's theta_bar)."""
+    theta = prob.prior_mean.copy()
+
+    def logpost(t):
+        A, B, C = cv_moments(prob.family, prob.X, prob.y, t, prob.sigma)
+        lp, gp = log_prior(t, prob.prior_mean, prob.prior_var)
+        return A + lp, B + gp, C - np.diag(1.0 / prob.prior_var)
+
+    f, g, H = logpost(theta)
+    for _ in range(iters):
+        step = np.linalg.solve(-H, g)
+        t = 1.0
+        while True:
+            cand = theta + t * step
+            fc, gc, Hc = logpost(cand)
+            if fc >= f or t < 1e-8:
+                break
+            t *= 0.5
+        theta, f, g, H = cand, fc, gc, Hc
+        if np.max(np.abs(t * step)) < tol:
+            break
+    return theta
+
+
+def loglik_batch(prob: Problem, m, G, thetas, us, a=1.0, grad=True, blocks=False):
+    thetas = np.ascontiguousarray(thetas, np.float64)
+    us = np.ascontiguousarray(us, np.int64)
+    Bn = thetas.shape[0]
+    ell = np.zeros(Bn)
+    s2 = np.zeros(Bn)
+    g = np.zeros((Bn, prob.p)) if grad else None
+    blk = np.zeros((Bn, G, 2)) if blocks else None
+    lib().orc_loglik_batch(*prob.args(m, G), Bn, thetas, us, a, ell, s2,
+                           g.ctypes.data if grad else None, blk.ctypes.data if blocks else None)
+    out = {"ell": ell, "sigma2": s2}
+    if grad:
+        out["grad"] = g
+    if blocks:
+        out["blocks"] = blk
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# SMC steps (Algorithm 2) and moves (Algorithm 1)
+# ----------------------------------------------------------------------------------------------
+def init_particles(seed, N, p, m, n, prior_mean, prior_var):
+    th = np.zeros((N, p))
+    us = np.zeros((N, m), dtype=np.int64)
+    lib().orc_init(seed, N, p, m, n, np.ascontiguousarray(prior_mean, np.float64),
+                   np.ascontiguousarray(prior_var, np.float64), th, us)
+    return th, us
+
+
+def upm_move(prob, m, G, seed, stage, move, a, thetas, us):
+    N = thetas.shape[0]
+    acc = np.zeros(N, dtype=np.int32)
+    lib().orc_upm_move(*prob.args(m, G), N, seed, stage_move(stage, move), a,
+                       np.ascontiguousarray(thetas, np.float64), us, acc)
+    return acc
+
+
+def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us):
+    N = thetas.shape[0]
+    acc = np.zeros(N, dtype=np.int32)
+    lib().orc_hmc_move(*prob.args(m, G), N, seed, stage_move(stage, move), a, eps, L,
+                       np.ascontiguousarray(Sigma, np.float64), np.ascontiguousarray(Lc, np.float64),
+                       thetas, np.ascontiguousarray(us, np.int64), acc)
+    return acc
+
+
+def ess_at(logW, ell, sig2, a, D):
+    return float(lib().orc_ess_at(len(logW), np.ascontiguousarray(logW, np.float64),
+                                  np.ascontiguousarray(ell, np.float64),
+                                  np.ascontiguousarray(sig2, np.float64), a, D))
+
+
+def reweight(logW, ell, sig2, a, tau, K=16, rounds=10):
+    """Returns (a_new, logW_new, W_new, log_z_inc, ess); inputs are not modified."""
+    lw = np.array(logW, dtype=np.float64)
+    W = np.zeros_like(lw)
+    lz = ctypes.c_double()
+    ess = ctypes.c_double()
+    a_new = lib().orc_reweight(len(lw), lw, W, np.ascontiguousarray(ell, np.float64),
+                               np.ascontiguousarray(sig2, np.float64), a, tau, K, rounds,
+                               ctypes.byref(lz), ctypes.byref(ess))
+    return float(a_new), lw, W, lz.value, ess.value
+
+
+def cholesky(S):
+    S = np.ascontiguousarray(S, np.float64)
+    Lc = np.zeros_like(S)
+    rc = lib().orc_cholesky(S.shape[0], S, Lc)
+    return Lc if rc == 0 else None
+
+
+def moments(W, thetas):
+    N, p = thetas.shape
+    mean = np.zeros(p)
+    S = np.zeros((p, p))
+    Lc = np.zeros((p, p))
+    rc = lib().orc_moments(N, p, np.ascontiguousarray(W, np.float64),
+                           np.ascontiguousarray(thetas, np.float64), mean, S, Lc)
+    return mean, S, Lc, rc
+
+
+def resample(W, U):
+    W = np.ascontiguousarray(W, np.float64)
+    anc = np.zeros(W.shape[0], dtype=np.int32)
+    lib().orc_resample(W.shape[0], W, U, anc)
+    return anc
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+@dataclass
+class SMCConfig:
+    N: int
+    m: int
+    G: int
+    L: int
+    R: int
+    seed: int
+    tau: float = 0.5
+    K: int = 16
+    rounds: int = 10
+    eps0: float | None = None      # default 0.5 * p^(-1/4)
+    max_stages: int = 1000
+
+
+@dataclass
+class SMCState:
+    stage: int
+    a: float
+    eps: float
+    thetas: np.ndarray
+    us: np.ndarray
+    logW: np.ndarray
+    W: np.ndarray
+    ell: np.ndarray
+    sig2: np.ndarray
+    log_z: float = 0.0
+    history: list = field(default_factory=list)
+
+
+def smc_init(prob: Problem, cfg: SMCConfig) -> SMCState:
+    """Algorithm 2 step 1: particles from the prior and p(u), equal weights, cached estimates."""
+    th, us = init_particles(cfg.seed, cfg.N, prob.p, cfg.m, prob.n, prob.prior_mean,
+                            prob.prior_var)
+    out = loglik_batch(prob, cfg.m, cfg.G, th, us, a=0.0, grad=False)
+    eps = cfg.eps0 if cfg.eps0 is not None else 0.5 * prob.p ** -0.25
+    logW = np.full(cfg.N, -math.log(cfg.N))
+    return SMCState(0, 0.0, eps, th, us, logW, np.exp(logW), out["ell"], out["sigma2"])
+
+
+def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
+    """One pass of Algorithm 2's loop body: (a) stage+1, (b)-(c) temperature and reweighting,
+    (d) weighted moments and mass matrix, (e) resampling, (f) R moves of Algorithm 1."""
+    st.stage += 1
+    s = st.stage
+    a_new, logW, W, lz, ess = reweight(st.logW, st.ell, st.sig2, st.a, cfg.tau, cfg.K,
+                                       cfg.rounds)
+    mean, Sigma, Lc, _ = moments(W, st.thetas)
+    U = uniform(r64(cfg.seed, TAG_RESAMPLE, stage_move(s, 0), 0, 0))
+    anc = resample(W, U)
+    st.thetas = st.thetas[anc].copy()
+    st.us = st.us[anc].copy()
+    st.a = a_new
+    st.log_z += lz
+    st.logW = np.full(cfg.N, -math.log(cfg.N))
+    st.W = np.exp(st.logW)
+    acc_u = acc_t = 0
+    for r in range(cfg.R):
+        acc_u += int(upm_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.thetas, st.us).sum())
+        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.eps, cfg.L, Sigma, Lc,
+                              st.thetas, st.us).sum())
+    out = loglik_batch(prob, cfg.m, cfg.G, st.thetas, st.us, a=st.a, grad=False)
+    st.ell, st.sig2 = out["ell"], out["sigma2"]
+    rate = acc_t / float(cfg.N * cfg.R)
+    st.history.append(dict(stage=s, a=st.a, ess=ess, log_z_inc=lz, eps=st.eps,
+                           acc_u=acc_u / float(cfg.N * cfg.R), acc_theta=rate))
+    st.eps = st.eps * min(2.0, max(0.5, math.exp(rate - 0.65)))
+    return st
+
+
+def smc_run(prob: Problem, cfg: SMCConfig) -> SMCState:
+    st = smc_init(prob, cfg)
+    while st.a < 1.0 and st.stage < cfg.max_stages:
+        smc_stage(prob, cfg, st)
+    return st

@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs shaped like the paper's GLM workloads.
+
+This module only generates data (covariates, responses, priors and run settings). It holds none
+of the method's arithmetic and is the one piece shared by the CUDA tests, the oracle tests and the
+benchmark. Every array is produced from ``numpy.random.Generator(PCG64(seed))``.
+
+Stored precision: ``x_dtype`` names how X is stored on the device ("f64", "f32" or "bf16").
+``Workload.X`` always holds the *stored* values upcast to float64, so the oracle sees exactly what
+the GPU reads; ``Workload.X_store`` holds the raw storage (float64, float32, or the uint16 bit
+patterns of bfloat16). The response y is stored as float64 for "f64" problems and float32
+otherwise; ``Workload.y`` is its float64 upcast.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+BASE_SEED = 20180508
+
+
+def round_to_bf16_bits(a32: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even); returns the uint16 bits."""
+    b = np.ascontiguousarray(a32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return b.astype(np.uint16)
+
+
+def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@dataclass
+class Workload:
+    name: str
+    family: str
+    x_dtype: str
+    X: np.ndarray          # [n, p] float64: stored values, upcast
+    X_store: np.ndarray    # [n, p] raw storage
+    y: np.ndarray          # [n] float64: stored values, upcast
+    y_store: np.ndarray    # [n] raw storage (float64 or float32)
+    prior_mean: np.ndarray
+    prior_var: np.ndarray
+    N: int
+    m: int
+    G: int
+    L: int
+    R: int
+    seed: int
+    sigma: float = 1.0
+    theta_true: np.ndarray | None = None
+
+    @property
+    def n(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def p(self) -> int:
+        return self.X.shape[1]
+
+
+def _store(X: np.ndarray, y: np.ndarray, x_dtype: str):
+    if x_dtype == "f64":
+        Xs = np.ascontiguousarray(X, dtype=np.float64)
+        ys = np.ascontiguousarray(y, dtype=np.float64)
+        return Xs, Xs, ys, ys
+    ys = np.ascontiguousarray(y, dtype=np.float32)
+    if x_dtype == "f32":
+        Xs = np.ascontiguousarray(X, dtype=np.float32)
+        return Xs.astype(np.float64), Xs, ys.astype(np.float64), ys
+    if x_dtype == "bf16":
+        bits = round_to_bf16_bits(np.asarray(X, dtype=np.float32))
+        return bf16_bits_to_f64(bits), bits, ys.astype(np.float64), ys
+    raise ValueError(x_dtype)
+
+
+def _respond(rng, family: str, eta: np.ndarray, sigma: float = 1.0) -> np.ndarray:
+    if family == "logistic":
+        return (rng.random(eta.shape[0]) < 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
+    if family == "probit":
+        from scipy.special import ndtr
+        return (rng.random(eta.shape[0]) < ndtr(eta)).astype(np.float64)
+    if family == "poisson":
+        return rng.poisson(np.exp(eta)).astype(np.float64)
+    if family == "gaussian":
+        return eta + sigma * rng.standard_normal(eta.shape[0])
+    raise ValueError(family)
+
+
+def small_glm(family: str = "logistic", n: int = 2000, p: int = 5, N: int = 64, m: int = 50,
+              G: int = 5, L: int = 5, R: int = 2, x_dtype: str = "f64", seed: int = 1,
+              sigma: float = 0.5, theta_scale: float = 0.5, prior_var: float = 10.0,
+              x_scale: float = 1.0) -> Workload:
+    """Small seeded GLM (intercept + iid N(0, x_scale^2) covariates) for parity and pin tests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = np.empty((n, p))
+    X[:, 0] = 1.0
+    X[:, 1:] = x_scale * rng.standard_normal((n, p - 1))
+    theta = theta_scale * rng.standard_normal(p)
+    Xs64, Xs, _, _ = _store(X, np.zeros(n), x_dtype)
+    y = _respond(rng, family, Xs64 @ theta, sigma)
+    Xd, Xs, yd, ys = _store(X, y, x_dtype)
+    return Workload(f"small-{family}", family, x_dtype, Xd, Xs, yd, ys, np.zeros(p),
+                    np.full(p, prior_var), N, m, G, L, R, seed, sigma, theta)
+
+
+def logistic_1e4(seed_offset: int = 0) -> Workload:
+    """Plain method in FP64: logistic regression, n=10,000, p=5 (intercept + 4 iid N(0,1)),
+    theta_true ~ N(0, 0.5^2 I), prior N(0, 10 I); N=256 particles, m=100, G=10, L=10, R=5."""
+    seed = BASE_SEED + 0 + seed_offset
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n, p = 10_000, 5
+    X = np.empty((n, p))
+    X[:, 0] = 1.0
+    X[:, 1:] = rng.standard_normal((n, p - 1))
+    theta = 0.5 * rng.standard_normal(p)
+    y = _respond(rng, "logistic", X @ theta)
+    Xd, Xs, yd, ys = _store(X, y, "f64")
+    return Workload("logistic-n1e4-p5-f64", "logistic", "f64", Xd, Xs, yd, ys, np.zeros(p),
+                    np.full(p, 10.0), 256, 100, 10, 10, 5, seed, 1.0, theta)
+
+
+def logistic_1e6(x_dtype: str = "bf16", n: int = 1_000_000) -> Workload:
+    """Logistic regression at scale: n=1,000,000, p=20 (intercept + 19 N(0,1) covariates with
+    AR(1) correlation 0.5 across columns), theta_true ~ N(0, 0.3^2 I), prior N(0, 10 I);
+    N=4096 particles, m=1000, G=10, L=20, R=5. X stored as FP32 or BF16."""
+    seed = BASE_SEED + 1
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p, rho = 20, 0.5
+    X = np.empty((n, p), dtype=np.float32)
+    X[:, 0] = 1.0
+    prev = rng.standard_normal(n)
+    X[:, 1] = prev
+    s = math.sqrt(1.0 - rho * rho)
+    for c in range(2, p):
+        prev = rho * prev + s * rng.standard_normal(n)
+        X[:, c] = prev
+    theta = 0.3 * rng.standard_normal(p)
+    Xs64, _, _, _ = _store(X, np.zeros(n), x_dtype)
+    y = _respond(rng, "logistic", Xs64 @ theta)
+    Xd, Xs, yd, ys = _store(X, y, x_dtype)
+    return Workload(f"logistic-n1e6-p20-{x_dtype}", "logistic", x_dtype, Xd, Xs, yd, ys,
+                    np.zeros(p), np.full(p, 10.0), 4096, 1000, 10, 20, 5, seed, 1.0, theta)
+
+
+def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000) -> Workload:
+    """Poisson regression: n=5,000,000, p=50 (intercept + 49 N(0, 0.1^2) covariates),
+    theta_true ~ N(0, 0.2^2 I) with intercept 1.0, prior N(0, 0.1 I); N=8192, m=2000, G=20,
+    L=20, R=5. X stored as BF16."""
+    seed = BASE_SEED + 2
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = 50
+    X = np.empty((n, p), dtype=np.float32)
+    X[:, 0] = 1.0
+    X[:, 1:] = 0.1 * rng.standard_normal((n, p - 1), dtype=np.float32)
+    theta = 0.2 * rng.standard_normal(p)
+    theta[0] = 1.0
+    Xs64, _, _, _ = _store(X, np.zeros(n), x_dtype)
+    y = _respond(rng, "poisson", Xs64 @ theta)
+    Xd, Xs, yd, ys = _store(X, y, x_dtype)
+    return Workload(f"poisson-n5e6-p50-{x_dtype}", "poisson", x_dtype, Xd, Xs, yd, ys,
+                    np.zeros(p), np.full(p, 0.1), 8192, 2000, 20, 20, 5, seed, 1.0, theta)
