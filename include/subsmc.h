@@ -1,0 +1,181 @@
+/*
+ * subsmc.h -- C ABI of the GB300 (sm_103a) library for likelihood-annealed subsampling SMC
+ * (Gunawan, Dang, Quiroz, Kohn & Tran, arXiv:1805.03317).
+ *
+ * Conventions for every entry point:
+ *   - Return value: SMC_OK (0) or a negative smc_status. Nothing throws across the ABI.
+ *     smc_last_error() returns a NUL-terminated description of the last failure on a context.
+ *   - Pointers marked "device" are CUDA device pointers; "host" are ordinary host pointers;
+ *     "any" accepts either (the library copies with cudaMemcpyDefault, so host memory may be
+ *     pageable or pinned). The caller owns every buffer it passes; the library owns the context
+ *     and all memory it allocates, and frees it in smc_free().
+ *   - All GPU work is enqueued on the stream given to smc_init(). Entry points that return host
+ *     scalars synchronise that stream before returning.
+ *   - Particle state precision ("state type"): double when the problem's x_dtype is SMC_F64,
+ *     float otherwise. theta, gradients and caller-provided particle buffers use it. Control-variate
+ *     moments, log weights, the temperature, the log marginal likelihood and MH log ratios are FP64.
+ *   - Notation follows the paper: n rows, p parameters, N particles (the paper's M), subsample
+ *     size m, G blocks of u, L leapfrog steps, temperature a in [0,1].
+ */
+#ifndef SUBSMC_H
+#define SUBSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smc_ctx smc_ctx;
+
+typedef enum {
+  SMC_OK = 0,
+  SMC_ERR_ARG = -1,       /* invalid argument, shape or layout                                  */
+  SMC_ERR_CUDA = -2,      /* a CUDA runtime call failed (message in smc_last_error)            */
+  SMC_ERR_NONFINITE = -3, /* a non-finite value appeared where the method needs a finite one    */
+  SMC_ERR_TIMEOUT = -4,   /* an iteration cap in a device loop was reached                       */
+  SMC_ERR_OOM = -5,       /* device allocation failed                                           */
+  SMC_ERR_STATE = -6      /* call out of order (e.g. a stage step before smc_init finished)      */
+} smc_status;
+
+/* Per-row likelihood families l_k(theta) = log p(y_k | x_k' theta) (Sec. 3.1, Eq. likelihood).
+ * Logistic: Sec. 4.2 (Experiment 1); Poisson with log link: Sec. 4.3 (Experiment 2);
+ * Gaussian response with known sd and probit: used by the synthetic workloads. */
+typedef enum { SMC_LOGISTIC = 0, SMC_PROBIT = 1, SMC_POISSON = 2, SMC_GAUSSIAN = 3 } smc_family;
+
+/* Storage type of the covariate matrix X. */
+typedef enum { SMC_F64 = 0, SMC_F32 = 1, SMC_BF16 = 2 } smc_dtype;
+
+/* The paper's problem statement (Sec. 2.1 and Sec. 3.1): independent rows (x_k, y_k), a GLM
+ * likelihood, and a prior p(theta), here a diagonal Gaussian N(prior_mean, diag(prior_var)). */
+typedef struct {
+  int32_t family;            /* smc_family                                                        */
+  int64_t n;                 /* number of rows, >= 1                                              */
+  int32_t p;                 /* number of parameters, 1 <= p <= 126                              */
+  const void *X;             /* device, row-major [n, x_ld], element type x_dtype. Read only     */
+                             /* inside smc_init (the library keeps its own packed copy).         */
+  int32_t x_dtype;           /* smc_dtype                                                         */
+  int64_t x_ld;              /* row stride of X in elements, >= p                                 */
+  const void *y;             /* device [n]: double when x_dtype == SMC_F64, else float.           */
+                             /* Read only inside smc_init.                                        */
+  const double *prior_mean;  /* host [p]                                                          */
+  const double *prior_var;   /* host [p], every entry > 0                                         */
+  double noise_sigma;        /* Gaussian family: known response sd (> 0); ignored otherwise       */
+} smc_problem;
+
+/* Run settings. The paper's tuning knobs (Sec. 3.4, Sec. 4.1): M particles, m, G, the ESS target,
+ * the leapfrog step and count; R moves per stage is an argument of smc_move(). */
+typedef struct {
+  int32_t N;                 /* particles (the paper's M), 1 <= N < 2^23                          */
+  int32_t m;                 /* subsample size, >= 1                                              */
+  int32_t G;                 /* blocks of u for the block pseudo-marginal update, 1 <= G <= m     */
+  int32_t L;                 /* leapfrog steps per HMC move, >= 1                                 */
+  double ess_frac;           /* ESS target as a fraction of N, in (0, 1]                          */
+  uint64_t seed;             /* key of the Philox4x32-10 streams                                  */
+  int32_t search_k;          /* K of the K-ary temperature search (2 = bisection); 0 -> 16        */
+  int32_t search_rounds;     /* refinement rounds; 0 -> 10                                        */
+  double eps0;               /* initial leapfrog step; <= 0 -> 0.5 * p^(-1/4)                     */
+  int32_t tile_hint;         /* estimator tile: 0 = automatic, k >= 1 = compiled tile k-1         */
+} smc_config;
+
+/* ------------------------------------------------------------------------------------------- */
+/* Lifetime                                                                                     */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Create a context (Algorithm 2 step 1). Packs X and y into the library's row layout, sets the
+ * control-variate centre theta_bar (host [p]; NULL = the full-data posterior mode, found by Newton's
+ * method on the device), computes the moments A, B, C at theta_bar (Sec. 3.2), draws theta ~ p(theta)
+ * and u ~ p(u) for every particle, sets W = 1/N and caches l_hat, sigma2_hat per particle.
+ * stream: a cudaStream_t (NULL = legacy default stream). On failure *out is NULL. */
+int smc_init(smc_ctx **out, const smc_problem *prob, const smc_config *cfg,
+             const double *theta_bar, void *stream);
+
+/* Release the context and all library-owned device memory. NULL is allowed. */
+int smc_free(smc_ctx *ctx);
+
+/* Description of the last error on ctx (or of the last failed smc_init when ctx is NULL). */
+const char *smc_last_error(const smc_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------------- */
+/* One SMC stage: smc_reweight, smc_resample, smc_move (Algorithm 2 steps (a)-(f))               */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Steps (a)-(d): advance the stage counter; choose the next temperature a_s so that the ESS of the
+ * new weights stays at ess_frac*N (Sec. 2.2; K-ary refinement of a bracket, Algorithm 2 (b));
+ * reweight with w_i = W_i exp((a_s - a_{s-1}) l_hat_i - (a_s^2 - a_{s-1}^2) sigma2_hat_i / 2)
+ * (Sec. 3.3) and normalise in FP64; accumulate log Z_s/Z_{s-1} (Sec. 3.5); form the weighted
+ * particle covariance Sigma and its Cholesky factor for the HMC mass matrix H = Sigma^{-1}.
+ * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS. */
+int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
+
+/* Step (e): systematic resampling with the current weights (integer-quantised, exact; see the
+ * design notes), carrying theta, u and the cached estimates; then W = 1/N.
+ * ancestors: device [N] int32 or NULL. */
+int smc_resample(smc_ctx *ctx, int32_t *ancestors);
+
+/* Step (f): R Markov moves of Algorithm 1 at the current temperature, each a block pseudo-marginal
+ * update of u (Eq. acc_prop_u) followed by an HMC move of theta given u. Afterwards the leapfrog
+ * step adapts: eps *= clip(exp(theta_acceptance - 0.65), 0.5, 2).
+ * Host outputs (may be NULL): acceptance rates of the u and theta updates over these R moves. */
+int smc_move(smc_ctx *ctx, int32_t R, double *acc_u, double *acc_theta);
+
+/* ------------------------------------------------------------------------------------------- */
+/* The subsampled estimator on caller-supplied particles (Sec. 3.2, Eq. difference_estimator_logl)*/
+/* ------------------------------------------------------------------------------------------- */
+
+/* For B particles: l_hat_m(theta_b; u_b) and sigma2_hat_m(theta_b; u_b).
+ * theta: device [B, p] state type; u: device [B, m] int32 row indices in [0, n);
+ * ell, sigma2: device [B] double. Out-of-range indices return SMC_ERR_ARG (checked on device). */
+int loglik_est(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, double *ell,
+               double *sigma2);
+
+/* As loglik_est, plus the gradient of a*l_hat - (a^2/2)*sigma2_hat + log p(theta) for fixed u
+ * (the HMC force of Algorithm 1 step 2). grad: device [B, p] state type; ell, sigma2 may be NULL. */
+int loglik_grad(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, double a,
+                void *grad, double *ell, double *sigma2);
+
+/* ------------------------------------------------------------------------------------------- */
+/* State access (for checkpointing, tests and host-resident callers)                             */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Copy out theta [N,p] (state type), u [N,m] int32 and normalised weights W [N] double.
+ * Pointers are "any" (host or device); each may be NULL. */
+int smc_get_particles(smc_ctx *ctx, void *theta, int32_t *u, double *W);
+
+/* Replace the particle cloud. theta [N,p] state type, u [N,m] int32, W [N] double (normalised,
+ * or NULL for 1/N); "any" pointers. The cached l_hat, sigma2_hat are recomputed. */
+int smc_set_particles(smc_ctx *ctx, const void *theta, const int32_t *u, const double *W);
+
+/* Cached per-particle estimates: ell, sigma2 [N] double; blocks [N, G, 2] double holding, per
+ * block of u, (sum of d_j, sum of d_j^2) with d_j = l_{u_j} - q_{u_j}. "any" pointers or NULL. */
+int smc_get_cache(smc_ctx *ctx, double *ell, double *sigma2, double *blocks);
+
+/* Control-variate centre and moments (host): theta_bar [p], A, B [p], C [p,p]; any may be NULL. */
+int smc_get_centre(smc_ctx *ctx, double *theta_bar, double *A, double *B, double *C);
+
+/* Moments at an arbitrary point theta (host [p]) without changing the context's centre:
+ * A = sum_k l_k, B = sum_k grad l_k, C = sum_k hess l_k (host outputs, C row-major [p,p]). */
+int smc_cv_moments(smc_ctx *ctx, const double *theta, double *A, double *B, double *C);
+
+/* Mass-matrix inputs of the current stage (host): Sigma [p,p] and its lower Cholesky factor. */
+int smc_get_mass(smc_ctx *ctx, double *Sigma, double *chol);
+
+/* Scalars: temperature a, accumulated log Z, stage index, leapfrog step. Host, each may be NULL. */
+int smc_get_status(smc_ctx *ctx, double *a, double *log_z, int32_t *stage, double *eps);
+
+/* Overwrite the scalars (stage index, temperature, leapfrog step); log Z is reset to log_z.
+ * The cached estimates stay valid (they do not depend on a). */
+int smc_set_scalars(smc_ctx *ctx, int32_t stage, double a, double eps, double log_z);
+
+/* Time the estimator's compiled tile shapes on this context's own particles and keep the fastest.
+ * Host output (may be NULL): the chosen tile as a tile_hint value (>= 1). */
+int smc_autotune(smc_ctx *ctx, int32_t *tile);
+
+/* Number of kernels this context has launched so far (every launch is counted). */
+int64_t smc_launch_count(const smc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUBSMC_H */

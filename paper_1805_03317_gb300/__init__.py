@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) library for likelihood-annealed subsampling SMC (arXiv:1805.03317).
+
+The compute path is the CUDA library built from ``csrc/`` and declared in ``include/subsmc.h``;
+this package is its Python binding (``smc``) and build script (``build``).
+"""
+from .smc import (Context, SubsampledSMC, loglik_est, loglik_grad, smc_autotune, smc_cv_moments,
+                  smc_free, smc_get_cache, smc_get_centre, smc_get_mass, smc_get_particles,
+                  smc_get_status, smc_init, smc_launch_count, smc_move, smc_resample,
+                  smc_reweight, smc_set_particles, smc_set_scalars)
+
+__all__ = ["Context", "SubsampledSMC", "loglik_est", "loglik_grad", "smc_autotune",
+           "smc_cv_moments", "smc_free", "smc_get_cache", "smc_get_centre", "smc_get_mass",
+           "smc_get_particles", "smc_get_status", "smc_init", "smc_launch_count", "smc_move",
+           "smc_resample", "smc_reweight", "smc_set_particles", "smc_set_scalars"]

@@ -1,0 +1,745 @@
+// C ABI of the subsampling-SMC library (declared in include/subsmc.h). Host orchestration only:
+// every arithmetic step of the method runs in the kernels of estimator.cuh and stage.cu.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "subsmc.h"
+
+using namespace subsmc;
+
+struct smc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // problem
+  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, p = 0;
+  int64_t n = 0;
+  double noise_sigma = 1.0;
+  std::vector<double> mu_h, var_h;
+  double log_prior_const = 0.0;
+  // configuration
+  int N = 0, m = 0, G = 0, L = 0, K = 16, rounds = 10, tile = 0;
+  double tau = 0.5, eps0 = 0.0;
+  uint64_t seed = 0;
+  // device memory (library-owned)
+  std::vector<void *> allocs;
+  void *Xp = nullptr;
+  double *mu_d = nullptr, *var_d = nullptr;
+  void *mu_ct = nullptr, *ivar_ct = nullptr;
+  double *tb_d = nullptr, *A_d = nullptr, *B_d = nullptr, *C_d = nullptr;
+  void *tb_ct = nullptr, *B_ct = nullptr, *C_ct = nullptr;
+  double A_h = 0.0;
+  void *theta = nullptr, *theta_alt = nullptr, *grad_scratch = nullptr;
+  int32_t *u = nullptr, *u_alt = nullptr, *unew = nullptr, *anc = nullptr;
+  int maxblk = 1;
+  double *logW = nullptr, *W = nullptr;
+  double *ell = nullptr, *sig2 = nullptr, *blk = nullptr;
+  double *ell_alt = nullptr, *sig2_alt = nullptr, *blk_alt = nullptr, *blk_prop = nullptr;
+  double *mean_d = nullptr, *Sigma_raw = nullptr, *Sigma_d = nullptr, *chol_d = nullptr;
+  double *mass_work = nullptr;
+  void *Sigma_ct = nullptr, *Linv_ct = nullptr;
+  double *part = nullptr;
+  size_t part_bytes = 0;
+  uint64_t *cum = nullptr;
+  double *scratch_d = nullptr;  // small FP64 scratch (Newton, moments at a point)
+  int *info_d = nullptr;
+  DevState *st = nullptr;
+  // host mirrors
+  int stage = 0, moves_in_stage = 0;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_init_error;
+
+int fail(smc_ctx *c, int code, const std::string &msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_init_error = msg;
+  return code;
+}
+
+#define CUDA_OK(c, expr)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (cudaError_t)(expr);                                                \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(c, SMC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define LAUNCH(c, expr, nlaunch)                                                        \
+  do {                                                                                 \
+    int e_ = (expr);                                                                   \
+    (c)->launches += (nlaunch);                                                        \
+    if (e_ != 0)                                                                       \
+      return fail(c, SMC_ERR_CUDA,                                                     \
+                  std::string(#expr) + ": " + cudaGetErrorString((cudaError_t)e_));    \
+  } while (0)
+
+template <typename P> int dalloc(smc_ctx *c, P **ptr, size_t bytes) {
+  void *q = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                    cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *ptr = reinterpret_cast<P *>(q);
+  return SMC_OK;
+}
+
+#define ALLOC(c, ptr, bytes)                  \
+  do {                                        \
+    int r_ = dalloc((c), &(ptr), (bytes));    \
+    if (r_ != SMC_OK) return r_;              \
+  } while (0)
+
+size_t ct_size(const smc_ctx *c) { return c->is_f64 ? sizeof(double) : sizeof(float); }
+
+int est_tiles(const smc_ctx *c, Tile *out, int cap) {
+  if (c->x_dtype == SMC_F64) return est_tiles_f64(out, cap);
+  if (c->x_dtype == SMC_F32) return est_tiles_f32(out, cap);
+  return est_tiles_bf16(out, cap);
+}
+
+int est_launch(smc_ctx *c, int op, const EstArgs &a) {
+  c->launches += 1;
+  if (c->x_dtype == SMC_F64) return est_launch_f64(op, c->tile, a, c->stream);
+  if (c->x_dtype == SMC_F32) return est_launch_f32(op, c->tile, a, c->stream);
+  return est_launch_bf16(op, c->tile, a, c->stream);
+}
+
+// Smallest compiled tile that covers the packed row (fewest idle slots, then fewest lanes/row).
+int default_tile(const smc_ctx *c) {
+  Tile t[32];
+  const int nt = est_tiles(c, t, 32);
+  int best = -1;
+  for (int i = 0; i < nt; ++i) {
+    if (t[i].T * t[i].CPL < c->S) continue;
+    if (best < 0) {
+      best = i;
+      continue;
+    }
+    const int wi = t[i].T * t[i].CPL, wb = t[best].T * t[best].CPL;
+    if (wi < wb || (wi == wb && t[i].T < t[best].T)) best = i;
+  }
+  return best;
+}
+
+EstArgs base_args(const smc_ctx *c) {
+  EstArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Xp = c->Xp;
+  a.n = c->n;
+  a.p = c->p;
+  a.S = c->S;
+  a.m = c->m;
+  a.G = c->G;
+  a.fam = c->fam;
+  a.inv_s2 = 1.0 / (c->noise_sigma * c->noise_sigma);
+  a.A = c->A_h;
+  a.B_ct = c->B_ct;
+  a.C_ct = c->C_ct;
+  a.tb_ct = c->tb_ct;
+  a.mu_ct = c->mu_ct;
+  a.ivar_ct = c->ivar_ct;
+  a.log_prior_const = c->log_prior_const;
+  a.L = c->L;
+  a.Sigma_ct = c->Sigma_ct;
+  a.Linv_ct = c->Linv_ct;
+  a.seed = c->seed;
+  a.stage = c->stage;
+  a.unew = c->unew;
+  a.maxblk = c->maxblk;
+  a.st = c->st;
+  return a;
+}
+
+int sync_state(smc_ctx *c, DevState *h) {
+  CUDA_OK(c, cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int check_err_bits(smc_ctx *c, const DevState &h) {
+  if (h.err == 0) return SMC_OK;
+  const int bits = h.err;
+  CUDA_OK(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+  if (bits & kErrIndex) return fail(c, SMC_ERR_ARG, "subsample index outside [0, n)");
+  if (bits & kErrChol) return fail(c, SMC_ERR_NONFINITE, "particle covariance not positive definite");
+  if (bits & kErrCap) return fail(c, SMC_ERR_TIMEOUT, "device iteration cap reached");
+  return fail(c, SMC_ERR_NONFINITE, "non-finite estimate or weight");
+}
+
+// A, B, C at a device point theta (FP64) into A_out/B_out/C_out (device).
+int moments_at(smc_ctx *c, const double *theta_d, double *A_out, double *B_out, double *C_out) {
+  LAUNCH(c,
+         cv_moments(c->Xp, c->x_dtype, c->n, c->p, c->S, c->fam,
+                    c->noise_sigma * c->noise_sigma, theta_d, c->part,
+                    cv_moments_blocks(c->p), A_out, B_out, C_out, c->stream),
+         2);
+  return SMC_OK;
+}
+
+__global__ void k_log_post(int p, const double *theta, const double *mu, const double *var,
+                           const double *A, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double lp = *A;
+    for (int c = 0; c < p; ++c) {
+      const double r = theta[c] - mu[c];
+      lp += -0.5 * r * r / var[c];
+    }
+    *out = lp;
+  }
+}
+
+// Posterior mode by Newton's method with step halving (FP64, on the device).
+int newton_map(smc_ctx *c, double *theta_d) {
+  const int p = c->p;
+  double *A0 = c->scratch_d, *B0 = A0 + 1, *C0 = B0 + p;
+  double *A1 = C0 + p * p, *B1 = A1 + 1, *C1 = B1 + p;
+  double *step = C1 + p * p, *cand = step + p, *f_d = cand + p;
+  CUDA_OK(c, cudaMemcpyAsync(theta_d, c->mu_d, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  int r = moments_at(c, theta_d, A0, B0, C0);
+  if (r) return r;
+  double f, fc;
+  std::vector<double> sh(p);
+  auto objective = [&](const double *th, const double *A, double *out) -> int {
+    k_log_post<<<1, 32, 0, c->stream>>>(p, th, c->mu_d, c->var_d, A, f_d);
+    c->launches += 1;
+    CUDA_OK(c, cudaGetLastError());
+    CUDA_OK(c, cudaMemcpyAsync(out, f_d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    return SMC_OK;
+  };
+  if ((r = objective(theta_d, A0, &f))) return r;
+  for (int it = 0; it < 60; ++it) {
+    LAUNCH(c, newton_step(p, theta_d, B0, C0, c->mu_d, c->var_d, step, nullptr, c->info_d,
+                          c->stream),
+           1);
+    int info = 0;
+    CUDA_OK(c, cudaMemcpyAsync(&info, c->info_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(sh.data(), step, sizeof(double) * p, cudaMemcpyDeviceToHost,
+                               c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    if (info) return fail(c, SMC_ERR_NONFINITE, "Newton step: negative Hessian not positive definite");
+    double t = 1.0;
+    while (true) {
+      LAUNCH(c, axpy_vec(p, theta_d, t, step, cand, c->stream), 1);
+      if ((r = moments_at(c, cand, A1, B1, C1))) return r;
+      if ((r = objective(cand, A1, &fc))) return r;
+      if (fc >= f || t < 1e-8) break;
+      t *= 0.5;
+    }
+    CUDA_OK(c, cudaMemcpyAsync(theta_d, cand, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(A0, A1, sizeof(double) * (1 + p + p * p),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    f = fc;
+    double mx = 0.0;
+    for (int k = 0; k < p; ++k) mx = fmax(mx, fabs(t * sh[k]));
+    if (mx < 1e-10) break;
+  }
+  return SMC_OK;
+}
+
+// Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies.
+int set_centre(smc_ctx *c) {
+  const int p = c->p;
+  LAUNCH(c, round_to_state_type(c->is_f64, p, c->tb_d, c->stream), c->is_f64 ? 0 : 1);
+  int r = moments_at(c, c->tb_d, c->A_d, c->B_d, c->C_d);
+  if (r) return r;
+  LAUNCH(c, to_state_type(c->is_f64, p, c->tb_d, c->tb_ct, c->stream), 1);
+  LAUNCH(c, to_state_type(c->is_f64, p, c->B_d, c->B_ct, c->stream), 1);
+  LAUNCH(c, to_state_type(c->is_f64, p * p, c->C_d, c->C_ct, c->stream), 1);
+  CUDA_OK(c, cudaMemcpyAsync(&c->A_h, c->A_d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (!isfinite(c->A_h)) return fail(c, SMC_ERR_NONFINITE, "A(theta_bar) is not finite");
+  return SMC_OK;
+}
+
+// Recompute the per-particle cache (l_hat, sigma2_hat, block sums) at the current particles.
+int refresh_cache(smc_ctx *c) {
+  EstArgs a = base_args(c);
+  a.B = c->N;
+  a.theta = c->theta;
+  a.u = c->u;
+  a.ell = c->ell;
+  a.sig2 = c->sig2;
+  a.blk = c->blk;
+  a.a_host = 0.0;
+  LAUNCH(c, est_launch(c, 0, a), 0);
+  return SMC_OK;
+}
+
+// Mass matrix from a covariance held in Sigma_raw (device FP64).
+int set_mass(smc_ctx *c) {
+  LAUNCH(c,
+         mass_matrix(c->is_f64, c->p, c->Sigma_raw, c->Sigma_d, c->chol_d, c->Sigma_ct,
+                     c->Linv_ct, c->mass_work, c->st, c->stream),
+         1);
+  return SMC_OK;
+}
+
+int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const double *theta_bar) {
+  const int p = c->p;
+  const size_t cts = ct_size(c);
+  // packed rows
+  ALLOC(c, c->Xp, (size_t)c->n * c->S * c->esz);
+  LAUNCH(c, pack_rows(P->X, c->x_dtype, c->n, p, P->x_ld, P->y, c->Xp, c->S, c->stream), 1);
+  // prior
+  ALLOC(c, c->mu_d, sizeof(double) * p);
+  ALLOC(c, c->var_d, sizeof(double) * p);
+  ALLOC(c, c->mu_ct, cts * p);
+  ALLOC(c, c->ivar_ct, cts * p);
+  std::vector<double> ivar(p);
+  for (int k = 0; k < p; ++k) ivar[k] = 1.0 / c->var_h[k];
+  CUDA_OK(c, cudaMemcpyAsync(c->mu_d, c->mu_h.data(), sizeof(double) * p, cudaMemcpyHostToDevice,
+                             c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(c->var_d, c->var_h.data(), sizeof(double) * p,
+                             cudaMemcpyHostToDevice, c->stream));
+  double *tmp = nullptr;
+  ALLOC(c, tmp, sizeof(double) * p);
+  CUDA_OK(c, cudaMemcpyAsync(tmp, ivar.data(), sizeof(double) * p, cudaMemcpyHostToDevice,
+                             c->stream));
+  LAUNCH(c, to_state_type(c->is_f64, p, c->mu_d, c->mu_ct, c->stream), 1);
+  LAUNCH(c, to_state_type(c->is_f64, p, tmp, c->ivar_ct, c->stream), 1);
+  // scratch
+  const int cvw = 1 + p + p * (p + 1) / 2;
+  size_t part = (size_t)cv_moments_blocks(p) * cvw * sizeof(double);
+  const size_t part_mom = (size_t)152 * p * p * sizeof(double);
+  const size_t part_rw = (size_t)64 * 32 * 3 * sizeof(double);
+  if (part_mom > part) part = part_mom;
+  if (part_rw > part) part = part_rw;
+  ALLOC(c, c->part, part);
+  c->part_bytes = part;
+  ALLOC(c, c->scratch_d, sizeof(double) * (2 * (1 + p + p * p) + 3 * p + 8));
+  ALLOC(c, c->info_d, sizeof(int) * 4);
+  ALLOC(c, c->st, sizeof(DevState));
+  CUDA_OK(c, cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  // control-variate centre and moments
+  ALLOC(c, c->tb_d, sizeof(double) * p);
+  ALLOC(c, c->A_d, sizeof(double) * (1 + p + p * p));
+  c->B_d = c->A_d + 1;
+  c->C_d = c->B_d + p;
+  ALLOC(c, c->tb_ct, cts * p);
+  ALLOC(c, c->B_ct, cts * p);
+  ALLOC(c, c->C_ct, cts * p * p);
+  int r;
+  if (theta_bar) {
+    CUDA_OK(c, cudaMemcpyAsync(c->tb_d, theta_bar, sizeof(double) * p, cudaMemcpyHostToDevice,
+                               c->stream));
+  } else if ((r = newton_map(c, c->tb_d))) {
+    return r;
+  }
+  if ((r = set_centre(c))) return r;
+  // particles
+  const size_t Np = (size_t)c->N * p, Nm = (size_t)c->N * c->m, NG = (size_t)c->N * c->G * 2;
+  ALLOC(c, c->theta, cts * Np);
+  ALLOC(c, c->theta_alt, cts * Np);
+  ALLOC(c, c->grad_scratch, cts * Np);
+  ALLOC(c, c->u, sizeof(int32_t) * Nm);
+  ALLOC(c, c->u_alt, sizeof(int32_t) * Nm);
+  c->maxblk = (c->m + c->G - 1) / c->G + 1;
+  ALLOC(c, c->unew, sizeof(int32_t) * (size_t)c->N * c->maxblk);
+  ALLOC(c, c->anc, sizeof(int32_t) * c->N);
+  ALLOC(c, c->cum, sizeof(uint64_t) * c->N);
+  ALLOC(c, c->logW, sizeof(double) * c->N);
+  ALLOC(c, c->W, sizeof(double) * c->N);
+  ALLOC(c, c->ell, sizeof(double) * c->N);
+  ALLOC(c, c->sig2, sizeof(double) * c->N);
+  ALLOC(c, c->ell_alt, sizeof(double) * c->N);
+  ALLOC(c, c->sig2_alt, sizeof(double) * c->N);
+  ALLOC(c, c->blk, sizeof(double) * NG);
+  ALLOC(c, c->blk_alt, sizeof(double) * NG);
+  ALLOC(c, c->blk_prop, sizeof(double) * NG);
+  ALLOC(c, c->mean_d, sizeof(double) * p);
+  ALLOC(c, c->Sigma_raw, sizeof(double) * p * p);
+  ALLOC(c, c->Sigma_d, sizeof(double) * p * p);
+  ALLOC(c, c->chol_d, sizeof(double) * p * p);
+  ALLOC(c, c->mass_work, sizeof(double) * p * p);
+  ALLOC(c, c->Sigma_ct, cts * p * p);
+  ALLOC(c, c->Linv_ct, cts * p * p);
+  LAUNCH(c,
+         init_particles(c->is_f64, c->N, p, c->m, c->n, c->seed, c->mu_d, c->var_d, c->theta, c->u,
+                        c->logW, c->W, c->stream),
+         1);
+  if ((r = refresh_cache(c))) return r;
+  // initial mass matrix: the prior covariance
+  std::vector<double> S0((size_t)p * p, 0.0);
+  for (int k = 0; k < p; ++k) S0[(size_t)k * p + k] = c->var_h[k];
+  CUDA_OK(c, cudaMemcpyAsync(c->Sigma_raw, S0.data(), sizeof(double) * p * p,
+                             cudaMemcpyHostToDevice, c->stream));
+  if ((r = set_mass(c))) return r;
+  // scalars
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.eps = c->eps0 > 0 ? c->eps0 : 0.5 * pow((double)p, -0.25);
+  CUDA_OK(c, cudaMemcpyAsync(c->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  if ((r = sync_state(c, &h))) return r;
+  (void)cfg;
+  return check_err_bits(c, h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const double *theta_bar,
+             void *stream) {
+  if (!out) return fail(nullptr, SMC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!P || !cfg) return fail(nullptr, SMC_ERR_ARG, "problem or config is NULL");
+  if (P->family < 0 || P->family > 3) return fail(nullptr, SMC_ERR_ARG, "unknown family");
+  if (P->x_dtype < 0 || P->x_dtype > 2) return fail(nullptr, SMC_ERR_ARG, "unknown x_dtype");
+  if (P->n < 1 || P->n > 0x7fffffffLL) return fail(nullptr, SMC_ERR_ARG, "n must be in [1, 2^31)");
+  if (P->p < 1 || P->p > 126) return fail(nullptr, SMC_ERR_ARG, "p must be in [1, 126]");
+  if (P->x_ld < P->p) return fail(nullptr, SMC_ERR_ARG, "x_ld < p");
+  if (!P->X || !P->y || !P->prior_mean || !P->prior_var)
+    return fail(nullptr, SMC_ERR_ARG, "X, y, prior_mean and prior_var are required");
+  for (int k = 0; k < P->p; ++k)
+    if (!(P->prior_var[k] > 0) || !isfinite(P->prior_mean[k]))
+      return fail(nullptr, SMC_ERR_ARG, "prior variances must be > 0 and means finite");
+  if (P->family == SMC_GAUSSIAN && !(P->noise_sigma > 0))
+    return fail(nullptr, SMC_ERR_ARG, "Gaussian family needs noise_sigma > 0");
+  if (cfg->N < 1 || cfg->N >= (1 << 23)) return fail(nullptr, SMC_ERR_ARG, "N must be in [1, 2^23)");
+  if (cfg->m < 1 || cfg->G < 1 || cfg->G > cfg->m)
+    return fail(nullptr, SMC_ERR_ARG, "need m >= 1 and 1 <= G <= m");
+  if (cfg->L < 1) return fail(nullptr, SMC_ERR_ARG, "L must be >= 1");
+  if (!(cfg->ess_frac > 0 && cfg->ess_frac <= 1)) return fail(nullptr, SMC_ERR_ARG, "ess_frac in (0,1]");
+  const int K = cfg->search_k ? cfg->search_k : 16, rounds = cfg->search_rounds ? cfg->search_rounds : 10;
+  if (K < 2 || K > 32 || rounds < 1 || rounds > 64)
+    return fail(nullptr, SMC_ERR_ARG, "search_k in [2, 32], search_rounds in [1, 64]");
+
+  smc_ctx *c = new smc_ctx();
+  cudaGetDevice(&c->device);
+  c->stream = (cudaStream_t)stream;
+  c->fam = P->family;
+  c->x_dtype = P->x_dtype;
+  c->is_f64 = P->x_dtype == SMC_F64;
+  c->esz = P->x_dtype == SMC_F64 ? 8 : (P->x_dtype == SMC_F32 ? 4 : 2);
+  c->YS = c->is_f64 ? 1 : 4 / c->esz;
+  const int vec = 16 / c->esz;
+  c->S = ((c->YS + P->p + vec - 1) / vec) * vec;
+  c->n = P->n;
+  c->p = P->p;
+  c->noise_sigma = P->family == SMC_GAUSSIAN ? P->noise_sigma : 1.0;
+  c->mu_h.assign(P->prior_mean, P->prior_mean + P->p);
+  c->var_h.assign(P->prior_var, P->prior_var + P->p);
+  for (int k = 0; k < P->p; ++k) c->log_prior_const += -0.5 * log(6.283185307179586 * c->var_h[k]);
+  c->N = cfg->N;
+  c->m = cfg->m;
+  c->G = cfg->G;
+  c->L = cfg->L;
+  c->tau = cfg->ess_frac;
+  c->seed = cfg->seed;
+  c->K = K;
+  c->rounds = rounds;
+  c->eps0 = cfg->eps0;
+  c->tile = cfg->tile_hint > 0 ? cfg->tile_hint - 1 : default_tile(c);
+  Tile tl[32];
+  const int nt = est_tiles(c, tl, 32);
+  if (c->tile < 0 || c->tile >= nt || tl[c->tile].T * tl[c->tile].CPL < c->S) {
+    g_init_error = "no compiled tile covers this row width";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  const int r = init_impl(c, P, cfg, theta_bar);
+  if (r != SMC_OK) {
+    g_init_error = c->err;
+    smc_free(c);
+    return r;
+  }
+  *out = c;
+  return SMC_OK;
+}
+
+int smc_free(smc_ctx *c) {
+  if (!c) return SMC_OK;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  for (void *q : c->allocs) cudaFree(q);
+  delete c;
+  return SMC_OK;
+}
+
+const char *smc_last_error(const smc_ctx *c) {
+  return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
+  if (!c) return SMC_ERR_ARG;
+  c->stage += 1;
+  c->moves_in_stage = 0;
+  int nl = 0;
+  int e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->st, c->part,
+                   &nl, c->stream);
+  c->launches += nl;
+  if (e) return fail(c, SMC_ERR_CUDA, std::string("reweight: ") + cudaGetErrorString((cudaError_t)e));
+  LAUNCH(c,
+         weighted_moments(c->is_f64, c->N, c->p, c->W, c->theta, c->part, c->mean_d, c->Sigma_raw,
+                          c->stream),
+         4);
+  int r = set_mass(c);
+  if (r) return r;
+  if (a_next || log_z_inc || ess) {
+    DevState h;
+    if ((r = sync_state(c, &h))) return r;
+    if (a_next) *a_next = h.a;
+    if (log_z_inc) *log_z_inc = h.log_z_inc;
+    if (ess) *ess = h.ess;
+    return check_err_bits(c, h);
+  }
+  return SMC_OK;
+}
+
+int smc_resample(smc_ctx *c, int32_t *ancestors) {
+  if (!c) return SMC_ERR_ARG;
+  LAUNCH(c,
+         resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->W, c->cum, c->anc,
+                  c->theta, c->theta_alt, c->u, c->u_alt, c->ell, c->ell_alt, c->sig2,
+                  c->sig2_alt, c->blk, c->blk_alt, c->logW, c->W, c->st, c->stream),
+         3);
+  std::swap(c->theta, c->theta_alt);
+  std::swap(c->u, c->u_alt);
+  std::swap(c->ell, c->ell_alt);
+  std::swap(c->sig2, c->sig2_alt);
+  std::swap(c->blk, c->blk_alt);
+  if (ancestors)
+    CUDA_OK(c, cudaMemcpyAsync(ancestors, c->anc, sizeof(int32_t) * c->N, cudaMemcpyDefault,
+                               c->stream));
+  return SMC_OK;
+}
+
+int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
+  if (!c) return SMC_ERR_ARG;
+  if (R < 1) return fail(c, SMC_ERR_ARG, "R must be >= 1");
+  if (c->moves_in_stage + R > 256) return fail(c, SMC_ERR_ARG, "at most 256 moves per stage");
+  CUDA_OK(c, cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream));
+  for (int r = 0; r < R; ++r) {
+    EstArgs a = base_args(c);
+    a.B = c->N;
+    a.theta = c->theta;
+    a.theta_out = c->theta;
+    a.u = c->u;
+    a.u_mut = c->u;
+    a.ell = c->ell;
+    a.sig2 = c->sig2;
+    a.blk = c->blk;
+    a.blk_prop = c->blk_prop;
+    a.move = c->moves_in_stage + r;
+    LAUNCH(c, est_launch(c, 1, a), 0);
+    LAUNCH(c, est_launch(c, 2, a), 0);
+  }
+  c->moves_in_stage += R;
+  LAUNCH(c, eps_update(c->N, R, c->st, c->stream), 1);
+  if (acc_u || acc_theta) {
+    DevState h;
+    int r = sync_state(c, &h);
+    if (r) return r;
+    if (acc_u) *acc_u = (double)h.acc_u / ((double)c->N * R);
+    if (acc_theta) *acc_theta = (double)h.acc_theta / ((double)c->N * R);
+    return check_err_bits(c, h);
+  }
+  return SMC_OK;
+}
+
+static int estimate_impl(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, double a,
+                         void *grad, double *ell, double *sigma2) {
+  if (!c) return SMC_ERR_ARG;
+  if (B < 0 || (B > 0 && (!theta || !u))) return fail(c, SMC_ERR_ARG, "bad batch arguments");
+  EstArgs ea = base_args(c);
+  ea.B = B;
+  ea.theta = theta;
+  ea.u = u;
+  ea.ell = ell;
+  ea.sig2 = sigma2;
+  ea.grad = grad;
+  ea.a_host = a;
+  LAUNCH(c, est_launch(c, 0, ea), 0);
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  return check_err_bits(c, h);
+}
+
+int loglik_est(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, double *ell,
+               double *sigma2) {
+  return estimate_impl(c, B, theta, u, 0.0, nullptr, ell, sigma2);
+}
+
+int loglik_grad(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, double a, void *grad,
+                double *ell, double *sigma2) {
+  if (!grad) return fail(c, SMC_ERR_ARG, "grad is NULL");
+  return estimate_impl(c, B, theta, u, a, grad, ell, sigma2);
+}
+
+int smc_get_particles(smc_ctx *c, void *theta, int32_t *u, double *W) {
+  if (!c) return SMC_ERR_ARG;
+  if (theta)
+    CUDA_OK(c, cudaMemcpyAsync(theta, c->theta, ct_size(c) * c->N * c->p, cudaMemcpyDefault,
+                               c->stream));
+  if (u)
+    CUDA_OK(c, cudaMemcpyAsync(u, c->u, sizeof(int32_t) * c->N * c->m, cudaMemcpyDefault,
+                               c->stream));
+  if (W) CUDA_OK(c, cudaMemcpyAsync(W, c->W, sizeof(double) * c->N, cudaMemcpyDefault, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_set_particles(smc_ctx *c, const void *theta, const int32_t *u, const double *W) {
+  if (!c) return SMC_ERR_ARG;
+  if (theta)
+    CUDA_OK(c, cudaMemcpyAsync(c->theta, theta, ct_size(c) * c->N * c->p, cudaMemcpyDefault,
+                               c->stream));
+  if (u)
+    CUDA_OK(c, cudaMemcpyAsync(c->u, u, sizeof(int32_t) * c->N * c->m, cudaMemcpyDefault,
+                               c->stream));
+  double *Wd = nullptr;
+  if (W) {
+    Wd = c->ell_alt;  // staging buffer of N doubles
+    CUDA_OK(c, cudaMemcpyAsync(Wd, W, sizeof(double) * c->N, cudaMemcpyDefault, c->stream));
+  }
+  LAUNCH(c, weights_from(c->N, Wd, c->logW, c->W, c->stream), 1);
+  int r = refresh_cache(c);
+  if (r) return r;
+  DevState h;
+  if ((r = sync_state(c, &h))) return r;
+  return check_err_bits(c, h);
+}
+
+int smc_get_cache(smc_ctx *c, double *ell, double *sigma2, double *blocks) {
+  if (!c) return SMC_ERR_ARG;
+  if (ell)
+    CUDA_OK(c, cudaMemcpyAsync(ell, c->ell, sizeof(double) * c->N, cudaMemcpyDefault, c->stream));
+  if (sigma2)
+    CUDA_OK(c, cudaMemcpyAsync(sigma2, c->sig2, sizeof(double) * c->N, cudaMemcpyDefault,
+                               c->stream));
+  if (blocks)
+    CUDA_OK(c, cudaMemcpyAsync(blocks, c->blk, sizeof(double) * c->N * c->G * 2,
+                               cudaMemcpyDefault, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_get_centre(smc_ctx *c, double *theta_bar, double *A, double *B, double *C) {
+  if (!c) return SMC_ERR_ARG;
+  const int p = c->p;
+  if (theta_bar)
+    CUDA_OK(c, cudaMemcpyAsync(theta_bar, c->tb_d, sizeof(double) * p, cudaMemcpyDeviceToHost,
+                               c->stream));
+  if (A) CUDA_OK(c, cudaMemcpyAsync(A, c->A_d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (B)
+    CUDA_OK(c, cudaMemcpyAsync(B, c->B_d, sizeof(double) * p, cudaMemcpyDeviceToHost, c->stream));
+  if (C)
+    CUDA_OK(c, cudaMemcpyAsync(C, c->C_d, sizeof(double) * p * p, cudaMemcpyDeviceToHost,
+                               c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_cv_moments(smc_ctx *c, const double *theta, double *A, double *B, double *C) {
+  if (!c || !theta) return SMC_ERR_ARG;
+  const int p = c->p;
+  double *th = c->scratch_d, *A1 = th + p, *B1 = A1 + 1, *C1 = B1 + p;
+  CUDA_OK(c, cudaMemcpyAsync(th, theta, sizeof(double) * p, cudaMemcpyHostToDevice, c->stream));
+  int r = moments_at(c, th, A1, B1, C1);
+  if (r) return r;
+  if (A) CUDA_OK(c, cudaMemcpyAsync(A, A1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (B) CUDA_OK(c, cudaMemcpyAsync(B, B1, sizeof(double) * p, cudaMemcpyDeviceToHost, c->stream));
+  if (C)
+    CUDA_OK(c, cudaMemcpyAsync(C, C1, sizeof(double) * p * p, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_get_mass(smc_ctx *c, double *Sigma, double *chol) {
+  if (!c) return SMC_ERR_ARG;
+  const size_t b = sizeof(double) * c->p * c->p;
+  if (Sigma) CUDA_OK(c, cudaMemcpyAsync(Sigma, c->Sigma_d, b, cudaMemcpyDeviceToHost, c->stream));
+  if (chol) CUDA_OK(c, cudaMemcpyAsync(chol, c->chol_d, b, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_get_status(smc_ctx *c, double *a, double *log_z, int32_t *stage, double *eps) {
+  if (!c) return SMC_ERR_ARG;
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  if (a) *a = h.a;
+  if (log_z) *log_z = h.log_z;
+  if (stage) *stage = c->stage;
+  if (eps) *eps = h.eps;
+  return SMC_OK;
+}
+
+int smc_set_scalars(smc_ctx *c, int32_t stage, double a, double eps, double log_z) {
+  if (!c) return SMC_ERR_ARG;
+  if (stage < 0 || !(a >= 0 && a <= 1) || !(eps > 0)) return fail(c, SMC_ERR_ARG, "bad scalars");
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  h.a = a;
+  h.eps = eps;
+  h.log_z = log_z;
+  CUDA_OK(c, cudaMemcpyAsync(c->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->stage = stage;
+  c->moves_in_stage = 0;
+  return SMC_OK;
+}
+
+int smc_autotune(smc_ctx *c, int32_t *tile) {
+  if (!c) return SMC_ERR_ARG;
+  Tile tl[32];
+  const int nt = est_tiles(c, tl, 32);
+  cudaEvent_t e0, e1;
+  CUDA_OK(c, cudaEventCreate(&e0));
+  CUDA_OK(c, cudaEventCreate(&e1));
+  const int keep = c->tile;
+  int best = keep;
+  float best_ms = 1e30f;
+  for (int t = 0; t < nt; ++t) {
+    if (tl[t].T * tl[t].CPL < c->S) continue;
+    c->tile = t;
+    EstArgs a = base_args(c);
+    a.B = c->N;
+    a.theta = c->theta;
+    a.u = c->u;
+    a.grad = c->grad_scratch;
+    a.a_host = 1.0;
+    float total = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      CUDA_OK(c, cudaEventRecord(e0, c->stream));
+      LAUNCH(c, est_launch(c, 0, a), 0);
+      CUDA_OK(c, cudaEventRecord(e1, c->stream));
+      CUDA_OK(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_OK(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep) total += ms;  // first launch is a warm-up
+    }
+    if (total < best_ms) {
+      best_ms = total;
+      best = t;
+    }
+  }
+  c->tile = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tile) *tile = best + 1;
+  return SMC_OK;
+}
+
+int64_t smc_launch_count(const smc_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

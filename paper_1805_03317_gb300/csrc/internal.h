@@ -1,0 +1,112 @@
+// Internal declarations shared by the kernel translation units and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace subsmc {
+
+// Scalars that live on the device so that a whole stage runs without host round trips.
+struct DevState {
+  double a;          // current temperature a_s
+  double a_prev;     // a_{s-1}
+  double log_z;      // accumulated log marginal likelihood estimate (Sec. 3.5)
+  double log_z_inc;  // last increment
+  double ess;        // ESS at the chosen increment
+  double eps;        // leapfrog step
+  double lo, hi, dmax, D;  // temperature search bracket
+  double lse_new, lse_old, lse_new2;
+  int stage;
+  int search_done;
+  int err;           // bit 0: index out of range, bit 1: non-finite, bit 2: cholesky failed,
+                     // bit 3: iteration cap
+  int chol_retries;
+  unsigned int ticket;       // last-block-done counter for grid reductions
+  unsigned int ticket2;
+  unsigned long long acc_u, acc_theta;  // accept counters of the current smc_move call
+  unsigned long long res_T;  // resampling: total quantised weight
+  unsigned long long res_off;
+};
+
+enum ErrBits { kErrIndex = 1, kErrNonFinite = 2, kErrChol = 4, kErrCap = 8 };
+
+// Everything a per-particle estimator kernel needs. Pointers to "CT" data use the state type
+// (double for FP64 problems, float otherwise).
+struct EstArgs {
+  // problem
+  const void *Xp;  // packed rows [n, S]
+  int64_t n;
+  int p, S, m, G, fam;
+  double inv_s2;   // Gaussian family: 1/sigma^2
+  double A;        // sum_k l_k(theta_bar)
+  const void *B_ct, *C_ct, *tb_ct;  // B [p], C [p,p] (symmetric), theta_bar [p]
+  const void *mu_ct, *ivar_ct;      // prior mean, 1/prior variance [p]
+  double log_prior_const;           // -0.5 * sum log(2 pi v)
+  // particles
+  int B;                  // number of particles in this launch
+  const void *theta;      // [B, p]
+  void *theta_out;        // HMC: updated in place (may equal theta)
+  const int32_t *u;       // [B, m]
+  int32_t *u_mut;         // u-update: indices written here on acceptance
+  double *ell, *sig2;     // [B]
+  double *blk;            // [B, G, 2] cache of block sums (may be null for the plain estimator)
+  double *blk_prop;       // [B, G, 2] scratch: block sums at the HMC end point
+  void *grad;             // [B, p] or null
+  double a_host;          // temperature when a_from_state == 0
+  int a_from_state;
+  // moves
+  int L;
+  const void *Sigma_ct;   // [p, p] mass-matrix inverse (particle covariance)
+  const void *Linv_ct;    // [p, p] inverse of the lower Cholesky factor of Sigma
+  uint64_t seed;
+  int stage, move;
+  int32_t *unew;          // [B, maxblk] scratch for proposed block indices
+  int maxblk;
+  DevState *st;
+};
+
+// Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots.
+struct Tile {
+  int T, CPL, U, warps;
+};
+
+// Launchers, one set per storage type (defined in est_f64.cu, est_f32.cu, est_bf16.cu).
+// op: 0 = plain estimator (optionally with gradient), 1 = u-update, 2 = HMC move.
+// Returns a cudaError_t; -1 if the tile id is not compiled for this storage type.
+int est_launch_f64(int op, int tile, const EstArgs &a, cudaStream_t s);
+int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s);
+int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s);
+int est_tiles_f64(Tile *out, int cap);
+int est_tiles_f32(Tile *out, int cap);
+int est_tiles_bf16(Tile *out, int cap);
+
+// Stage kernels (stage.cu). All return cudaError_t.
+int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,
+              int S, cudaStream_t s);
+int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int fam, double sigma2,
+               const double *theta, double *partials, int nblocks, double *A, double *B,
+               double *C, cudaStream_t s);
+int cv_moments_blocks(int p);
+int newton_step(int p, const double *theta, const double *B, const double *C, const double *mu,
+                const double *var, double *step, double *work, int *info, cudaStream_t s);
+int axpy_vec(int p, const double *x, double t, const double *s, double *out, cudaStream_t st);
+int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, const double *mu,
+                   const double *var, void *theta, int32_t *u, double *logW, double *W,
+                   cudaStream_t s);
+int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
+             int K, int rounds, DevState *st, double *partials, int *launches, cudaStream_t s);
+int weighted_moments(int is_f64, int N, int p, const double *W, const void *theta,
+                     double *partials, double *mean, double *Sigma, cudaStream_t s);
+int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double *chol,
+                void *Sigma_ct, void *Linv_ct, double *work, DevState *st, cudaStream_t s);
+int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, const double *W,
+             uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
+             int32_t *u_out, const double *ell, double *ell_out, const double *sig2,
+             double *sig2_out, const double *blk, double *blk_out, double *logW, double *Wout,
+             DevState *st, cudaStream_t s);
+int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_t s);
+int eps_update(int N, int R, DevState *st, cudaStream_t s);
+int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);
+int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s);
+
+}  // namespace subsmc

@@ -1,0 +1,237 @@
+"""Python binding of the C ABI (include/subsmc.h): same entry-point names, argument marshalling only.
+
+Device buffers are torch CUDA tensors; the library computes everything in its own kernels. The
+functions ``smc_init`` ... ``smc_launch_count`` mirror the C entry points one for one;
+``SubsampledSMC`` bundles them around one context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import DTYPE, FAMILY, SmcConfig, SmcProblem, check
+
+_TORCH_X = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16"}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns one smc_ctx; the handle is passed to the module-level entry points."""
+
+    def __init__(self, handle: ctypes.c_void_p, N: int, m: int, G: int, p: int, n: int,
+                 state_dtype: torch.dtype, device: torch.device, keepalive):
+        self.handle = handle
+        self.N, self.m, self.G, self.p, self.n = N, m, G, p, n
+        self.state_dtype = state_dtype
+        self.device = device
+        self._keepalive = keepalive
+
+    def __del__(self):
+        try:
+            smc_free(self)
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ------------------------------------------------------------------------------------------------
+def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_var, *, N: int,
+             m: int, G: int, L: int, seed: int, ess_frac: float = 0.5, noise_sigma: float = 1.0,
+             theta_bar=None, search_k: int = 16, search_rounds: int = 10, eps0: float = 0.0,
+             tile_hint: int = 0, stream=None) -> Context:
+    lib = _abi.load()
+    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    x_dtype = _TORCH_X[X.dtype]
+    y_dtype = torch.float64 if x_dtype == "f64" else torch.float32
+    y = y.to(device=X.device, dtype=y_dtype).contiguous()
+    n, p = X.shape
+    pm = np.ascontiguousarray(prior_mean, dtype=np.float64)
+    pv = np.ascontiguousarray(prior_var, dtype=np.float64)
+    prob = SmcProblem(FAMILY[family], n, p, X.data_ptr(), DTYPE[x_dtype], X.stride(0),
+                      y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma))
+    cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
+                    search_rounds, float(eps0), tile_hint)
+    tb = None
+    tb_ptr = None
+    if theta_bar is not None:
+        tb = np.ascontiguousarray(theta_bar, dtype=np.float64)
+        tb_ptr = _dp(tb)
+    handle = ctypes.c_void_p()
+    with torch.cuda.device(X.device):
+        rc = lib.smc_init(ctypes.byref(handle), ctypes.byref(prob), ctypes.byref(cfg), tb_ptr,
+                          _stream_handle(stream))
+    check(rc, "smc_init", None)
+    state = torch.float64 if x_dtype == "f64" else torch.float32
+    return Context(handle, N, m, G, p, n, state, X.device, (y, pm, pv))
+
+
+def smc_free(ctx: Context) -> None:
+    if ctx.handle:
+        _abi.load().smc_free(ctx.handle)
+        ctx.handle = ctypes.c_void_p()
+
+
+def smc_reweight(ctx: Context):
+    a, lz, ess = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(_abi.load().smc_reweight(ctx.handle, ctypes.byref(a), ctypes.byref(lz),
+                                   ctypes.byref(ess)), "smc_reweight", ctx.handle)
+    return a.value, lz.value, ess.value
+
+
+def smc_resample(ctx: Context, ancestors: torch.Tensor | None = None) -> None:
+    check(_abi.load().smc_resample(ctx.handle, _ptr(ancestors)), "smc_resample", ctx.handle)
+
+
+def smc_move(ctx: Context, R: int):
+    au, at = ctypes.c_double(), ctypes.c_double()
+    check(_abi.load().smc_move(ctx.handle, R, ctypes.byref(au), ctypes.byref(at)), "smc_move",
+          ctx.handle)
+    return au.value, at.value
+
+
+def loglik_est(ctx: Context, theta: torch.Tensor, u: torch.Tensor):
+    B = theta.shape[0]
+    theta = theta.to(ctx.state_dtype).contiguous()
+    u = u.to(torch.int32).contiguous()
+    ell = torch.empty(B, dtype=torch.float64, device=theta.device)
+    s2 = torch.empty_like(ell)
+    check(_abi.load().loglik_est(ctx.handle, B, _ptr(theta), _ptr(u), _ptr(ell), _ptr(s2)),
+          "loglik_est", ctx.handle)
+    return ell, s2
+
+
+def loglik_grad(ctx: Context, theta: torch.Tensor, u: torch.Tensor, a: float):
+    B = theta.shape[0]
+    theta = theta.to(ctx.state_dtype).contiguous()
+    u = u.to(torch.int32).contiguous()
+    grad = torch.empty_like(theta)
+    ell = torch.empty(B, dtype=torch.float64, device=theta.device)
+    s2 = torch.empty_like(ell)
+    check(_abi.load().loglik_grad(ctx.handle, B, _ptr(theta), _ptr(u), float(a), _ptr(grad),
+                                  _ptr(ell), _ptr(s2)), "loglik_grad", ctx.handle)
+    return grad, ell, s2
+
+
+def smc_get_particles(ctx: Context, theta=None, u=None, W=None):
+    """Fill (or allocate on the context's device) theta [N,p], u [N,m] int32, W [N] float64."""
+    dev = ctx.device
+    theta = theta if theta is not None else torch.empty(ctx.N, ctx.p, dtype=ctx.state_dtype,
+                                                        device=dev)
+    u = u if u is not None else torch.empty(ctx.N, ctx.m, dtype=torch.int32, device=dev)
+    W = W if W is not None else torch.empty(ctx.N, dtype=torch.float64, device=dev)
+    check(_abi.load().smc_get_particles(ctx.handle, _ptr(theta), _ptr(u), _ptr(W)),
+          "smc_get_particles", ctx.handle)
+    return theta, u, W
+
+
+def smc_set_particles(ctx: Context, theta, u, W=None) -> None:
+    theta = theta.to(ctx.state_dtype).contiguous()
+    u = u.to(torch.int32).contiguous()
+    W = None if W is None else W.to(torch.float64).contiguous()
+    check(_abi.load().smc_set_particles(ctx.handle, _ptr(theta), _ptr(u), _ptr(W)),
+          "smc_set_particles", ctx.handle)
+
+
+def smc_get_cache(ctx: Context):
+    dev = ctx.device
+    ell = torch.empty(ctx.N, dtype=torch.float64, device=dev)
+    s2 = torch.empty_like(ell)
+    blk = torch.empty(ctx.N, ctx.G, 2, dtype=torch.float64, device=dev)
+    check(_abi.load().smc_get_cache(ctx.handle, _ptr(ell), _ptr(s2), _ptr(blk)), "smc_get_cache",
+          ctx.handle)
+    return ell, s2, blk
+
+
+def smc_get_centre(ctx: Context):
+    p = ctx.p
+    tb, A, B, C = np.zeros(p), np.zeros(1), np.zeros(p), np.zeros((p, p))
+    check(_abi.load().smc_get_centre(ctx.handle, _dp(tb), _dp(A), _dp(B), _dp(C)),
+          "smc_get_centre", ctx.handle)
+    return tb, float(A[0]), B, C
+
+
+def smc_cv_moments(ctx: Context, theta):
+    p = ctx.p
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    A, B, C = np.zeros(1), np.zeros(p), np.zeros((p, p))
+    check(_abi.load().smc_cv_moments(ctx.handle, _dp(th), _dp(A), _dp(B), _dp(C)),
+          "smc_cv_moments", ctx.handle)
+    return float(A[0]), B, C
+
+
+def smc_get_mass(ctx: Context):
+    p = ctx.p
+    S, L = np.zeros((p, p)), np.zeros((p, p))
+    check(_abi.load().smc_get_mass(ctx.handle, _dp(S), _dp(L)), "smc_get_mass", ctx.handle)
+    return S, L
+
+
+def smc_get_status(ctx: Context) -> dict:
+    a, lz, eps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    stage = ctypes.c_int32()
+    check(_abi.load().smc_get_status(ctx.handle, ctypes.byref(a), ctypes.byref(lz),
+                                     ctypes.byref(stage), ctypes.byref(eps)), "smc_get_status",
+          ctx.handle)
+    return {"a": a.value, "log_z": lz.value, "stage": stage.value, "eps": eps.value}
+
+
+def smc_set_scalars(ctx: Context, stage: int, a: float, eps: float, log_z: float = 0.0) -> None:
+    check(_abi.load().smc_set_scalars(ctx.handle, stage, a, eps, log_z), "smc_set_scalars",
+          ctx.handle)
+
+
+def smc_autotune(ctx: Context) -> int:
+    t = ctypes.c_int32()
+    check(_abi.load().smc_autotune(ctx.handle, ctypes.byref(t)), "smc_autotune", ctx.handle)
+    return t.value
+
+
+def smc_launch_count(ctx: Context) -> int:
+    return int(_abi.load().smc_launch_count(ctx.handle))
+
+
+# ------------------------------------------------------------------------------------------------
+# Convenience wrapper
+# ------------------------------------------------------------------------------------------------
+class SubsampledSMC:
+    """Likelihood-annealed subsampling SMC (Algorithm 2) on one GPU."""
+
+    def __init__(self, X, y, family, prior_mean, prior_var, **kw):
+        self.ctx = smc_init(X, y, family, prior_mean, prior_var, **kw)
+        self.history = []
+
+    def stage(self, R: int) -> dict:
+        a, lz, ess = smc_reweight(self.ctx)
+        smc_resample(self.ctx)
+        au, at = smc_move(self.ctx, R)
+        rec = {"a": a, "log_z_inc": lz, "ess": ess, "acc_u": au, "acc_theta": at}
+        self.history.append(rec)
+        return rec
+
+    def run(self, R: int, max_stages: int = 1000) -> dict:
+        while smc_get_status(self.ctx)["a"] < 1.0 and len(self.history) < max_stages:
+            self.stage(R)
+        return smc_get_status(self.ctx)
+
+    def particles(self):
+        return smc_get_particles(self.ctx)
+
+    def close(self):
+        smc_free(self.ctx)

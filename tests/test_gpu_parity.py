@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
+inputs. Sizes span several tiles with ragged tails (m not a multiple of the rows per warp step, G
+not dividing m, odd p)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import make_pair, oracle_problem, state_round, tol
+from oracle import oracle as O
+from smc_workloads import small_glm
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def S():
+    import paper_1805_03317_gb300 as pkg
+    return pkg
+
+
+def _wl(family, x_dtype, p=7, n=5000, N=64, m=77, G=5, seed=11):
+    kw = dict(x_scale=0.3) if family == "poisson" else {}
+    return small_glm(family, n=n, p=p, N=N, m=m, G=G, L=4, x_dtype=x_dtype, seed=seed, **kw)
+
+
+def _particles(prob, B, m, scale, x_dtype, seed=3):
+    rng = np.random.default_rng(seed)
+    th = state_round(prob.theta_bar + scale * rng.standard_normal((B, prob.p)), x_dtype)
+    u = rng.integers(0, prob.n, size=(B, m)).astype(np.int64)
+    return th, u
+
+
+def _check_estimates(x_dtype, got, ref):
+    t = tol(x_dtype)
+    ell, s2, g = got
+    np.testing.assert_allclose(ell, ref["ell"], rtol=t["ell"], atol=0)
+    # sigma2_hat enters the log target additively (-a^2/2 sigma2_hat), so its error is held to its
+    # own relative bar plus the bar of l_hat in the same units
+    bound = t["sig2"] * np.max(np.abs(ref["sigma2"])) + t["ell"] * np.max(np.abs(ref["ell"]))
+    assert np.max(np.abs(s2 - ref["sigma2"])) <= bound
+    if g is not None:
+        gs = np.maximum(np.max(np.abs(ref["grad"]), axis=1, keepdims=True), 1.0)
+        err = np.abs(g - ref["grad"]) / gs
+        assert err.max() <= t["grad"], err.max()
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("family", ["logistic", "poisson", "gaussian", "probit"])
+@pytest.mark.parametrize("hint", range(0, 8))
+def test_estimator_and_gradient_match_oracle(family, x_dtype, hint):
+    wl = _wl(family, x_dtype)
+    try:
+        prob, ctx = make_pair(wl, tile_hint=hint)
+    except S()._abi.SmcError as e:
+        if e.code == -1 and hint > 0:
+            pytest.skip("tile not compiled for this storage type or too narrow")
+        raise
+    th, u = _particles(prob, 37, wl.m, 0.1, x_dtype)
+    a = 0.8
+    g, ell, s2 = S().loglik_grad(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV), a)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=a)
+    _check_estimates(x_dtype, (ell.cpu().numpy(), s2.cpu().numpy(),
+                               g.cpu().double().numpy()), ref)
+    ell2, s22 = S().loglik_est(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV))
+    _check_estimates(x_dtype, (ell2.cpu().numpy(), s22.cpu().numpy(), None), ref)
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
+def test_control_variate_moments_match_oracle(x_dtype):
+    wl = _wl("logistic", x_dtype, n=20011)
+    prob, ctx = make_pair(wl)
+    tb, A, B, C = S().smc_get_centre(ctx)
+    np.testing.assert_array_equal(tb, prob.theta_bar)
+    assert A == pytest.approx(prob.A, rel=1e-12)
+    np.testing.assert_allclose(B, prob.B, rtol=1e-9, atol=1e-9 * np.abs(prob.B).max())
+    np.testing.assert_allclose(C, prob.C, rtol=1e-10, atol=1e-12 * np.abs(prob.C).max())
+    # at another point
+    pt = prob.theta_bar + 0.2
+    A2, B2, C2 = S().smc_cv_moments(ctx, pt)
+    Ar, Br, Cr = O.cv_moments("logistic", prob.X, prob.y, pt)
+    assert A2 == pytest.approx(Ar, rel=1e-12)
+    np.testing.assert_allclose(C2, Cr, rtol=1e-10, atol=1e-12 * np.abs(Cr).max())
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("family", ["logistic", "poisson", "probit", "gaussian"])
+def test_device_newton_centre_matches_oracle(family):
+    wl = _wl(family, "f64", n=8000)
+    from gpu_common import device_arrays
+    prob = oracle_problem(wl)
+    X, y = device_arrays(wl)
+    ctx = S().smc_init(X, y, family, wl.prior_mean, wl.prior_var, N=8, m=10, G=2, L=2, seed=1,
+                       noise_sigma=wl.sigma, theta_bar=None)
+    tb = S().smc_get_centre(ctx)[0]
+    np.testing.assert_allclose(tb, prob.theta_bar, rtol=1e-8, atol=1e-10)
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32"])
+def test_initial_particles_and_cache_match_oracle(x_dtype):
+    wl = _wl("logistic", x_dtype, N=50, m=31, G=4)
+    prob, ctx = make_pair(wl)
+    th, u, W = S().smc_get_particles(ctx)
+    th_o, u_o = O.init_particles(wl.seed, wl.N, wl.p, wl.m, wl.n, wl.prior_mean, wl.prior_var)
+    np.testing.assert_array_equal(u.cpu().numpy(), u_o)
+    np.testing.assert_allclose(th.cpu().double().numpy(), state_round(th_o, x_dtype), rtol=1e-12,
+                               atol=1e-12)
+    np.testing.assert_array_equal(W.cpu().numpy(), np.full(wl.N, 1.0 / wl.N))
+    ell, s2, blk = S().smc_get_cache(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th.cpu().double().numpy(), u_o, grad=False,
+                         blocks=True)
+    _check_estimates(x_dtype, (ell.cpu().numpy(), s2.cpu().numpy(), None), ref)
+    rb = ref["blocks"]
+    assert np.max(np.abs(blk.cpu().numpy() - rb)) <= tol(x_dtype)["sig2"] * max(1e-300,
+                                                                                np.abs(rb).max())
+    S().smc_free(ctx)
+
+
+def _random_cloud(prob, wl, x_dtype, seed=5, spread=0.05):
+    rng = np.random.default_rng(seed)
+    th = state_round(prob.theta_bar + spread * rng.standard_normal((wl.N, wl.p)), x_dtype)
+    u = rng.integers(0, wl.n, size=(wl.N, wl.m)).astype(np.int64)
+    W = rng.random(wl.N) ** 3
+    W /= W.sum()
+    return th, u, W
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32"])
+@pytest.mark.parametrize("a0", [0.0, 0.05, 0.9])
+def test_reweight_moments_and_mass_match_oracle(x_dtype, a0):
+    wl = _wl("logistic", x_dtype, N=300, m=40, G=4)
+    prob, ctx = make_pair(wl)
+    th, u, W = _random_cloud(prob, wl, x_dtype)
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    S().smc_set_scalars(ctx, 4, a0, 0.3, 0.0)
+    a_new, lz, ess = S().smc_reweight(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)
+    ra, rlogW, rW, rlz, ress = O.reweight(np.log(W), ref["ell"], ref["sigma2"], a0, 0.5)
+    t = tol(x_dtype)
+    rtol = 1e-12 if x_dtype == "f64" else 1e-5
+    assert a_new == pytest.approx(ra, rel=rtol, abs=1e-15)
+    assert lz == pytest.approx(rlz, rel=rtol, abs=t["ell"] * abs(ref["ell"]).max() * abs(a_new - a0))
+    assert ess == pytest.approx(ress, rel=max(rtol, 1e-9))
+    _, _, Wg = S().smc_get_particles(ctx)
+    np.testing.assert_allclose(Wg.cpu().numpy(), rW, rtol=1e-6 if x_dtype != "f64" else 1e-9,
+                               atol=1e-12)
+    mean, Sig, Lc, rc = O.moments(Wg.cpu().numpy(), th)
+    Sg, Lg = S().smc_get_mass(ctx)
+    np.testing.assert_allclose(Sg, Sig, rtol=1e-9, atol=1e-12 * np.abs(Sig).max())
+    np.testing.assert_allclose(Lg, Lc, rtol=1e-8, atol=1e-10 * np.abs(Lc).max())
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("N", [1, 7, 300, 5000])
+def test_resampling_ancestors_bit_exact(N):
+    wl = _wl("logistic", "f64", N=N, m=9, G=3)
+    prob, ctx = make_pair(wl)
+    rng = np.random.default_rng(N)
+    th = prob.theta_bar + 0.1 * rng.standard_normal((N, wl.p))
+    u = rng.integers(0, wl.n, size=(N, wl.m)).astype(np.int64)
+    W = rng.random(N) ** 6
+    W /= W.sum()
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    stage = 9
+    S().smc_set_scalars(ctx, stage, 0.5, 0.3, 0.0)
+    anc = torch.empty(N, dtype=torch.int32, device=DEV)
+    S().smc_resample(ctx, anc)
+    U = O.uniform(O.r64(wl.seed, O.TAG_RESAMPLE, O.stage_move(stage, 0), 0, 0))
+    ref = O.resample(W, U)
+    np.testing.assert_array_equal(anc.cpu().numpy(), ref)
+    th2, u2, W2 = S().smc_get_particles(ctx)
+    np.testing.assert_array_equal(th2.cpu().numpy(), th[ref])
+    np.testing.assert_array_equal(u2.cpu().numpy(), u[ref])
+    np.testing.assert_array_equal(W2.cpu().numpy(), np.full(N, 1.0 / N))
+    S().smc_free(ctx)
+
+
+def test_moves_match_oracle_fp64():
+    """One Algorithm-1 move (u block update, then HMC) on identical particles: indices and accept
+    decisions bit-exact, theta to FP64 rounding."""
+    wl = _wl("logistic", "f64", N=200, m=60, G=6)
+    prob, ctx = make_pair(wl)
+    th, u, W = _random_cloud(prob, wl, "f64", spread=0.03)
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    S().smc_set_scalars(ctx, 2, 0.3, 0.4, 0.0)
+    a, _, _ = S().smc_reweight(ctx)  # stage 3: also sets the mass matrix from this cloud
+    Sg, Lg = S().smc_get_mass(ctx)
+    st = S().smc_get_status(ctx)
+    eps = st["eps"]
+    acc_u, acc_t = S().smc_move(ctx, 1)
+    th_g, u_g, _ = S().smc_get_particles(ctx)
+    # oracle: same cloud, same temperature, same mass matrix inputs (from the oracle's moments)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)
+    ra, _, rW, _, _ = O.reweight(np.log(W), ref["ell"], ref["sigma2"], 0.3, 0.5)
+    assert a == pytest.approx(ra, rel=1e-12)
+    _, Sig, Lc, _ = O.moments(rW, th)
+    th_o, u_o = th.copy(), u.copy()
+    au = O.upm_move(prob, wl.m, wl.G, wl.seed, 3, 0, ra, th_o, u_o)
+    at = O.hmc_move(prob, wl.m, wl.G, wl.seed, 3, 0, ra, eps, wl.L, Sig, Lc, th_o, u_o)
+    np.testing.assert_array_equal(u_g.cpu().numpy(), u_o)
+    assert acc_u == pytest.approx(au.mean()) and acc_t == pytest.approx(at.mean())
+    np.testing.assert_allclose(th_g.cpu().numpy(), th_o, rtol=1e-9, atol=1e-11)
+    ell, s2, _ = S().smc_get_cache(ctx)
+    ref2 = O.loglik_batch(prob, wl.m, wl.G, th_o, u_o, grad=False)
+    np.testing.assert_allclose(ell.cpu().numpy(), ref2["ell"], rtol=1e-11)
+    S().smc_free(ctx)
+
+
+def test_full_smc_run_matches_oracle_fp64():
+    wl = small_glm("logistic", n=4000, p=4, N=128, m=50, G=5, L=6, R=2, x_dtype="f64", seed=21)
+    prob, ctx = make_pair(wl)
+    cfg = O.SMCConfig(N=wl.N, m=wl.m, G=wl.G, L=wl.L, R=wl.R, seed=wl.seed, tau=0.5)
+    st_o = O.smc_run(prob, cfg)
+    runner = S().SubsampledSMC.__new__(S().SubsampledSMC)
+    runner.ctx, runner.history = ctx, []
+    st = runner.run(wl.R)
+    assert st["stage"] == st_o.stage
+    np.testing.assert_allclose([h["a"] for h in runner.history], [h["a"] for h in st_o.history],
+                               rtol=1e-9)
+    assert st["log_z"] == pytest.approx(st_o.log_z, abs=1e-7)
+    th, u, _ = S().smc_get_particles(ctx)
+    np.testing.assert_array_equal(u.cpu().numpy(), st_o.us)
+    np.testing.assert_allclose(th.cpu().numpy(), st_o.thetas, rtol=1e-7, atol=1e-9)
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
+def test_conjugate_gaussian_log_marginal_on_gpu(x_dtype):
+    """Gaussian response: the second-order control variate is exact, so SMC targets the exact
+    posterior; the seed-averaged log marginal likelihood matches the closed form."""
+    from scipy import stats
+    errs = []
+    for seed in range(1, 7):
+        wl = small_glm("gaussian", n=300, p=3, N=2048, m=8, G=2, L=8, R=3, x_dtype=x_dtype,
+                       seed=3, sigma=0.8, prior_var=4.0)
+        X, y = wl.X, wl.y
+        logml = stats.multivariate_normal(mean=np.zeros(wl.n),
+                                          cov=0.64 * np.eye(wl.n) + 4.0 * X @ X.T).logpdf(y)
+        Sinv = X.T @ X / 0.64 + np.eye(3) / 4.0
+        mu = np.linalg.solve(Sinv, X.T @ y / 0.64)
+        prob, ctx = make_pair(wl, theta_bar=mu, seed=seed)
+        runner = S().SubsampledSMC.__new__(S().SubsampledSMC)
+        runner.ctx, runner.history = ctx, []
+        st = runner.run(wl.R)
+        errs.append(st["log_z"] - logml)
+        th, _, _ = S().smc_get_particles(ctx)
+        sd = np.sqrt(np.diag(np.linalg.inv(Sinv)))
+        assert np.all(np.abs(th.cpu().double().numpy().mean(0) - mu) < 0.15 * sd)
+        S().smc_free(ctx)
+    assert abs(np.mean(errs)) < 0.1, errs
+
+
+def test_edge_cases():
+    # p = 1, m = 1, G = 1, N = 1, empty batch, out-of-range index
+    wl = small_glm("logistic", n=50, p=1, N=1, m=1, G=1, L=1, x_dtype="f32", seed=2)
+    prob, ctx = make_pair(wl)
+    e, s = S().loglik_est(ctx, torch.zeros(0, 1, device=DEV), torch.zeros(0, 1, dtype=torch.int32,
+                                                                         device=DEV))
+    assert e.numel() == 0
+    th = torch.tensor([[0.1]], device=DEV)
+    ell, s2 = S().loglik_est(ctx, th, torch.tensor([[49]], device=DEV))
+    ref = O.loglik_batch(prob, 1, 1, np.array([[np.float32(0.1)]], dtype=np.float64),
+                         np.array([[49]]), grad=False)
+    assert ell.item() == pytest.approx(ref["ell"][0], rel=1e-5)
+    assert s2.item() == 0.0
+    with pytest.raises(S()._abi.SmcError) as ei:
+        S().loglik_est(ctx, th, torch.tensor([[50]], device=DEV))
+    assert ei.value.code == -1
+    a, lz, ess = S().smc_reweight(ctx)  # N = 1: ESS is 1 for every increment
+    assert a == 1.0 and ess == pytest.approx(1.0)
+    S().smc_resample(ctx)
+    S().smc_move(ctx, 2)
+    S().smc_free(ctx)
+    # G = m: every block is one row
+    wl = _wl("poisson", "bf16", N=33, m=12, G=12)
+    prob, ctx = make_pair(wl)
+    ell, s2, blk = S().smc_get_cache(ctx)
+    th, u, _ = S().smc_get_particles(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th.cpu().double().numpy(), u.cpu().numpy(),
+                         grad=False, blocks=True)
+    np.testing.assert_allclose(ell.cpu().numpy(), ref["ell"], rtol=1e-5)
+    S().smc_free(ctx)
+
+
+def test_bad_arguments_are_rejected():
+    wl = small_glm("logistic", n=50, p=3, N=4, m=5, G=2, L=1, x_dtype="f32", seed=2)
+    from gpu_common import device_arrays
+    X, y = device_arrays(wl)
+    with pytest.raises(S()._abi.SmcError):
+        S().smc_init(X, y, "logistic", wl.prior_mean, wl.prior_var, N=4, m=5, G=6, L=1, seed=1)
+    with pytest.raises(S()._abi.SmcError):
+        S().smc_init(X, y, "logistic", wl.prior_mean, -wl.prior_var, N=4, m=5, G=2, L=1, seed=1)
+    with pytest.raises(S()._abi.SmcError):
+        S().smc_init(X, y, "logistic", wl.prior_mean, wl.prior_var, N=4, m=5, G=2, L=0, seed=1)
