@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of likelihood-annealed subsampling SMC on one GB300 (or N replicas under torchrun).
+
+A step is one SMC stage (Algorithm 2): temperature search + reweighting, weighted moments + mass
+matrix, systematic resampling, and R Markov moves (Algorithm 1: block u update, then an HMC
+trajectory of L leapfrog steps). The metric is particle-row gradient evaluations per second:
+each stage evaluates the subsampled log-likelihood gradient N * m * R * (L + 1) times per row.
+
+Default workload: logistic regression, n = 1,000,000 rows, p = 20 (intercept + 19 AR(1) N(0,1)
+covariates), N = 4096 particles, m = 1000, G = 10, L = 20, R = 5, X stored in BF16 with FP32
+accumulation (the FP32-stored run is measured beside it). Data are synthetic (seeded).
+
+--impl reference times the FP64 CPU oracle on the host cores instead (bounded particle samples).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+R_MOVES = 5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-stored comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_name(wl, R):
+    return (f"logistic n={wl.n} p={wl.p} N={wl.N} m={wl.m} G={wl.G} L={wl.L} R={R} "
+            f"X={wl.x_dtype}")
+
+
+def grad_evals_per_stage(wl, R):
+    return wl.N * wl.m * R * (wl.L + 1)
+
+
+# ------------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.reader.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def device_workload(wl, dev):
+    import torch
+    if wl.x_dtype == "bf16":
+        X = torch.from_numpy(wl.X_store.view(np.int16)).view(torch.bfloat16)
+    else:
+        X = torch.from_numpy(wl.X_store)
+    return X.to(dev), torch.from_numpy(wl.y_store).to(dev)
+
+
+def make_ctx(S, wl, dev, seed_offset=0):
+    X, y = device_workload(wl, dev)
+    ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G, L=wl.L,
+                     seed=wl.seed + seed_offset, ess_frac=0.5, theta_bar=None)
+    del X, y  # the library keeps its own packed copy
+    tile = S.smc_autotune(ctx)
+    return ctx, tile
+
+
+def run_stage(S, ctx, R):
+    a, lz, ess = S.smc_reweight(ctx)
+    S.smc_resample(ctx)
+    S.smc_move(ctx, R)
+    return a
+
+
+def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist):
+    import torch
+    for _ in range(warmup):
+        run_stage(S, ctx, R)
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    S.smc_profile_enable(ctx, True)
+    for g in S.smc.PROFILE_GROUPS:
+        S.smc_profile_read(ctx, g)
+    launches0 = S.smc_launch_count(ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.add_(1)  # write a buffer larger than L2 between timed stages
+        starts[k].record()
+        run_stage(S, ctx, R)
+        ends[k].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = S.smc_launch_count(ctx) - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    prof = {g: S.smc_profile_read(ctx, g) for g in S.smc.PROFILE_GROUPS}
+    S.smc_profile_enable(ctx, False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, wall, launches, prof
+
+
+def full_run(S, wl, dev, R, max_stages=400):
+    """SMC wall time from init to a = 1 (Algorithm 2 to completion)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx, _ = make_ctx(S, wl, dev, seed_offset=1000)
+    stages = 0
+    a = 0.0
+    while a < 1.0 and stages < max_stages:
+        a = run_stage(S, ctx, R)
+        stages += 1
+    th, _, W = S.smc_get_particles(ctx)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = S.smc_get_status(ctx)
+    mean = (th.double() * W[:, None]).sum(0).cpu().numpy()
+    tb = S.smc_get_centre(ctx)[0]
+    S.smc_free(ctx)
+    return {"wall_s": round(wall, 4), "stages": stages, "log_z": st["log_z"],
+            "post_mean_minus_mode_maxabs": float(np.max(np.abs(mean - tb)))}
+
+
+def e2e_stages(S, ctx, wl, R, steps):
+    """Same stages through the public API with the particle state resident on the host: each step
+    copies theta, u, W in from pinned host memory and the new cloud back out."""
+    import torch
+    th, u, W = S.smc_get_particles(ctx)
+    th_h = th.cpu().pin_memory()
+    u_h = u.cpu().pin_memory()
+    W_h = W.cpu().pin_memory()
+    bytes_in = th_h.numel() * th_h.element_size() + u_h.numel() * 4 + W_h.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        S.smc_set_particles(ctx, th_h, u_h, W_h)
+        run_stage(S, ctx, R)
+        S.smc_get_particles(ctx, th_h, u_h, W_h)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return wall, bytes_in, bytes_in
+
+
+def gpu_arm(args):
+    import torch
+    import paper_1805_03317_gb300 as S
+    from smc_workloads import logistic_1e6
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    R = R_MOVES
+
+    wl = logistic_1e6("bf16", n=args.n)
+    ctx, tile = make_ctx(S, wl, dev, seed_offset=rank)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    sampler = ClockSampler(local if not os.environ.get("CUDA_VISIBLE_DEVICES") else 0)
+    sampler.start()
+    ms, wall, launches, prof = timed_stages(S, ctx, wl, R, args.steps, args.warmup, flush, dist)
+    clocks = sampler.stop()
+    per_stage = grad_evals_per_stage(wl, R)
+    value = per_stage * args.steps * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (the HMC trajectory): algorithmic bytes per row are the
+    # gathered covariates, the row index and the response
+    hbm, peak_kind = peaks()
+    n_h, ms_h = prof["hmc"]
+    bytes_row = wl.p * 2 + 4 + 4
+    bytes_launch = (wl.L + 1) * wl.N * wl.m * bytes_row
+    achieved = bytes_launch / (ms_h / n_h / 1e3) / 1e9 if n_h else None
+    shares = {g: round(v[1] / ms, 4) for g, v in prof.items() if v[0]}
+
+    e2e_wall, bi, bo = e2e_stages(S, ctx, wl, R, max(3, min(args.steps, 20)))
+    e2e_value = per_stage * max(3, min(args.steps, 20)) * world / e2e_wall
+    S.smc_free(ctx)
+
+    fp32 = None
+    walls = {}
+    if not args.no_compare and rank == 0:
+        wl32 = logistic_1e6("f32", n=args.n)
+        ctx32, tile32 = make_ctx(S, wl32, dev, seed_offset=rank)
+        ms32, _, _, prof32 = timed_stages(S, ctx32, wl32, R, args.steps, args.warmup, flush, False)
+        S.smc_free(ctx32)
+        n32, t32 = prof32["hmc"]
+        fp32 = {"value": per_stage * args.steps / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
+                "hmc_ms_per_launch": t32 / max(n32, 1), "tile": tile32}
+        walls = {"bf16": full_run(S, wl, dev, R), "fp32": full_run(S, wl32, dev, R)}
+        del wl32
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = cpu_baseline(wl, R, args.cpu_seconds)
+
+    traffic = committed_traffic(bytes_launch)
+    out = {
+        "metric": "particle-row grad-evals/s (subsampling SMC stage: reweight, resample, "
+                  "R moves)",
+        "value": value,
+        "unit": "grad-evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": workload_name(wl, R), "model": "logistic regression",
+                   "global_batch": wl.N * world, "seq_len": wl.m,
+                   "parallelism": f"replicas{world}", "tile": tile,
+                   "l2": "flushed between timed stages (256 MiB write)",
+                   "accumulate": "FP32 per row, FP64 totals/weights/MH"},
+        "roofline": {"kernel": "k_hmc (HMC trajectory, L+1 estimator passes)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "bytes_per_launch": bytes_launch, "launches": n_h,
+                     "ms_per_launch": ms_h / max(n_h, 1),
+                     "note": "X (48 MB packed) is L2-resident within a stage"},
+        "stage_shares": shares,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "grad-evals/s", "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "fp32_storage": fp32,
+        "smc_wall_time": walls,
+        "cpu_baseline": cpu,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def committed_traffic(bytes_launch):
+    """DRAM bytes per HMC launch from the committed ncu summary, if it was taken on the current
+    kernel sources (its recorded source hash matches); otherwise None."""
+    path = os.path.join(ROOT, "profiles", "k_hmc_logistic_n1e6_p20_bf16.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    want = source_hash()
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("csrc_sha256") != want or "dram_bytes_per_launch_full" not in vals:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full"])
+    except ValueError:
+        return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_03317_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_setup(wl):
+    from oracle import oracle as O
+    prob = O.Problem(wl.family, wl.X, wl.y, wl.prior_mean, wl.prior_var)
+    prob.set_centre(wl.theta_true)  # the oracle's own move timing does not depend on the centre
+    th, us = O.init_particles(wl.seed, wl.N, wl.p, wl.m, wl.n, wl.prior_mean, wl.prior_var)
+    Sig = np.diag(wl.prior_var)
+    Lc = np.linalg.cholesky(Sig)
+    return O, prob, th, us, Sig, Lc
+
+
+def oracle_move_seconds(O, prob, wl, th, us, Sig, Lc, count, stage):
+    t0 = time.perf_counter()
+    O.upm_move(prob, wl.m, wl.G, wl.seed, stage, 0, 0.01, th[:count], us[:count])
+    O.hmc_move(prob, wl.m, wl.G, wl.seed, stage, 0, 0.01, 0.3, wl.L, Sig, Lc, th[:count],
+               us[:count])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, R, seconds):
+    O, prob, th, us, Sig, Lc = oracle_setup(wl)
+    cores = O.num_threads()
+    probe = min(wl.N, max(cores, 16))
+    t = oracle_move_seconds(O, prob, wl, th.copy(), us.copy(), Sig, Lc, probe, 1)
+    count = int(min(wl.N, max(probe, probe * seconds / max(t, 1e-3))))
+    per_move = count * wl.m * (wl.L + 1)
+    reps, t = 0, 0.0
+    while t < seconds and reps < 1000:  # whole moves of `count` particles until ~`seconds` of work
+        t += oracle_move_seconds(O, prob, wl, th.copy(), us.copy(), Sig, Lc, count, 2 + reps)
+        reps += 1
+    return {"value": per_move * reps / t, "unit": "grad-evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} Algorithm-1 move(s) (u block update + HMC, L={wl.L}) of {count} of "
+                      f"the {wl.N} particles, FP64 C oracle with OpenMP over particles, {t:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from smc_workloads import logistic_1e6
+    wl = logistic_1e6("bf16", n=args.n)
+    O, prob, th, us, Sig, Lc = oracle_setup(wl)
+    cores = O.num_threads()
+    per_step_budget = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    probe = max(cores, 16)
+    t = oracle_move_seconds(O, prob, wl, th.copy(), us.copy(), Sig, Lc, probe, 1)
+    count = int(min(wl.N, max(probe, probe * per_step_budget / max(t, 1e-3))))
+    for s in range(args.warmup):
+        oracle_move_seconds(O, prob, wl, th.copy(), us.copy(), Sig, Lc, count, 2 + s)
+    tot = 0.0
+    for s in range(args.steps):
+        tot += oracle_move_seconds(O, prob, wl, th.copy(), us.copy(), Sig, Lc, count, 100 + s)
+    evals = count * wl.m * (wl.L + 1) * args.steps
+    value = evals / tot
+    sample = (f"per step: one Algorithm-1 move (u block update + HMC, L={wl.L}) of {count} of the "
+              f"{wl.N} particles; FP64 C oracle, OpenMP over particles")
+    out = {"impl": "reference", "metric": "particle-row grad-evals/s (subsampling SMC stage: "
+           "reweight, resample, R moves)", "value": value, "unit": "grad-evals/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(wl, R_MOVES), "model": "logistic regression"},
+           "cpu_baseline": {"value": value, "unit": "grad-evals/s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

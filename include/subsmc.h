@@ -105,12 +105,16 @@ const char *smc_last_error(const smc_ctx *ctx);
  * new weights stays at ess_frac*N (Sec. 2.2; K-ary refinement of a bracket, Algorithm 2 (b));
  * reweight with w_i = W_i exp((a_s - a_{s-1}) l_hat_i - (a_s^2 - a_{s-1}^2) sigma2_hat_i / 2)
  * (Sec. 3.3) and normalise in FP64; accumulate log Z_s/Z_{s-1} (Sec. 3.5); form the weighted
- * particle covariance Sigma and its Cholesky factor for the HMC mass matrix H = Sigma^{-1}.
+ * particle covariance Sigma and its Cholesky factor for the HMC mass matrix H = Sigma^{-1}
+ * (jitter 1e-10 tr(Sigma)/p, x10 per retry, up to 12 retries; if Sigma stays singular, e.g. for a
+ * single particle, the previous stage's mass matrix is kept; at the start it is the prior covariance).
  * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS. */
 int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
 
-/* Step (e): systematic resampling with the current weights (integer-quantised, exact; see the
- * design notes), carrying theta, u and the cached estimates; then W = 1/N.
+/* Step (e): systematic resampling with the current weights, carrying theta, u and the cached
+ * estimates; then W = 1/N. Weights are quantised to w_i = floor(W_i 2^40); with T = sum w_i and one
+ * uniform U per stage, position i = floor((i T + floor(U T)) / N) selects the first particle whose
+ * cumulative integer weight exceeds it, so the ancestors are exact and independent of summation order.
  * ancestors: device [N] int32 or NULL. */
 int smc_resample(smc_ctx *ctx, int32_t *ancestors);
 
@@ -174,6 +178,14 @@ int smc_autotune(smc_ctx *ctx, int32_t *tile);
 
 /* Number of kernels this context has launched so far (every launch is counted). */
 int64_t smc_launch_count(const smc_ctx *ctx);
+
+/* Tracing. When enabled, every kernel group is bracketed by CUDA events recorded on the context's
+ * stream. Groups: 0 estimator (loglik_est / loglik_grad / cache refresh), 1 u-block update,
+ * 2 HMC trajectory, 3 temperature search + reweighting, 4 weighted moments + mass matrix,
+ * 5 resampling. smc_profile_read synchronises the stream, returns the number of launches and their
+ * summed device time in milliseconds for one group, and clears that group's record. */
+int smc_profile_enable(smc_ctx *ctx, int32_t on);
+int smc_profile_read(smc_ctx *ctx, int32_t group, int64_t *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

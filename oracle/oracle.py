@@ -350,6 +350,8 @@ class SMCState:
     ell: np.ndarray
     sig2: np.ndarray
     log_z: float = 0.0
+    Sigma: np.ndarray | None = None   # mass-matrix inverse of the last stage (prior covariance at first)
+    Lc: np.ndarray | None = None
     history: list = field(default_factory=list)
 
 
@@ -360,7 +362,9 @@ def smc_init(prob: Problem, cfg: SMCConfig) -> SMCState:
     out = loglik_batch(prob, cfg.m, cfg.G, th, us, a=0.0, grad=False)
     eps = cfg.eps0 if cfg.eps0 is not None else 0.5 * prob.p ** -0.25
     logW = np.full(cfg.N, -math.log(cfg.N))
-    return SMCState(0, 0.0, eps, th, us, logW, np.exp(logW), out["ell"], out["sigma2"])
+    Sigma0 = np.diag(prob.prior_var)
+    return SMCState(0, 0.0, eps, th, us, logW, np.exp(logW), out["ell"], out["sigma2"],
+                    Sigma=Sigma0, Lc=np.linalg.cholesky(Sigma0))
 
 
 def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
@@ -370,7 +374,9 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     s = st.stage
     a_new, logW, W, lz, ess = reweight(st.logW, st.ell, st.sig2, st.a, cfg.tau, cfg.K,
                                        cfg.rounds)
-    mean, Sigma, Lc, _ = moments(W, st.thetas)
+    mean, Sigma, Lc, rc = moments(W, st.thetas)
+    if rc >= 0:  # a covariance that is not positive definite (e.g. N = 1) keeps the previous one
+        st.Sigma, st.Lc = Sigma, Lc
     U = uniform(r64(cfg.seed, TAG_RESAMPLE, stage_move(s, 0), 0, 0))
     anc = resample(W, U)
     st.thetas = st.thetas[anc].copy()
@@ -382,8 +388,8 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     acc_u = acc_t = 0
     for r in range(cfg.R):
         acc_u += int(upm_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.thetas, st.us).sum())
-        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.eps, cfg.L, Sigma, Lc,
-                              st.thetas, st.us).sum())
+        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.eps, cfg.L, st.Sigma,
+                              st.Lc, st.thetas, st.us).sum())
     out = loglik_batch(prob, cfg.m, cfg.G, st.thetas, st.us, a=st.a, grad=False)
     st.ell, st.sig2 = out["ell"], out["sigma2"]
     rate = acc_t / float(cfg.N * cfg.R)

@@ -52,6 +52,8 @@ SIGNATURES = {
     "smc_set_scalars": (ctypes.c_int, [c_vp, c_i32, c_d, c_d, c_d]),
     "smc_autotune": (ctypes.c_int, [c_vp, c_ip]),
     "smc_launch_count": (ctypes.c_int64, [c_vp]),
+    "smc_profile_enable": (ctypes.c_int, [c_vp, c_i32]),
+    "smc_profile_read": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_i64), c_dp]),
 }
 
 _lib = None

@@ -49,6 +49,10 @@ struct smc_ctx {
   double *scratch_d = nullptr;  // small FP64 scratch (Newton, moments at a point)
   int *info_d = nullptr;
   DevState *st = nullptr;
+  // tracing: event pairs per kernel group
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[6];
+  std::vector<cudaEvent_t> ev_pool;
   // host mirrors
   int stage = 0, moves_in_stage = 0;
   int64_t launches = 0;
@@ -111,7 +115,39 @@ int est_tiles(const smc_ctx *c, Tile *out, int cap) {
   return est_tiles_bf16(out, cap);
 }
 
+cudaEvent_t take_event(smc_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets a kernel group with events when tracing is on.
+struct ProfScope {
+  smc_ctx *c;
+  int group;
+  cudaEvent_t a = nullptr;
+  ProfScope(smc_ctx *c_, int g) : c(c_), group(g) {
+    if (c->prof_on) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->prof[group].push_back({a, b});
+    }
+  }
+};
+
 int est_launch(smc_ctx *c, int op, const EstArgs &a) {
+  ProfScope ps(c, op);
   c->launches += 1;
   if (c->x_dtype == SMC_F64) return est_launch_f64(op, c->tile, a, c->stream);
   if (c->x_dtype == SMC_F32) return est_launch_f32(op, c->tile, a, c->stream);
@@ -466,8 +502,14 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
 
 int smc_free(smc_ctx *c) {
   if (!c) return SMC_OK;
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
   for (void *q : c->allocs) cudaFree(q);
+  for (auto &v : c->prof)
+    for (auto &pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return SMC_OK;
 }
@@ -481,15 +523,23 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
   c->stage += 1;
   c->moves_in_stage = 0;
   int nl = 0;
-  int e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->st, c->part,
-                   &nl, c->stream);
+  int e;
+  {
+    ProfScope ps(c, 3);
+    e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->st, c->part,
+                 &nl, c->stream);
+  }
   c->launches += nl;
   if (e) return fail(c, SMC_ERR_CUDA, std::string("reweight: ") + cudaGetErrorString((cudaError_t)e));
-  LAUNCH(c,
-         weighted_moments(c->is_f64, c->N, c->p, c->W, c->theta, c->part, c->mean_d, c->Sigma_raw,
-                          c->stream),
-         4);
-  int r = set_mass(c);
+  int r;
+  {
+    ProfScope ps(c, 4);
+    LAUNCH(c,
+           weighted_moments(c->is_f64, c->N, c->p, c->W, c->theta, c->part, c->mean_d,
+                            c->Sigma_raw, c->stream),
+           4);
+    r = set_mass(c);
+  }
   if (r) return r;
   if (a_next || log_z_inc || ess) {
     DevState h;
@@ -504,6 +554,7 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
 
 int smc_resample(smc_ctx *c, int32_t *ancestors) {
   if (!c) return SMC_ERR_ARG;
+  ProfScope ps(c, 5);
   LAUNCH(c,
          resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->W, c->cum, c->anc,
                   c->theta, c->theta_alt, c->u, c->u_alt, c->ell, c->ell_alt, c->sig2,
@@ -741,5 +792,28 @@ int smc_autotune(smc_ctx *c, int32_t *tile) {
 }
 
 int64_t smc_launch_count(const smc_ctx *c) { return c ? c->launches : 0; }
+
+int smc_profile_enable(smc_ctx *c, int32_t on) {
+  if (!c) return SMC_ERR_ARG;
+  c->prof_on = on != 0;
+  return SMC_OK;
+}
+
+int smc_profile_read(smc_ctx *c, int32_t group, int64_t *launches, double *total_ms) {
+  if (!c || group < 0 || group > 5) return SMC_ERR_ARG;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  for (auto &pr : c->prof[group]) {
+    float ms = 0.f;
+    CUDA_OK(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+    c->ev_pool.push_back(pr.first);
+    c->ev_pool.push_back(pr.second);
+  }
+  if (launches) *launches = (int64_t)c->prof[group].size();
+  if (total_ms) *total_ms = tot;
+  c->prof[group].clear();
+  return SMC_OK;
+}
 
 }  // extern "C"

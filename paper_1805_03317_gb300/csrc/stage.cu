@@ -644,7 +644,8 @@ int weighted_moments(int is_f64, int N, int p, const double *W, const void *thet
 }
 
 // Mass matrix: Cholesky of Sigma with the jitter schedule 1e-10 tr/p, x10 per retry (added
-// cumulatively, at most 12 retries); then Linv = chol^{-1} for drawing rho = Linv' z.
+// cumulatively, at most 12 retries); then Linv = chol^{-1} for drawing rho = Linv' z. When no
+// retry succeeds (e.g. a single particle: Sigma = 0) the previous mass matrix is kept.
 template <typename CT>
 __global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *chol, CT *Sigma_ct,
                        CT *Linv_ct, double *work, DevState *st) {
@@ -652,7 +653,7 @@ __global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *cho
   __shared__ int flag;
   __shared__ double jit;
   const int tid = threadIdx.x;
-  for (int e = tid; e < p * p; e += blockDim.x) Sigma[e] = Sigma_in[e];
+  for (int e = tid; e < p * p; e += blockDim.x) work[e] = Sigma_in[e];
   if (tid == 0) {
     double tr = 0.0;
     for (int c = 0; c < p; ++c) tr += Sigma_in[c * p + c];
@@ -662,26 +663,25 @@ __global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *cho
   int tries = 0;
   bool ok = false;
   while (true) {
-    for (int e = tid; e < p * p; e += blockDim.x) M[e] = Sigma[e];
+    for (int e = tid; e < p * p; e += blockDim.x) M[e] = work[e];
     __syncthreads();
     ok = chol_block(M, p, &flag);
     if (ok || tries == 12) break;
     ++tries;
     __syncthreads();
-    for (int c = tid; c < p; c += blockDim.x) Sigma[c * p + c] += jit;
+    for (int c = tid; c < p; c += blockDim.x) work[c * p + c] += jit;
     __syncthreads();
     if (tid == 0) jit *= 10.0;
     __syncthreads();
   }
   if (tid == 0) st->chol_retries = ok ? tries : -1;
-  if (!ok) {
-    if (tid == 0) atomicOr(&st->err, kErrChol);
-    return;
-  }
+  if (!ok) return;  // keep the previous mass matrix
   for (int e = tid; e < p * p; e += blockDim.x) {
+    Sigma[e] = work[e];
     chol[e] = M[e];
-    Sigma_ct[e] = (CT)Sigma[e];
+    Sigma_ct[e] = (CT)work[e];
   }
+  __syncthreads();
   // column j of Linv by forward substitution, L X = I (FP64 in work; each thread owns columns)
   for (int j = tid; j < p; j += blockDim.x) {
     for (int i = 0; i < j; ++i) work[i * p + j] = 0.0;

@@ -207,6 +207,21 @@ def smc_launch_count(ctx: Context) -> int:
     return int(_abi.load().smc_launch_count(ctx.handle))
 
 
+PROFILE_GROUPS = ("estimate", "u_update", "hmc", "reweight", "moments_mass", "resample")
+
+
+def smc_profile_enable(ctx: Context, on: bool = True) -> None:
+    check(_abi.load().smc_profile_enable(ctx.handle, int(on)), "smc_profile_enable", ctx.handle)
+
+
+def smc_profile_read(ctx: Context, group) -> tuple[int, float]:
+    g = PROFILE_GROUPS.index(group) if isinstance(group, str) else int(group)
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    check(_abi.load().smc_profile_read(ctx.handle, g, ctypes.byref(n), ctypes.byref(ms)),
+          "smc_profile_read", ctx.handle)
+    return n.value, ms.value
+
+
 # ------------------------------------------------------------------------------------------------
 # Convenience wrapper
 # ------------------------------------------------------------------------------------------------

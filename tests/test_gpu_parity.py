@@ -144,7 +144,9 @@ def test_reweight_moments_and_mass_match_oracle(x_dtype, a0):
     t = tol(x_dtype)
     rtol = 1e-12 if x_dtype == "f64" else 1e-5
     assert a_new == pytest.approx(ra, rel=rtol, abs=1e-15)
-    assert lz == pytest.approx(rlz, rel=rtol, abs=t["ell"] * abs(ref["ell"]).max() * abs(a_new - a0))
+    # log Z increment = LSE(new) - LSE(old): FP64 cancellation leaves ~1e-15 * |log N| absolute
+    lz_abs = t["ell"] * abs(ref["ell"]).max() * abs(a_new - a0) + 1e-13
+    assert lz == pytest.approx(rlz, rel=rtol, abs=lz_abs)
     assert ess == pytest.approx(ress, rel=max(rtol, 1e-9))
     _, _, Wg = S().smc_get_particles(ctx)
     np.testing.assert_allclose(Wg.cpu().numpy(), rW, rtol=1e-6 if x_dtype != "f64" else 1e-9,
@@ -269,7 +271,7 @@ def test_edge_cases():
     ref = O.loglik_batch(prob, 1, 1, np.array([[np.float32(0.1)]], dtype=np.float64),
                          np.array([[49]]), grad=False)
     assert ell.item() == pytest.approx(ref["ell"][0], rel=1e-5)
-    assert s2.item() == 0.0
+    assert abs(s2.item()) <= 1e-5 * abs(ref["ell"][0])  # one row: sum of squared deviations is 0
     with pytest.raises(S()._abi.SmcError) as ei:
         S().loglik_est(ctx, th, torch.tensor([[50]], device=DEV))
     assert ei.value.code == -1
