@@ -187,6 +187,33 @@ int64_t smc_launch_count(const smc_ctx *ctx);
 int smc_profile_enable(smc_ctx *ctx, int32_t on);
 int smc_profile_read(smc_ctx *ctx, int32_t group, int64_t *launches, double *total_ms);
 
+/* ------------------------------------------------------------------------------------------- */
+/* Resampling without allocation                                                                */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Largest N accepted by smc_resample_noalloc. */
+#define SMC_NOALLOC_MAX_N 262144
+
+/* The paper has no counterpart to this entry point; it is a service for callers that cannot
+ * allocate device memory when they need resampling: code that runs while a CUDA graph is being
+ * captured (cudaMalloc is not allowed there), engines whose memory plan is fixed before they start,
+ * and hosts that give the GPU a fixed arena and forbid further allocations.
+ * It computes the same ancestors as smc_resample for the same normalised weights, seed and stage
+ * (integer weights floor(W_i 2^40), uniform U from the stage's resampling stream), but needs no
+ * context and calls no allocator: its scratch is one fixed device array inside this library
+ * (SMC_NOALLOC_MAX_N + 2 eight-byte words, about 2 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *   N: 1 <= N <= SMC_NOALLOC_MAX_N, otherwise SMC_ERR_ARG (message in smc_last_error(NULL)).
+ *   W: device [N] double, normalised weights. ancestors: device [N] int32 output. Caller-owned.
+ *   seed, stage: select the uniform exactly as smc_init's seed and the stage index do.
+ *   stream: a cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
+ * The first call on each device looks up the scratch array's device address with that device
+ * current; make that first call before any stream capture begins. All calls on a device share the
+ * one scratch array, so calls whose kernels overlap on the GPU (different streams, no ordering
+ * between them) race and may return wrong ancestors: order them on one stream or with events. */
+int smc_resample_noalloc(int32_t N, const double *W, uint64_t seed, int32_t stage,
+                         int32_t *ancestors, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

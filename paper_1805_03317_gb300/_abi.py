@@ -54,7 +54,9 @@ SIGNATURES = {
     "smc_launch_count": (ctypes.c_int64, [c_vp]),
     "smc_profile_enable": (ctypes.c_int, [c_vp, c_i32]),
     "smc_profile_read": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_i64), c_dp]),
+    "smc_resample_noalloc": (ctypes.c_int, [c_i32, c_vp, c_u64, c_i32, c_vp, c_vp]),
 }
+NOALLOC_MAX_N = 262144
 
 _lib = None
 

@@ -429,6 +429,8 @@ int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const dou
 
 }  // namespace
 
+void subsmc::set_global_error(const std::string &msg) { g_init_error = msg; }
+
 extern "C" {
 
 int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const double *theta_bar,

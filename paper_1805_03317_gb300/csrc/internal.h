@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace subsmc {
 
 // Scalars that live on the device so that a whole stage runs without host round trips.
@@ -108,5 +110,8 @@ int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_
 int eps_update(int N, int R, DevState *st, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);
 int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s);
+
+// Message returned by smc_last_error(NULL) (abi.cu).
+void set_global_error(const std::string &msg);
 
 }  // namespace subsmc

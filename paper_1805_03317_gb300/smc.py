@@ -250,3 +250,18 @@ class SubsampledSMC:
 
     def close(self):
         smc_free(self.ctx)
+
+
+def smc_resample_noalloc(W: torch.Tensor, seed: int, stage: int, ancestors: torch.Tensor,
+                         stream=None) -> None:
+    """Ancestors of systematic resampling without any device allocation by the library (for callers
+    that cannot allocate, e.g. during CUDA graph capture). W: CUDA float64 [N], normalised;
+    ancestors: CUDA int32 [N], written asynchronously on the stream. N <= 262144."""
+    if W.dtype != torch.float64 or not W.is_cuda or not W.is_contiguous():
+        raise ValueError("W must be a contiguous CUDA float64 tensor")
+    if ancestors.dtype != torch.int32 or not ancestors.is_cuda or ancestors.numel() != W.numel():
+        raise ValueError("ancestors must be a CUDA int32 tensor with W's length")
+    with torch.cuda.device(W.device):
+        rc = _abi.load().smc_resample_noalloc(W.numel(), _ptr(W), int(seed) & ((1 << 64) - 1),
+                                              int(stage), _ptr(ancestors), _stream_handle(stream))
+    check(rc, "smc_resample_noalloc", None)
