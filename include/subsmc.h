@@ -77,6 +77,9 @@ typedef struct {
   int32_t search_rounds;     /* refinement rounds; 0 -> 10                                        */
   double eps0;               /* initial leapfrog step; <= 0 -> 0.5 * p^(-1/4)                     */
   int32_t tile_hint;         /* estimator tile: 0 = automatic, k >= 1 = compiled tile k-1         */
+  int32_t hmc_kernel;        /* HMC trajectory kernel: 0 = automatic (rows resident in shared      */
+                             /* memory when they fit, else streamed), 1 = streamed, k >= 2 =      */
+                             /* resident tile k-2                                                  */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */
@@ -172,9 +175,12 @@ int smc_get_status(smc_ctx *ctx, double *a, double *log_z, int32_t *stage, doubl
  * The cached estimates stay valid (they do not depend on a). */
 int smc_set_scalars(smc_ctx *ctx, int32_t stage, double a, double eps, double log_z);
 
-/* Time the estimator's compiled tile shapes on this context's own particles and keep the fastest.
- * Host output (may be NULL): the chosen tile as a tile_hint value (>= 1). */
-int smc_autotune(smc_ctx *ctx, int32_t *tile);
+/* Time the estimator's compiled tile shapes on this context's own particles and keep the fastest;
+ * then time the HMC trajectory kernels (streamed, and every resident tile that fits) on scratch
+ * copies of the particles and keep the fastest. The particle state is not changed.
+ * Host outputs (may be NULL): the estimator tile as a tile_hint value (>= 1) and the HMC kernel as
+ * an hmc_kernel value (1 = streamed, >= 2 = resident tile). */
+int smc_autotune(smc_ctx *ctx, int32_t *tile, int32_t *hmc_kernel);
 
 /* Number of kernels this context has launched so far (every launch is counted). */
 int64_t smc_launch_count(const smc_ctx *ctx);

@@ -28,7 +28,7 @@ class SmcProblem(ctypes.Structure):
 class SmcConfig(ctypes.Structure):
     _fields_ = [("N", c_i32), ("m", c_i32), ("G", c_i32), ("L", c_i32), ("ess_frac", c_d),
                 ("seed", c_u64), ("search_k", c_i32), ("search_rounds", c_i32), ("eps0", c_d),
-                ("tile_hint", c_i32)]
+                ("tile_hint", c_i32), ("hmc_kernel", c_i32)]
 
 
 # name -> (restype, argtypes)
@@ -50,7 +50,7 @@ SIGNATURES = {
     "smc_get_mass": (ctypes.c_int, [c_vp, c_dp, c_dp]),
     "smc_get_status": (ctypes.c_int, [c_vp, c_dp, c_dp, c_ip, c_dp]),
     "smc_set_scalars": (ctypes.c_int, [c_vp, c_i32, c_d, c_d, c_d]),
-    "smc_autotune": (ctypes.c_int, [c_vp, c_ip]),
+    "smc_autotune": (ctypes.c_int, [c_vp, c_ip, c_ip]),
     "smc_launch_count": (ctypes.c_int64, [c_vp]),
     "smc_profile_enable": (ctypes.c_int, [c_vp, c_i32]),
     "smc_profile_read": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_i64), c_dp]),

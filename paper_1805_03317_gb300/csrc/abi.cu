@@ -17,13 +17,15 @@ struct smc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   // problem
-  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, p = 0;
+  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, Sx = 0, p = 0;
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
   double log_prior_const = 0.0;
   // configuration
   int N = 0, m = 0, G = 0, L = 0, K = 16, rounds = 10, tile = 0;
+  int res_tile = -1;  // resident HMC tile, -1 = streamed trajectory kernel
+  int sms = 1;
   double tau = 0.5, eps0 = 0.0;
   uint64_t seed = 0;
   // device memory (library-owned)
@@ -146,6 +148,28 @@ struct ProfScope {
   }
 };
 
+int res_launch(smc_ctx *c, int tile, const EstArgs &a, bool dry) {
+  if (c->x_dtype == SMC_F64) return res_launch_f64(tile, a, c->stream, c->sms, dry);
+  if (c->x_dtype == SMC_F32) return res_launch_f32(tile, a, c->stream, c->sms, dry);
+  return res_launch_bf16(tile, a, c->stream, c->sms, dry);
+}
+
+int res_tiles(const smc_ctx *c, Tile *out, int cap) {
+  if (c->x_dtype == SMC_F64) return res_tiles_f64(out, cap);
+  if (c->x_dtype == SMC_F32) return res_tiles_f32(out, cap);
+  return res_tiles_bf16(out, cap);
+}
+
+// HMC trajectory launch: resident rows when chosen, else the streamed kernel.
+int hmc_launch(smc_ctx *c, const EstArgs &a) {
+  ProfScope ps(c, 2);
+  c->launches += 1;
+  if (c->res_tile >= 0) return res_launch(c, c->res_tile, a, false);
+  if (c->x_dtype == SMC_F64) return est_launch_f64(2, c->tile, a, c->stream);
+  if (c->x_dtype == SMC_F32) return est_launch_f32(2, c->tile, a, c->stream);
+  return est_launch_bf16(2, c->tile, a, c->stream);
+}
+
 int est_launch(smc_ctx *c, int op, const EstArgs &a) {
   ProfScope ps(c, op);
   c->launches += 1;
@@ -160,13 +184,30 @@ int default_tile(const smc_ctx *c) {
   const int nt = est_tiles(c, t, 32);
   int best = -1;
   for (int i = 0; i < nt; ++i) {
-    if (t[i].T * t[i].CPL < c->S) continue;
+    if (t[i].T * t[i].CPL < c->Sx) continue;
     if (best < 0) {
       best = i;
       continue;
     }
     const int wi = t[i].T * t[i].CPL, wb = t[best].T * t[best].CPL;
     if (wi < wb || (wi == wb && t[i].T < t[best].T)) best = i;
+  }
+  return best;
+}
+
+EstArgs base_args(const smc_ctx *c);
+
+// Smallest resident tile (4 warps) whose covariate slots cover p and whose plan fits on an SM.
+int default_res_tile(smc_ctx *c) {
+  Tile t[32];
+  const int nt = res_tiles(c, t, 32);
+  EstArgs a = base_args(c);
+  a.B = c->N;
+  int best = -1;
+  for (int i = 0; i < nt; ++i) {
+    if (t[i].warps != 4 || t[i].CPL < c->p) continue;
+    if (res_launch(c, i, a, true) != 0) continue;
+    if (best < 0 || t[i].CPL < t[best].CPL) best = i;
   }
   return best;
 }
@@ -354,7 +395,7 @@ int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const dou
   const int cvw = 1 + p + p * (p + 1) / 2;
   size_t part = (size_t)cv_moments_blocks(p) * cvw * sizeof(double);
   const size_t part_mom = (size_t)152 * p * p * sizeof(double);
-  const size_t part_rw = (size_t)64 * 32 * 3 * sizeof(double);
+  const size_t part_rw = (size_t)reweight_scratch_doubles() * sizeof(double);
   if (part_mom > part) part = part_mom;
   if (part_rw > part) part = part_rw;
   ALLOC(c, c->part, part);
@@ -469,6 +510,7 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->YS = c->is_f64 ? 1 : 4 / c->esz;
   const int vec = 16 / c->esz;
   c->S = ((c->YS + P->p + vec - 1) / vec) * vec;
+  c->Sx = ((P->p + vec - 1) / vec) * vec;
   c->n = P->n;
   c->p = P->p;
   c->noise_sigma = P->family == SMC_GAUSSIAN ? P->noise_sigma : 1.0;
@@ -487,16 +529,32 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->tile = cfg->tile_hint > 0 ? cfg->tile_hint - 1 : default_tile(c);
   Tile tl[32];
   const int nt = est_tiles(c, tl, 32);
-  if (c->tile < 0 || c->tile >= nt || tl[c->tile].T * tl[c->tile].CPL < c->S) {
+  if (c->tile < 0 || c->tile >= nt || tl[c->tile].T * tl[c->tile].CPL < c->Sx) {
     g_init_error = "no compiled tile covers this row width";
     delete c;
     return SMC_ERR_ARG;
   }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->sms < 1) c->sms = 1;
   const int r = init_impl(c, P, cfg, theta_bar);
   if (r != SMC_OK) {
     g_init_error = c->err;
     smc_free(c);
     return r;
+  }
+  if (cfg->hmc_kernel == 0) {
+    c->res_tile = default_res_tile(c);
+  } else if (cfg->hmc_kernel >= 2) {
+    Tile tr[32];
+    const int nr = res_tiles(c, tr, 32);
+    EstArgs a = base_args(c);
+    a.B = c->N;
+    if (cfg->hmc_kernel - 2 >= nr || res_launch(c, cfg->hmc_kernel - 2, a, true) != 0) {
+      g_init_error = "resident HMC tile not compiled or does not fit this problem";
+      smc_free(c);
+      return SMC_ERR_ARG;
+    }
+    c->res_tile = cfg->hmc_kernel - 2;
   }
   *out = c;
   return SMC_OK;
@@ -591,7 +649,7 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     a.blk_prop = c->blk_prop;
     a.move = c->moves_in_stage + r;
     LAUNCH(c, est_launch(c, 1, a), 0);
-    LAUNCH(c, est_launch(c, 2, a), 0);
+    LAUNCH(c, hmc_launch(c, a), 0);
   }
   c->moves_in_stage += R;
   LAUNCH(c, eps_update(c->N, R, c->st, c->stream), 1);
@@ -752,18 +810,32 @@ int smc_set_scalars(smc_ctx *c, int32_t stage, double a, double eps, double log_
   return SMC_OK;
 }
 
-int smc_autotune(smc_ctx *c, int32_t *tile) {
+int smc_autotune(smc_ctx *c, int32_t *tile, int32_t *hmc_kernel) {
   if (!c) return SMC_ERR_ARG;
   Tile tl[32];
   const int nt = est_tiles(c, tl, 32);
   cudaEvent_t e0, e1;
   CUDA_OK(c, cudaEventCreate(&e0));
   CUDA_OK(c, cudaEventCreate(&e1));
-  const int keep = c->tile;
-  int best = keep;
+  auto time_it = [&](auto &&launch, int reps, float *out_ms) -> int {
+    float total = 0.f;
+    for (int rep = 0; rep < reps + 1; ++rep) {
+      CUDA_OK(c, cudaEventRecord(e0, c->stream));
+      LAUNCH(c, launch(), 0);
+      CUDA_OK(c, cudaEventRecord(e1, c->stream));
+      CUDA_OK(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_OK(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep) total += ms;  // the first launch is a warm-up
+    }
+    *out_ms = total;
+    return SMC_OK;
+  };
+  // 1. estimator tile (plain estimator with gradient on the context's particles)
+  int best = c->tile;
   float best_ms = 1e30f;
   for (int t = 0; t < nt; ++t) {
-    if (tl[t].T * tl[t].CPL < c->S) continue;
+    if (tl[t].T * tl[t].CPL < c->Sx) continue;
     c->tile = t;
     EstArgs a = base_args(c);
     a.B = c->N;
@@ -771,25 +843,55 @@ int smc_autotune(smc_ctx *c, int32_t *tile) {
     a.u = c->u;
     a.grad = c->grad_scratch;
     a.a_host = 1.0;
-    float total = 0.f;
-    for (int rep = 0; rep < 4; ++rep) {
-      CUDA_OK(c, cudaEventRecord(e0, c->stream));
-      LAUNCH(c, est_launch(c, 0, a), 0);
-      CUDA_OK(c, cudaEventRecord(e1, c->stream));
-      CUDA_OK(c, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CUDA_OK(c, cudaEventElapsedTime(&ms, e0, e1));
-      if (rep) total += ms;  // first launch is a warm-up
-    }
-    if (total < best_ms) {
-      best_ms = total;
+    float ms = 0.f;
+    int r = time_it([&]() { return est_launch(c, 0, a); }, 3, &ms);
+    if (r) return r;
+    if (ms < best_ms) {
+      best_ms = ms;
       best = t;
     }
   }
   c->tile = best;
+  // 2. HMC trajectory kernel, on scratch copies (theta_alt, ell_alt, sig2_alt, blk_alt)
+  const size_t cts = ct_size(c);
+  CUDA_OK(c, cudaMemcpyAsync(c->theta_alt, c->theta, cts * c->N * c->p, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  EstArgs a = base_args(c);
+  a.B = c->N;
+  a.theta = c->theta_alt;
+  a.theta_out = c->theta_alt;
+  a.u = c->u;
+  a.ell = c->ell_alt;
+  a.sig2 = c->sig2_alt;
+  a.blk = c->blk_alt;
+  a.blk_prop = c->blk_prop;
+  a.move = 255;
+  const int keep_res = c->res_tile;
+  int best_res = -1;
+  float best_hmc = 1e30f;
+  Tile tr[32];
+  const int nr = res_tiles(c, tr, 32);
+  for (int t = -1; t < nr; ++t) {
+    if (t >= 0 && res_launch(c, t, a, true) != 0) continue;
+    c->res_tile = t;
+    float ms = 0.f;
+    int r = time_it([&]() { return hmc_launch(c, a); }, 2, &ms);
+    if (r) {
+      c->res_tile = keep_res;
+      return r;
+    }
+    if (ms < best_hmc) {
+      best_hmc = ms;
+      best_res = t;
+    }
+  }
+  c->res_tile = best_res;
+  CUDA_OK(c, cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (tile) *tile = best + 1;
+  if (hmc_kernel) *hmc_kernel = best_res < 0 ? 1 : best_res + 2;
   return SMC_OK;
 }
 

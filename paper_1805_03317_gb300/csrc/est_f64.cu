@@ -1,5 +1,6 @@
 // Estimator kernels for f64 storage of X: one instantiation per compiled tile shape.
 #include "estimator.cuh"
+#include "resident.cuh"
 
 namespace subsmc {
 namespace {
@@ -18,6 +19,29 @@ int est_launch_f64(int op, int tile, const EstArgs &a, cudaStream_t s) {
     case 0: return launch_tile<XT, 1, 8, 1, 4>(op, a, s);
     case 1: return launch_tile<XT, 4, 8, 1, 4>(op, a, s);
     case 2: return launch_tile<XT, 8, 16, 1, 4>(op, a, s);
+    default: return -1;
+  }
+}
+
+namespace {
+const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
+                          {1, 24, 1, 8}};
+}  // namespace
+
+int res_tiles_f64(Tile *out, int cap) {
+  const int n = (int)(sizeof(kResTiles) / sizeof(kResTiles[0]));
+  for (int i = 0; i < n && i < cap; ++i) out[i] = kResTiles[i];
+  return n;
+}
+
+int res_launch_f64(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry) {
+  switch (tile) {
+    case 0: return launch_res<XT, 8, 4>(a, s, sms, dry);
+    case 1: return launch_res<XT, 16, 4>(a, s, sms, dry);
+    case 2: return launch_res<XT, 24, 4>(a, s, sms, dry);
+    case 3: return launch_res<XT, 32, 4>(a, s, sms, dry);
+    case 4: return launch_res<XT, 16, 8>(a, s, sms, dry);
+    case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
     default: return -1;
   }
 }

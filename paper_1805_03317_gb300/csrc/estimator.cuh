@@ -41,19 +41,19 @@ struct WarpEval {
     gl = lane & (T - 1);
     rs = lane / T;
   }
-  // Slot s of this lane is element gl*CPL + s of a packed row, i.e. column gl*CPL + s - YS.
+  // Slot s of this lane is element (column) gl*CPL + s of a packed row.
   __device__ __forceinline__ void load_slots(const CT *vec, int p, CT *dst) const {
 #pragma unroll
     for (int s = 0; s < CPL; ++s) {
-      const int c = gl * CPL + s - SD::YS;
-      dst[s] = (c >= 0 && c < p) ? vec[c] : CT(0);
+      const int c = gl * CPL + s;
+      dst[s] = c < p ? vec[c] : CT(0);
     }
   }
 
   // Rows [j0, j1) of the index list idx. Accumulates gradient partials into g1, g2 (if GRAD)
   // and returns this lane's partial sums of d and d^2 (nonzero only on group leaders).
   template <bool GRAD>
-  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int64_t n,
+  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int p, int64_t n,
                                        const int32_t *idx, int j0, int j1, int fam,
                                        CT inv_s2, CT *g1, CT *g2, CT &sd, CT &sd2,
                                        DevState *st) const {
@@ -71,18 +71,20 @@ struct WarpEval {
           valid[q] = false;
           k = 0;
         }
-        const uint4 *rowp = reinterpret_cast<const uint4 *>(Xp + (int64_t)k * S + gl * CPL);
-        yv[q] = YT(0);
+        const XT *row = Xp + (int64_t)k * S;
+        const uint4 *rowp = reinterpret_cast<const uint4 *>(row + gl * CPL);
+        yv[q] = (gl == 0 && valid[q]) ? __ldg(reinterpret_cast<const YT *>(row + S - SD::YS))
+                                      : YT(0);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           uint4 w = make_uint4(0u, 0u, 0u, 0u);
-          if (valid[q] && gl * CPL + v * SD::VEC < S) w = __ldg(rowp + v);
-          if (v == 0) yv[q] = SD::y_of(w);
+          if (valid[q] && gl * CPL + v * SD::VEC < p) w = __ldg(rowp + v);
           SD::unpack(w, &xv[q][v * SD::VEC]);
         }
-        if (gl == 0) {
+        if (SD::YS == 2) {  // BF16: the halves of y read as BF16 may not be finite; zero them
 #pragma unroll
-          for (int s = 0; s < SD::YS; ++s) xv[q][s] = CT(0);
+          for (int s = 0; s < CPL; ++s)
+            if (gl * CPL + s >= p) xv[q][s] = CT(0);
         }
       }
 #pragma unroll
@@ -166,7 +168,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
     for (int g = 0; g < a.G; ++g) {
       const int j0 = (int)(((int64_t)g * a.m) / a.G), j1 = (int)(((int64_t)(g + 1) * a.m) / a.G);
       CT sd = CT(0), sd2 = CT(0);
-      W.template rows<GRAD>(Xp, a.S, a.n, idx, j0, j1, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
+      W.template rows<GRAD>(Xp, a.S, a.p, a.n, idx, j0, j1, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
       const double bs = warp_sum((double)sd), bq = warp_sum((double)sd2);
       if (W.lane == 0) {
         blk_out[2 * g] = bs;
@@ -177,7 +179,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
     }
   } else {
     CT sd = CT(0), sd2 = CT(0);
-    W.template rows<GRAD>(Xp, a.S, a.n, idx, 0, a.m, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
+    W.template rows<GRAD>(Xp, a.S, a.p, a.n, idx, 0, a.m, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
     S = warp_sum((double)sd);
     Q = warp_sum((double)sd2);
   }
@@ -213,8 +215,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
     const CT bc = ldg_ct<CT>(a.B_ct, c), dc = sm.dl[c];
     qlin += (double)(dc * (bc + CT(0.5) * cd));
     if (GRAD) {
-      const int slot = c + Store<XT>::YS;
-      const CT G1 = sm.G1[slot], G2 = sm.G2[slot];
+      const CT G1 = sm.G1[c], G2 = sm.G2[c];
       const CT pg = -(sm.th[c] - ldg_ct<CT>(a.mu_ct, c)) * ldg_ct<CT>(a.ivar_ct, c);
       sm.g[c] = ta * (bc + cd) + tnm * G1 - ta2 * (G2 - cdbar * G1) + pg;
     }
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   __syncwarp();
   refresh_delta(W, a, sm);
   CT sd = CT(0), sd2 = CT(0);
-  W.template rows<false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n, unew, 0, nb, a.fam,
+  W.template rows<false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.p, a.n, unew, 0, nb, a.fam,
                          (CT)a.inv_s2, nullptr, nullptr, sd, sd2, a.st);
   const double Sg = warp_sum((double)sd), Qg = warp_sum((double)sd2);
   double *blk = a.blk + (int64_t)i * a.G * 2;

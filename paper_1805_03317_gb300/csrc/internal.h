@@ -81,6 +81,16 @@ int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s);
 int est_tiles_f64(Tile *out, int cap);
 int est_tiles_f32(Tile *out, int cap);
 int est_tiles_bf16(Tile *out, int cap);
+// HMC trajectory with the subsample resident in shared memory (resident.cuh): one lane per row,
+// Tile.CPL covariate slots per lane, Tile.warps warps per CTA. Returns a cudaError_t, -1 for an
+// unknown tile, -2 when the plan does not fit (p > CPL or too much shared memory). dry: check
+// the fit only.
+int res_launch_f64(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
+int res_launch_f32(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
+int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
+int res_tiles_f64(Tile *out, int cap);
+int res_tiles_f32(Tile *out, int cap);
+int res_tiles_bf16(Tile *out, int cap);
 
 // Stage kernels (stage.cu). All return cudaError_t.
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,
@@ -97,6 +107,7 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
                    cudaStream_t s);
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
              int K, int rounds, DevState *st, double *partials, int *launches, cudaStream_t s);
+int reweight_scratch_doubles();
 int weighted_moments(int is_f64, int N, int p, const double *W, const void *theta,
                      double *partials, double *mean, double *Sigma, cudaStream_t s);
 int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double *chol,

@@ -1,0 +1,393 @@
+// HMC trajectory with the particle's subsample resident in shared memory (Algorithm 1 step 2).
+//
+// u is fixed for the whole trajectory, so the m rows x_{u_j} are gathered once per particle
+// (cp.async, 16-byte copies) and kept in shared memory; so are the trajectory-invariant per-row
+// control-variate constants (which depend on eta_bar_j and y_j only). The L + 1 estimator passes
+// then read shared memory: one lane per row, D_j = x_j'(theta - theta_bar) and the increment terms
+// d_j, r_j (device.cuh), gradient partials in registers, a shuffle reduce-scatter per warp and one
+// CTA barrier per pass (partials double-buffered). Every warp then assembles the totals and the
+// gradient and runs the leapfrog update itself, with theta, rho and the gradient held one column
+// per lane, so no warp waits for another between passes. One CTA handles one particle at a time
+// and loops over particles (persistent grid).
+#pragma once
+
+#include "estimator.cuh"
+
+namespace subsmc {
+
+// Shared-memory plan of one CTA.
+struct ResPlan {
+  int rb;    // bytes per resident row (covariates only): an odd multiple of 16 (conflict-free LDS.128)
+  int nvec;  // 16-byte vectors of covariates per row
+  int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, total;
+};
+
+inline __host__ __device__ int round16(int v) { return (v + 15) & ~15; }
+
+template <typename CT>
+inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
+  ResPlan P;
+  const int xb = round16(p * esz);
+  P.nvec = xb / 16;
+  P.rb = ((xb / 16) % 2 == 0) ? xb + 16 : xb;
+  int off = m * P.rb;
+  P.off_consts = off;
+  off = round16(off + m * (int)sizeof(RowC<CT>));
+  P.off_d = off;
+  off = round16(off + m * (int)sizeof(CT));
+  P.off_vec = off;  // initial momentum, theta_bar [cpl each]
+  off = round16(off + 2 * cpl * (int)sizeof(CT));
+  P.off_red = off;  // two buffers of [warps][2 cpl] gradient partials
+  off = round16(off + 2 * warps * 2 * cpl * (int)sizeof(CT));
+  P.off_redd = off;  // two buffers of [warps][2] sums of d, d^2
+  off = round16(off + 2 * warps * 2 * (int)sizeof(double));
+  P.off_blk = off;
+  off = round16(off + G * 2 * (int)sizeof(double));
+  P.off_mat = off;  // C and Sigma, zero-padded to [cpl, cpl], state type
+  off = round16(off + 2 * cpl * cpl * (int)sizeof(CT));
+  P.total = off;
+  return P;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Reduce-scatter of K values per lane over the 32 lanes of a warp (recursive halving, then a
+// butterfly once the count is odd). On return v[0..kfinal(K)) hold sums over all 32 lanes of the
+// original entries base + i.
+template <int K, int O, typename V>
+__device__ __forceinline__ void reduce_scatter(V *v, int lane, int &base) {
+  if constexpr (O > 0) {
+    if constexpr (K % 2 == 0) {
+      constexpr int H = K / 2;
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const V send = up ? v[i] : v[i + H];
+        const V keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += H;
+      reduce_scatter<H, O / 2, V>(v, lane, base);
+    } else {
+#pragma unroll
+      for (int i = 0; i < K; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], O);
+      reduce_scatter<K, O / 2, V>(v, lane, base);
+    }
+  }
+}
+template <int K, int O> __host__ __device__ constexpr int kfinal() {
+  if constexpr (O == 0)
+    return K;
+  else if constexpr (K % 2 == 0)
+    return kfinal<K / 2, O / 2>();
+  else
+    return kfinal<K, O / 2>();
+}
+
+template <typename XT, int CPL>
+__device__ __forceinline__ void load_res_row(const unsigned char *row,
+                                             typename Store<XT>::CT *x) {
+  using SD = Store<XT>;
+  constexpr int NV = CPL / SD::VEC;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const uint4 w = *reinterpret_cast<const uint4 *>(row + 16 * v);
+    SD::unpack(w, x + v * SD::VEC);
+  }
+}
+
+template <typename XT, int CPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
+  using SD = Store<XT>;
+  using CT = typename SD::CT;
+  using YT = typename SD::YT;
+  static_assert(CPL <= 32, "one column per lane");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p = a.p, m = a.m, G = a.G, S = a.S;
+  const XT *Xp = reinterpret_cast<const XT *>(a.Xp);
+  unsigned char *rows = smem;
+  RowC<CT> *cst = reinterpret_cast<RowC<CT> *>(smem + P.off_consts);
+  CT *dv = reinterpret_cast<CT *>(smem + P.off_d);
+  CT *rho0 = reinterpret_cast<CT *>(smem + P.off_vec);  // [CPL] initial momentum
+  CT *tbs = rho0 + CPL;                                  // [CPL] theta_bar, zero-padded
+  CT *red = reinterpret_cast<CT *>(smem + P.off_red);            // [2][WARPS][2*CPL]
+  double *redd = reinterpret_cast<double *>(smem + P.off_redd);  // [2][WARPS][2]
+  double *blks = reinterpret_cast<double *>(smem + P.off_blk);   // [G][2]
+  CT *Cs = reinterpret_cast<CT *>(smem + P.off_mat);  // [CPL, CPL] zero-padded
+  CT *Sgs = Cs + CPL * CPL;                            // [CPL, CPL] zero-padded
+  const double temp = a.st->a;
+  const CT eps = (CT)a.st->eps;
+  const CT inv_s2 = (CT)a.inv_s2;
+  const double nm = (double)a.n / (double)m, inv_m = 1.0 / (double)m;
+  const CT ta = (CT)temp, ta2 = (CT)(temp * temp * nm * nm), tnm = (CT)(temp * nm);
+  const uint32_t smv = stage_move(a.stage, a.move);
+  const int fam = a.fam;
+  const bool col = lane < p;
+  // per-lane column constants (lane c holds column c)
+  const CT Bc = col ? ldg_ct<CT>(a.B_ct, lane) : CT(0);
+  const CT muc = col ? ldg_ct<CT>(a.mu_ct, lane) : CT(0);
+  const CT ivc = col ? ldg_ct<CT>(a.ivar_ct, lane) : CT(0);
+  const CT tbc = col ? ldg_ct<CT>(a.tb_ct, lane) : CT(0);
+
+  for (int c = tid; c < CPL; c += blockDim.x) tbs[c] = c < p ? ldg_ct<CT>(a.tb_ct, c) : CT(0);
+  for (int e = tid; e < CPL * CPL; e += blockDim.x) {
+    const int r = e / CPL, c = e - r * CPL;
+    const bool in = r < p && c < p;
+    Cs[e] = in ? ldg_ct<CT>(a.C_ct, r * p + c) : CT(0);
+    Sgs[e] = in ? ldg_ct<CT>(a.Sigma_ct, r * p + c) : CT(0);
+  }
+
+  for (int i = blockIdx.x; i < a.B; i += gridDim.x) {
+    const int32_t *u = a.u + (int64_t)i * m;
+    __syncthreads();  // the previous particle is finished with shared memory
+    // 1. gather the covariates of x_{u_j} (16-byte copies), zero invalid rows
+    for (int t = tid; t < m * P.nvec; t += blockDim.x) {
+      const int j = t / P.nvec, q = t - j * P.nvec;
+      const int k = u[j];
+      unsigned char *dst = rows + (size_t)j * P.rb + 16 * q;
+      if (k < 0 || (int64_t)k >= a.n) {
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        if (q == 0) set_err(a.st, kErrIndex);
+        continue;
+      }
+      cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * q);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // slots p .. nvec*VEC-1 hold padding or the halves of y: zero them
+    const int pad = P.nvec * SD::VEC - p;
+    if (pad > 0) {
+      for (int t = tid; t < m * pad; t += blockDim.x) {
+        const int j = t / pad, s = p + (t - j * pad);
+        XT *row = reinterpret_cast<XT *>(rows + (size_t)j * P.rb);
+        row[s] = XT(0.0f);
+      }
+      __syncthreads();
+    }
+    // 2. trajectory-invariant per-row constants
+    for (int j = tid; j < m; j += blockDim.x) {
+      CT x[CPL];
+      load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
+      CT eb = CT(0);
+#pragma unroll
+      for (int s = 0; s < CPL; ++s) eb = fma(x[s], tbs[s], eb);
+      const int k = u[j];
+      const bool ok = k >= 0 && (int64_t)k < a.n;
+      const CT y = ok ? (CT)__ldg(reinterpret_cast<const YT *>(Xp + (int64_t)k * S + S - SD::YS))
+                      : CT(0);
+      RowC<CT> c;
+      switch (fam) {
+        case 0: c = row_consts<0, CT>(eb, y, inv_s2); break;
+        case 1: c = row_consts<1, CT>(eb, y, inv_s2); break;
+        case 2: c = row_consts<2, CT>(eb, y, inv_s2); break;
+        default: c = row_consts<3, CT>(eb, y, inv_s2); break;
+      }
+      cst[j] = c;
+    }
+    // 3. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
+    CT *thg = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
+    if (warp == 0) {
+      const Stream smom(a.seed, kMomentum, smv, (uint32_t)i);
+      CT z = col ? (CT)stream_normal(smom, (uint32_t)lane) : CT(0);
+      CT acc = CT(0);
+      for (int c = 0; c < p; ++c) {  // rho_r = sum_{c >= r} Linv[c, r] z_c
+        const CT zc = __shfl_sync(0xffffffffu, z, c);
+        if (col && c >= lane) acc = fma(ldg_ct<CT>(a.Linv_ct, c * p + lane), zc, acc);
+      }
+      if (lane < CPL) rho0[lane] = col ? acc : CT(0);
+    }
+    __syncthreads();
+    // every warp now carries the trajectory in its lanes: theta_c, rho_c, grad_c at lane c
+    CT th = col ? thg[lane] : CT(0);
+    CT rho = lane < CPL ? rho0[lane] : CT(0);
+    CT gr = CT(0);
+    CT dr[CPL];
+    auto set_delta = [&]() {
+      const CT dl = col ? th - tbc : CT(0);
+#pragma unroll
+      for (int s = 0; s < CPL; ++s) dr[s] = __shfl_sync(0xffffffffu, dl, s);
+    };
+    auto kinetic = [&]() -> double {  // rho' Sigma rho / 2 (every lane of the warp)
+      CT v = CT(0);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) v = fma(Sgs[k * CPL + (lane < CPL ? lane : 0)],
+                                            __shfl_sync(0xffffffffu, rho, k), v);
+      return 0.5 * warp_sum(col ? (double)rho * (double)v : 0.0);
+    };
+    auto log_prior = [&]() -> double {
+      const double rr = (double)th - (double)muc;
+      return warp_sum(col ? -0.5 * rr * rr * (double)ivc : 0.0) + a.log_prior_const;
+    };
+    set_delta();
+    double ell = 0.0, sig = 0.0;
+    int buf = 0;
+    // One estimator pass at the current delta (dr). Every warp ends with the gradient at its lanes
+    // and l_hat, sigma2_hat; FINAL also fills the block sums blks.
+    auto pass = [&](bool final) {
+      CT v[2 * CPL];
+#pragma unroll
+      for (int s = 0; s < 2 * CPL; ++s) v[s] = CT(0);
+      CT sd = CT(0), sd2 = CT(0);
+      for (int j = warp * 32 + lane; j < m; j += WARPS * 32) {
+        CT x[CPL];
+        load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
+        CT q0 = CT(0), q1 = CT(0), q2 = CT(0), q3 = CT(0);
+#pragma unroll
+        for (int s = 0; s < CPL; s += 4) {
+          q0 = fma(x[s], dr[s], q0);
+          if (s + 1 < CPL) q1 = fma(x[s + 1], dr[s + 1], q1);
+          if (s + 2 < CPL) q2 = fma(x[s + 2], dr[s + 2], q2);
+          if (s + 3 < CPL) q3 = fma(x[s + 3], dr[s + 3], q3);
+        }
+        const CT D = (q0 + q1) + (q2 + q3);
+        const RowC<CT> c = cst[j];
+        CT d, r;
+        switch (fam) {
+          case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
+          case 1: row_incr<1, CT>(c, D, inv_s2, d, r); break;
+          case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
+          default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
+        }
+        const CT drr = d * r;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+          v[s] = fma(r, x[s], v[s]);
+          v[CPL + s] = fma(drr, x[s], v[CPL + s]);
+        }
+        sd += d;
+        sd2 = fma(d, d, sd2);
+        if (final) dv[j] = d;
+      }
+      int base = 0;
+      reduce_scatter<2 * CPL, 16, CT>(v, lane, base);
+      constexpr int KF = kfinal<2 * CPL, 16>();
+      CT *rb = red + buf * WARPS * 2 * CPL;
+      double *rd = redd + buf * WARPS * 2;
+#pragma unroll
+      for (int q = 0; q < KF; ++q) rb[warp * 2 * CPL + base + q] = v[q];
+      const CT s1 = warp_sum(sd), s2 = warp_sum(sd2);
+      if (lane == 0) {
+        rd[2 * warp] = (double)s1;
+        rd[2 * warp + 1] = (double)s2;
+      }
+      __syncthreads();  // all warps' partial sums of this pass are in buffer buf
+      double S1 = 0.0, S2 = 0.0;
+      if (final) {  // block sums of d (floor partition of u into G blocks)
+        for (int g = warp; g < G; g += WARPS) {
+          const int j0 = (int)(((int64_t)g * m) / G), j1 = (int)(((int64_t)(g + 1) * m) / G);
+          CT bs = CT(0), bq = CT(0);
+          for (int j = j0 + lane; j < j1; j += 32) {
+            const CT dj = dv[j];
+            bs += dj;
+            bq = fma(dj, dj, bq);
+          }
+          bs = warp_sum(bs);
+          bq = warp_sum(bq);
+          if (lane == 0) {
+            blks[2 * g] = (double)bs;
+            blks[2 * g + 1] = (double)bq;
+          }
+        }
+        __syncthreads();
+        for (int g = 0; g < G; ++g) {
+          S1 += blks[2 * g];
+          S2 += blks[2 * g + 1];
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+          S1 += rd[2 * w];
+          S2 += rd[2 * w + 1];
+        }
+      }
+      // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at lane c; l_hat and sigma2_hat
+      const CT dbar = (CT)(S1 * inv_m);
+      CT G1 = CT(0), G2 = CT(0);
+      if (col) {
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+          G1 += rb[w * 2 * CPL + lane];
+          G2 += rb[w * 2 * CPL + CPL + lane];
+        }
+      }
+      CT cd = CT(0);
+      const int cl = lane < CPL ? lane : 0;
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) cd = fma(Cs[k * CPL + cl], dr[k], cd);
+      const CT dc = col ? th - tbc : CT(0);
+      const CT qlin = warp_sum(col ? dc * (Bc + CT(0.5) * cd) : CT(0));
+      gr = col ? ta * (Bc + cd) + tnm * G1 - ta2 * (G2 - dbar * G1) - (th - muc) * ivc : CT(0);
+      ell = a.A + (double)qlin + nm * S1;
+      sig = nm * nm * (S2 - S1 * S1 * inv_m);
+      buf ^= 1;
+    };
+
+    // 4. trajectory
+    const double kin0 = kinetic(), lp0 = log_prior();
+    pass(false);
+    const double H0 = -(temp * ell - 0.5 * temp * temp * sig + lp0) + kin0;
+    for (int l = 0; l < a.L; ++l) {
+      rho += CT(0.5) * eps * gr;
+      CT vs = CT(0);  // (Sigma rho)_c
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) vs = fma(Sgs[k * CPL + (lane < CPL ? lane : 0)],
+                                             __shfl_sync(0xffffffffu, rho, k), vs);
+      if (col) th += eps * vs;
+      set_delta();
+      pass(l == a.L - 1);
+      rho += CT(0.5) * eps * gr;
+    }
+    // 5. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
+    const double kin1 = kinetic(), lp1 = log_prior();
+    if (warp == 0) {
+      const double H1 = -(temp * ell - 0.5 * temp * temp * sig + lp1) + kin1;
+      const Stream smh(a.seed, kMhTheta, smv, (uint32_t)i);
+      const double Uu = draw_uniform(smh.draw(0));
+      const bool acc = log(Uu) < H0 - H1;  // false when H1 is NaN
+      if (acc) {
+        if (col) thg[lane] = th;
+        double *blk = a.blk + (int64_t)i * G * 2;
+        for (int h = lane; h < 2 * G; h += 32) blk[h] = blks[h];
+        if (lane == 0) {
+          a.ell[i] = ell;
+          a.sig2[i] = sig;
+          atomicAdd(&a.st->acc_theta, 1ull);
+        }
+      }
+    }
+  }
+}
+
+// dry: only check that the plan fits (no launch).
+template <typename XT, int CPL, int WARPS>
+inline int launch_res(const EstArgs &a, cudaStream_t s, int sms, bool dry) {
+  using CT = typename Store<XT>::CT;
+  if (a.p > CPL) return -2;
+  const ResPlan P = res_plan<CT>(a.p, a.m, a.G, (int)sizeof(XT), WARPS, CPL);
+  cudaError_t e = cudaFuncSetAttribute(k_hmc_res<XT, CPL, WARPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, P.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hmc_res<XT, CPL, WARPS>,
+                                                    WARPS * 32, P.total);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return -2;
+  }
+  if (dry || a.B <= 0) return 0;
+  const int grid = a.B < per_sm * sms ? a.B : per_sm * sms;
+  k_hmc_res<XT, CPL, WARPS><<<grid, WARPS * 32, P.total, s>>>(a, P);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace subsmc

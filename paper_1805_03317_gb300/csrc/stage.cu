@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -26,61 +28,6 @@ __device__ double block_sum(double v, double *red) {
   return t;
 }
 
-// (max, s1, s2) triples of an online log-sum-exp of x and 2x: s1 = sum e^{x-max}, s2 = sum e^{2(x-max)}.
-struct Lse {
-  double m, s1, s2;
-  __device__ __forceinline__ Lse() : m(-INFINITY), s1(0.0), s2(0.0) {}
-  __device__ __forceinline__ void add(double x) {
-    if (!(x > -INFINITY)) return;  // zero weight (or NaN: flagged by the caller)
-    if (x > m) {
-      const double r = exp(m - x);
-      s1 = s1 * r + 1.0;
-      s2 = s2 * r * r + 1.0;
-      m = x;
-    } else {
-      const double e = exp(x - m);
-      s1 += e;
-      s2 += e * e;
-    }
-  }
-  __device__ __forceinline__ void merge(const Lse &o) {
-    if (!(o.m > -INFINITY)) return;
-    if (!(m > -INFINITY)) {
-      *this = o;
-      return;
-    }
-    if (o.m > m) {
-      const double r = exp(m - o.m);
-      s1 = s1 * r + o.s1;
-      s2 = s2 * r * r + o.s2;
-      m = o.m;
-    } else {
-      const double r = exp(o.m - m);
-      s1 += o.s1 * r;
-      s2 += o.s2 * r * r;
-    }
-  }
-  __device__ __forceinline__ Lse shfl_xor(int o) const {
-    Lse t;
-    t.m = __shfl_xor_sync(0xffffffffu, m, o);
-    t.s1 = __shfl_xor_sync(0xffffffffu, s1, o);
-    t.s2 = __shfl_xor_sync(0xffffffffu, s2, o);
-    return t;
-  }
-};
-
-__device__ Lse block_lse(Lse v, Lse *red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v.merge(v.shfl_xor(o));
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  Lse t;
-  for (int k = 0; k < nw; ++k) t.merge(red[k]);
-  return t;
-}
-
 template <typename CT> __device__ __forceinline__ double ld_state(const void *p, int64_t i) {
   return (double)reinterpret_cast<const CT *>(p)[i];
 }
@@ -88,8 +35,8 @@ template <typename CT> __device__ __forceinline__ double ld_state(const void *p,
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
-// Packing: row k of Xp = [y_k | x_k | 0 ...], stride S elements. y is stored in the first 8 (FP64)
-// or 4 (otherwise) bytes of the row.
+// Packing: row k of Xp = [x_k | 0 ... | y_k], stride S elements; y occupies the last 8 (FP64) or 4
+// (otherwise) bytes of the row.
 // ------------------------------------------------------------------------------------------------
 template <typename E, typename YT>
 __global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E *Xp, int S) {
@@ -100,11 +47,11 @@ __global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E 
     const int64_t k = t / S;
     const int s = (int)(t - k * S);
     E v;
-    if (s < YS) {
+    if (s >= S - YS) {
       const YT yk = y[k];
-      v = reinterpret_cast<const E *>(&yk)[s];
-    } else if (s - YS < p) {
-      v = X[k * ld + (s - YS)];
+      v = reinterpret_cast<const E *>(&yk)[s - (S - YS)];
+    } else if (s < p) {
+      v = X[k * ld + s];
     } else {
       v = E(0);
     }
@@ -129,9 +76,12 @@ int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const vo
 }
 
 // ------------------------------------------------------------------------------------------------
-// Control-variate moments at theta (Sec. 3.2), FP64: A = sum_k l_k, B = sum_k l'_k x_k,
-// C = sum_k l''_k x_k x_k'. Each block takes tiles of 32 rows; its threads own fixed (r, c) pairs
-// of the upper triangle. Block partials are summed in block order by a second kernel.
+// Control-variate moments at theta (Sec. 3.2): A = sum_k l_k, B = sum_k l'_k x_k,
+// C = sum_k l''_k x_k x_k'. Rows go through shared memory in tiles of 32: one lane per row forms
+// eta_bar in FP64 and evaluates the family terms in FP64; the tile's contributions to C are
+// accumulated in AT (FP64 for FP64 storage, FP32 otherwise: products of stored FP32/BF16 values) and
+// added to per-thread FP64 accumulators once per tile; A and B stay FP64 throughout. Each thread
+// owns fixed (r, c) pairs of the upper triangle; block partials are summed in block order.
 // ------------------------------------------------------------------------------------------------
 constexpr int kCvThreads = 256, kCvTile = 32, kCvMaxPairs = 32;
 
@@ -147,29 +97,30 @@ template <>
 __device__ __forceinline__ double packed_x<__nv_bfloat16>(const __nv_bfloat16 *row, int slot) {
   return (double)__bfloat162float(row[slot]);
 }
-template <typename XT> __device__ __forceinline__ double packed_y(const XT *row) {
-  if (sizeof(XT) == 8) return *reinterpret_cast<const double *>(row);
-  return (double)*reinterpret_cast<const float *>(row);
+template <typename XT> __device__ __forceinline__ double packed_y(const XT *row, int S) {
+  if (sizeof(XT) == 8) return *reinterpret_cast<const double *>(row + S - 1);
+  return (double)*reinterpret_cast<const float *>(row + S - 4 / (int)sizeof(XT));
 }
 
-template <typename XT>
+template <typename XT, int MAXQ>
 __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_t n, int p, int S,
                                                             int fam, double s2,
                                                             const double *theta, double *part) {
-  constexpr int YS = sizeof(XT) == 8 ? 1 : 4 / (int)sizeof(XT);
+  using AT = typename std::conditional<sizeof(XT) == 8, double, float>::type;
   extern __shared__ double sh[];
-  double *xs = sh;                    // [kCvTile][p]
-  double *wx = xs + kCvTile * p;      // [kCvTile][p]   l'' * x
-  double *d1s = wx + kCvTile * p;     // [kCvTile]
-  double *ths = d1s + kCvTile;        // [p]
-  double *red = ths + p;              // [32]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double *ths = sh;                                   // [p]
+  double *d1s = ths + p;                              // [kCvTile]
+  double *red = d1s + kCvTile;                        // [32]
+  AT *xs = reinterpret_cast<AT *>(red + 32);          // [kCvTile][p]
+  AT *wx = xs + kCvTile * p;                          // [kCvTile][p]   l'' * x
+  AT *d2s = wx + kCvTile * p;                         // [kCvTile]
+  const int tid = threadIdx.x;
   const int np = p * (p + 1) / 2;
   for (int c = tid; c < p; c += blockDim.x) ths[c] = theta[c];
-  int qr[kCvMaxPairs], qc[kCvMaxPairs];
-  double acc[kCvMaxPairs];
+  int qr[MAXQ], qc[MAXQ];
+  double acc[MAXQ];
 #pragma unroll
-  for (int i = 0; i < kCvMaxPairs; ++i) {
+  for (int i = 0; i < MAXQ; ++i) {
     const int q = tid + i * kCvThreads;
     int r = 0, c = 0;
     if (q < np) {  // row-major enumeration of the upper triangle
@@ -189,23 +140,21 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
   const int64_t ntiles = (n + kCvTile - 1) / kCvTile;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t k0 = tile * kCvTile;
-    for (int rr = warp; rr < kCvTile; rr += kCvThreads / 32) {
+    // stage the tile's covariates (row-major over the tile)
+    for (int e = tid; e < kCvTile * p; e += blockDim.x) {
+      const int rr = e / p, c = e - rr * p;
       const int64_t k = k0 + rr;
-      double eta = 0.0;
-      if (k < n) {
-        const XT *row = Xp + k * S;
-        for (int c = lane; c < p; c += 32) {
-          const double x = packed_x<XT>(row, YS + c);
-          xs[rr * p + c] = x;
-          eta += x * ths[c];
-        }
-      } else {
-        for (int c = lane; c < p; c += 32) xs[rr * p + c] = 0.0;
-      }
-      eta = warp_sum_d(eta);
+      xs[e] = k < n ? (AT)packed_x<XT>(Xp + k * S, c) : AT(0);
+    }
+    __syncthreads();
+    // one lane per row: eta_bar and the family terms in FP64
+    if (tid < kCvTile) {
+      const int64_t k = k0 + tid;
       double l = 0.0, d1 = 0.0, d2 = 0.0;
       if (k < n) {
-        const double y = packed_y<XT>(Xp + k * S);
+        double eta = 0.0;
+        for (int c = 0; c < p; ++c) eta = fma((double)xs[tid * p + c], ths[c], eta);
+        const double y = packed_y<XT>(Xp + k * S, S);
         switch (fam) {
           case 0: row_value<0>(eta, y, s2, l, d1, d2); break;
           case 1: row_value<1>(eta, y, s2, l, d1, d2); break;
@@ -213,20 +162,24 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
           default: row_value<3>(eta, y, s2, l, d1, d2); break;
         }
       }
-      if (lane == 0) {
-        d1s[rr] = d1;
-        Aacc += l;
-      }
-      __syncwarp();
-      for (int c = lane; c < p; c += 32) wx[rr * p + c] = d2 * xs[rr * p + c];
+      d1s[tid] = d1;
+      d2s[tid] = (AT)d2;
+      Aacc += l;
     }
     __syncthreads();
-    for (int rr = 0; rr < kCvTile; ++rr) {
+    for (int e = tid; e < kCvTile * p; e += blockDim.x) wx[e] = d2s[e / p] * xs[e];
+    __syncthreads();
 #pragma unroll
-      for (int i = 0; i < kCvMaxPairs; ++i)
-        if (tid + i * kCvThreads < np) acc[i] = fma(wx[rr * p + qr[i]], xs[rr * p + qc[i]], acc[i]);
-      if (tid < p) Bacc = fma(d1s[rr], xs[rr * p + tid], Bacc);
+    for (int i = 0; i < MAXQ; ++i) {
+      if (tid + i * kCvThreads < np) {
+        AT t = AT(0);
+#pragma unroll 8
+        for (int rr = 0; rr < kCvTile; ++rr) t = fma(wx[rr * p + qr[i]], xs[rr * p + qc[i]], t);
+        acc[i] += (double)t;
+      }
     }
+    if (tid < p)
+      for (int rr = 0; rr < kCvTile; ++rr) Bacc = fma(d1s[rr], (double)xs[rr * p + tid], Bacc);
     __syncthreads();
   }
   double *out = part + (int64_t)blockIdx.x * (1 + p + np);
@@ -234,7 +187,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
   if (tid == 0) out[0] = A;
   if (tid < p) out[1 + tid] = Bacc;
 #pragma unroll
-  for (int i = 0; i < kCvMaxPairs; ++i) {
+  for (int i = 0; i < MAXQ; ++i) {
     const int q = tid + i * kCvThreads;
     if (q < np) out[1 + p + q] = acc[i];
   }
@@ -242,9 +195,13 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
 
 __global__ void k_cv_reduce(const double *part, int nblk, int p, double *A, double *B, double *C) {
   const int np = p * (p + 1) / 2, width = 1 + p + np;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * width + e];
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < width; e += warps) {
+    double s = 0.0;  // lanes over blocks, then a fixed warp tree: deterministic
+    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * width + e];
+    s = warp_sum(s);
+    if (lane != 0) continue;
     if (e == 0) {
       *A = s;
     } else if (e <= p) {
@@ -262,6 +219,28 @@ __global__ void k_cv_reduce(const double *part, int nblk, int p, double *A, doub
   }
 }
 
+template <typename XT, int MAXQ>
+cudaError_t launch_cv_q(int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n, int p,
+                        int S, int fam, double s2, const double *theta, double *part) {
+  cudaError_t e = cudaFuncSetAttribute(k_cv_partials<XT, MAXQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_cv_partials<XT, MAXQ><<<nblocks, kCvThreads, smem, s>>>(Xp, n, p, S, fam, s2, theta, part);
+  return cudaGetLastError();
+}
+
+// Pair slots per thread: the smallest compiled count that covers p(p+1)/2 pairs.
+template <typename XT>
+cudaError_t launch_cv(int need, int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n,
+                      int p, int S, int fam, double s2, const double *theta, double *part) {
+  if (need <= 1) return launch_cv_q<XT, 1>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+  if (need <= 2) return launch_cv_q<XT, 2>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+  if (need <= 4) return launch_cv_q<XT, 4>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+  if (need <= 8) return launch_cv_q<XT, 8>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+  if (need <= 16) return launch_cv_q<XT, 16>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+  return launch_cv_q<XT, 32>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+}
+
 int cv_moments_blocks(int p) {
   (void)p;
   return 2 * 152;
@@ -271,27 +250,22 @@ int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int fam, do
                const double *theta, double *partials, int nblocks, double *A, double *B,
                double *C, cudaStream_t s) {
   if (p * (p + 1) / 2 > kCvThreads * kCvMaxPairs) return (int)cudaErrorInvalidValue;
-  const size_t smem = (size_t)(2 * kCvTile * p + kCvTile + p + 32) * sizeof(double);
+  const size_t at = x_dtype == 0 ? sizeof(double) : sizeof(float);
+  const size_t smem = (size_t)(p + kCvTile + 32) * sizeof(double) + (2 * kCvTile * p + kCvTile) * at;
+  const int np = p * (p + 1) / 2, need = (np + kCvThreads - 1) / kCvThreads;
   cudaError_t e;
-  if (x_dtype == 0) {
-    e = cudaFuncSetAttribute(k_cv_partials<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    k_cv_partials<double><<<nblocks, kCvThreads, smem, s>>>((const double *)Xp, n, p, S, fam,
-                                                            sigma2, theta, partials);
-  } else if (x_dtype == 1) {
-    e = cudaFuncSetAttribute(k_cv_partials<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    k_cv_partials<float><<<nblocks, kCvThreads, smem, s>>>((const float *)Xp, n, p, S, fam,
-                                                           sigma2, theta, partials);
-  } else {
-    e = cudaFuncSetAttribute(k_cv_partials<__nv_bfloat16>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cv_partials<__nv_bfloat16><<<nblocks, kCvThreads, smem, s>>>(
-        (const __nv_bfloat16 *)Xp, n, p, S, fam, sigma2, theta, partials);
-  }
+  if (x_dtype == 0)
+    e = launch_cv<double>(need, nblocks, smem, s, (const double *)Xp, n, p, S, fam, sigma2, theta,
+                          partials);
+  else if (x_dtype == 1)
+    e = launch_cv<float>(need, nblocks, smem, s, (const float *)Xp, n, p, S, fam, sigma2, theta,
+                         partials);
+  else
+    e = launch_cv<__nv_bfloat16>(need, nblocks, smem, s, (const __nv_bfloat16 *)Xp, n, p, S, fam,
+                                 sigma2, theta, partials);
   if (e != cudaSuccess) return (int)e;
   const int width = 1 + p + p * (p + 1) / 2;
-  k_cv_reduce<<<(width + 255) / 256, 256, 0, s>>>(partials, nblocks, p, A, B, C);
+  k_cv_reduce<<<(width + 7) / 8, 256, 0, s>>>(partials, nblocks, p, A, B, C);
   return (int)cudaGetLastError();
 }
 
@@ -431,40 +405,114 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 // evaluates the K-1 interior points of the bracket and keeps the first sub-interval whose right end
 // has ESS < tau N. Partials of every block are merged in block order by the last block to finish.
 // ------------------------------------------------------------------------------------------------
-constexpr int kRwThreads = 128, kMaxK = 32;
+constexpr int kRwThreads = 32, kMaxK = 32, kRwMaxBlocks = 152;  // one warp per block
 
-__device__ __forceinline__ double lw_at(double logW, double ell, double sig2, double a, double D) {
-  return logW + D * ell - 0.5 * ((a + D) * (a + D) - a * a) * sig2;
+// Candidates of a search round: round -1 tests D = 1 - a alone; later rounds the K - 1 interior
+// points lo + (hi - lo) k / K of the bracket.
+__device__ __forceinline__ int candidates(const DevState *st, int K, int round, double &lo,
+                                          double &hi) {
+  lo = round < 0 ? 0.0 : st->lo;
+  hi = round < 0 ? st->dmax : st->hi;
+  return round < 0 ? 1 : K - 1;
+}
+__device__ __forceinline__ double candidate(int round, double lo, double hi, int K, int k) {
+  return round < 0 ? hi : lo + (hi - lo) * (k + 1) / K;
 }
 
+// Per-block table of the round's candidates: D_k and h_k = ((a + D_k)^2 - a^2) / 2, so that
+// lw_i(D_k) = log W_i + D_k l_hat_i - h_k sigma2_hat_i.
+__device__ __forceinline__ int load_candidates(const DevState *st, int K, int round, double *Dk,
+                                               double *hk, double &lo, double &hi) {
+  const int ncand = candidates(st, K, round, lo, hi);
+  const double a = st->a;
+  for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+    const double D = candidate(round, lo, hi, K, k);
+    Dk[k] = D;
+    hk[k] = 0.5 * ((a + D) * (a + D) - a * a);
+  }
+  __syncwarp();
+  return ncand;
+}
+
+// Phase 1 of a round: the maximum of lw_i(D_k) over all particles, per candidate.
 __global__ void __launch_bounds__(kRwThreads)
-    k_search_round(int N, const double *ell, const double *sig2, const double *logW, double tau,
-                   int K, int round, int last_round, DevState *st, Lse *part) {
-  __shared__ Lse red[kRwThreads / 32];
+    k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
+                 int round, DevState *st, double *pmax, double *gmax) {
+  __shared__ double Dk[kMaxK], hk[kMaxK];
   __shared__ bool is_last;
   if (st->search_done) return;  // uniform across the grid
-  const double a = st->a;
-  const double lo = round < 0 ? 0.0 : st->lo, hi = round < 0 ? st->dmax : st->hi;
-  const int ncand = round < 0 ? 1 : K - 1;
+  double lo, hi;
+  const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
+  const int stride = gridDim.x * blockDim.x;
   for (int k = 0; k < ncand; ++k) {
-    const double D = round < 0 ? hi : lo + (hi - lo) * (k + 1) / K;
-    Lse acc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-      acc.add(lw_at(logW[i], ell[i], sig2[i], a, D));
-    acc = block_lse(acc, red);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxK + k] = acc;
+    const double D = Dk[k], h = hk[k];
+    double mx = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+      mx = fmax(mx, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
+    mx = warp_max(mx);
+    if (threadIdx.x == 0) pmax[blockIdx.x * kMaxK + k] = mx;
   }
   __threadfence();
   if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
+  __syncwarp();
   if (!is_last) return;
-  __shared__ double ess_k[kMaxK];
-  if (threadIdx.x < ncand) {  // one thread per candidate merges the block partials in order
-    Lse t;
-    for (int b = 0; b < (int)gridDim.x; ++b) t.merge(part[(int64_t)b * kMaxK + threadIdx.x]);
-    ess_k[threadIdx.x] = t.s1 * t.s1 / t.s2;
+  __threadfence();
+  for (int k = 0; k < ncand; ++k) {  // lanes over blocks
+    double M = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) M = fmax(M, pmax[b * kMaxK + k]);
+    M = warp_max(M);
+    if (threadIdx.x == 0) gmax[k] = M;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) st->ticket = 0;
+}
+
+// Phase 2: s1 = sum e^{lw - M}, s2 = sum e^{2(lw - M)} (one exponential per particle and
+// candidate), ESS = s1^2 / s2; the last block sums the block partials in block order (lanes over
+// blocks, fixed tree) and updates the bracket: the first sub-interval whose right end has
+// ESS < tau N.
+__global__ void __launch_bounds__(kRwThreads)
+    k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
+                 int K, int round, int last_round, DevState *st, const double *gmax,
+                 double *psum) {
+  __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK];
+  __shared__ bool is_last;
+  if (st->search_done) return;
+  double lo, hi;
+  const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
+  const int stride = gridDim.x * blockDim.x;
+  for (int k = 0; k < ncand; ++k) {
+    const double D = Dk[k], h = hk[k], M = gmax[k];
+    double s1 = 0.0, s2 = 0.0;
+    if (M > -INFINITY) {
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M);
+        s1 += e;
+        s2 = fma(e, e, s2);
+      }
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (threadIdx.x == 0) {
+      psum[2 * (blockIdx.x * kMaxK + k)] = s1;
+      psum[2 * (blockIdx.x * kMaxK + k) + 1] = s2;
+    }
+  }
+  __threadfence();
+  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  __syncwarp();
+  if (!is_last) return;
+  __threadfence();
+  for (int k = 0; k < ncand; ++k) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+      s1 += psum[2 * (b * kMaxK + k)];
+      s2 += psum[2 * (b * kMaxK + k) + 1];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (threadIdx.x == 0) ess_k[k] = s1 * s1 / s2;
+  }
+  __syncwarp();
   if (threadIdx.x != 0) return;
   const double target = tau * (double)N;
   int first = ncand + 1;  // 1-based index of the first candidate with ESS < target
@@ -497,42 +545,77 @@ __global__ void __launch_bounds__(kRwThreads)
   st->ticket = 0;
 }
 
-// Final pass: log-sum-exps of the new and old log weights, ESS, log Z increment (Sec. 3.5).
+// Final reweighting: log-sum-exps of the new (x = lw(D)) and old (x = log W) log weights, the
+// ESS at D and the log Z increment (Sec. 3.5). Same two phases; index 0 = new, 1 = old.
 __global__ void __launch_bounds__(kRwThreads)
-    k_reweight_final(int N, const double *ell, const double *sig2, const double *logW,
-                     DevState *st, Lse *part) {
-  __shared__ Lse red[kRwThreads / 32];
+    k_final_max(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                double *pmax, double *gmax) {
   __shared__ bool is_last;
-  const double a = st->a, D = st->D;
-  Lse nw, ow;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    nw.add(lw_at(logW[i], ell[i], sig2[i], a, D));
-    ow.add(logW[i]);
+  const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
+  const int stride = gridDim.x * blockDim.x;
+  double m0 = -INFINITY, m1 = -INFINITY;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
+    m1 = fmax(m1, logW[i]);
   }
-  nw = block_lse(nw, red);
-  ow = block_lse(ow, red);
+  m0 = warp_max(m0);
+  m1 = warp_max(m1);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = nw;
-    part[2 * blockIdx.x + 1] = ow;
+    pmax[2 * blockIdx.x] = m0;
+    pmax[2 * blockIdx.x + 1] = m1;
   }
   __threadfence();
   if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
+  __syncwarp();
   if (!is_last) return;
   __threadfence();
-  __shared__ Lse tot[2];
-  if (threadIdx.x < 2) {
-    Lse t;
-    for (int b = 0; b < (int)gridDim.x; ++b) t.merge(part[2 * b + threadIdx.x]);
-    tot[threadIdx.x] = t;
+  for (int k = 0; k < 2; ++k) {
+    double M = -INFINITY;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) M = fmax(M, pmax[2 * b + k]);
+    M = warp_max(M);
+    if (threadIdx.x == 0) gmax[k] = M;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) st->ticket = 0;
+}
+
+__global__ void __launch_bounds__(kRwThreads)
+    k_final_sum(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                const double *gmax, double *psum) {
+  __shared__ bool is_last;
+  const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
+  const double M0 = gmax[0], M1 = gmax[1];
+  const int stride = gridDim.x * blockDim.x;
+  double s1 = 0.0, s2 = 0.0, so = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M0);
+    s1 += e;
+    s2 = fma(e, e, s2);
+    so += exp(logW[i] - M1);
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  so = warp_sum(so);
+  if (threadIdx.x == 0) {
+    psum[3 * blockIdx.x] = s1;
+    psum[3 * blockIdx.x + 1] = s2;
+    psum[3 * blockIdx.x + 2] = so;
+  }
+  __threadfence();
+  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  __syncwarp();
+  if (!is_last) return;
+  __threadfence();
+  double tot[3];
+  for (int k = 0; k < 3; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += psum[3 * b + k];
+    tot[k] = warp_sum(t);
+  }
   if (threadIdx.x != 0) return;
-  const Lse tn = tot[0], to = tot[1];
-  const double lse_new = tn.m + log(tn.s1), lse_old = to.m + log(to.s1);
+  const double lse_new = M0 + log(tot[0]), lse_old = M1 + log(tot[2]);
   st->lse_new = lse_new;
   st->lse_old = lse_old;
-  st->ess = tn.s1 * tn.s1 / tn.s2;
+  st->ess = tot[0] * tot[0] / tot[1];
   st->log_z_inc = lse_new - lse_old;
   st->log_z += st->log_z_inc;
   st->a_prev = a;
@@ -544,8 +627,9 @@ __global__ void __launch_bounds__(kRwThreads)
 __global__ void k_normalise(int N, const double *ell, const double *sig2, double *logW, double *W,
                             const DevState *st) {
   const double a = st->a_prev, D = st->D, lse = st->lse_new;
+  const double h = 0.5 * ((a + D) * (a + D) - a * a);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double l = lw_at(logW[i], ell[i], sig2[i], a, D) - lse;
+    const double l = fma(-h, sig2[i], fma(D, ell[i], logW[i])) - lse;
     logW[i] = l;
     W[i] = exp(l);
   }
@@ -564,21 +648,29 @@ int reweight(int N, const double *ell, const double *sig2, double *logW, double 
              int K, int rounds, DevState *st, double *partials, int *launches, cudaStream_t s) {
   if (K < 2 || K > kMaxK) return (int)cudaErrorInvalidValue;
   int nb = (N + kRwThreads - 1) / kRwThreads;
-  if (nb > 64) nb = 64;
-  Lse *part = reinterpret_cast<Lse *>(partials);
+  if (nb > kRwMaxBlocks) nb = kRwMaxBlocks;
+  double *gmax = partials;                  // [kMaxK]
+  double *pmax = gmax + kMaxK;              // [nb][kMaxK]
+  double *psum = pmax + kRwMaxBlocks * kMaxK;  // [nb][kMaxK][2]
   int count = 0;
   k_search_begin<<<1, 1, 0, s>>>(st);
   ++count;
   for (int r = -1; r < rounds; ++r) {
-    k_search_round<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1, st, part);
-    ++count;
+    k_search_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, K, r, st, pmax, gmax);
+    k_search_sum<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1, st, gmax,
+                                           psum);
+    count += 2;
   }
-  k_reweight_final<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, part);
+  k_final_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, pmax, gmax);
+  k_final_sum<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, gmax, psum);
   k_normalise<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, W, st);
-  count += 2;
+  count += 3;
   if (launches) *launches += count;
   return (int)cudaGetLastError();
 }
+
+// Doubles of scratch the temperature search needs.
+int reweight_scratch_doubles() { return kMaxK + kRwMaxBlocks * kMaxK * 3; }
 
 // ------------------------------------------------------------------------------------------------
 // Weighted particle moments (Algorithm 2 (d)): mean = sum W_i theta_i, then
@@ -596,12 +688,16 @@ __global__ void k_mean_partials(int N, int p, const double *W, const CT *theta, 
 }
 __global__ void k_sum_partials(const double *part, int nblk, int width, double *out,
                                int symmetric_p) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < width; e += warps) {
+    if (symmetric_p && e % symmetric_p < e / symmetric_p) continue;  // lower triangle: mirrored
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * width + e];
+    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * width + e];
+    s = warp_sum(s);
+    if (lane != 0) continue;
     if (symmetric_p) {
       const int r = e / symmetric_p, c = e % symmetric_p;
-      if (c < r) continue;
       out[r * symmetric_p + c] = s;
       out[c * symmetric_p + r] = s;
     } else {
@@ -632,14 +728,14 @@ int weighted_moments(int is_f64, int N, int p, const double *W, const void *thet
     k_mean_partials<double><<<nb, 128, 0, s>>>(N, p, W, (const double *)theta, partials);
   else
     k_mean_partials<float><<<nb, 128, 0, s>>>(N, p, W, (const float *)theta, partials);
-  k_sum_partials<<<1, 128, 0, s>>>(partials, nb, p, mean, 0);
+  k_sum_partials<<<(p + 7) / 8, 256, 0, s>>>(partials, nb, p, mean, 0);
   if (is_f64)
     k_cov_partials<double><<<nb, kMomThreads, 0, s>>>(N, p, W, (const double *)theta, mean,
                                                       partials);
   else
     k_cov_partials<float><<<nb, kMomThreads, 0, s>>>(N, p, W, (const float *)theta, mean,
                                                      partials);
-  k_sum_partials<<<(p * p + 255) / 256, 256, 0, s>>>(partials, nb, p * p, Sigma, p);
+  k_sum_partials<<<(p * p + 7) / 8, 256, 0, s>>>(partials, nb, p * p, Sigma, p);
   return (int)cudaGetLastError();
 }
 
