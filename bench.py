@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 R_MOVES = 5
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 80.6: SMs x FP32 lanes x FMA x max SM clock
 
 
 def parse():
@@ -43,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--no-gather", action="store_true",
+                    help="skip the HBM-bound gather leg (Poisson n=5e6, p=50)")
+    ap.add_argument("--gather-only", action="store_true",
+                    help="run only the HBM-bound gather leg and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -204,6 +209,58 @@ def full_run(S, wl, dev, R, max_stages=400):
             "post_mean_minus_mode_maxabs": float(np.max(np.abs(mean - tb)))}
 
 
+def gather_leg(S, dev, hbm, reps=20, stages=3):
+    """HBM-bound leg: Poisson regression, n = 5e6, p = 50, BF16 X (560 MB packed, far above L2),
+    N = 8192, m = 2000. Times the subsampled estimator with gradient over all particles (one gather
+    of N*m rows per call, the streamed kernel) and a few full SMC stages, whose 112 KB x 2000 rows
+    per particle do not fit in shared memory (streamed HMC kernel)."""
+    import torch
+    from smc_workloads import poisson_5e6
+    wl = poisson_5e6("bf16", upcast=False)
+    X, y = device_workload(wl, dev)
+    ctx = S.smc_init(X, y, "poisson", wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
+                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None)
+    del X, y
+    tile = S.smc_autotune(ctx)
+    theta, u, _ = S.smc_get_particles(ctx)
+    for _ in range(3):
+        S.loglik_grad(ctx, theta, u, 1.0)
+    S.smc_profile_enable(ctx, True)
+    S.smc_profile_read(ctx, "estimate")
+    for _ in range(reps):
+        S.loglik_grad(ctx, theta, u, 1.0)
+    n_e, ms_e = S.smc_profile_read(ctx, "estimate")
+    bytes_row = wl.p * 2 + 4 + 4
+    bytes_call = wl.N * wl.m * bytes_row
+    per_call = ms_e / max(n_e, 1)
+    for g in S.smc.PROFILE_GROUPS:
+        S.smc_profile_read(ctx, g)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(stages)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(stages)]
+    for k in range(stages):
+        starts[k].record()
+        run_stage(S, ctx, wl.R)
+        ends[k].record()
+    torch.cuda.synchronize()
+    ms_stage = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / stages
+    n_h, ms_h = S.smc_profile_read(ctx, "hmc")
+    S.smc_profile_enable(ctx, False)
+    S.smc_free(ctx)
+    achieved = bytes_call / (per_call / 1e3) / 1e9
+    hmc_bytes = (wl.L + 1) * bytes_call
+    return {"workload": f"poisson n={wl.n} p={wl.p} N={wl.N} m={wl.m} G={wl.G} L={wl.L} "
+                        f"R={wl.R} X=bf16 (packed X 560 MB > L2)",
+            "tile": tile,
+            "estimator": {"kernel": "k_estimate (loglik_grad over all particles)",
+                          "ms_per_call": per_call, "bytes_per_call": bytes_call,
+                          "achieved_gbs": achieved, "frac_of_hbm": achieved / hbm,
+                          "grad_evals_per_s": wl.N * wl.m / (per_call / 1e3)},
+            "stage": {"ms_per_stage": ms_stage,
+                      "grad_evals_per_s": wl.N * wl.m * wl.R * (wl.L + 1) / (ms_stage / 1e3),
+                      "hmc_ms_per_launch": ms_h / max(n_h, 1),
+                      "hmc_achieved_gbs": hmc_bytes / (ms_h / max(n_h, 1) / 1e3) / 1e9}}
+
+
 def e2e_stages(S, ctx, wl, R, steps):
     """Same stages through the public API with the particle state resident on the host: each step
     copies theta, u, W in from pinned host memory and the new cloud back out."""
@@ -249,13 +306,19 @@ def gpu_arm(args):
     per_stage = grad_evals_per_stage(wl, R)
     value = per_stage * args.steps * world / (ms / 1e3)
 
-    # roofline of the dominant kernel (the HMC trajectory): algorithmic bytes per row are the
-    # gathered covariates, the row index and the response
+    # roofline of the dominant kernel, the HMC trajectory with the subsample resident in shared
+    # memory. It reads X once per trajectory and then runs L+1 estimator passes out of shared
+    # memory, so it is bound by the FP32/integer issue rate, not by HBM: bound "alu" against the
+    # FP32 peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz. Algorithmic FLOPs per particle-row
+    # evaluation: 2p (x'delta) + 4p (gradient partials) + 20 (increment terms d, r).
     hbm, peak_kind = peaks()
     n_h, ms_h = prof["hmc"]
+    units = (wl.L + 1) * wl.N * wl.m
+    flops_launch = units * (6 * wl.p + 20)
+    sec = ms_h / max(n_h, 1) / 1e3
+    achieved = flops_launch / sec / 1e12 if n_h else None
     bytes_row = wl.p * 2 + 4 + 4
-    bytes_launch = (wl.L + 1) * wl.N * wl.m * bytes_row
-    achieved = bytes_launch / (ms_h / n_h / 1e3) / 1e9 if n_h else None
+    bytes_launch = units * bytes_row
     shares = {g: round(v[1] / ms, 4) for g, v in prof.items() if v[0]}
 
     e2e_wall, bi, bo = e2e_stages(S, ctx, wl, R, max(3, min(args.steps, 20)))
@@ -274,6 +337,10 @@ def gpu_arm(args):
                 "hmc_ms_per_launch": t32 / max(n32, 1), "tile": tile32}
         walls = {"bf16": full_run(S, wl, dev, R), "fp32": full_run(S, wl32, dev, R)}
         del wl32
+
+    gather = None
+    if not args.no_gather and rank == 0:
+        gather = gather_leg(S, dev, hbm)
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -299,18 +366,24 @@ def gpu_arm(args):
                    "parallelism": f"replicas{world}", "tile": tile,
                    "l2": "flushed between timed stages (256 MiB write)",
                    "accumulate": "FP32 per row, FP64 totals/weights/MH"},
-        "roofline": {"kernel": "k_hmc (HMC trajectory, L+1 estimator passes)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                     "bytes_per_launch": bytes_launch, "launches": n_h,
-                     "ms_per_launch": ms_h / max(n_h, 1),
-                     "note": "X (48 MB packed) is L2-resident within a stage"},
+        "roofline": {"kernel": "k_hmc_res (HMC trajectory, rows resident in shared memory)",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic, "flops_per_launch": flops_launch,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "algorithmic_gbs": bytes_launch / sec / 1e9 if n_h else None,
+                     "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind,
+                     "launches": n_h, "ms_per_launch": ms_h / max(n_h, 1),
+                     "note": "traffic = DRAM bytes per launch (ncu); the rows of a particle are "
+                             "gathered once per trajectory, the L+1 passes read shared memory"},
         "stage_shares": shares,
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "grad-evals/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "fp32_storage": fp32,
+        "hbm_gather_leg": gather,
         "smc_wall_time": walls,
         "cpu_baseline": cpu,
         "wall_s_timed": wall,
@@ -325,7 +398,7 @@ def gpu_arm(args):
 def committed_traffic(bytes_launch):
     """DRAM bytes per HMC launch from the committed ncu summary, if it was taken on the current
     kernel sources (its recorded source hash matches); otherwise None."""
-    path = os.path.join(ROOT, "profiles", "k_hmc_logistic_n1e6_p20_bf16.txt")
+    path = os.path.join(ROOT, "profiles", "k_hmc_res_logistic_n1e6_p20_bf16.txt")
     try:
         text = open(path).read()
     except OSError:
@@ -345,10 +418,10 @@ def committed_traffic(bytes_launch):
 
 
 def source_hash():
-    """Hash of the sources that define the HMC trajectory kernel for BF16 storage."""
+    """Hash of the sources that define the HMC trajectory kernels for BF16 storage."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1805_03317_gb300", "csrc")
-    for f in ("device.cuh", "estimator.cuh", "est_bf16.cu", "internal.h"):
+    for f in ("device.cuh", "estimator.cuh", "resident.cuh", "est_bf16.cu", "internal.h"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -428,6 +501,12 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.gather_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(gather_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0),
+                                    peaks()[0])), flush=True)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

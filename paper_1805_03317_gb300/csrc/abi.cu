@@ -17,7 +17,7 @@ struct smc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   // problem
-  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, Sx = 0, p = 0;
+  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, Sx = 0, Yo = 0, p = 0;
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
@@ -219,6 +219,7 @@ EstArgs base_args(const smc_ctx *c) {
   a.n = c->n;
   a.p = c->p;
   a.S = c->S;
+  a.Yo = c->Yo;
   a.m = c->m;
   a.G = c->G;
   a.fam = c->fam;
@@ -260,7 +261,7 @@ int check_err_bits(smc_ctx *c, const DevState &h) {
 // A, B, C at a device point theta (FP64) into A_out/B_out/C_out (device).
 int moments_at(smc_ctx *c, const double *theta_d, double *A_out, double *B_out, double *C_out) {
   LAUNCH(c,
-         cv_moments(c->Xp, c->x_dtype, c->n, c->p, c->S, c->fam,
+         cv_moments(c->Xp, c->x_dtype, c->n, c->p, c->S, c->Yo, c->fam,
                     c->noise_sigma * c->noise_sigma, theta_d, c->part,
                     cv_moments_blocks(c->p), A_out, B_out, C_out, c->stream),
          2);
@@ -373,7 +374,8 @@ int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const dou
   const size_t cts = ct_size(c);
   // packed rows
   ALLOC(c, c->Xp, (size_t)c->n * c->S * c->esz);
-  LAUNCH(c, pack_rows(P->X, c->x_dtype, c->n, p, P->x_ld, P->y, c->Xp, c->S, c->stream), 1);
+  LAUNCH(c, pack_rows(P->X, c->x_dtype, c->n, p, P->x_ld, P->y, c->Xp, c->S, c->Yo, c->stream),
+         1);
   // prior
   ALLOC(c, c->mu_d, sizeof(double) * p);
   ALLOC(c, c->var_d, sizeof(double) * p);
@@ -508,9 +510,12 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->is_f64 = P->x_dtype == SMC_F64;
   c->esz = P->x_dtype == SMC_F64 ? 8 : (P->x_dtype == SMC_F32 ? 4 : 2);
   c->YS = c->is_f64 ? 1 : 4 / c->esz;
-  const int vec = 16 / c->esz;
-  c->S = ((c->YS + P->p + vec - 1) / vec) * vec;
-  c->Sx = ((P->p + vec - 1) / vec) * vec;
+  // packed row: x, then y in its own 16-byte vector, stride a multiple of 64 bytes so that a row
+  // occupies whole DRAM fetch units
+  const int xbytes = ((P->p * c->esz + 15) / 16) * 16;
+  c->Yo = xbytes / c->esz;
+  c->S = ((xbytes + 16 + 63) / 64) * 64 / c->esz;
+  c->Sx = c->Yo + 16 / c->esz;  // streamed tiles cover the covariates and the y vector
   c->n = P->n;
   c->p = P->p;
   c->noise_sigma = P->family == SMC_GAUSSIAN ? P->noise_sigma : 1.0;

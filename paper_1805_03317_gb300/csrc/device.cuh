@@ -139,17 +139,15 @@ template <typename CT> __device__ __forceinline__ CT sigmoid_(CT x) {
 template <typename CT, int K0> __device__ __forceinline__ CT exp_tail(CT D) {
   if (fabs(D) <= CT(0.5)) {
     constexpr int NT = sizeof(CT) == 8 ? 19 : 10;  // terms k0 .. k0+NT-1; remainder < ulp
+    // s = sum_{j>=0} D^j k0!/(k0+j)!, by Horner with the constant reciprocals 1/k
     CT s = CT(1);
 #pragma unroll
-    for (int k = K0 + NT - 1; k > K0; --k) s = CT(1) + s * D / CT(k);
-    // s = sum_{j>=0} D^j k0!/(k0+j)!
-    CT f = CT(1);
-#pragma unroll
-    for (int k = 2; k <= K0; ++k) f *= CT(k);
+    for (int k = K0 + NT - 1; k > K0; --k) s = fma(s * D, CT(1.0 / k), CT(1));
+    constexpr double inv_f = K0 == 2 ? 0.5 : 1.0 / 6.0;  // 1/k0!
     CT Dk = D;
 #pragma unroll
     for (int k = 1; k < K0; ++k) Dk *= D;
-    return Dk / f * s;
+    return Dk * CT(inv_f) * s;
   }
   CT t = expm1(D) - D;
   if (K0 == 3) t -= CT(0.5) * D * D;

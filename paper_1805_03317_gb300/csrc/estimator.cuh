@@ -23,23 +23,50 @@ __device__ __forceinline__ void set_err(DevState *st, int bit) {
   if (st) atomicOr(&st->err, bit);
 }
 
-template <typename XT, int T, int CPL, int U>
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Streamed rows. T lanes share a row and each holds CPL element slots of it (slot s of the lane
+// is element gl*CPL + s of the packed row). Rows reach the lanes through a per-warp ring of NST
+// stages in shared memory filled with 16-byte cp.async copies: while stage `step` is consumed the
+// copies of stage step + NST - 1 are in flight. Each lane copies and later reads only its own
+// chunk, so the ring needs no barriers, only the lane's own cp.async group accounting.
+template <typename XT, int T, int CPL, int NST>
 struct WarpEval {
   using SD = Store<XT>;
   using CT = typename SD::CT;
   using YT = typename SD::YT;
-  static constexpr int RPW = 32 / T;        // rows per warp per sub-step
-  static constexpr int NV = CPL / SD::VEC;  // 128-bit loads per lane per row
+  static constexpr int RPW = 32 / T;                 // rows per warp per step
+  static constexpr int NV = CPL / SD::VEC;           // 16-byte vectors per lane per row
+  static constexpr int LB = CPL * (int)sizeof(XT);   // bytes per lane per row
+  // lane stride in the ring: an odd multiple of 16 bytes, so 128-bit accesses of 8 consecutive
+  // lanes fall in distinct bank groups
+  static constexpr int LS = (LB / 16) % 2 ? LB : LB + 16;
+  static constexpr int RING = NST * 32 * LS;         // ring bytes per warp
   static_assert(CPL % SD::VEC == 0, "CPL must be a whole number of 16-byte vectors");
   static_assert(T >= 1 && T <= 32 && (T & (T - 1)) == 0, "T must be a power of two");
+  static_assert(NST >= 2, "at least double buffering");
 
   CT tb[CPL], dl[CPL];
   int lane, gl, rs;
+  unsigned char *mine;  // this lane's chunk of stage 0 of the ring
+  int ylane, yoff;      // the lane of a row group that holds y, and y's byte offset in its chunk
 
-  __device__ __forceinline__ WarpEval() {
+  // ring: this warp's RING bytes (16-byte aligned). Yo: element at which y starts its own
+  // 16-byte vector in the packed row (the covariates occupy the vectors before it).
+  __device__ __forceinline__ void init(unsigned char *ring, int Yo) {
     lane = threadIdx.x & 31;
     gl = lane & (T - 1);
     rs = lane / T;
+    mine = ring + lane * LS;
+    ylane = Yo / CPL;
+    yoff = (Yo - ylane * CPL) * (int)sizeof(XT);
   }
   // Slot s of this lane is element (column) gl*CPL + s of a packed row.
   __device__ __forceinline__ void load_slots(const CT *vec, int p, CT *dst) const {
@@ -53,79 +80,89 @@ struct WarpEval {
   // Rows [j0, j1) of the index list idx. Accumulates gradient partials into g1, g2 (if GRAD)
   // and returns this lane's partial sums of d and d^2 (nonzero only on group leaders).
   template <bool GRAD>
-  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int p, int64_t n,
+  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int Yo, int p, int64_t n,
                                        const int32_t *idx, int j0, int j1, int fam,
                                        CT inv_s2, CT *g1, CT *g2, CT &sd, CT &sd2,
                                        DevState *st) const {
-    for (int jb = j0; jb < j1; jb += RPW * U) {
-      CT xv[U][CPL];
-      YT yv[U];
-      bool valid[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int j = jb + q * RPW + rs;
-        valid[q] = j < j1;
-        int k = valid[q] ? idx[j] : 0;  // plain load: u-update indices are written by this warp
-        if (valid[q] && (k < 0 || (int64_t)k >= n)) {
+    const int nsteps = (j1 - j0 + RPW - 1) / RPW;
+    auto issue = [&](int step) {
+      if (step < nsteps) {
+        const int j = j0 + step * RPW + rs;
+        unsigned char *dst = mine + (step % NST) * 32 * LS;
+        bool ok = j < j1;
+        const int k = ok ? idx[j] : 0;  // plain load: u-update indices are written by this warp
+        if (ok && (k < 0 || (int64_t)k >= n)) {
           set_err(st, kErrIndex);
-          valid[q] = false;
-          k = 0;
+          ok = false;
         }
-        const XT *row = Xp + (int64_t)k * S;
-        const uint4 *rowp = reinterpret_cast<const uint4 *>(row + gl * CPL);
-        yv[q] = (gl == 0 && valid[q]) ? __ldg(reinterpret_cast<const YT *>(row + S - SD::YS))
-                                      : YT(0);
+        const unsigned char *src =
+            reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + gl * LB;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          uint4 w = make_uint4(0u, 0u, 0u, 0u);
-          if (valid[q] && gl * CPL + v * SD::VEC < p) w = __ldg(rowp + v);
-          SD::unpack(w, &xv[q][v * SD::VEC]);
-        }
-        if (SD::YS == 2) {  // BF16: the halves of y read as BF16 may not be finite; zero them
-#pragma unroll
-          for (int s = 0; s < CPL; ++s)
-            if (gl * CPL + s >= p) xv[q][s] = CT(0);
+          if (gl * CPL + v * SD::VEC > Yo) continue;  // vectors past the y vector are not read
+          if (ok)
+            cp_async16(dst + 16 * v, src + 16 * v);
+          else
+            *reinterpret_cast<uint4 *>(dst + 16 * v) = make_uint4(0u, 0u, 0u, 0u);
         }
       }
+      cp_async_commit();  // one group per step (empty past the end) keeps the counting uniform
+    };
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        CT pe = CT(0), pd = CT(0);
+    for (int q = 0; q < NST - 1; ++q) issue(q);
+    for (int step = 0; step < nsteps; ++step) {
+      issue(step + NST - 1);
+      cp_async_wait<NST - 1>();  // this lane's copies of `step` have landed
+      const unsigned char *src = mine + (step % NST) * 32 * LS;
+      CT xv[CPL];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {  // covariate vectors only; the y vector and beyond are zero
+        if (gl * CPL + v * SD::VEC < Yo) {
+          SD::unpack(*reinterpret_cast<const uint4 *>(src + 16 * v), &xv[v * SD::VEC]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < SD::VEC; ++e) xv[v * SD::VEC + e] = CT(0);
+        }
+      }
+      YT yl = YT(0);
+      if (gl == ylane) yl = *reinterpret_cast<const YT *>(src + yoff);
+      CT pe = CT(0), pd = CT(0);
+#pragma unroll
+      for (int s = 0; s < CPL; ++s) {
+        pe = fma(xv[s], tb[s], pe);
+        pd = fma(xv[s], dl[s], pd);
+      }
+#pragma unroll
+      for (int o = T / 2; o; o >>= 1) {
+        pe += __shfl_xor_sync(0xffffffffu, pe, o);
+        pd += __shfl_xor_sync(0xffffffffu, pd, o);
+      }
+      const CT y = (CT)__shfl_sync(0xffffffffu, yl, (lane & ~(T - 1)) + ylane);
+      CT d, r;
+      switch (fam) {
+        case 0: row_terms<0, CT>(pe, pd, y, inv_s2, d, r); break;
+        case 1: row_terms<1, CT>(pe, pd, y, inv_s2, d, r); break;
+        case 2: row_terms<2, CT>(pe, pd, y, inv_s2, d, r); break;
+        default: row_terms<3, CT>(pe, pd, y, inv_s2, d, r); break;
+      }
+      if (j0 + step * RPW + rs >= j1) {
+        d = CT(0);
+        r = CT(0);
+      }
+      if (GRAD) {
+        const CT dr = d * r;
 #pragma unroll
         for (int s = 0; s < CPL; ++s) {
-          pe = fma(xv[q][s], tb[s], pe);
-          pd = fma(xv[q][s], dl[s], pd);
-        }
-#pragma unroll
-        for (int o = T / 2; o; o >>= 1) {
-          pe += __shfl_xor_sync(0xffffffffu, pe, o);
-          pd += __shfl_xor_sync(0xffffffffu, pd, o);
-        }
-        CT y = (CT)__shfl_sync(0xffffffffu, yv[q], lane & ~(T - 1));
-        CT d, r;
-        switch (fam) {
-          case 0: row_terms<0, CT>(pe, pd, y, inv_s2, d, r); break;
-          case 1: row_terms<1, CT>(pe, pd, y, inv_s2, d, r); break;
-          case 2: row_terms<2, CT>(pe, pd, y, inv_s2, d, r); break;
-          default: row_terms<3, CT>(pe, pd, y, inv_s2, d, r); break;
-        }
-        if (!valid[q]) {
-          d = CT(0);
-          r = CT(0);
-        }
-        if (GRAD) {
-          const CT dr = d * r;
-#pragma unroll
-          for (int s = 0; s < CPL; ++s) {
-            g1[s] = fma(r, xv[q][s], g1[s]);
-            g2[s] = fma(dr, xv[q][s], g2[s]);
-          }
-        }
-        if (gl == 0) {
-          sd += d;
-          sd2 = fma(d, d, sd2);
+          g1[s] = fma(r, xv[s], g1[s]);
+          g2[s] = fma(dr, xv[s], g2[s]);
         }
       }
+      if (gl == 0) {
+        sd += d;
+        sd2 = fma(d, d, sd2);
+      }
     }
+    cp_async_wait<0>();
   }
 };
 
@@ -144,6 +181,14 @@ template <typename CT> struct WarpSmem {
   }
   static __host__ __device__ int count(int p, int slots) { return 5 * p + 2 * slots; }
 };
+
+// Bytes of dynamic shared memory per warp: the row ring, then the WarpSmem arrays.
+template <typename XT, int T, int CPL, int NST>
+__host__ __device__ inline int warp_smem_bytes(int p) {
+  using CT = typename Store<XT>::CT;
+  const int b = WarpEval<XT, T, CPL, NST>::RING + WarpSmem<CT>::count(p, T * CPL) * (int)sizeof(CT);
+  return (b + 15) & ~15;
+}
 
 template <typename CT> __device__ __forceinline__ CT ldg_ct(const void *p, int i) {
   return __ldg(reinterpret_cast<const CT *>(p) + i);
@@ -168,7 +213,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
     for (int g = 0; g < a.G; ++g) {
       const int j0 = (int)(((int64_t)g * a.m) / a.G), j1 = (int)(((int64_t)(g + 1) * a.m) / a.G);
       CT sd = CT(0), sd2 = CT(0);
-      W.template rows<GRAD>(Xp, a.S, a.p, a.n, idx, j0, j1, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
+      W.template rows<GRAD>(Xp, a.S, a.Yo, a.p, a.n, idx, j0, j1, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
       const double bs = warp_sum((double)sd), bq = warp_sum((double)sd2);
       if (W.lane == 0) {
         blk_out[2 * g] = bs;
@@ -179,7 +224,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
     }
   } else {
     CT sd = CT(0), sd2 = CT(0);
-    W.template rows<GRAD>(Xp, a.S, a.p, a.n, idx, 0, a.m, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
+    W.template rows<GRAD>(Xp, a.S, a.Yo, a.p, a.n, idx, 0, a.m, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
     S = warp_sum((double)sd);
     Q = warp_sum((double)sd2);
   }
@@ -258,8 +303,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
   if (i >= a.B) return;  // whole warp leaves together; no block-level barriers follow
   WarpEval<XT, T, CPL, U> W;
   const int slots = T * CPL;
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(smem_raw) + warp * WarpSmem<CT>::count(a.p, slots), a.p,
-                  slots);
+  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
+  W.init(wbase, a.Yo);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), a.p, slots);
   W.load_slots(reinterpret_cast<const CT *>(a.tb_ct), a.p, W.tb);
   const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * a.p;
   for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
@@ -305,8 +351,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   if (i >= a.B) return;
   WarpEval<XT, T, CPL, U> W;
   const int slots = T * CPL;
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(smem_raw) + warp * WarpSmem<CT>::count(a.p, slots), a.p,
-                  slots);
+  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
+  W.init(wbase, a.Yo);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), a.p, slots);
   const uint32_t smv = stage_move(a.stage, a.move);
   const Stream sblk(a.seed, kUpmBlock, smv, (uint32_t)i);
   const Stream sidx(a.seed, kUpmIdx, smv, (uint32_t)i);
@@ -326,7 +373,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   __syncwarp();
   refresh_delta(W, a, sm);
   CT sd = CT(0), sd2 = CT(0);
-  W.template rows<false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.p, a.n, unew, 0, nb, a.fam,
+  W.template rows<false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.Yo, a.p, a.n, unew, 0, nb,
+                         a.fam,
                          (CT)a.inv_s2, nullptr, nullptr, sd, sd2, a.st);
   const double Sg = warp_sum((double)sd), Qg = warp_sum((double)sd2);
   double *blk = a.blk + (int64_t)i * a.G * 2;
@@ -379,8 +427,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   WarpEval<XT, T, CPL, U> W;
   const int slots = T * CPL;
   const int p = a.p;
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(smem_raw) + warp * WarpSmem<CT>::count(p, slots), p,
-                  slots);
+  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(p);
+  W.init(wbase, a.Yo);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), p, slots);
   const uint32_t smv = stage_move(a.stage, a.move);
   const double temp = a.st->a;
   const CT eps = (CT)a.st->eps;
@@ -456,16 +505,24 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
 template <typename XT, int T, int CPL, int U, int WARPS>
 inline int launch_tile(int op, const EstArgs &a, cudaStream_t s) {
   using CT = typename Store<XT>::CT;
-  const size_t smem = (size_t)WARPS * WarpSmem<CT>::count(a.p, T * CPL) * sizeof(CT);
+  const size_t smem = (size_t)WARPS * warp_smem_bytes<XT, T, CPL, U>(a.p);
   const dim3 grid((a.B + WARPS - 1) / WARPS), block(WARPS * 32);
   if (a.B <= 0) return 0;
+  cudaError_t e;
   if (op == 0) {
-    k_estimate<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    e = cudaFuncSetAttribute(k_estimate<XT, T, CPL, U, WARPS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_estimate<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
   } else if (op == 1) {
-    k_upm<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    e = cudaFuncSetAttribute(k_upm<XT, T, CPL, U, WARPS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_upm<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
   } else {
-    k_hmc<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    e = cudaFuncSetAttribute(k_hmc<XT, T, CPL, U, WARPS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_hmc<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
   }
+  if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }
 

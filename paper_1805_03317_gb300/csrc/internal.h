@@ -36,9 +36,9 @@ enum ErrBits { kErrIndex = 1, kErrNonFinite = 2, kErrChol = 4, kErrCap = 8 };
 // (double for FP64 problems, float otherwise).
 struct EstArgs {
   // problem
-  const void *Xp;  // packed rows [n, S]
+  const void *Xp;  // packed rows [n, S]: x in [0, p), y at element Yo (its own 16-byte vector)
   int64_t n;
-  int p, S, m, G, fam;
+  int p, S, Yo, m, G, fam;
   double inv_s2;   // Gaussian family: 1/sigma^2
   double A;        // sum_k l_k(theta_bar)
   const void *B_ct, *C_ct, *tb_ct;  // B [p], C [p,p] (symmetric), theta_bar [p]
@@ -67,9 +67,10 @@ struct EstArgs {
   DevState *st;
 };
 
-// Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots.
+// Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots; NST
+// stages of streamed rows in flight per warp (resident kernel: unused); warps per CTA.
 struct Tile {
-  int T, CPL, U, warps;
+  int T, CPL, NST, warps;
 };
 
 // Launchers, one set per storage type (defined in est_f64.cu, est_f32.cu, est_bf16.cu).
@@ -94,8 +95,8 @@ int res_tiles_bf16(Tile *out, int cap);
 
 // Stage kernels (stage.cu). All return cudaError_t.
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,
-              int S, cudaStream_t s);
-int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int fam, double sigma2,
+              int S, int Yo, cudaStream_t s);
+int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
                const double *theta, double *partials, int nblocks, double *A, double *B,
                double *C, cudaStream_t s);
 int cv_moments_blocks(int p);

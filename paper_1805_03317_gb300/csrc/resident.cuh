@@ -49,10 +49,6 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   return P;
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -161,16 +157,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     }
     cp_async_wait_all();
     __syncthreads();
-    // slots p .. nvec*VEC-1 hold padding or the halves of y: zero them
-    const int pad = P.nvec * SD::VEC - p;
-    if (pad > 0) {
-      for (int t = tid; t < m * pad; t += blockDim.x) {
-        const int j = t / pad, s = p + (t - j * pad);
-        XT *row = reinterpret_cast<XT *>(rows + (size_t)j * P.rb);
-        row[s] = XT(0.0f);
-      }
-      __syncthreads();
-    }
     // 2. trajectory-invariant per-row constants
     for (int j = tid; j < m; j += blockDim.x) {
       CT x[CPL];
@@ -180,8 +166,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       for (int s = 0; s < CPL; ++s) eb = fma(x[s], tbs[s], eb);
       const int k = u[j];
       const bool ok = k >= 0 && (int64_t)k < a.n;
-      const CT y = ok ? (CT)__ldg(reinterpret_cast<const YT *>(Xp + (int64_t)k * S + S - SD::YS))
-                      : CT(0);
+      const CT y = ok ? (CT)__ldg(reinterpret_cast<const YT *>(Xp + (int64_t)k * S + a.Yo)) : CT(0);
       RowC<CT> c;
       switch (fam) {
         case 0: c = row_consts<0, CT>(eb, y, inv_s2); break;
@@ -230,7 +215,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     int buf = 0;
     // One estimator pass at the current delta (dr). Every warp ends with the gradient at its lanes
     // and l_hat, sigma2_hat; FINAL also fills the block sums blks.
-    auto pass = [&](bool final) {
+    auto pass = [&](bool final, bool want_totals) {
       CT v[2 * CPL];
 #pragma unroll
       for (int s = 0; s < 2 * CPL; ++s) v[s] = CT(0);
@@ -269,16 +254,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       reduce_scatter<2 * CPL, 16, CT>(v, lane, base);
       constexpr int KF = kfinal<2 * CPL, 16>();
       CT *rb = red + buf * WARPS * 2 * CPL;
-      double *rd = redd + buf * WARPS * 2;
+      CT *rd = reinterpret_cast<CT *>(redd) + buf * WARPS * 2;
 #pragma unroll
       for (int q = 0; q < KF; ++q) rb[warp * 2 * CPL + base + q] = v[q];
       const CT s1 = warp_sum(sd), s2 = warp_sum(sd2);
       if (lane == 0) {
-        rd[2 * warp] = (double)s1;
-        rd[2 * warp + 1] = (double)s2;
+        rd[2 * warp] = s1;
+        rd[2 * warp + 1] = s2;
       }
       __syncthreads();  // all warps' partial sums of this pass are in buffer buf
-      double S1 = 0.0, S2 = 0.0;
+      CT S1f = CT(0);   // sum of d over the subsample (the gradient needs only its mean)
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) S1f += rd[2 * w];
       if (final) {  // block sums of d (floor partition of u into G blocks)
         for (int g = warp; g < G; g += WARPS) {
           const int j0 = (int)(((int64_t)g * m) / G), j1 = (int)(((int64_t)(g + 1) * m) / G);
@@ -296,19 +283,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
           }
         }
         __syncthreads();
-        for (int g = 0; g < G; ++g) {
-          S1 += blks[2 * g];
-          S2 += blks[2 * g + 1];
-        }
-      } else {
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-          S1 += rd[2 * w];
-          S2 += rd[2 * w + 1];
-        }
       }
-      // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at lane c; l_hat and sigma2_hat
-      const CT dbar = (CT)(S1 * inv_m);
+      // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at lane c (every warp, FP32)
+      const CT dbar = S1f * (CT)inv_m;
       CT G1 = CT(0), G2 = CT(0);
       if (col) {
 #pragma unroll
@@ -321,17 +298,36 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       const int cl = lane < CPL ? lane : 0;
 #pragma unroll
       for (int k = 0; k < CPL; ++k) cd = fma(Cs[k * CPL + cl], dr[k], cd);
-      const CT dc = col ? th - tbc : CT(0);
-      const CT qlin = warp_sum(col ? dc * (Bc + CT(0.5) * cd) : CT(0));
       gr = col ? ta * (Bc + cd) + tnm * G1 - ta2 * (G2 - dbar * G1) - (th - muc) * ivc : CT(0);
-      ell = a.A + (double)qlin + nm * S1;
-      sig = nm * nm * (S2 - S1 * S1 * inv_m);
+      if (want_totals && warp == 0) {  // l_hat and sigma2_hat in FP64 (first and last pass)
+        const CT dc = col ? th - tbc : CT(0);
+        const CT qlin = warp_sum(col ? dc * (Bc + CT(0.5) * cd) : CT(0));
+        double S1 = 0.0, S2 = 0.0;
+        if (final) {
+          for (int g = 0; g < G; ++g) {
+            S1 += blks[2 * g];
+            S2 += blks[2 * g + 1];
+          }
+        } else {
+#pragma unroll
+          for (int w = 0; w < WARPS; ++w) {
+            S1 += (double)rd[2 * w];
+            S2 += (double)rd[2 * w + 1];
+          }
+        }
+        ell = a.A + (double)qlin + nm * S1;
+        sig = nm * nm * (S2 - S1 * S1 * inv_m);
+      }
       buf ^= 1;
     };
 
-    // 4. trajectory
-    const double kin0 = kinetic(), lp0 = log_prior();
-    pass(false);
+    // 4. trajectory (the Hamiltonian is needed by warp 0 only)
+    double kin0 = 0.0, lp0 = 0.0;
+    if (warp == 0) {
+      kin0 = kinetic();
+      lp0 = log_prior();
+    }
+    pass(false, true);
     const double H0 = -(temp * ell - 0.5 * temp * temp * sig + lp0) + kin0;
     for (int l = 0; l < a.L; ++l) {
       rho += CT(0.5) * eps * gr;
@@ -341,12 +337,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
                                              __shfl_sync(0xffffffffu, rho, k), vs);
       if (col) th += eps * vs;
       set_delta();
-      pass(l == a.L - 1);
+      pass(l == a.L - 1, l == a.L - 1);
       rho += CT(0.5) * eps * gr;
     }
     // 5. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
-    const double kin1 = kinetic(), lp1 = log_prior();
     if (warp == 0) {
+      const double kin1 = kinetic(), lp1 = log_prior();
       const double H1 = -(temp * ell - 0.5 * temp * temp * sig + lp1) + kin1;
       const Stream smh(a.seed, kMhTheta, smv, (uint32_t)i);
       const double Uu = draw_uniform(smh.draw(0));

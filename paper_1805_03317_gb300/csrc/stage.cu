@@ -35,11 +35,12 @@ template <typename CT> __device__ __forceinline__ double ld_state(const void *p,
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
-// Packing: row k of Xp = [x_k | 0 ... | y_k], stride S elements; y occupies the last 8 (FP64) or 4
-// (otherwise) bytes of the row.
+// Packing: row k of Xp = [x_k | 0 .. | y_k | 0 ..], stride S elements (a multiple of 64 bytes); y
+// starts the 16-byte vector that follows the covariates (element Yo), so no vector holds both.
 // ------------------------------------------------------------------------------------------------
 template <typename E, typename YT>
-__global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E *Xp, int S) {
+__global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E *Xp, int S,
+                       int Yo) {
   constexpr int YS = sizeof(YT) / sizeof(E);
   const int64_t total = n * (int64_t)S;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -47,9 +48,9 @@ __global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E 
     const int64_t k = t / S;
     const int s = (int)(t - k * S);
     E v;
-    if (s >= S - YS) {
+    if (s >= Yo && s < Yo + YS) {
       const YT yk = y[k];
-      v = reinterpret_cast<const E *>(&yk)[s - (S - YS)];
+      v = reinterpret_cast<const E *>(&yk)[s - Yo];
     } else if (s < p) {
       v = X[k * ld + s];
     } else {
@@ -60,18 +61,18 @@ __global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E 
 }
 
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,
-              int S, cudaStream_t s) {
+              int S, int Yo, cudaStream_t s) {
   const int64_t total = n * (int64_t)S;
   const int grid = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
   if (x_dtype == 0)
     k_pack<uint64_t, double><<<grid, 256, 0, s>>>((const uint64_t *)X, n, p, ld,
-                                                  (const double *)y, (uint64_t *)Xp, S);
+                                                  (const double *)y, (uint64_t *)Xp, S, Yo);
   else if (x_dtype == 1)
     k_pack<uint32_t, float><<<grid, 256, 0, s>>>((const uint32_t *)X, n, p, ld, (const float *)y,
-                                                (uint32_t *)Xp, S);
+                                                (uint32_t *)Xp, S, Yo);
   else
     k_pack<uint16_t, float><<<grid, 256, 0, s>>>((const uint16_t *)X, n, p, ld, (const float *)y,
-                                                (uint16_t *)Xp, S);
+                                                (uint16_t *)Xp, S, Yo);
   return (int)cudaGetLastError();
 }
 
@@ -97,14 +98,14 @@ template <>
 __device__ __forceinline__ double packed_x<__nv_bfloat16>(const __nv_bfloat16 *row, int slot) {
   return (double)__bfloat162float(row[slot]);
 }
-template <typename XT> __device__ __forceinline__ double packed_y(const XT *row, int S) {
-  if (sizeof(XT) == 8) return *reinterpret_cast<const double *>(row + S - 1);
-  return (double)*reinterpret_cast<const float *>(row + S - 4 / (int)sizeof(XT));
+template <typename XT> __device__ __forceinline__ double packed_y(const XT *row, int Yo) {
+  if (sizeof(XT) == 8) return *reinterpret_cast<const double *>(row + Yo);
+  return (double)*reinterpret_cast<const float *>(row + Yo);
 }
 
 template <typename XT, int MAXQ>
 __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_t n, int p, int S,
-                                                            int fam, double s2,
+                                                            int Yo, int fam, double s2,
                                                             const double *theta, double *part) {
   using AT = typename std::conditional<sizeof(XT) == 8, double, float>::type;
   extern __shared__ double sh[];
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
       if (k < n) {
         double eta = 0.0;
         for (int c = 0; c < p; ++c) eta = fma((double)xs[tid * p + c], ths[c], eta);
-        const double y = packed_y<XT>(Xp + k * S, S);
+        const double y = packed_y<XT>(Xp + k * S, Yo);
         switch (fam) {
           case 0: row_value<0>(eta, y, s2, l, d1, d2); break;
           case 1: row_value<1>(eta, y, s2, l, d1, d2); break;
@@ -221,24 +222,25 @@ __global__ void k_cv_reduce(const double *part, int nblk, int p, double *A, doub
 
 template <typename XT, int MAXQ>
 cudaError_t launch_cv_q(int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n, int p,
-                        int S, int fam, double s2, const double *theta, double *part) {
+                        int S, int Yo, int fam, double s2, const double *theta, double *part) {
   cudaError_t e = cudaFuncSetAttribute(k_cv_partials<XT, MAXQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_cv_partials<XT, MAXQ><<<nblocks, kCvThreads, smem, s>>>(Xp, n, p, S, fam, s2, theta, part);
+  k_cv_partials<XT, MAXQ><<<nblocks, kCvThreads, smem, s>>>(Xp, n, p, S, Yo, fam, s2, theta,
+                                                            part);
   return cudaGetLastError();
 }
 
 // Pair slots per thread: the smallest compiled count that covers p(p+1)/2 pairs.
 template <typename XT>
 cudaError_t launch_cv(int need, int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n,
-                      int p, int S, int fam, double s2, const double *theta, double *part) {
-  if (need <= 1) return launch_cv_q<XT, 1>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
-  if (need <= 2) return launch_cv_q<XT, 2>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
-  if (need <= 4) return launch_cv_q<XT, 4>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
-  if (need <= 8) return launch_cv_q<XT, 8>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
-  if (need <= 16) return launch_cv_q<XT, 16>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
-  return launch_cv_q<XT, 32>(nblocks, smem, s, Xp, n, p, S, fam, s2, theta, part);
+                      int p, int S, int Yo, int fam, double s2, const double *theta, double *part) {
+  if (need <= 1) return launch_cv_q<XT, 1>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+  if (need <= 2) return launch_cv_q<XT, 2>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+  if (need <= 4) return launch_cv_q<XT, 4>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+  if (need <= 8) return launch_cv_q<XT, 8>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+  if (need <= 16) return launch_cv_q<XT, 16>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+  return launch_cv_q<XT, 32>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
 }
 
 int cv_moments_blocks(int p) {
@@ -246,7 +248,7 @@ int cv_moments_blocks(int p) {
   return 2 * 152;
 }
 
-int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int fam, double sigma2,
+int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
                const double *theta, double *partials, int nblocks, double *A, double *B,
                double *C, cudaStream_t s) {
   if (p * (p + 1) / 2 > kCvThreads * kCvMaxPairs) return (int)cudaErrorInvalidValue;
@@ -255,14 +257,14 @@ int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int fam, do
   const int np = p * (p + 1) / 2, need = (np + kCvThreads - 1) / kCvThreads;
   cudaError_t e;
   if (x_dtype == 0)
-    e = launch_cv<double>(need, nblocks, smem, s, (const double *)Xp, n, p, S, fam, sigma2, theta,
-                          partials);
+    e = launch_cv<double>(need, nblocks, smem, s, (const double *)Xp, n, p, S, Yo, fam, sigma2,
+                          theta, partials);
   else if (x_dtype == 1)
-    e = launch_cv<float>(need, nblocks, smem, s, (const float *)Xp, n, p, S, fam, sigma2, theta,
-                         partials);
+    e = launch_cv<float>(need, nblocks, smem, s, (const float *)Xp, n, p, S, Yo, fam, sigma2,
+                         theta, partials);
   else
-    e = launch_cv<__nv_bfloat16>(need, nblocks, smem, s, (const __nv_bfloat16 *)Xp, n, p, S, fam,
-                                 sigma2, theta, partials);
+    e = launch_cv<__nv_bfloat16>(need, nblocks, smem, s, (const __nv_bfloat16 *)Xp, n, p, S, Yo,
+                                 fam, sigma2, theta, partials);
   if (e != cudaSuccess) return (int)e;
   const int width = 1 + p + p * (p + 1) / 2;
   k_cv_reduce<<<(width + 7) / 8, 256, 0, s>>>(partials, nblocks, p, A, B, C);
@@ -405,18 +407,20 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 // evaluates the K-1 interior points of the bracket and keeps the first sub-interval whose right end
 // has ESS < tau N. Partials of every block are merged in block order by the last block to finish.
 // ------------------------------------------------------------------------------------------------
-constexpr int kRwThreads = 32, kMaxK = 32, kRwMaxBlocks = 152;  // one warp per block
+constexpr int kRwThreads = 32, kMaxK = 32, kRwMaxBlocks = 152;  // final kernels: one warp
+constexpr int kSwWarps = 4;  // search kernels: warps per block, lanes = candidates
 
-// Candidates of a search round: round -1 tests D = 1 - a alone; later rounds the K - 1 interior
-// points lo + (hi - lo) k / K of the bracket.
+// Candidates of a search round. Round 0 evaluates the K - 1 interior points of [0, 1 - a] and
+// the end point 1 - a itself (the test "ESS(1 - a) >= tau N" of the rule); later rounds evaluate
+// the K - 1 interior points lo + (hi - lo) k / K of the current bracket.
 __device__ __forceinline__ int candidates(const DevState *st, int K, int round, double &lo,
                                           double &hi) {
-  lo = round < 0 ? 0.0 : st->lo;
-  hi = round < 0 ? st->dmax : st->hi;
-  return round < 0 ? 1 : K - 1;
+  lo = round == 0 ? 0.0 : st->lo;
+  hi = round == 0 ? st->dmax : st->hi;
+  return round == 0 ? K : K - 1;
 }
-__device__ __forceinline__ double candidate(int round, double lo, double hi, int K, int k) {
-  return round < 0 ? hi : lo + (hi - lo) * (k + 1) / K;
+__device__ __forceinline__ double candidate(double lo, double hi, int K, int k) {
+  return k == K - 1 ? hi : lo + (hi - lo) * (k + 1) / K;
 }
 
 // Per-block table of the round's candidates: D_k and h_k = ((a + D_k)^2 - a^2) / 2, so that
@@ -426,7 +430,7 @@ __device__ __forceinline__ int load_candidates(const DevState *st, int K, int ro
   const int ncand = candidates(st, K, round, lo, hi);
   const double a = st->a;
   for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
-    const double D = candidate(round, lo, hi, K, k);
+    const double D = candidate(lo, hi, K, k);
     Dk[k] = D;
     hk[k] = 0.5 * ((a + D) * (a + D) - a * a);
   }
@@ -434,113 +438,137 @@ __device__ __forceinline__ int load_candidates(const DevState *st, int K, int ro
   return ncand;
 }
 
-// Phase 1 of a round: the maximum of lw_i(D_k) over all particles, per candidate.
-__global__ void __launch_bounds__(kRwThreads)
+// Phase 1 of a round: the maximum of lw_i(D_k) over all particles, per candidate. Each block
+// takes a contiguous chunk of particles; lane k handles candidate k over the whole chunk (the
+// particle loads are broadcasts), so the candidates' chains run side by side.
+__global__ void __launch_bounds__(kSwWarps * 32)
     k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
                  int round, DevState *st, double *pmax, double *gmax) {
   __shared__ double Dk[kMaxK], hk[kMaxK];
+  __shared__ double wmax[kSwWarps][kMaxK];
   __shared__ bool is_last;
   if (st->search_done) return;  // uniform across the grid
   double lo, hi;
   const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
-  const int stride = gridDim.x * blockDim.x;
-  for (int k = 0; k < ncand; ++k) {
-    const double D = Dk[k], h = hk[k];
+  __syncthreads();
+  const int chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < ncand) {
+    // The maximum sets the shift M of the sums below. It must be the FP64 maximum: early in the
+    // run |lw| reaches ~1e11, where a float maximum can miss the true one by ~1e4 and overflow exp.
+    const double D = Dk[lane], h = hk[lane];
     double mx = -INFINITY;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+#pragma unroll 4
+    for (int i = i0 + warp; i < i1; i += kSwWarps)
       mx = fmax(mx, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
-    mx = warp_max(mx);
-    if (threadIdx.x == 0) pmax[blockIdx.x * kMaxK + k] = mx;
+    wmax[warp][lane] = mx;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < ncand) {
+    double mx = wmax[0][lane];
+#pragma unroll
+    for (int w = 1; w < kSwWarps; ++w) mx = fmax(mx, wmax[w][lane]);
+    pmax[blockIdx.x * kMaxK + lane] = mx;
   }
   __threadfence();
   if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncwarp();
-  if (!is_last) return;
+  __syncthreads();
+  if (!is_last || warp != 0) return;
   __threadfence();
-  for (int k = 0; k < ncand; ++k) {  // lanes over blocks
+  if (lane < ncand) {  // lane k: candidate k, loads over blocks in flight together
     double M = -INFINITY;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) M = fmax(M, pmax[b * kMaxK + k]);
-    M = warp_max(M);
-    if (threadIdx.x == 0) gmax[k] = M;
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) M = fmax(M, pmax[b * kMaxK + lane]);
+    gmax[lane] = M;
   }
-  if (threadIdx.x == 0) st->ticket = 0;
+  if (lane == 0) st->ticket = 0;
 }
 
 // Phase 2: s1 = sum e^{lw - M}, s2 = sum e^{2(lw - M)} (one exponential per particle and
 // candidate), ESS = s1^2 / s2; the last block sums the block partials in block order (lanes over
 // blocks, fixed tree) and updates the bracket: the first sub-interval whose right end has
 // ESS < tau N.
-__global__ void __launch_bounds__(kRwThreads)
+__global__ void __launch_bounds__(kSwWarps * 32)
     k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
                  int K, int round, int last_round, DevState *st, const double *gmax,
                  double *psum) {
   __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK];
+  __shared__ double wsum[kSwWarps][kMaxK][2];
   __shared__ bool is_last;
   if (st->search_done) return;
   double lo, hi;
   const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
-  const int stride = gridDim.x * blockDim.x;
-  for (int k = 0; k < ncand; ++k) {
-    const double D = Dk[k], h = hk[k], M = gmax[k];
+  __syncthreads();
+  const int chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < ncand) {  // lane k: candidate k over this warp's share of the block's particles
+    const double D = Dk[lane], h = hk[lane], M = gmax[lane];
     double s1 = 0.0, s2 = 0.0;
     if (M > -INFINITY) {
-      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+#pragma unroll 4
+      for (int i = i0 + warp; i < i1; i += kSwWarps) {
         const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M);
         s1 += e;
         s2 = fma(e, e, s2);
       }
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (threadIdx.x == 0) {
-      psum[2 * (blockIdx.x * kMaxK + k)] = s1;
-      psum[2 * (blockIdx.x * kMaxK + k) + 1] = s2;
+    wsum[warp][lane][0] = s1;
+    wsum[warp][lane][1] = s2;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < ncand) {  // warps combined in a fixed order
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSwWarps; ++w) {
+      s1 += wsum[w][lane][0];
+      s2 += wsum[w][lane][1];
     }
+    psum[2 * (blockIdx.x * kMaxK + lane)] = s1;
+    psum[2 * (blockIdx.x * kMaxK + lane) + 1] = s2;
   }
   __threadfence();
   if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncwarp();
-  if (!is_last) return;
+  __syncthreads();
+  if (!is_last || warp != 0) return;
   __threadfence();
-  for (int k = 0; k < ncand; ++k) {
+  if ((int)threadIdx.x < ncand) {  // lane k: candidate k, block partials summed in block order
+    const int k = threadIdx.x;
     double s1 = 0.0, s2 = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) {
       s1 += psum[2 * (b * kMaxK + k)];
       s2 += psum[2 * (b * kMaxK + k) + 1];
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (threadIdx.x == 0) ess_k[k] = s1 * s1 / s2;
+    ess_k[k] = s1 * s1 / s2;
   }
   __syncwarp();
   if (threadIdx.x != 0) return;
   const double target = tau * (double)N;
-  int first = ncand + 1;  // 1-based index of the first candidate with ESS < target
-  for (int k = 0; k < ncand; ++k) {
-    const double ess = ess_k[k];
-    if (!(ess == ess)) atomicOr(&st->err, kErrNonFinite);
-    if (ess < target) {
+  const int ninner = round == 0 ? K - 1 : ncand;  // interior points (round 0 adds the end point)
+  for (int k = 0; k < ncand; ++k)
+    if (!(ess_k[k] == ess_k[k])) atomicOr(&st->err, kErrNonFinite);
+  if (round == 0 && ess_k[K - 1] >= target) {  // ESS(1 - a) >= target: go straight to a = 1
+    st->D = st->dmax;
+    st->search_done = 1;
+    st->ticket = 0;
+    return;
+  }
+  int first = ninner + 1;  // 1-based index of the first interior candidate with ESS < target
+  for (int k = 0; k < ninner; ++k) {
+    if (ess_k[k] < target) {
       first = k + 1;
       break;
     }
   }
-  if (round < 0) {
-    if (first > ncand) {  // ESS(1 - a) >= target: go straight to a = 1
-      st->D = st->dmax;
-      st->search_done = 1;
-    } else {
-      st->lo = 0.0;
-      st->hi = st->dmax;
-    }
-  } else {
-    const double nlo = lo + (hi - lo) * (first - 1) / K;
-    const double nhi = first <= ncand ? lo + (hi - lo) * first / K : hi;
-    st->lo = nlo;
-    st->hi = nhi;
-    if (round == last_round) {
-      st->D = nlo > 0.0 ? nlo : nhi;
-      st->search_done = 1;
-    }
+  const double nlo = lo + (hi - lo) * (first - 1) / K;
+  const double nhi = first <= ninner ? lo + (hi - lo) * first / K : hi;
+  st->lo = nlo;
+  st->hi = nhi;
+  if (round == last_round) {
+    st->D = nlo > 0.0 ? nlo : nhi;
+    st->search_done = 1;
   }
   st->ticket = 0;
 }
@@ -553,7 +581,7 @@ __global__ void __launch_bounds__(kRwThreads)
   __shared__ bool is_last;
   const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
   const int stride = gridDim.x * blockDim.x;
-  double m0 = -INFINITY, m1 = -INFINITY;
+  double m0 = -INFINITY, m1 = -INFINITY;  // FP64 shifts (see k_search_max)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
     m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
     m1 = fmax(m1, logW[i]);
@@ -569,11 +597,11 @@ __global__ void __launch_bounds__(kRwThreads)
   __syncwarp();
   if (!is_last) return;
   __threadfence();
-  for (int k = 0; k < 2; ++k) {
+  if (threadIdx.x < 2) {
     double M = -INFINITY;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) M = fmax(M, pmax[2 * b + k]);
-    M = warp_max(M);
-    if (threadIdx.x == 0) gmax[k] = M;
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) M = fmax(M, pmax[2 * b + threadIdx.x]);
+    gmax[threadIdx.x] = M;
   }
   if (threadIdx.x == 0) st->ticket = 0;
 }
@@ -605,12 +633,14 @@ __global__ void __launch_bounds__(kRwThreads)
   __syncwarp();
   if (!is_last) return;
   __threadfence();
-  double tot[3];
-  for (int k = 0; k < 3; ++k) {
+  __shared__ double tot[3];
+  if (threadIdx.x < 3) {
     double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += psum[3 * b + k];
-    tot[k] = warp_sum(t);
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) t += psum[3 * b + threadIdx.x];
+    tot[threadIdx.x] = t;
   }
+  __syncwarp();
   if (threadIdx.x != 0) return;
   const double lse_new = M0 + log(tot[0]), lse_old = M1 + log(tot[2]);
   st->lse_new = lse_new;
@@ -649,16 +679,18 @@ int reweight(int N, const double *ell, const double *sig2, double *logW, double 
   if (K < 2 || K > kMaxK) return (int)cudaErrorInvalidValue;
   int nb = (N + kRwThreads - 1) / kRwThreads;
   if (nb > kRwMaxBlocks) nb = kRwMaxBlocks;
+  int nbs = (N + 4 * kSwWarps - 1) / (4 * kSwWarps);  // search: at least 4 particles per warp
+  if (nbs > kRwMaxBlocks) nbs = kRwMaxBlocks;
   double *gmax = partials;                  // [kMaxK]
   double *pmax = gmax + kMaxK;              // [nb][kMaxK]
   double *psum = pmax + kRwMaxBlocks * kMaxK;  // [nb][kMaxK][2]
   int count = 0;
   k_search_begin<<<1, 1, 0, s>>>(st);
   ++count;
-  for (int r = -1; r < rounds; ++r) {
-    k_search_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, K, r, st, pmax, gmax);
-    k_search_sum<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1, st, gmax,
-                                           psum);
+  for (int r = 0; r < rounds; ++r) {
+    k_search_max<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, K, r, st, pmax, gmax);
+    k_search_sum<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1, st,
+                                               gmax, psum);
     count += 2;
   }
   k_final_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, pmax, gmax);

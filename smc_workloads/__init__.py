@@ -53,14 +53,14 @@ class Workload:
 
     @property
     def n(self) -> int:
-        return self.X.shape[0]
+        return self.X_store.shape[0]
 
     @property
     def p(self) -> int:
-        return self.X.shape[1]
+        return self.X_store.shape[1]
 
 
-def _store(X: np.ndarray, y: np.ndarray, x_dtype: str):
+def _store(X: np.ndarray, y: np.ndarray, x_dtype: str, upcast: bool = True):
     if x_dtype == "f64":
         Xs = np.ascontiguousarray(X, dtype=np.float64)
         ys = np.ascontiguousarray(y, dtype=np.float64)
@@ -71,7 +71,7 @@ def _store(X: np.ndarray, y: np.ndarray, x_dtype: str):
         return Xs.astype(np.float64), Xs, ys.astype(np.float64), ys
     if x_dtype == "bf16":
         bits = round_to_bf16_bits(np.asarray(X, dtype=np.float32))
-        return bf16_bits_to_f64(bits), bits, ys.astype(np.float64), ys
+        return (bf16_bits_to_f64(bits) if upcast else None), bits, ys.astype(np.float64), ys
     raise ValueError(x_dtype)
 
 
@@ -144,10 +144,10 @@ def logistic_1e6(x_dtype: str = "bf16", n: int = 1_000_000) -> Workload:
                     np.zeros(p), np.full(p, 10.0), 4096, 1000, 10, 20, 5, seed, 1.0, theta)
 
 
-def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000) -> Workload:
+def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000, upcast: bool = True) -> Workload:
     """Poisson regression: n=5,000,000, p=50 (intercept + 49 N(0, 0.1^2) covariates),
     theta_true ~ N(0, 0.2^2 I) with intercept 1.0, prior N(0, 0.1 I); N=8192, m=2000, G=20,
-    L=20, R=5. X stored as BF16."""
+    L=20, R=5. X stored as BF16. upcast=False skips the float64 copy of X (Workload.X is None)."""
     seed = BASE_SEED + 2
     rng = np.random.Generator(np.random.PCG64(seed))
     p = 50
@@ -156,8 +156,10 @@ def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000) -> Workload:
     X[:, 1:] = 0.1 * rng.standard_normal((n, p - 1), dtype=np.float32)
     theta = 0.2 * rng.standard_normal(p)
     theta[0] = 1.0
-    Xs64, _, _, _ = _store(X, np.zeros(n), x_dtype)
-    y = _respond(rng, "poisson", Xs64 @ theta)
-    Xd, Xs, yd, ys = _store(X, y, x_dtype)
+    _, Xs, _, _ = _store(X, np.zeros(n), x_dtype, upcast=False)
+    Xv = bf16_bits_to_f64(Xs).astype(np.float32) if x_dtype == "bf16" else Xs
+    y = _respond(rng, "poisson", Xv.astype(np.float64) @ theta)
+    del Xv
+    Xd, Xs, yd, ys = _store(X, y, x_dtype, upcast=upcast)
     return Workload(f"poisson-n5e6-p50-{x_dtype}", "poisson", x_dtype, Xd, Xs, yd, ys,
                     np.zeros(p), np.full(p, 0.1), 8192, 2000, 20, 20, 5, seed, 1.0, theta)
