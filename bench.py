@@ -48,6 +48,8 @@ def parse():
                     help="skip the HBM-bound gather leg (Poisson n=5e6, p=50)")
     ap.add_argument("--gather-only", action="store_true",
                     help="run only the HBM-bound gather leg and print its JSON (for profiling)")
+    ap.add_argument("--gather-tile", type=int, default=0,
+                    help="estimator tile hint for the gather leg (0: autotune)")
     return ap.parse_args()
 
 
@@ -209,7 +211,7 @@ def full_run(S, wl, dev, R, max_stages=400):
             "post_mean_minus_mode_maxabs": float(np.max(np.abs(mean - tb)))}
 
 
-def gather_leg(S, dev, hbm, reps=20, stages=3):
+def gather_leg(S, dev, hbm, reps=20, stages=3, tile_hint=0):
     """HBM-bound leg: Poisson regression, n = 5e6, p = 50, BF16 X (560 MB packed, far above L2),
     N = 8192, m = 2000. Times the subsampled estimator with gradient over all particles (one gather
     of N*m rows per call, the streamed kernel) and a few full SMC stages, whose 112 KB x 2000 rows
@@ -219,9 +221,9 @@ def gather_leg(S, dev, hbm, reps=20, stages=3):
     wl = poisson_5e6("bf16", upcast=False)
     X, y = device_workload(wl, dev)
     ctx = S.smc_init(X, y, "poisson", wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
-                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None)
+                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None, tile_hint=tile_hint)
     del X, y
-    tile = S.smc_autotune(ctx)
+    tile = S.smc_autotune(ctx) if tile_hint == 0 else (tile_hint, 1)
     theta, u, _ = S.smc_get_particles(ctx)
     for _ in range(3):
         S.loglik_grad(ctx, theta, u, 1.0)
@@ -505,7 +507,7 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(gather_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0),
-                                    peaks()[0])), flush=True)
+                                    peaks()[0], tile_hint=args.gather_tile)), flush=True)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -17,7 +17,7 @@ struct smc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   // problem
-  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, YS = 1, S = 0, Sx = 0, Yo = 0, p = 0;
+  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0;
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
@@ -331,7 +331,8 @@ int newton_map(smc_ctx *c, double *theta_d) {
   return SMC_OK;
 }
 
-// Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies.
+// Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies,
+// and the per-row constants at the centre in every packed row's tail.
 int set_centre(smc_ctx *c) {
   const int p = c->p;
   LAUNCH(c, round_to_state_type(c->is_f64, p, c->tb_d, c->stream), c->is_f64 ? 0 : 1);
@@ -340,6 +341,10 @@ int set_centre(smc_ctx *c) {
   LAUNCH(c, to_state_type(c->is_f64, p, c->tb_d, c->tb_ct, c->stream), 1);
   LAUNCH(c, to_state_type(c->is_f64, p, c->B_d, c->B_ct, c->stream), 1);
   LAUNCH(c, to_state_type(c->is_f64, p * p, c->C_d, c->C_ct, c->stream), 1);
+  LAUNCH(c,
+         row_consts(c->Xp, c->x_dtype, c->n, p, c->S, c->Yo, c->fam, c->tb_ct,
+                    1.0 / (c->noise_sigma * c->noise_sigma), c->stream),
+         1);
   CUDA_OK(c, cudaMemcpyAsync(&c->A_h, c->A_d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   if (!isfinite(c->A_h)) return fail(c, SMC_ERR_NONFINITE, "A(theta_bar) is not finite");
@@ -509,13 +514,13 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->x_dtype = P->x_dtype;
   c->is_f64 = P->x_dtype == SMC_F64;
   c->esz = P->x_dtype == SMC_F64 ? 8 : (P->x_dtype == SMC_F32 ? 4 : 2);
-  c->YS = c->is_f64 ? 1 : 4 / c->esz;
-  // packed row: x, then y in its own 16-byte vector, stride a multiple of 64 bytes so that a row
-  // occupies whole DRAM fetch units
+  // packed row: x, then the tail {c0, c1, c2, y} (four state-type values) from the next 16-byte
+  // boundary, stride a multiple of 64 bytes so that a row occupies whole DRAM fetch units
   const int xbytes = ((P->p * c->esz + 15) / 16) * 16;
+  const int tbytes = 4 * (c->is_f64 ? 8 : 4);
   c->Yo = xbytes / c->esz;
-  c->S = ((xbytes + 16 + 63) / 64) * 64 / c->esz;
-  c->Sx = c->Yo + 16 / c->esz;  // streamed tiles cover the covariates and the y vector
+  c->S = ((xbytes + tbytes + 63) / 64) * 64 / c->esz;
+  c->Sx = c->Yo;  // streamed tiles cover the covariate vectors; tails travel separately
   c->n = P->n;
   c->p = P->p;
   c->noise_sigma = P->family == SMC_GAUSSIAN ? P->noise_sigma : 1.0;

@@ -81,15 +81,18 @@ __device__ __forceinline__ double stream_normal(const Stream &st, uint32_t j) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Packed row layout. Row k of the library's copy of the data holds [x_k1 .. x_kp | zeros | y_k]:
-// x from element 0 (so every row and its covariates start 16-byte aligned), y in the last YS element
-// slots (4 bytes, 8 for FP64), row stride S elements (a multiple of 16 bytes). Padding is zero.
+// Packed row layout. Row k of the library's copy of the data holds
+//   [x_k1 .. x_kp | zeros to a 16-byte boundary | RowC tail {c0, c1, c2, y_k} | zeros]
+// with x from element 0 (every row and its covariates start 16-byte aligned), the tail at element
+// Yo in the state type (16 bytes; 32 for FP64) and the row stride S a multiple of 64 bytes, so a
+// gathered row occupies whole DRAM fetch units. c0..c2 are the trajectory-invariant constants of
+// the row at the control-variate centre (row_consts below); they are rewritten whenever the centre
+// changes.
 // ------------------------------------------------------------------------------------------------
 template <typename XT> struct Store;
 template <> struct Store<double> {
   using CT = double;  // arithmetic type of the per-row terms
-  using YT = double;
-  static constexpr int YS = 1, VEC = 2;
+  static constexpr int VEC = 2;
   __device__ __forceinline__ static void unpack(const uint4 &v, CT *out) {
     out[0] = __hiloint2double((int)v.y, (int)v.x);
     out[1] = __hiloint2double((int)v.w, (int)v.z);
@@ -97,8 +100,7 @@ template <> struct Store<double> {
 };
 template <> struct Store<float> {
   using CT = float;
-  using YT = float;
-  static constexpr int YS = 1, VEC = 4;
+  static constexpr int VEC = 4;
   __device__ __forceinline__ static void unpack(const uint4 &v, CT *out) {
     out[0] = __uint_as_float(v.x);
     out[1] = __uint_as_float(v.y);
@@ -108,8 +110,7 @@ template <> struct Store<float> {
 };
 template <> struct Store<__nv_bfloat16> {
   using CT = float;
-  using YT = float;
-  static constexpr int YS = 2, VEC = 8;
+  static constexpr int VEC = 8;
   __device__ __forceinline__ static void unpack(const uint4 &v, CT *out) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -165,33 +166,37 @@ template <typename CT> __device__ __forceinline__ void log_phi_(CT z, CT &lp, CT
     lp = log1p(CT(-0.5) * erfc(-x));
 }
 
-// Trajectory-invariant per-row constants (they depend on eta_bar and y only) and the increment
-// terms d, r given those constants and D. row_terms = row_incr(row_consts(...)).
-template <typename CT> struct RowC {
-  CT c0, c1, c2, c3;
+// Trajectory-invariant per-row constants: they depend on eta_bar = x'theta_bar and y only, so they
+// are computed once per centre and stored in the row's tail. row_terms = row_incr(row_consts(...)).
+//   logistic: c0 = sigma(eta_bar), c1 = c0 (1 - c0), c2 = eta_bar
+//   Poisson:  c0 = e^eta_bar
+//   Gaussian: c0 = y - eta_bar
+//   probit:   c0 = z_bar = s eta_bar (s = 2y - 1), c1 = log Phi(z_bar), c2 = lambda(z_bar)
+template <typename CT> struct alignas(16) RowC {
+  CT c0, c1, c2, y;
 };
 
 template <int FAM, typename CT>
 __device__ __forceinline__ RowC<CT> row_consts(CT eb, CT y, CT inv_s2) {
   RowC<CT> c;
-  c.c0 = c.c1 = c.c2 = c.c3 = CT(0);
-  if (FAM == 0) {  // logistic: sigma(eta_bar), its derivative, eta_bar
+  c.c0 = c.c1 = c.c2 = CT(0);
+  c.y = y;
+  if (FAM == 0) {
     const CT sb = sigmoid_(eb);
     c.c0 = sb;
     c.c1 = sb * (CT(1) - sb);
     c.c2 = eb;
-  } else if (FAM == 2) {  // Poisson: e^eta_bar
+  } else if (FAM == 2) {
     c.c0 = exp(eb);
-  } else if (FAM == 3) {  // Gaussian: residual at eta_bar
+  } else if (FAM == 3) {
     c.c0 = y - eb;
-  } else {  // probit: s = 2y - 1, z_bar = s eta_bar, log Phi(z_bar), lambda(z_bar)
-    const CT s = CT(2) * y - CT(1), zb = s * eb;
+  } else {
+    const CT zb = (CT(2) * y - CT(1)) * eb;
     CT lpb, lamb;
     log_phi_(zb, lpb, lamb);
-    c.c0 = s;
-    c.c1 = zb;
-    c.c2 = lpb;
-    c.c3 = lamb;
+    c.c0 = zb;
+    c.c1 = lpb;
+    c.c2 = lamb;
   }
   (void)inv_s2;
   return c;
@@ -259,7 +264,7 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
     d = dl - res * inv_s2 * D + CT(0.5) * inv_s2 * D * D;
     r = (res - D) * inv_s2 - res * inv_s2 + inv_s2 * D;
   } else {  // probit: l = log Phi(s*eta)
-    const CT s = c.c0, zb = c.c1, lpb = c.c2, lamb = c.c3, z = zb + s * D;
+    const CT s = CT(2) * c.y - CT(1), zb = c.c0, lpb = c.c1, lamb = c.c2, z = zb + s * D;
     CT lp, lam;
     log_phi_(z, lp, lam);
     const CT h = lamb * (zb + lamb);  // -l''(eta_bar)
@@ -314,6 +319,39 @@ template <typename V> __device__ __forceinline__ V warp_max(V v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// Reduce-scatter of K values per lane over lane groups of size 2*O (recursive halving at offsets
+// O, O/2, .., 1, then a butterfly while the count is odd). On return v[0..kfinal(K)) hold sums over
+// the group of the original entries base + i.
+template <int K, int O, typename V>
+__device__ __forceinline__ void reduce_scatter(V *v, int lane, int &base) {
+  if constexpr (O > 0) {
+    if constexpr (K % 2 == 0) {
+      constexpr int H = K / 2;
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const V send = up ? v[i] : v[i + H];
+        const V keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += H;
+      reduce_scatter<H, O / 2, V>(v, lane, base);
+    } else {
+#pragma unroll
+      for (int i = 0; i < K; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], O);
+      reduce_scatter<K, O / 2, V>(v, lane, base);
+    }
+  }
+}
+template <int K, int O> __host__ __device__ constexpr int kfinal() {
+  if constexpr (O == 0)
+    return K;
+  else if constexpr (K % 2 == 0)
+    return kfinal<K / 2, O / 2>();
+  else
+    return kfinal<K, O / 2>();
 }
 
 }  // namespace subsmc

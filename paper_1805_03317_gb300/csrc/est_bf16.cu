@@ -5,7 +5,8 @@
 namespace subsmc {
 namespace {
 using XT = __nv_bfloat16;
-const Tile kTiles[] = {{2, 16, 4, 4}, {4, 8, 8, 4}, {4, 16, 8, 4}, {8, 16, 4, 4}, {16, 8, 8, 4}, {4, 16, 4, 4}};
+const Tile kTiles[] = {{1, 8, 3, 4}, {2, 8, 3, 4}, {4, 8, 2, 4}, {2, 16, 2, 4}, {4, 16, 2, 4},
+                       {8, 8, 2, 4}, {8, 8, 3, 4}, {8, 16, 2, 4}, {16, 8, 2, 4}};
 }  // namespace
 
 int est_tiles_bf16(Tile *out, int cap) {
@@ -16,12 +17,15 @@ int est_tiles_bf16(Tile *out, int cap) {
 
 int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_tile<XT, 2, 16, 4, 4>(op, a, s);
-    case 1: return launch_tile<XT, 4, 8, 8, 4>(op, a, s);
-    case 2: return launch_tile<XT, 4, 16, 8, 4>(op, a, s);
-    case 3: return launch_tile<XT, 8, 16, 4, 4>(op, a, s);
-    case 4: return launch_tile<XT, 16, 8, 8, 4>(op, a, s);
-    case 5: return launch_tile<XT, 4, 16, 4, 4>(op, a, s);
+    case 0: return launch_tile<XT, 1, 8, 3, 4>(op, a, s);
+    case 1: return launch_tile<XT, 2, 8, 3, 4>(op, a, s);
+    case 2: return launch_tile<XT, 4, 8, 2, 4>(op, a, s);
+    case 3: return launch_tile<XT, 2, 16, 2, 4>(op, a, s);
+    case 4: return launch_tile<XT, 4, 16, 2, 4>(op, a, s);
+    case 5: return launch_tile<XT, 8, 8, 2, 4>(op, a, s);
+    case 6: return launch_tile<XT, 8, 8, 3, 4>(op, a, s);
+    case 7: return launch_tile<XT, 8, 16, 2, 4>(op, a, s);
+    case 8: return launch_tile<XT, 16, 8, 2, 4>(op, a, s);
     default: return -1;
   }
 }

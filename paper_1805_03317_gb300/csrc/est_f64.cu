@@ -5,7 +5,8 @@
 namespace subsmc {
 namespace {
 using XT = double;
-const Tile kTiles[] = {{1, 8, 4, 4}, {4, 8, 4, 4}, {8, 16, 4, 4}};
+const Tile kTiles[] = {{1, 2, 3, 4}, {2, 2, 3, 4}, {1, 6, 3, 4}, {4, 2, 2, 4}, {2, 4, 2, 4},
+                       {8, 2, 2, 4}, {4, 4, 2, 4}, {8, 4, 2, 4}};
 }  // namespace
 
 int est_tiles_f64(Tile *out, int cap) {
@@ -16,9 +17,14 @@ int est_tiles_f64(Tile *out, int cap) {
 
 int est_launch_f64(int op, int tile, const EstArgs &a, cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_tile<XT, 1, 8, 4, 4>(op, a, s);
-    case 1: return launch_tile<XT, 4, 8, 4, 4>(op, a, s);
-    case 2: return launch_tile<XT, 8, 16, 4, 4>(op, a, s);
+    case 0: return launch_tile<XT, 1, 2, 3, 4>(op, a, s);
+    case 1: return launch_tile<XT, 2, 2, 3, 4>(op, a, s);
+    case 2: return launch_tile<XT, 1, 6, 3, 4>(op, a, s);
+    case 3: return launch_tile<XT, 4, 2, 2, 4>(op, a, s);
+    case 4: return launch_tile<XT, 2, 4, 2, 4>(op, a, s);
+    case 5: return launch_tile<XT, 8, 2, 2, 4>(op, a, s);
+    case 6: return launch_tile<XT, 4, 4, 2, 4>(op, a, s);
+    case 7: return launch_tile<XT, 8, 4, 2, 4>(op, a, s);
     default: return -1;
   }
 }

@@ -1,10 +1,10 @@
 // Warp-per-particle subsampled estimator and the kernels built on it.
 //
 // One warp owns one particle. Its m subsampled rows are gathered straight from the packed row
-// copy of the data: T lanes share a row and each lane reads CPL element slots with 128-bit loads,
-// so a warp has 32/T rows in flight per step (times U for the unrolled variants). Per row the
-// lanes form eta_bar = x'theta_bar and D = x'(theta - theta_bar) with an intra-group shuffle
-// reduction, evaluate the increment-form terms d and r (device.cuh), and accumulate
+// copy of the data (WarpEval below: 32 rows per sweep, one row owned per lane, covariates split
+// over groups of T lanes). Per row the warp forms D = x'(theta - theta_bar), evaluates the
+// increment-form terms d and r (device.cuh) from the row's stored constants at the centre, and
+// accumulates
 //   sum d, sum d^2                 (per block of u when the block cache is refreshed)
 //   sum r x, sum d r x             (gradient partials, kept in registers)
 // which give (Sec. 3.2, Eq. difference_estimator_logl)
@@ -32,41 +32,66 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Streamed rows. T lanes share a row and each holds CPL element slots of it (slot s of the lane
-// is element gl*CPL + s of the packed row). Rows reach the lanes through a per-warp ring of NST
-// stages in shared memory filled with 16-byte cp.async copies: while stage `step` is consumed the
-// copies of stage step + NST - 1 are in flight. Each lane copies and later reads only its own
-// chunk, so the ring needs no barriers, only the lane's own cp.async group accounting.
+// Streamed rows. A warp takes its particle's rows 32 at a time (a sweep) and lane l owns row l of
+// the sweep. For the covariates the warp splits into 32/T groups of T lanes: group r covers rows
+// rT .. rT+T-1 of the sweep, and lane g of the group holds element slots g*CPL .. g*CPL+CPL-1 of
+// each of them. Per sweep a lane forms partial x'delta over its slots for its group's T rows; a
+// reduce-scatter inside the group leaves every lane the full D of the row it owns; the lane
+// evaluates d and r for that row alone, from the constants in the row's tail; an all-gather inside
+// the group then hands every lane r and d*r of the group's rows for the gradient partials over its
+// slots. So the family terms are evaluated once per row, not once per lane of the row.
+//
+// Rows reach the lanes through a per-warp ring of NST sweeps in shared memory, filled by 16-byte
+// cp.async copies issued NST-1 sweeps ahead (the row indices one sweep further ahead still). Each
+// lane copies exactly what it later reads (its covariate chunks of the group's rows and the tail of
+// its own row), so the ring needs no barrier, only the lane's own cp.async group accounting.
+// Chunk vectors are XOR-swizzled so that 128-bit reads of 8 consecutive lanes hit distinct bank
+// groups; chunk vectors that lie past the covariates are never copied and stay zero.
 template <typename XT, int T, int CPL, int NST>
 struct WarpEval {
   using SD = Store<XT>;
   using CT = typename SD::CT;
-  using YT = typename SD::YT;
-  static constexpr int RPW = 32 / T;                 // rows per warp per step
-  static constexpr int NV = CPL / SD::VEC;           // 16-byte vectors per lane per row
-  static constexpr int LB = CPL * (int)sizeof(XT);   // bytes per lane per row
-  // lane stride in the ring: an odd multiple of 16 bytes, so 128-bit accesses of 8 consecutive
-  // lanes fall in distinct bank groups
-  static constexpr int LS = (LB / 16) % 2 ? LB : LB + 16;
-  static constexpr int RING = NST * 32 * LS;         // ring bytes per warp
+  static constexpr int NV = CPL / SD::VEC;               // 16-byte vectors per lane per row
+  static constexpr int TB = (int)sizeof(RowC<CT>);       // tail bytes per row
+  static constexpr int XBYTES = 32 * T * NV * 16;        // covariate chunks of one sweep
+  static constexpr int STAGE = XBYTES + 32 * TB;         // one sweep: chunks, then owned tails
+  static constexpr int RING = NST * STAGE;               // ring bytes per warp
   static_assert(CPL % SD::VEC == 0, "CPL must be a whole number of 16-byte vectors");
+  static_assert(NV == 1 || NV == 2 || NV == 3 || NV == 4 || NV == 8, "vectors per lane");
   static_assert(T >= 1 && T <= 32 && (T & (T - 1)) == 0, "T must be a power of two");
-  static_assert(NST >= 2, "at least double buffering");
+  static_assert(NST >= 2 && NST <= 32, "ring depth");
 
-  CT tb[CPL], dl[CPL];
-  int lane, gl, rs;
-  unsigned char *mine;  // this lane's chunk of stage 0 of the ring
-  int ylane, yoff;      // the lane of a row group that holds y, and y's byte offset in its chunk
+  CT dl[CPL];
+  int lane, gl, gb, swz, tail_off;
+  unsigned cmask;        // bit v: chunk vector v of this lane holds covariates (is copied)
+  unsigned char *ring;
 
-  // ring: this warp's RING bytes (16-byte aligned). Yo: element at which y starts its own
-  // 16-byte vector in the packed row (the covariates occupy the vectors before it).
-  __device__ __forceinline__ void init(unsigned char *ring, int Yo) {
+  // ring: this warp's RING bytes (16-byte aligned). Yo: element at which the row's tail starts.
+  __device__ __forceinline__ void init(unsigned char *ring_, int Yo) {
     lane = threadIdx.x & 31;
     gl = lane & (T - 1);
-    rs = lane / T;
-    mine = ring + lane * LS;
-    ylane = Yo / CPL;
-    yoff = (Yo - ylane * CPL) * (int)sizeof(XT);
+    gb = lane & ~(T - 1);
+    swz = (NV == 2 || NV == 4 || NV == 8) ? ((lane / (8 / NV)) & (NV - 1)) : 0;
+    ring = ring_;
+    tail_off = Yo * (int)sizeof(XT);
+    const int nvx = tail_off / 16;
+    cmask = 0u;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (gl * NV + v < nvx) cmask |= 1u << v;
+    for (int st = 0; st < NST; ++st)
+#pragma unroll
+      for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (!((cmask >> v) & 1u))
+            *reinterpret_cast<uint4 *>(chunk(st, t, v)) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __device__ __forceinline__ unsigned char *chunk(int st, int t, int v) const {
+    return ring + st * STAGE + ((t * 32 + lane) * NV + (v ^ swz)) * 16;
+  }
+  __device__ __forceinline__ unsigned char *tail(int st) const {
+    return ring + st * STAGE + XBYTES + lane * TB;
   }
   // Slot s of this lane is element (column) gl*CPL + s of a packed row.
   __device__ __forceinline__ void load_slots(const CT *vec, int p, CT *dst) const {
@@ -77,92 +102,158 @@ struct WarpEval {
     }
   }
 
-  // Rows [j0, j1) of the index list idx. Accumulates gradient partials into g1, g2 (if GRAD)
-  // and returns this lane's partial sums of d and d^2 (nonzero only on group leaders).
-  template <bool GRAD>
-  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int Yo, int p, int64_t n,
-                                       const int32_t *idx, int j0, int j1, int fam,
-                                       CT inv_s2, CT *g1, CT *g2, CT &sd, CT &sd2,
+  // One pass over rows idx[0..nrows). GRAD: accumulates the gradient partials sum r x, sum d r x
+  // over this lane's slots into g1, g2. Returns S = sum d and Q = sum d^2 on every lane; BLOCKS
+  // also writes per-block (sum d, sum d^2) of the floor partition of the nrows rows into G blocks
+  // to blk_out[2G].
+  template <bool GRAD, bool BLOCKS>
+  __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int64_t n,
+                                       const int32_t *idx, int nrows, int fam, CT inv_s2, CT *g1,
+                                       CT *g2, double *blk_out, int G, double &Ssum, double &Qsum,
                                        DevState *st) const {
-    const int nsteps = (j1 - j0 + RPW - 1) / RPW;
-    auto issue = [&](int step) {
-      if (step < nsteps) {
-        const int j = j0 + step * RPW + rs;
-        unsigned char *dst = mine + (step % NST) * 32 * LS;
-        bool ok = j < j1;
-        const int k = ok ? idx[j] : 0;  // plain load: u-update indices are written by this warp
-        if (ok && (k < 0 || (int64_t)k >= n)) {
-          set_err(st, kErrIndex);
-          ok = false;
-        }
-        const unsigned char *src =
-            reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + gl * LB;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (gl * CPL + v * SD::VEC > Yo) continue;  // vectors past the y vector are not read
-          if (ok)
-            cp_async16(dst + 16 * v, src + 16 * v);
-          else
-            *reinterpret_cast<uint4 *>(dst + 16 * v) = make_uint4(0u, 0u, 0u, 0u);
-        }
+    const int nsw = (nrows + 31) >> 5;
+    // rows past the end copy the last row again (already on chip) and are masked out
+    const int klast = nrows > 0 ? idx[nrows - 1] : 0;
+    unsigned bad = 0u;  // bit b: the row this lane owns in ring stage b had an invalid index
+    int kq = 0;         // index of this lane's row in the next sweep to issue
+    auto fetch = [&](int s) {
+      if (s < nsw) {
+        const int j = (s << 5) + lane;
+        kq = j < nrows ? idx[j] : klast;  // plain load: u-update indices are written by this warp
       }
-      cp_async_commit();  // one group per step (empty past the end) keeps the counting uniform
     };
-#pragma unroll
-    for (int q = 0; q < NST - 1; ++q) issue(q);
-    for (int step = 0; step < nsteps; ++step) {
-      issue(step + NST - 1);
-      cp_async_wait<NST - 1>();  // this lane's copies of `step` have landed
-      const unsigned char *src = mine + (step % NST) * 32 * LS;
-      CT xv[CPL];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {  // covariate vectors only; the y vector and beyond are zero
-        if (gl * CPL + v * SD::VEC < Yo) {
-          SD::unpack(*reinterpret_cast<const uint4 *>(src + 16 * v), &xv[v * SD::VEC]);
+    auto issue = [&](int s) {
+      if (s < nsw) {
+        const int b = s % NST;
+        int k = kq;
+        if (k < 0 || (int64_t)k >= n) {
+          if ((s << 5) + lane < nrows) set_err(st, kErrIndex);
+          bad |= 1u << b;
+          k = 0;
         } else {
+          bad &= ~(1u << b);
+        }
+        const unsigned char *row = reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S);
 #pragma unroll
-          for (int e = 0; e < SD::VEC; ++e) xv[v * SD::VEC + e] = CT(0);
+        for (int q = 0; q < TB / 16; ++q) cp_async16(tail(b) + 16 * q, row + tail_off + 16 * q);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int kt = __shfl_sync(0xffffffffu, k, gb + t);
+          const unsigned char *src =
+              reinterpret_cast<const unsigned char *>(Xp + (int64_t)kt * S) + gl * (NV * 16);
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            if ((cmask >> v) & 1u) cp_async16(chunk(b, t, v), src + 16 * v);
         }
       }
-      YT yl = YT(0);
-      if (gl == ylane) yl = *reinterpret_cast<const YT *>(src + yoff);
-      CT pe = CT(0), pd = CT(0);
+      cp_async_commit();  // one group per sweep (empty past the end) keeps the counting uniform
+    };
+    if (BLOCKS) {
+      for (int h = lane; h < 2 * G; h += 32) blk_out[h] = 0.0;  // blocks with no rows stay zero
+      __syncwarp();
+    }
+    fetch(0);
 #pragma unroll
-      for (int s = 0; s < CPL; ++s) {
-        pe = fma(xv[s], tb[s], pe);
-        pd = fma(xv[s], dl[s], pd);
-      }
+    for (int q = 0; q < NST - 1; ++q) {
+      issue(q);
+      fetch(q + 1);
+    }
+    CT sd = CT(0), sd2 = CT(0);
+    double cs = 0.0, cq = 0.0;  // BLOCKS: sums of the open block cg
+    int cg = -1;
+    Ssum = Qsum = 0.0;
+    for (int s = 0; s < nsw; ++s) {
+      issue(s + NST - 1);
+      fetch(s + NST);
+      cp_async_wait<NST - 1>();  // this lane's copies of sweep s have landed
+      const int b = s % NST;
+      CT pd[T];
 #pragma unroll
-      for (int o = T / 2; o; o >>= 1) {
-        pe += __shfl_xor_sync(0xffffffffu, pe, o);
-        pd += __shfl_xor_sync(0xffffffffu, pd, o);
+      for (int t = 0; t < T; ++t) {
+        CT x[CPL];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
+        CT q0 = CT(0), q1 = CT(0);
+#pragma unroll
+        for (int e = 0; e < CPL; e += 2) {
+          q0 = fma(x[e], dl[e], q0);
+          if (e + 1 < CPL) q1 = fma(x[e + 1], dl[e + 1], q1);
+        }
+        pd[t] = q0 + q1;
       }
-      const CT y = (CT)__shfl_sync(0xffffffffu, yl, (lane & ~(T - 1)) + ylane);
+      int base = 0;
+      reduce_scatter<T, T / 2, CT>(pd, lane, base);  // pd[0]: D of the row this lane owns
+      const RowC<CT> c = *reinterpret_cast<const RowC<CT> *>(tail(b));
       CT d, r;
       switch (fam) {
-        case 0: row_terms<0, CT>(pe, pd, y, inv_s2, d, r); break;
-        case 1: row_terms<1, CT>(pe, pd, y, inv_s2, d, r); break;
-        case 2: row_terms<2, CT>(pe, pd, y, inv_s2, d, r); break;
-        default: row_terms<3, CT>(pe, pd, y, inv_s2, d, r); break;
+        case 0: row_incr<0, CT>(c, pd[0], inv_s2, d, r); break;
+        case 1: row_incr<1, CT>(c, pd[0], inv_s2, d, r); break;
+        case 2: row_incr<2, CT>(c, pd[0], inv_s2, d, r); break;
+        default: row_incr<3, CT>(c, pd[0], inv_s2, d, r); break;
       }
-      if (j0 + step * RPW + rs >= j1) {
+      const int j = (s << 5) + lane;
+      if (j >= nrows || ((bad >> b) & 1u)) {
         d = CT(0);
         r = CT(0);
       }
       if (GRAD) {
+        // the chunks are read again rather than kept: holding T rows of covariates across the
+        // family terms would cost T*CPL registers
+        asm volatile("" ::: "memory");
         const CT dr = d * r;
 #pragma unroll
-        for (int s = 0; s < CPL; ++s) {
-          g1[s] = fma(r, xv[s], g1[s]);
-          g2[s] = fma(dr, xv[s], g2[s]);
+        for (int t = 0; t < T; ++t) {
+          const CT rt = __shfl_sync(0xffffffffu, r, gb + t);
+          const CT drt = __shfl_sync(0xffffffffu, dr, gb + t);
+          CT x[CPL];
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) {
+            g1[e] = fma(rt, x[e], g1[e]);
+            g2[e] = fma(drt, x[e], g2[e]);
+          }
         }
       }
-      if (gl == 0) {
+      if (BLOCKS) {  // block of row j: largest g with floor(g nrows / G) <= j
+        const int r1 = min((s << 5) + 31, nrows - 1);
+        const int gA = (int)(((unsigned)((s << 5) + 1) * (unsigned)G - 1u) / (unsigned)nrows);
+        const int gB = (int)(((unsigned)(r1 + 1) * (unsigned)G - 1u) / (unsigned)nrows);
+        const int gj =
+            j < nrows ? (int)(((unsigned)(j + 1) * (unsigned)G - 1u) / (unsigned)nrows) : -1;
+        for (int g = gA; g <= gB; ++g) {
+          const CT bs = warp_sum(gj == g ? d : CT(0));
+          const CT bq = warp_sum(gj == g ? d * d : CT(0));
+          if (g != cg) {
+            if (cg >= 0 && lane == 0) {
+              blk_out[2 * cg] = cs;
+              blk_out[2 * cg + 1] = cq;
+            }
+            cg = g;
+            cs = cq = 0.0;
+          }
+          cs += (double)bs;
+          cq += (double)bq;
+          Ssum += (double)bs;
+          Qsum += (double)bq;
+        }
+      } else {
         sd += d;
         sd2 = fma(d, d, sd2);
       }
     }
     cp_async_wait<0>();
+    if (BLOCKS) {
+      if (cg >= 0 && lane == 0) {
+        blk_out[2 * cg] = cs;
+        blk_out[2 * cg + 1] = cq;
+      }
+    } else {
+      Ssum = warp_sum((double)sd);
+      Qsum = warp_sum((double)sd2);
+    }
   }
 };
 
@@ -208,26 +299,9 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
   CT g1[CPL], g2[CPL];
 #pragma unroll
   for (int s = 0; s < CPL; ++s) g1[s] = g2[s] = CT(0);
-  double S = 0.0, Q = 0.0;
-  if (BLOCKS) {
-    for (int g = 0; g < a.G; ++g) {
-      const int j0 = (int)(((int64_t)g * a.m) / a.G), j1 = (int)(((int64_t)(g + 1) * a.m) / a.G);
-      CT sd = CT(0), sd2 = CT(0);
-      W.template rows<GRAD>(Xp, a.S, a.Yo, a.p, a.n, idx, j0, j1, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
-      const double bs = warp_sum((double)sd), bq = warp_sum((double)sd2);
-      if (W.lane == 0) {
-        blk_out[2 * g] = bs;
-        blk_out[2 * g + 1] = bq;
-      }
-      S += bs;
-      Q += bq;
-    }
-  } else {
-    CT sd = CT(0), sd2 = CT(0);
-    W.template rows<GRAD>(Xp, a.S, a.Yo, a.p, a.n, idx, 0, a.m, a.fam, inv_s2, g1, g2, sd, sd2, a.st);
-    S = warp_sum((double)sd);
-    Q = warp_sum((double)sd2);
-  }
+  double S, Q;
+  W.template rows<GRAD, BLOCKS>(Xp, a.S, a.n, idx, a.m, a.fam, inv_s2, g1, g2, blk_out, a.G, S, Q,
+                                a.st);
   const double nm = (double)a.n / (double)a.m;
   const double dbar = S / (double)a.m;
   if (GRAD) {
@@ -240,7 +314,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, 
         g2[s] += __shfl_xor_sync(0xffffffffu, g2[s], o);
       }
     }
-    if (W.rs == 0) {
+    if (W.gb == 0) {
 #pragma unroll
       for (int s = 0; s < CPL; ++s) {
         sm.G1[W.gl * CPL + s] = g1[s];
@@ -306,7 +380,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
   W.init(wbase, a.Yo);
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), a.p, slots);
-  W.load_slots(reinterpret_cast<const CT *>(a.tb_ct), a.p, W.tb);
   const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * a.p;
   for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
   __syncwarp();
@@ -367,16 +440,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
     unew[t] = (int32_t)draw_index(r0, (uint64_t)a.n);
     if (t + 1 < nb) unew[t + 1] = (int32_t)draw_index(r1, (uint64_t)a.n);
   }
-  W.load_slots(reinterpret_cast<const CT *>(a.tb_ct), a.p, W.tb);
   const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * a.p;
   for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
   __syncwarp();
   refresh_delta(W, a, sm);
-  CT sd = CT(0), sd2 = CT(0);
-  W.template rows<false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.Yo, a.p, a.n, unew, 0, nb,
-                         a.fam,
-                         (CT)a.inv_s2, nullptr, nullptr, sd, sd2, a.st);
-  const double Sg = warp_sum((double)sd), Qg = warp_sum((double)sd2);
+  double Sg, Qg;
+  W.template rows<false, false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n, unew, nb, a.fam,
+                                (CT)a.inv_s2, nullptr, nullptr, nullptr, 0, Sg, Qg, a.st);
   double *blk = a.blk + (int64_t)i * a.G * 2;
   // totals over blocks from the cache (lanes over blocks)
   double St = 0.0, Qt = 0.0;
@@ -433,7 +503,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   const uint32_t smv = stage_move(a.stage, a.move);
   const double temp = a.st->a;
   const CT eps = (CT)a.st->eps;
-  W.load_slots(reinterpret_cast<const CT *>(a.tb_ct), p, W.tb);
   CT *th_g = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
   for (int c = W.lane; c < p; c += 32) sm.th[c] = th_g[c];
   // momentum: z ~ N(0, I) in sm.v, rho = Linv' z  (rho_r = sum_c Linv[c, r] z_c, c >= r)

@@ -36,7 +36,7 @@ enum ErrBits { kErrIndex = 1, kErrNonFinite = 2, kErrChol = 4, kErrCap = 8 };
 // (double for FP64 problems, float otherwise).
 struct EstArgs {
   // problem
-  const void *Xp;  // packed rows [n, S]: x in [0, p), y at element Yo (its own 16-byte vector)
+  const void *Xp;  // packed rows [n, S]: x in [0, p), the RowC tail {c0, c1, c2, y} at element Yo
   int64_t n;
   int p, S, Yo, m, G, fam;
   double inv_s2;   // Gaussian family: 1/sigma^2
@@ -96,6 +96,9 @@ int res_tiles_bf16(Tile *out, int cap);
 // Stage kernels (stage.cu). All return cudaError_t.
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,
               int S, int Yo, cudaStream_t s);
+// Rewrites the constants c0..c2 in every packed row's tail for the centre tb_ct (state type).
+int row_consts(void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, const void *tb_ct,
+               double inv_s2, cudaStream_t s);
 int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
                const double *theta, double *partials, int nblocks, double *A, double *B,
                double *C, cudaStream_t s);

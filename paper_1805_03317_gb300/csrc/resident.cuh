@@ -1,8 +1,8 @@
 // HMC trajectory with the particle's subsample resident in shared memory (Algorithm 1 step 2).
 //
 // u is fixed for the whole trajectory, so the m rows x_{u_j} are gathered once per particle
-// (cp.async, 16-byte copies) and kept in shared memory; so are the trajectory-invariant per-row
-// control-variate constants (which depend on eta_bar_j and y_j only). The L + 1 estimator passes
+// (cp.async, 16-byte copies) and kept in shared memory, together with each row's stored
+// control-variate constants (its tail: they depend on eta_bar_j and y_j only). The L + 1 estimator passes
 // then read shared memory: one lane per row, D_j = x_j'(theta - theta_bar) and the increment terms
 // d_j, r_j (device.cuh), gradient partials in registers, a shuffle reduce-scatter per warp and one
 // CTA barrier per pass (partials double-buffered). Every warp then assembles the totals and the
@@ -35,8 +35,8 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   off = round16(off + m * (int)sizeof(RowC<CT>));
   P.off_d = off;
   off = round16(off + m * (int)sizeof(CT));
-  P.off_vec = off;  // initial momentum, theta_bar [cpl each]
-  off = round16(off + 2 * cpl * (int)sizeof(CT));
+  P.off_vec = off;  // initial momentum [cpl]
+  off = round16(off + cpl * (int)sizeof(CT));
   P.off_red = off;  // two buffers of [warps][2 cpl] gradient partials
   off = round16(off + 2 * warps * 2 * cpl * (int)sizeof(CT));
   P.off_redd = off;  // two buffers of [warps][2] sums of d, d^2
@@ -51,39 +51,6 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Reduce-scatter of K values per lane over the 32 lanes of a warp (recursive halving, then a
-// butterfly once the count is odd). On return v[0..kfinal(K)) hold sums over all 32 lanes of the
-// original entries base + i.
-template <int K, int O, typename V>
-__device__ __forceinline__ void reduce_scatter(V *v, int lane, int &base) {
-  if constexpr (O > 0) {
-    if constexpr (K % 2 == 0) {
-      constexpr int H = K / 2;
-      const bool up = (lane & O) != 0;
-#pragma unroll
-      for (int i = 0; i < H; ++i) {
-        const V send = up ? v[i] : v[i + H];
-        const V keep = up ? v[i + H] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
-      }
-      if (up) base += H;
-      reduce_scatter<H, O / 2, V>(v, lane, base);
-    } else {
-#pragma unroll
-      for (int i = 0; i < K; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], O);
-      reduce_scatter<K, O / 2, V>(v, lane, base);
-    }
-  }
-}
-template <int K, int O> __host__ __device__ constexpr int kfinal() {
-  if constexpr (O == 0)
-    return K;
-  else if constexpr (K % 2 == 0)
-    return kfinal<K / 2, O / 2>();
-  else
-    return kfinal<K, O / 2>();
 }
 
 template <typename XT, int CPL>
@@ -102,7 +69,6 @@ template <typename XT, int CPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   using SD = Store<XT>;
   using CT = typename SD::CT;
-  using YT = typename SD::YT;
   static_assert(CPL <= 32, "one column per lane");
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -112,7 +78,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   RowC<CT> *cst = reinterpret_cast<RowC<CT> *>(smem + P.off_consts);
   CT *dv = reinterpret_cast<CT *>(smem + P.off_d);
   CT *rho0 = reinterpret_cast<CT *>(smem + P.off_vec);  // [CPL] initial momentum
-  CT *tbs = rho0 + CPL;                                  // [CPL] theta_bar, zero-padded
   CT *red = reinterpret_cast<CT *>(smem + P.off_red);            // [2][WARPS][2*CPL]
   double *redd = reinterpret_cast<double *>(smem + P.off_redd);  // [2][WARPS][2]
   double *blks = reinterpret_cast<double *>(smem + P.off_blk);   // [G][2]
@@ -132,7 +97,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   const CT ivc = col ? ldg_ct<CT>(a.ivar_ct, lane) : CT(0);
   const CT tbc = col ? ldg_ct<CT>(a.tb_ct, lane) : CT(0);
 
-  for (int c = tid; c < CPL; c += blockDim.x) tbs[c] = c < p ? ldg_ct<CT>(a.tb_ct, c) : CT(0);
   for (int e = tid; e < CPL * CPL; e += blockDim.x) {
     const int r = e / CPL, c = e - r * CPL;
     const bool in = r < p && c < p;
@@ -143,11 +107,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   for (int i = blockIdx.x; i < a.B; i += gridDim.x) {
     const int32_t *u = a.u + (int64_t)i * m;
     __syncthreads();  // the previous particle is finished with shared memory
-    // 1. gather the covariates of x_{u_j} (16-byte copies), zero invalid rows
-    for (int t = tid; t < m * P.nvec; t += blockDim.x) {
-      const int j = t / P.nvec, q = t - j * P.nvec;
+    // 1. gather x_{u_j} and the row's constants at the centre (its tail) with 16-byte copies;
+    // invalid indices are flagged and their rows zeroed
+    constexpr int NTV = (int)sizeof(RowC<CT>) / 16;
+    const int nvr = P.nvec + NTV;
+    for (int t = tid; t < m * nvr; t += blockDim.x) {
+      const int j = t / nvr, q = t - j * nvr;
       const int k = u[j];
-      unsigned char *dst = rows + (size_t)j * P.rb + 16 * q;
+      unsigned char *dst = q < P.nvec ? rows + (size_t)j * P.rb + 16 * q
+                                      : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvec);
       if (k < 0 || (int64_t)k >= a.n) {
         *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
         if (q == 0) set_err(a.st, kErrIndex);
@@ -156,27 +124,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * q);
     }
     cp_async_wait_all();
-    __syncthreads();
-    // 2. trajectory-invariant per-row constants
-    for (int j = tid; j < m; j += blockDim.x) {
-      CT x[CPL];
-      load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
-      CT eb = CT(0);
-#pragma unroll
-      for (int s = 0; s < CPL; ++s) eb = fma(x[s], tbs[s], eb);
-      const int k = u[j];
-      const bool ok = k >= 0 && (int64_t)k < a.n;
-      const CT y = ok ? (CT)__ldg(reinterpret_cast<const YT *>(Xp + (int64_t)k * S + a.Yo)) : CT(0);
-      RowC<CT> c;
-      switch (fam) {
-        case 0: c = row_consts<0, CT>(eb, y, inv_s2); break;
-        case 1: c = row_consts<1, CT>(eb, y, inv_s2); break;
-        case 2: c = row_consts<2, CT>(eb, y, inv_s2); break;
-        default: c = row_consts<3, CT>(eb, y, inv_s2); break;
-      }
-      cst[j] = c;
-    }
-    // 3. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
+    // 2. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
     CT *thg = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
     if (warp == 0) {
       const Stream smom(a.seed, kMomentum, smv, (uint32_t)i);
@@ -321,7 +269,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       buf ^= 1;
     };
 
-    // 4. trajectory (the Hamiltonian is needed by warp 0 only)
+    // 3. trajectory (the Hamiltonian is needed by warp 0 only)
     double kin0 = 0.0, lp0 = 0.0;
     if (warp == 0) {
       kin0 = kinetic();
@@ -340,7 +288,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       pass(l == a.L - 1, l == a.L - 1);
       rho += CT(0.5) * eps * gr;
     }
-    // 5. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
+    // 4. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
     if (warp == 0) {
       const double kin1 = kinetic(), lp1 = log_prior();
       const double H1 = -(temp * ell - 0.5 * temp * temp * sig + lp1) + kin1;

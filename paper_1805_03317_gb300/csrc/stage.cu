@@ -35,22 +35,25 @@ template <typename CT> __device__ __forceinline__ double ld_state(const void *p,
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
-// Packing: row k of Xp = [x_k | 0 .. | y_k | 0 ..], stride S elements (a multiple of 64 bytes); y
-// starts the 16-byte vector that follows the covariates (element Yo), so no vector holds both.
+// Packing: row k of Xp = [x_k | 0 .. | tail {c0, c1, c2, y_k} | 0 ..], stride S elements (a multiple
+// of 64 bytes). The tail starts the 16-byte vector that follows the covariates (element Yo) and
+// holds four values of the state type CT; its constants are written by k_row_consts once the
+// control-variate centre is known and are zero until then.
 // ------------------------------------------------------------------------------------------------
-template <typename E, typename YT>
-__global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const YT *y, E *Xp, int S,
+template <typename E, typename CT>
+__global__ void k_pack(const E *X, int64_t n, int p, int64_t ld, const CT *y, E *Xp, int S,
                        int Yo) {
-  constexpr int YS = sizeof(YT) / sizeof(E);
+  constexpr int YS = sizeof(CT) / sizeof(E);  // elements per state-type value
+  const int yo = Yo + 3 * YS;                 // y is the tail's fourth value
   const int64_t total = n * (int64_t)S;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = t / S;
     const int s = (int)(t - k * S);
     E v;
-    if (s >= Yo && s < Yo + YS) {
-      const YT yk = y[k];
-      v = reinterpret_cast<const E *>(&yk)[s - Yo];
+    if (s >= yo && s < yo + YS) {
+      const CT yk = y[k];
+      v = reinterpret_cast<const E *>(&yk)[s - yo];
     } else if (s < p) {
       v = X[k * ld + s];
     } else {
@@ -76,6 +79,57 @@ int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const vo
   return (int)cudaGetLastError();
 }
 
+// Per-row constants at the centre theta_bar (state type): one thread per row forms
+// eta_bar = x'theta_bar in column order and rewrites c0..c2 of the row's tail (device.cuh).
+template <typename XT, int FAM>
+__global__ void k_row_consts(XT *Xp, int64_t n, int p, int S, int Yo,
+                             const typename Store<XT>::CT *tb, typename Store<XT>::CT inv_s2) {
+  using SD = Store<XT>;
+  using CT = typename SD::CT;
+  const int nvx = Yo * (int)sizeof(XT) / 16;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    XT *row = Xp + k * S;
+    CT eb = CT(0);
+    for (int v = 0; v < nvx; ++v) {
+      CT x[SD::VEC];
+      SD::unpack(*reinterpret_cast<const uint4 *>(row + v * SD::VEC), x);
+#pragma unroll
+      for (int e = 0; e < SD::VEC; ++e) {
+        const int c = v * SD::VEC + e;
+        if (c < p) eb = fma(x[e], tb[c], eb);
+      }
+    }
+    RowC<CT> *tl = reinterpret_cast<RowC<CT> *>(row + Yo);
+    *tl = row_consts<FAM, CT>(eb, tl->y, inv_s2);
+  }
+}
+
+template <typename XT>
+int launch_row_consts(XT *Xp, int64_t n, int p, int S, int Yo, int fam, const void *tb,
+                      double inv_s2, cudaStream_t s) {
+  using CT = typename Store<XT>::CT;
+  const int64_t need = (n + 255) / 256;
+  const int grid = (int)(need < 152 * 16 ? need : 152 * 16);
+  const CT *t = (const CT *)tb;
+  const CT i2 = (CT)inv_s2;
+  switch (fam) {
+    case 0: k_row_consts<XT, 0><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
+    case 1: k_row_consts<XT, 1><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
+    case 2: k_row_consts<XT, 2><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
+    default: k_row_consts<XT, 3><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+int row_consts(void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, const void *tb_ct,
+               double inv_s2, cudaStream_t s) {
+  if (n <= 0) return 0;
+  if (x_dtype == 0) return launch_row_consts<double>((double *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
+  if (x_dtype == 1) return launch_row_consts<float>((float *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
+  return launch_row_consts<__nv_bfloat16>((__nv_bfloat16 *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Control-variate moments at theta (Sec. 3.2): A = sum_k l_k, B = sum_k l'_k x_k,
 // C = sum_k l''_k x_k x_k'. Rows go through shared memory in tiles of 32: one lane per row forms
@@ -99,8 +153,7 @@ __device__ __forceinline__ double packed_x<__nv_bfloat16>(const __nv_bfloat16 *r
   return (double)__bfloat162float(row[slot]);
 }
 template <typename XT> __device__ __forceinline__ double packed_y(const XT *row, int Yo) {
-  if (sizeof(XT) == 8) return *reinterpret_cast<const double *>(row + Yo);
-  return (double)*reinterpret_cast<const float *>(row + Yo);
+  return (double)reinterpret_cast<const RowC<typename Store<XT>::CT> *>(row + Yo)->y;
 }
 
 template <typename XT, int MAXQ>
