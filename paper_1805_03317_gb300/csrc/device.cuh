@@ -135,11 +135,14 @@ template <typename CT> __device__ __forceinline__ CT sigmoid_(CT x) {
   return x >= CT(0) ? CT(1) / (CT(1) + exp(-x)) : exp(x) / (CT(1) + exp(x));
 }
 
-// e^D - 1 - D - D^2/2 (k0 = 3) or e^D - 1 - D (k0 = 2) by the Taylor series of exp for |D| <= 1/2,
-// directly from expm1 otherwise.
+// e^D - 1 - D - D^2/2 (k0 = 3) or e^D - 1 - D (k0 = 2) by the Taylor series of exp for |D| <= 1
+// (FP32; 1/2 in FP64), directly from expm1 otherwise.
 template <typename CT, int K0> __device__ __forceinline__ CT exp_tail(CT D) {
-  if (fabs(D) <= CT(0.5)) {
-    constexpr int NT = sizeof(CT) == 8 ? 19 : 10;  // terms k0 .. k0+NT-1; remainder < ulp
+  constexpr CT kMax = sizeof(CT) == 8 ? CT(0.5) : CT(1);
+  if (fabs(D) <= kMax) {
+    // terms k0 .. k0+NT-1: the remainder is below 1e-17 (FP64, |D| <= 1/2) or 1e-9 (FP32,
+    // |D| <= 1) relative to the first term
+    constexpr int NT = sizeof(CT) == 8 ? 19 : 10;
     // s = sum_{j>=0} D^j k0!/(k0+j)!, by Horner with the constant reciprocals 1/k
     CT s = CT(1);
 #pragma unroll
@@ -256,8 +259,9 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
     }
     d = -L1 + sb * D + CT(0.5) * w * D * D;
   } else if (FAM == 2) {  // Poisson: d = -e^eb tail3(D), r = -e^eb tail2(D)
-    d = -c.c0 * exp_tail<CT, 3>(D);
-    r = -c.c0 * exp_tail<CT, 2>(D);
+    const CT t3 = exp_tail<CT, 3>(D);  // e^D - 1 - D - D^2/2; e^D - 1 - D = t3 + D^2/2
+    d = -c.c0 * t3;
+    r = -c.c0 * fma(CT(0.5) * D, D, t3);
   } else if (FAM == 3) {  // Gaussian, known sd: the expansion is exact; evaluated as written
     const CT res = c.c0;
     const CT dl = (CT(2) * res * D - D * D) * (CT(0.5) * inv_s2);  // l(eta) - l(eta_bar)
@@ -319,6 +323,45 @@ template <typename V> __device__ __forceinline__ V warp_max(V v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// Per-lane sums over CPL element slots. FP32 uses the packed two-wide FMA of sm_100+ (__ffma2_rn:
+// two independent round-to-nearest FMAs per instruction), halving the FMA instruction count.
+template <int CPL>
+__device__ __forceinline__ float dot_slots(const float *x, const float *y) {
+  static_assert(CPL % 2 == 0, "pairs of slots");
+  float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < CPL; e += 4) {
+    a = __ffma2_rn(make_float2(x[e], x[e + 1]), make_float2(y[e], y[e + 1]), a);
+    if (e + 2 < CPL) b = __ffma2_rn(make_float2(x[e + 2], x[e + 3]), make_float2(y[e + 2], y[e + 3]), b);
+  }
+  return (a.x + b.x) + (a.y + b.y);
+}
+template <int CPL>
+__device__ __forceinline__ double dot_slots(const double *x, const double *y) {
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int e = 0; e < CPL; e += 2) {
+    a = fma(x[e], y[e], a);
+    if (e + 1 < CPL) b = fma(x[e + 1], y[e + 1], b);
+  }
+  return a + b;
+}
+// acc[s] += t * x[s] over the slots
+template <int CPL> __device__ __forceinline__ void axpy_slots(float t, const float *x, float *acc) {
+  const float2 tt = make_float2(t, t);
+#pragma unroll
+  for (int e = 0; e < CPL; e += 2) {
+    const float2 r = __ffma2_rn(tt, make_float2(x[e], x[e + 1]), make_float2(acc[e], acc[e + 1]));
+    acc[e] = r.x;
+    acc[e + 1] = r.y;
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void axpy_slots(double t, const double *x, double *acc) {
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) acc[e] = fma(t, x[e], acc[e]);
 }
 
 // Reduce-scatter of K values per lane over lane groups of size 2*O (recursive halving at offsets

@@ -5,8 +5,9 @@
 namespace subsmc {
 namespace {
 using XT = __nv_bfloat16;
-const Tile kTiles[] = {{1, 8, 3, 4}, {2, 8, 3, 4}, {4, 8, 2, 4}, {2, 16, 2, 4}, {4, 16, 2, 4},
-                       {8, 8, 2, 4}, {8, 8, 3, 4}, {8, 16, 2, 4}, {16, 8, 2, 4}};
+const Tile kTiles[] = {{1, 8, 3, 4, 0}, {2, 8, 3, 4, 0}, {4, 8, 2, 4, 0}, {2, 16, 2, 4, 0},
+                       {4, 16, 2, 4, 0}, {8, 8, 2, 4, 0}, {8, 8, 3, 4, 0}, {8, 16, 2, 4, 0},
+                       {16, 8, 2, 4, 0}, {4, 8, 3, 4, 1}, {4, 16, 3, 4, 1}, {8, 8, 3, 4, 1}};
 }  // namespace
 
 int est_tiles_bf16(Tile *out, int cap) {
@@ -26,6 +27,9 @@ int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s) {
     case 6: return launch_tile<XT, 8, 8, 3, 4>(op, a, s);
     case 7: return launch_tile<XT, 8, 16, 2, 4>(op, a, s);
     case 8: return launch_tile<XT, 16, 8, 2, 4>(op, a, s);
+    case 9: return launch_tile<XT, 4, 8, 3, 4, true>(op, a, s);
+    case 10: return launch_tile<XT, 4, 16, 3, 4, true>(op, a, s);
+    case 11: return launch_tile<XT, 8, 8, 3, 4, true>(op, a, s);
     default: return -1;
   }
 }

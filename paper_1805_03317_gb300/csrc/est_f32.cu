@@ -5,8 +5,8 @@
 namespace subsmc {
 namespace {
 using XT = float;
-const Tile kTiles[] = {{1, 4, 3, 4}, {2, 4, 3, 4}, {4, 4, 2, 4}, {2, 8, 2, 4}, {8, 4, 2, 4},
-                       {4, 8, 2, 4}, {8, 8, 2, 4}};
+const Tile kTiles[] = {{1, 4, 3, 4, 0}, {2, 4, 3, 4, 0}, {4, 4, 2, 4, 0}, {2, 8, 2, 4, 0},
+                       {8, 4, 2, 4, 0}, {4, 8, 2, 4, 0}, {8, 8, 2, 4, 0}};
 }  // namespace
 
 int est_tiles_f32(Tile *out, int cap) {
@@ -29,8 +29,8 @@ int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s) {
 }
 
 namespace {
-const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
-                          {1, 24, 1, 8}};
+const Tile kResTiles[] = {{1, 8, 1, 4, 0}, {1, 16, 1, 4, 0}, {1, 24, 1, 4, 0}, {1, 32, 1, 4, 0},
+                          {1, 16, 1, 8, 0}, {1, 24, 1, 8, 0}};
 }  // namespace
 
 int res_tiles_f32(Tile *out, int cap) {

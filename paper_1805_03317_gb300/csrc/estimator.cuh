@@ -42,12 +42,13 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // slots. So the family terms are evaluated once per row, not once per lane of the row.
 //
 // Rows reach the lanes through a per-warp ring of NST sweeps in shared memory, filled by 16-byte
-// cp.async copies issued NST-1 sweeps ahead (the row indices one sweep further ahead still). Each
-// lane copies exactly what it later reads (its covariate chunks of the group's rows and the tail of
-// its own row), so the ring needs no barrier, only the lane's own cp.async group accounting.
+// cp.async copies issued NST-1 sweeps ahead (the row indices one sweep further ahead still). The
+// lanes of a group copy a row's vectors contiguously (coalesced): covariate chunks into their own
+// ring slots, the tail vector into the tail slot of the row's owner, which reads it after a warp
+// barrier. (When the tiles' chunks end before the tail, the owner copies its tail itself.)
 // Chunk vectors are XOR-swizzled so that 128-bit reads of 8 consecutive lanes hit distinct bank
 // groups; chunk vectors that lie past the covariates are never copied and stay zero.
-template <typename XT, int T, int CPL, int NST>
+template <typename XT, int T, int CPL, int NST, bool PIPE = false>
 struct WarpEval {
   using SD = Store<XT>;
   using CT = typename SD::CT;
@@ -64,6 +65,8 @@ struct WarpEval {
   CT dl[CPL];
   int lane, gl, gb, swz, tail_off;
   unsigned cmask;        // bit v: chunk vector v of this lane holds covariates (is copied)
+  unsigned tmask;        // bit v: chunk vector v of this lane is a tail vector (copied to the tail slot)
+  bool tail_in_chunks;   // the tail vectors fall inside the group's chunks (else owners copy them)
   unsigned char *ring;
 
   // ring: this warp's RING bytes (16-byte aligned). Yo: element at which the row's tail starts.
@@ -75,10 +78,14 @@ struct WarpEval {
     ring = ring_;
     tail_off = Yo * (int)sizeof(XT);
     const int nvx = tail_off / 16;
-    cmask = 0u;
+    tail_in_chunks = nvx + TB / 16 <= T * NV;
+    cmask = tmask = 0u;
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (gl * NV + v < nvx) cmask |= 1u << v;
+    for (int v = 0; v < NV; ++v) {
+      const int vi = gl * NV + v;
+      if (vi < nvx) cmask |= 1u << v;
+      else if (tail_in_chunks && vi < nvx + TB / 16) tmask |= 1u << v;
+    }
     for (int st = 0; st < NST; ++st)
 #pragma unroll
       for (int t = 0; t < T; ++t)
@@ -90,9 +97,10 @@ struct WarpEval {
   __device__ __forceinline__ unsigned char *chunk(int st, int t, int v) const {
     return ring + st * STAGE + ((t * 32 + lane) * NV + (v ^ swz)) * 16;
   }
-  __device__ __forceinline__ unsigned char *tail(int st) const {
-    return ring + st * STAGE + XBYTES + lane * TB;
+  __device__ __forceinline__ unsigned char *tail(int st, int q) const {
+    return ring + st * STAGE + XBYTES + q * TB;
   }
+  __device__ __forceinline__ unsigned char *tail(int st) const { return tail(st, lane); }
   // Slot s of this lane is element (column) gl*CPL + s of a packed row.
   __device__ __forceinline__ void load_slots(const CT *vec, int p, CT *dst) const {
 #pragma unroll
@@ -133,17 +141,27 @@ struct WarpEval {
         } else {
           bad &= ~(1u << b);
         }
-        const unsigned char *row = reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S);
+        if (!tail_in_chunks) {  // the owner fetches its row's tail itself (uncoalesced)
+          const unsigned char *row = reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S);
 #pragma unroll
-        for (int q = 0; q < TB / 16; ++q) cp_async16(tail(b) + 16 * q, row + tail_off + 16 * q);
+          for (int q = 0; q < TB / 16; ++q) cp_async16(tail(b) + 16 * q, row + tail_off + 16 * q);
+        }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
           const int kt = __shfl_sync(0xffffffffu, k, gb + t);
           const unsigned char *src =
               reinterpret_cast<const unsigned char *>(Xp + (int64_t)kt * S) + gl * (NV * 16);
+          // the group's lanes read the row's vectors contiguously: covariate chunks go to this
+          // lane's ring slots, tail vectors to the tail slot of the row's owner
 #pragma unroll
-          for (int v = 0; v < NV; ++v)
-            if ((cmask >> v) & 1u) cp_async16(chunk(b, t, v), src + 16 * v);
+          for (int v = 0; v < NV; ++v) {
+            if (((cmask | tmask) >> v) & 1u) {  // one copy instruction for the whole group
+              unsigned char *dst = ((cmask >> v) & 1u)
+                                       ? chunk(b, t, v)
+                                       : tail(b, gb + t) + (gl * NV + v) * 16 - tail_off;
+              cp_async16(dst, src + 16 * v);
+            }
+          }
         }
       }
       cp_async_commit();  // one group per sweep (empty past the end) keeps the counting uniform
@@ -152,21 +170,13 @@ struct WarpEval {
       for (int h = lane; h < 2 * G; h += 32) blk_out[h] = 0.0;  // blocks with no rows stay zero
       __syncwarp();
     }
-    fetch(0);
-#pragma unroll
-    for (int q = 0; q < NST - 1; ++q) {
-      issue(q);
-      fetch(q + 1);
-    }
     CT sd = CT(0), sd2 = CT(0);
     double cs = 0.0, cq = 0.0;  // BLOCKS: sums of the open block cg
     int cg = -1;
     Ssum = Qsum = 0.0;
-    for (int s = 0; s < nsw; ++s) {
-      issue(s + NST - 1);
-      fetch(s + NST);
-      cp_async_wait<NST - 1>();  // this lane's copies of sweep s have landed
-      const int b = s % NST;
+    // partial x'delta of the group's T rows over this lane's slots, reduce-scattered: the full D of
+    // the row this lane owns
+    auto phase1 = [&](int b) -> CT {
       CT pd[T];
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -174,48 +184,25 @@ struct WarpEval {
 #pragma unroll
         for (int v = 0; v < NV; ++v)
           SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
-        CT q0 = CT(0), q1 = CT(0);
-#pragma unroll
-        for (int e = 0; e < CPL; e += 2) {
-          q0 = fma(x[e], dl[e], q0);
-          if (e + 1 < CPL) q1 = fma(x[e + 1], dl[e + 1], q1);
-        }
-        pd[t] = q0 + q1;
+        pd[t] = dot_slots<CPL>(x, dl);
       }
       int base = 0;
-      reduce_scatter<T, T / 2, CT>(pd, lane, base);  // pd[0]: D of the row this lane owns
+      reduce_scatter<T, T / 2, CT>(pd, lane, base);
+      return pd[0];
+    };
+    // d and r of the owned row of sweep s (stage b) at D, masked past the end; sums of d, d^2
+    auto terms = [&](int s, int b, CT D, CT &d, CT &r) {
       const RowC<CT> c = *reinterpret_cast<const RowC<CT> *>(tail(b));
-      CT d, r;
       switch (fam) {
-        case 0: row_incr<0, CT>(c, pd[0], inv_s2, d, r); break;
-        case 1: row_incr<1, CT>(c, pd[0], inv_s2, d, r); break;
-        case 2: row_incr<2, CT>(c, pd[0], inv_s2, d, r); break;
-        default: row_incr<3, CT>(c, pd[0], inv_s2, d, r); break;
+        case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
+        case 1: row_incr<1, CT>(c, D, inv_s2, d, r); break;
+        case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
+        default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
       }
       const int j = (s << 5) + lane;
       if (j >= nrows || ((bad >> b) & 1u)) {
         d = CT(0);
         r = CT(0);
-      }
-      if (GRAD) {
-        // the chunks are read again rather than kept: holding T rows of covariates across the
-        // family terms would cost T*CPL registers
-        asm volatile("" ::: "memory");
-        const CT dr = d * r;
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-          const CT rt = __shfl_sync(0xffffffffu, r, gb + t);
-          const CT drt = __shfl_sync(0xffffffffu, dr, gb + t);
-          CT x[CPL];
-#pragma unroll
-          for (int v = 0; v < NV; ++v)
-            SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
-#pragma unroll
-          for (int e = 0; e < CPL; ++e) {
-            g1[e] = fma(rt, x[e], g1[e]);
-            g2[e] = fma(drt, x[e], g2[e]);
-          }
-        }
       }
       if (BLOCKS) {  // block of row j: largest g with floor(g nrows / G) <= j
         const int r1 = min((s << 5) + 31, nrows - 1);
@@ -242,6 +229,69 @@ struct WarpEval {
       } else {
         sd += d;
         sd2 = fma(d, d, sd2);
+      }
+    };
+    // gradient partials over this lane's slots: all-gather r, d r of the group's rows
+    auto phase2 = [&](int b, CT r, CT dr) {
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const CT rt = __shfl_sync(0xffffffffu, r, gb + t);
+        const CT drt = __shfl_sync(0xffffffffu, dr, gb + t);
+        CT x[CPL];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
+        axpy_slots<CPL>(rt, x, g1);
+        axpy_slots<CPL>(drt, x, g2);
+      }
+    };
+    fetch(0);
+#pragma unroll
+    for (int q = 0; q < NST - 1; ++q) {
+      issue(q);
+      fetch(q + 1);
+    }
+    if constexpr (PIPE) {
+      // Software pipelined: iteration s evaluates the terms of sweep s, then runs the partial
+      // x'delta of sweep s+1 and the gradient partials of sweep s side by side (independent
+      // instruction streams for the scheduler). Needs NST >= 3: stages of s and s+1 are read while
+      // s+NST-1 is in flight.
+      static_assert(!PIPE || NST >= 3, "pipelined sweeps need three ring stages");
+      CT Dc = CT(0);
+      if (nsw > 0) {
+        cp_async_wait<NST - 2>();  // sweep 0 has landed
+        if (tail_in_chunks) __syncwarp();  // tails were copied by other lanes of the group
+        Dc = phase1(0);
+      }
+      for (int s = 0; s < nsw; ++s) {
+        const int b = s % NST;
+        issue(s + NST - 1);
+        fetch(s + NST);
+        CT d, r;
+        terms(s, b, Dc, d, r);
+        cp_async_wait<NST - 2>();  // sweep s+1 has landed
+        if (tail_in_chunks) __syncwarp();
+        CT Dn = CT(0);
+        if (s + 1 < nsw) Dn = phase1((s + 1) % NST);
+        if (GRAD) phase2(b, r, d * r);
+        Dc = Dn;
+      }
+    } else {
+      for (int s = 0; s < nsw; ++s) {
+        issue(s + NST - 1);
+        fetch(s + NST);
+        cp_async_wait<NST - 1>();  // this lane's copies of sweep s have landed
+        if (tail_in_chunks) __syncwarp();  // tails were copied by other lanes of the group
+        const int b = s % NST;
+        const CT D = phase1(b);
+        CT d, r;
+        terms(s, b, D, d, r);
+        if (GRAD) {
+          // the chunks are read again rather than held across the family terms (that would
+          // cost T*CPL registers)
+          asm volatile("" ::: "memory");
+          phase2(b, r, d * r);
+        }
       }
     }
     cp_async_wait<0>();
@@ -288,8 +338,8 @@ template <typename CT> __device__ __forceinline__ CT ldg_ct(const void *p, int i
 // One evaluation of the estimator for the warp's particle at theta (in sm.th / sm.dl).
 // Reads rows of idx[0..m); GRAD: writes the target gradient to sm.g; BLOCKS: writes per-block
 // (sum d, sum d^2) to blk_out[G*2]. Returns l_hat and sigma2_hat on every lane.
-template <typename XT, int T, int CPL, int U, bool GRAD, bool BLOCKS>
-__device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U> &W, const EstArgs &a,
+template <typename XT, int T, int CPL, int U, bool K, bool GRAD, bool BLOCKS>
+__device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &W, const EstArgs &a,
                                               const int32_t *idx, WarpSmem<typename Store<XT>::CT> &sm,
                                               double temp, double *blk_out, double &ell,
                                               double &sig2) {
@@ -356,8 +406,8 @@ template <typename CT> __device__ __forceinline__ double log_prior_warp(const Es
 }
 
 // sm.dl = theta - theta_bar, and the lane slots of the evaluator
-template <typename XT, int T, int CPL, int U>
-__device__ __forceinline__ void refresh_delta(WarpEval<XT, T, CPL, U> &W, const EstArgs &a,
+template <typename XT, int T, int CPL, int U, bool K>
+__device__ __forceinline__ void refresh_delta(WarpEval<XT, T, CPL, U, K> &W, const EstArgs &a,
                                               WarpSmem<typename Store<XT>::CT> &sm) {
   using CT = typename Store<XT>::CT;
   for (int c = W.lane; c < a.p; c += 32) sm.dl[c] = sm.th[c] - ldg_ct<CT>(a.tb_ct, c);
@@ -368,18 +418,18 @@ __device__ __forceinline__ void refresh_delta(WarpEval<XT, T, CPL, U> &W, const 
 // ------------------------------------------------------------------------------------------------
 // Kernel 1: the plain estimator on caller particles (loglik_est / loglik_grad, cache refresh).
 // ------------------------------------------------------------------------------------------------
-template <typename XT, int T, int CPL, int U, int WARPS>
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
 __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
   using CT = typename Store<XT>::CT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * WARPS + warp;
   if (i >= a.B) return;  // whole warp leaves together; no block-level barriers follow
-  WarpEval<XT, T, CPL, U> W;
+  WarpEval<XT, T, CPL, U, K> W;
   const int slots = T * CPL;
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
   W.init(wbase, a.Yo);
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), a.p, slots);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), a.p, slots);
   const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * a.p;
   for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
   __syncwarp();
@@ -390,16 +440,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
   double *blk = a.blk ? a.blk + (int64_t)i * a.G * 2 : nullptr;
   if (a.grad) {
     if (blk)
-      eval_particle<XT, T, CPL, U, true, true>(W, a, idx, sm, temp, blk, ell, sig2);
+      eval_particle<XT, T, CPL, U, K, true, true>(W, a, idx, sm, temp, blk, ell, sig2);
     else
-      eval_particle<XT, T, CPL, U, true, false>(W, a, idx, sm, temp, nullptr, ell, sig2);
+      eval_particle<XT, T, CPL, U, K, true, false>(W, a, idx, sm, temp, nullptr, ell, sig2);
     CT *g = reinterpret_cast<CT *>(a.grad) + (int64_t)i * a.p;
     for (int c = W.lane; c < a.p; c += 32) g[c] = sm.g[c];
   } else {
     if (blk)
-      eval_particle<XT, T, CPL, U, false, true>(W, a, idx, sm, temp, blk, ell, sig2);
+      eval_particle<XT, T, CPL, U, K, false, true>(W, a, idx, sm, temp, blk, ell, sig2);
     else
-      eval_particle<XT, T, CPL, U, false, false>(W, a, idx, sm, temp, nullptr, ell, sig2);
+      eval_particle<XT, T, CPL, U, K, false, false>(W, a, idx, sm, temp, nullptr, ell, sig2);
   }
   if (W.lane == 0) {
     if (a.ell) a.ell[i] = ell;
@@ -415,18 +465,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
 // control-variate total sum_k q_k(theta) is common to both estimates it cancels in the ratio:
 //   log r = a (n/m)(S_g* - S_g) - (a^2/2)(sigma2* - sigma2).
 // ------------------------------------------------------------------------------------------------
-template <typename XT, int T, int CPL, int U, int WARPS>
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
 __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   using CT = typename Store<XT>::CT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * WARPS + warp;
   if (i >= a.B) return;
-  WarpEval<XT, T, CPL, U> W;
+  WarpEval<XT, T, CPL, U, K> W;
   const int slots = T * CPL;
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
   W.init(wbase, a.Yo);
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), a.p, slots);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), a.p, slots);
   const uint32_t smv = stage_move(a.stage, a.move);
   const Stream sblk(a.seed, kUpmBlock, smv, (uint32_t)i);
   const Stream sidx(a.seed, kUpmIdx, smv, (uint32_t)i);
@@ -487,19 +537,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
 // then accept with probability min(1, exp(H0 - H1)), H = -log target + rho'Sigma rho / 2 (FP64).
 // On acceptance theta, l_hat, sigma2_hat and the block sums at the end point replace the cache.
 // ------------------------------------------------------------------------------------------------
-template <typename XT, int T, int CPL, int U, int WARPS>
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
 __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   using CT = typename Store<XT>::CT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * WARPS + warp;
   if (i >= a.B) return;
-  WarpEval<XT, T, CPL, U> W;
+  WarpEval<XT, T, CPL, U, K> W;
   const int slots = T * CPL;
   const int p = a.p;
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(p);
   W.init(wbase, a.Yo);
-  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U>::RING), p, slots);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), p, slots);
   const uint32_t smv = stage_move(a.stage, a.move);
   const double temp = a.st->a;
   const CT eps = (CT)a.st->eps;
@@ -528,7 +578,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   refresh_delta(W, a, sm);
   const int32_t *idx = a.u + (int64_t)i * a.m;
   double ell0, sig0;
-  eval_particle<XT, T, CPL, U, true, false>(W, a, idx, sm, temp, nullptr, ell0, sig0);
+  eval_particle<XT, T, CPL, U, K, true, false>(W, a, idx, sm, temp, nullptr, ell0, sig0);
   const double H0 = -(temp * ell0 - 0.5 * temp * temp * sig0 + log_prior_warp<CT>(a, sm.th)) + kin0;
   double ell1 = ell0, sig1 = sig0;
   double *bprop = a.blk_prop + (int64_t)i * a.G * 2;
@@ -545,9 +595,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
     __syncwarp();
     refresh_delta(W, a, sm);
     if (l == a.L - 1)
-      eval_particle<XT, T, CPL, U, true, true>(W, a, idx, sm, temp, bprop, ell1, sig1);
+      eval_particle<XT, T, CPL, U, K, true, true>(W, a, idx, sm, temp, bprop, ell1, sig1);
     else
-      eval_particle<XT, T, CPL, U, true, false>(W, a, idx, sm, temp, nullptr, ell1, sig1);
+      eval_particle<XT, T, CPL, U, K, true, false>(W, a, idx, sm, temp, nullptr, ell1, sig1);
     for (int c = W.lane; c < p; c += 32) sm.rho[c] += CT(0.5) * eps * sm.g[c];
     __syncwarp();
   }
@@ -571,7 +621,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
 // ------------------------------------------------------------------------------------------------
 // Launch helpers
 // ------------------------------------------------------------------------------------------------
-template <typename XT, int T, int CPL, int U, int WARPS>
+template <typename XT, int T, int CPL, int U, int WARPS, bool K = false>
 inline int launch_tile(int op, const EstArgs &a, cudaStream_t s) {
   using CT = typename Store<XT>::CT;
   const size_t smem = (size_t)WARPS * warp_smem_bytes<XT, T, CPL, U>(a.p);
@@ -579,17 +629,17 @@ inline int launch_tile(int op, const EstArgs &a, cudaStream_t s) {
   if (a.B <= 0) return 0;
   cudaError_t e;
   if (op == 0) {
-    e = cudaFuncSetAttribute(k_estimate<XT, T, CPL, U, WARPS>,
+    e = cudaFuncSetAttribute(k_estimate<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k_estimate<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    if (e == cudaSuccess) k_estimate<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
   } else if (op == 1) {
-    e = cudaFuncSetAttribute(k_upm<XT, T, CPL, U, WARPS>,
+    e = cudaFuncSetAttribute(k_upm<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k_upm<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    if (e == cudaSuccess) k_upm<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
   } else {
-    e = cudaFuncSetAttribute(k_hmc<XT, T, CPL, U, WARPS>,
+    e = cudaFuncSetAttribute(k_hmc<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) k_hmc<XT, T, CPL, U, WARPS><<<grid, block, smem, s>>>(a);
+    if (e == cudaSuccess) k_hmc<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
   }
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();

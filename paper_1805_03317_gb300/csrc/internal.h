@@ -68,9 +68,10 @@ struct EstArgs {
 };
 
 // Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots; NST
-// stages of streamed rows in flight per warp (resident kernel: unused); warps per CTA.
+// ring stages of streamed rows per warp (resident kernel: unused); warps per CTA; pipe: the
+// streamed kernels overlap the gradient partials of one sweep with x'delta of the next (NST >= 3).
 struct Tile {
-  int T, CPL, NST, warps;
+  int T, CPL, NST, warps, pipe;
 };
 
 // Launchers, one set per storage type (defined in est_f64.cu, est_f32.cu, est_bf16.cu).

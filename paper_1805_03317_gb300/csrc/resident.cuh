@@ -171,15 +171,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       for (int j = warp * 32 + lane; j < m; j += WARPS * 32) {
         CT x[CPL];
         load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
-        CT q0 = CT(0), q1 = CT(0), q2 = CT(0), q3 = CT(0);
-#pragma unroll
-        for (int s = 0; s < CPL; s += 4) {
-          q0 = fma(x[s], dr[s], q0);
-          if (s + 1 < CPL) q1 = fma(x[s + 1], dr[s + 1], q1);
-          if (s + 2 < CPL) q2 = fma(x[s + 2], dr[s + 2], q2);
-          if (s + 3 < CPL) q3 = fma(x[s + 3], dr[s + 3], q3);
-        }
-        const CT D = (q0 + q1) + (q2 + q3);
+        const CT D = dot_slots<CPL>(x, dr);
         const RowC<CT> c = cst[j];
         CT d, r;
         switch (fam) {
@@ -188,12 +180,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
           case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
           default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
         }
-        const CT drr = d * r;
-#pragma unroll
-        for (int s = 0; s < CPL; ++s) {
-          v[s] = fma(r, x[s], v[s]);
-          v[CPL + s] = fma(drr, x[s], v[CPL + s]);
-        }
+        axpy_slots<CPL>(r, x, v);
+        axpy_slots<CPL>(d * r, x, v + CPL);
         sd += d;
         sd2 = fma(d, d, sd2);
         if (final) dv[j] = d;

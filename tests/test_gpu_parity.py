@@ -49,7 +49,7 @@ def _check_estimates(x_dtype, got, ref):
 
 @pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("family", ["logistic", "poisson", "gaussian", "probit"])
-@pytest.mark.parametrize("hint", range(0, 10))
+@pytest.mark.parametrize("hint", range(0, 13))
 def test_estimator_and_gradient_match_oracle(family, x_dtype, hint):
     wl = _wl(family, x_dtype)
     try:
