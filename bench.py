@@ -50,6 +50,12 @@ def parse():
                     help="run only the HBM-bound gather leg and print its JSON (for profiling)")
     ap.add_argument("--gather-tile", type=int, default=0,
                     help="estimator tile hint for the gather leg (0: autotune)")
+    ap.add_argument("--no-gam", action="store_true",
+                    help="skip the GAM gather leg (n=1e7, p=101; about 10-30 s of data generation)")
+    ap.add_argument("--gam-n", type=int, default=10_000_000,
+                    help="rows of the GAM workload (smaller for profiling captures)")
+    ap.add_argument("--gam-only", action="store_true",
+                    help="run only the GAM gather leg and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -211,17 +217,20 @@ def full_run(S, wl, dev, R, max_stages=400):
             "post_mean_minus_mode_maxabs": float(np.max(np.abs(mean - tb)))}
 
 
-def gather_leg(S, dev, hbm, reps=20, stages=3, tile_hint=0):
-    """HBM-bound leg: Poisson regression, n = 5e6, p = 50, BF16 X (560 MB packed, far above L2),
-    N = 8192, m = 2000. Times the subsampled estimator with gradient over all particles (one gather
-    of N*m rows per call, the streamed kernel) and a few full SMC stages, whose 112 KB x 2000 rows
-    per particle do not fit in shared memory (streamed HMC kernel)."""
+def gather_leg(S, dev, hbm, wl=None, reps=20, stages=3, tile_hint=0):
+    """HBM-bound leg. Default workload: Poisson regression, n = 5e6, p = 50, BF16 X (640 MB packed,
+    far above L2), N = 8192, m = 2000 (the GAM workload, n = 1e7, p = 101, is the other one). Times
+    the subsampled estimator with gradient over all particles (one gather of N*m rows per call, the
+    streamed kernel; X is larger than L2, so no flush is needed between calls) and a few full SMC
+    stages, whose rows per particle do not fit in shared memory (streamed HMC kernel)."""
     import torch
-    from smc_workloads import poisson_5e6
-    wl = poisson_5e6("bf16", upcast=False)
+    if wl is None:
+        from smc_workloads import poisson_5e6
+        wl = poisson_5e6("bf16", upcast=False)
     X, y = device_workload(wl, dev)
-    ctx = S.smc_init(X, y, "poisson", wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
-                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None, tile_hint=tile_hint)
+    ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
+                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None, tile_hint=tile_hint,
+                     noise_sigma=wl.sigma)
     del X, y
     tile = S.smc_autotune(ctx) if tile_hint == 0 else (tile_hint, 1)
     theta, u, _ = S.smc_get_particles(ctx)
@@ -250,8 +259,10 @@ def gather_leg(S, dev, hbm, reps=20, stages=3, tile_hint=0):
     S.smc_free(ctx)
     achieved = bytes_call / (per_call / 1e3) / 1e9
     hmc_bytes = (wl.L + 1) * bytes_call
-    return {"workload": f"poisson n={wl.n} p={wl.p} N={wl.N} m={wl.m} G={wl.G} L={wl.L} "
-                        f"R={wl.R} X=bf16 (packed X 560 MB > L2)",
+    esz = 2
+    row_b = ((wl.p * esz + 15) // 16 * 16 + 16 + 63) // 64 * 64
+    return {"workload": f"{wl.family} n={wl.n} p={wl.p} N={wl.N} m={wl.m} G={wl.G} L={wl.L} "
+                        f"R={wl.R} X=bf16 (packed X {wl.n * row_b / 1e6:.0f} MB > L2)",
             "tile": tile,
             "estimator": {"kernel": "k_estimate (loglik_grad over all particles)",
                           "ms_per_call": per_call, "bytes_per_call": bytes_call,
@@ -261,6 +272,18 @@ def gather_leg(S, dev, hbm, reps=20, stages=3, tile_hint=0):
                       "grad_evals_per_s": wl.N * wl.m * wl.R * (wl.L + 1) / (ms_stage / 1e3),
                       "hmc_ms_per_launch": ms_h / max(n_h, 1),
                       "hmc_achieved_gbs": hmc_bytes / (ms_h / max(n_h, 1) / 1e3) / 1e9}}
+
+
+def gam_leg(S, dev, hbm, tile_hint=0, n=10_000_000):
+    """The GAM workload (Gaussian response, sigma = 0.5, n = 1e7, p = 101 B-spline columns, BF16;
+    N = 16384, m = 5000, L = 25) through the gather leg: 82M gathered rows per estimator call."""
+    from smc_workloads import gam_1e7
+    t0 = time.perf_counter()
+    wl = gam_1e7("bf16", n=n, upcast=False)
+    gen_s = time.perf_counter() - t0
+    out = gather_leg(S, dev, hbm, wl=wl, reps=10, stages=1, tile_hint=tile_hint)
+    out["data_generation_s"] = round(gen_s, 1)
+    return out
 
 
 def e2e_stages(S, ctx, wl, R, steps):
@@ -343,6 +366,9 @@ def gpu_arm(args):
     gather = None
     if not args.no_gather and rank == 0:
         gather = gather_leg(S, dev, hbm)
+    gam = None
+    if not args.no_gam and rank == 0:
+        gam = gam_leg(S, dev, hbm, n=args.gam_n)
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -386,6 +412,7 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": bo},
         "fp32_storage": fp32,
         "hbm_gather_leg": gather,
+        "gam_gather_leg": gam,
         "smc_wall_time": walls,
         "cpu_baseline": cpu,
         "wall_s_timed": wall,
@@ -508,6 +535,12 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps(gather_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0),
                                     peaks()[0], tile_hint=args.gather_tile)), flush=True)
+        return
+    if args.gam_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(gam_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0),
+                                 peaks()[0], tile_hint=args.gather_tile, n=args.gam_n)), flush=True)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -6,7 +6,7 @@ namespace subsmc {
 namespace {
 using XT = float;
 const Tile kTiles[] = {{1, 4, 3, 4, 0}, {2, 4, 3, 4, 0}, {4, 4, 2, 4, 0}, {2, 8, 2, 4, 0},
-                       {8, 4, 2, 4, 0}, {4, 8, 2, 4, 0}, {8, 8, 2, 4, 0}};
+                       {8, 4, 2, 4, 0}, {4, 8, 2, 4, 0}, {8, 8, 2, 4, 0}, {16, 8, 2, 4, 0}};
 }  // namespace
 
 int est_tiles_f32(Tile *out, int cap) {
@@ -24,6 +24,7 @@ int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s) {
     case 4: return launch_tile<XT, 8, 4, 2, 4>(op, a, s);
     case 5: return launch_tile<XT, 4, 8, 2, 4>(op, a, s);
     case 6: return launch_tile<XT, 8, 8, 2, 4>(op, a, s);
+    case 7: return launch_tile<XT, 16, 8, 2, 4>(op, a, s);
     default: return -1;
   }
 }

@@ -22,8 +22,8 @@ BASE_SEED = 20180508
 
 def round_to_bf16_bits(a32: np.ndarray) -> np.ndarray:
     """Round float32 values to the nearest bfloat16 (ties to even); returns the uint16 bits."""
-    b = np.ascontiguousarray(a32, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    b = np.ascontiguousarray(a32, dtype=np.float32).view(np.uint32)
+    b = (b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)
     return b.astype(np.uint16)
 
 
@@ -163,3 +163,83 @@ def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000, upcast: bool = True) 
     Xd, Xs, yd, ys = _store(X, y, x_dtype, upcast=upcast)
     return Workload(f"poisson-n5e6-p50-{x_dtype}", "poisson", x_dtype, Xd, Xs, yd, ys,
                     np.zeros(p), np.full(p, 0.1), 8192, 2000, 20, 20, 5, seed, 1.0, theta)
+
+
+GAM_KNOTS = np.r_[[0.0] * 4, np.arange(1, 7) / 7.0, [1.0] * 4]  # clamped cubic, 6 interior knots
+
+
+def gam_basis(u: np.ndarray) -> np.ndarray:
+    """Cubic B-spline basis (10 functions, 6 equally spaced interior knots on [0, 1], clamped ends)
+    of every column of u [n, q] in [0, 1): returns [n, 10 q] float32, covariate-major. Only the
+    four functions that are nonzero on a point's knot span are evaluated (de Boor's triangular
+    recurrence for the basis functions of one span)."""
+    n, q = u.shape
+    out = np.zeros((n, 10 * q), dtype=np.float32)
+    flat = out.reshape(-1)
+    t = GAM_KNOTS.astype(np.float32)
+    base = np.arange(n, dtype=np.int64) * (10 * q)
+    for j in range(q):
+        x = u[:, j].astype(np.float32)
+        span = np.minimum((x * 7).astype(np.int64), 6)
+        mu = 3 + span  # t[mu] <= x < t[mu + 1]
+        N = [np.ones(n, dtype=np.float32)]
+        left = [None] * 4
+        right = [None] * 4
+        for d in range(1, 4):
+            left[d] = x - t[mu + 1 - d]
+            right[d] = t[mu + d] - x
+            saved = np.zeros(n, dtype=np.float32)
+            nxt = []
+            for r in range(d):
+                tmp = N[r] / (right[r + 1] + left[d - r])
+                nxt.append(saved + right[r + 1] * tmp)
+                saved = left[d - r] * tmp
+            nxt.append(saved)
+            N = nxt
+        idx = base + 10 * j + span
+        for r in range(4):
+            flat[idx + r] = N[r]
+    return out
+
+
+def gam_1e7(x_dtype: str = "bf16", n: int = 10_000_000, N: int = 16384, m: int = 5000,
+            upcast: bool = True, chunk: int = 1_000_000) -> Workload:
+    """Generalized additive model, Gaussian response with known sigma = 0.5: 10 covariates
+    iid U[0, 1), each expanded into 10 cubic B-spline functions, plus an intercept (p = 101).
+    True smooth functions: covariate j has a * sin(2 pi b x + c) (even j) or a * (x - c)^2 (odd j)
+    with a, b, c drawn from the seed; intercept 1. Prior N(0, 100 I). N=16384, m=5000, G=10,
+    L=25, R=5. Rows are generated in chunks (the random stream depends on the chunk size)."""
+    seed = BASE_SEED + 4
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q, p = 10, 101
+    amp = rng.uniform(0.5, 2.0, q)
+    freq = rng.uniform(0.5, 2.0, q)
+    shift = rng.uniform(0.0, 1.0, q)
+    sigma = 0.5
+    Xs = np.empty((n, p), dtype=np.uint16 if x_dtype == "bf16" else
+                  (np.float32 if x_dtype == "f32" else np.float64))
+    y = np.empty(n)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        u = rng.random((r1 - r0, q))
+        f = np.ones(r1 - r0)
+        for j in range(q):
+            if j % 2 == 0:
+                f += amp[j] * np.sin(2 * np.pi * freq[j] * u[:, j] + 2 * np.pi * shift[j])
+            else:
+                f += amp[j] * (u[:, j] - shift[j]) ** 2
+        y[r0:r1] = f + sigma * rng.standard_normal(r1 - r0)
+        B = np.empty((r1 - r0, p), dtype=np.float32)
+        B[:, 0] = 1.0
+        B[:, 1:] = gam_basis(u)
+        if x_dtype == "bf16":
+            Xs[r0:r1] = round_to_bf16_bits(B)
+        else:
+            Xs[r0:r1] = B
+    ys = y.astype(np.float64 if x_dtype == "f64" else np.float32)
+    if x_dtype == "bf16":
+        Xd = bf16_bits_to_f64(Xs) if upcast else None
+    else:
+        Xd = Xs.astype(np.float64) if upcast else None
+    return Workload(f"gam-n{n}-p101-{x_dtype}", "gaussian", x_dtype, Xd, Xs, ys.astype(np.float64),
+                    ys, np.zeros(p), np.full(p, 100.0), N, m, 10, 25, 5, seed, sigma, None)

@@ -69,6 +69,37 @@ def test_estimator_and_gradient_match_oracle(family, x_dtype, hint):
     S().smc_free(ctx)
 
 
+@pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("hint", range(0, 13))
+def test_wide_rows_match_oracle(x_dtype, hint):
+    """p = 101 (the GAM's width): rows span 13-26 vectors, so only the widest tiles cover them."""
+    wl = small_glm("logistic", n=6000, p=101, N=24, m=333, G=10, L=3, x_dtype=x_dtype, seed=5,
+                   x_scale=0.1, theta_scale=0.1)
+    try:
+        prob, ctx = make_pair(wl, tile_hint=hint)
+    except S()._abi.SmcError as e:
+        if e.code == -1 and hint > 0:
+            pytest.skip("tile not compiled for this storage type or too narrow")
+        raise
+    th, u = _particles(prob, 24, wl.m, 0.05, x_dtype)
+    g, ell, s2 = S().loglik_grad(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV), 0.7)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=0.7)
+    _check_estimates(x_dtype, (ell.cpu().numpy(), s2.cpu().numpy(), g.cpu().double().numpy()), ref)
+    S().smc_free(ctx)
+
+
+def test_gam_basis_rows_match_oracle():
+    """The GAM workload's own rows (B-spline columns, Gaussian response) at small n."""
+    from smc_workloads import gam_1e7
+    wl = gam_1e7("bf16", n=20000, N=16, m=400, chunk=20000)
+    prob, ctx = make_pair(wl)
+    th, u = _particles(prob, 16, wl.m, 0.05, "bf16")
+    g, ell, s2 = S().loglik_grad(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV), 1.0)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=1.0)
+    _check_estimates("bf16", (ell.cpu().numpy(), s2.cpu().numpy(), g.cpu().double().numpy()), ref)
+    S().smc_free(ctx)
+
+
 @pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
 def test_control_variate_moments_match_oracle(x_dtype):
     wl = _wl("logistic", x_dtype, n=20011)
