@@ -80,6 +80,8 @@ typedef struct {
   int32_t hmc_kernel;        /* HMC trajectory kernel: 0 = automatic (rows resident in shared      */
                              /* memory when they fit, else streamed), 1 = streamed, k >= 2 =      */
                              /* resident tile k-2                                                  */
+  int32_t cv_kernel;         /* control-variate moments: 0 = automatic (tensor cores, tcgen05,     */
+                             /* for BF16 storage with p <= 128; SIMT otherwise), 1 = SIMT          */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */

@@ -17,7 +17,7 @@ struct smc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   // problem
-  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0;
+  int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0, cv_kernel = 0;
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
@@ -263,7 +263,7 @@ int moments_at(smc_ctx *c, const double *theta_d, double *A_out, double *B_out, 
   LAUNCH(c,
          cv_moments(c->Xp, c->x_dtype, c->n, c->p, c->S, c->Yo, c->fam,
                     c->noise_sigma * c->noise_sigma, theta_d, c->part,
-                    cv_moments_blocks(c->p), A_out, B_out, C_out, c->stream),
+                    cv_moments_blocks(c->p), A_out, B_out, C_out, c->cv_kernel, c->stream),
          2);
   return SMC_OK;
 }
@@ -536,6 +536,7 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->K = K;
   c->rounds = rounds;
   c->eps0 = cfg->eps0;
+  c->cv_kernel = cfg->cv_kernel == 1 ? 1 : 0;
   c->tile = cfg->tile_hint > 0 ? cfg->tile_hint - 1 : default_tile(c);
   Tile tl[32];
   const int nt = est_tiles(c, tl, 32);

@@ -100,9 +100,13 @@ int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const vo
 // Rewrites the constants c0..c2 in every packed row's tail for the centre tb_ct (state type).
 int row_consts(void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, const void *tb_ct,
                double inv_s2, cudaStream_t s);
+// mode 0: tensor cores (cv_mma.cu) for BF16 storage with p <= 128, SIMT otherwise; mode 1: SIMT.
 int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
                const double *theta, double *partials, int nblocks, double *A, double *B,
-               double *C, cudaStream_t s);
+               double *C, int mode, cudaStream_t s);
+int cv_moments_mma(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
+                   const double *theta, double *partials, int maxblocks, int *nblocks,
+                   cudaStream_t s);
 int cv_moments_blocks(int p);
 int newton_step(int p, const double *theta, const double *B, const double *C, const double *mu,
                 const double *var, double *step, double *work, int *info, cudaStream_t s);

@@ -303,7 +303,15 @@ int cv_moments_blocks(int p) {
 
 int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
                const double *theta, double *partials, int nblocks, double *A, double *B,
-               double *C, cudaStream_t s) {
+               double *C, int mode, cudaStream_t s) {
+  if (mode == 0 && x_dtype == 2 && p <= 128) {
+    int used = 0;
+    const int e = cv_moments_mma(Xp, n, p, S, Yo, fam, sigma2, theta, partials, nblocks, &used, s);
+    if (e != 0) return e;
+    const int width = 1 + p + p * (p + 1) / 2;
+    k_cv_reduce<<<(width + 7) / 8, 256, 0, s>>>(partials, used, p, A, B, C);
+    return (int)cudaGetLastError();
+  }
   if (p * (p + 1) / 2 > kCvThreads * kCvMaxPairs) return (int)cudaErrorInvalidValue;
   const size_t at = x_dtype == 0 ? sizeof(double) : sizeof(float);
   const size_t smem = (size_t)(p + kCvTile + 32) * sizeof(double) + (2 * kCvTile * p + kCvTile) * at;

@@ -54,7 +54,8 @@ class Context:
 def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_var, *, N: int,
              m: int, G: int, L: int, seed: int, ess_frac: float = 0.5, noise_sigma: float = 1.0,
              theta_bar=None, search_k: int = 16, search_rounds: int = 10, eps0: float = 0.0,
-             tile_hint: int = 0, hmc_kernel: int = 0, stream=None) -> Context:
+             tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
+             stream=None) -> Context:
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -67,7 +68,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
     prob = SmcProblem(FAMILY[family], n, p, X.data_ptr(), DTYPE[x_dtype], X.stride(0),
                       y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma))
     cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
-                    search_rounds, float(eps0), tile_hint, hmc_kernel)
+                    search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel)
     tb = None
     tb_ptr = None
     if theta_bar is not None:

@@ -122,6 +122,31 @@ def test_control_variate_moments_match_oracle(x_dtype):
 
 
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit", "gaussian"])
+@pytest.mark.parametrize("p", [3, 20, 50, 101, 120, 126])
+def test_tensor_core_moments_match_oracle(family, p):
+    """C = X' diag(l'') X on tcgen05 (BF16 storage): against the oracle's direct FP64 sums, and
+    against the SIMT moment kernel on the same stored values; n not a multiple of the 128-row
+    tile."""
+    kw = dict(x_scale=0.3 / math.sqrt(p)) if family == "poisson" else dict(x_scale=1.0 / math.sqrt(p))
+    wl = small_glm(family, n=9001, p=p, N=8, m=10, G=2, L=2, x_dtype="bf16", seed=13,
+                   theta_scale=0.3, **kw)
+    prob, ctx = make_pair(wl)
+    pt = prob.theta_bar + 0.05
+    A2, B2, C2 = S().smc_cv_moments(ctx, pt)
+    Ar, Br, Cr = O.cv_moments(family, prob.X, prob.y, pt, sigma=wl.sigma)
+    assert A2 == pytest.approx(Ar, rel=1e-12)
+    np.testing.assert_allclose(B2, Br, rtol=1e-9, atol=1e-9 * np.abs(Br).max())
+    np.testing.assert_allclose(C2, Cr, rtol=2e-6, atol=2e-8 * np.abs(Cr).max())
+    S().smc_free(ctx)
+    if p * (p + 1) // 2 > 8192:
+        return  # beyond the SIMT kernel's pair slots
+    prob2, ctx2 = make_pair(wl, cv_kernel=1)
+    A3, B3, C3 = S().smc_cv_moments(ctx2, pt)
+    np.testing.assert_allclose(C3, C2, rtol=4e-6, atol=4e-8 * np.abs(Cr).max())
+    S().smc_free(ctx2)
+
+
+@pytest.mark.parametrize("family", ["logistic", "poisson", "probit", "gaussian"])
 def test_device_newton_centre_matches_oracle(family):
     wl = _wl(family, "f64", n=8000)
     from gpu_common import device_arrays
