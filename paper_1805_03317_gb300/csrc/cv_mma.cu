@@ -192,14 +192,15 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
       const bool in = r0 + k < n;
       double l = 0.0, d1 = 0.0, d2 = 0.0;
       if (in) {
-        double eta = 0.0;
+        double ep[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // independent FP64 chains
         for (int c = 0; c < nvx; ++c) {
           const uint4 w = *reinterpret_cast<const uint4 *>(At + unit_off(k, c));
           float x[8];
           Store<__nv_bfloat16>::unpack(w, x);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) eta = fma((double)x[e], ths[8 * c + e], eta);
+          for (int e = 0; e < 8; ++e) ep[e] = fma((double)x[e], ths[8 * c + e], ep[e]);
         }
+        const double eta = ((ep[0] + ep[1]) + (ep[2] + ep[3])) + ((ep[4] + ep[5]) + (ep[6] + ep[7]));
         const RowC<float> *tl = reinterpret_cast<const RowC<float> *>(Xp + (r0 + k) * S + Yo);
         row_value<FAM>(eta, (double)__ldg(&tl->y), s2, l, d1, d2);
       }
@@ -247,11 +248,14 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
     }
     if (tid < p) {
       const int c = tid >> 3, e = tid & 7;
+      double b4[4] = {0.0, 0.0, 0.0, 0.0};  // independent FP64 chains
+#pragma unroll 4
       for (int k = 0; k < kRows; ++k) {
         const float x = __bfloat162float(
             *reinterpret_cast<const __nv_bfloat16 *>(At + unit_off(k, c) + 2 * e));
-        Bacc = fma(lps[k], (double)x, Bacc);
+        b4[k & 3] = fma(lps[k], (double)x, b4[k & 3]);
       }
+      Bacc += (b4[0] + b4[1]) + (b4[2] + b4[3]);
     }
     // 4. wait for the MMAs (bounded in time; a timeout is reported as a NaN A partial)
     {

@@ -47,3 +47,16 @@ def tol(x_dtype):
     if x_dtype == "f64":
         return dict(ell=1e-11, sig2=1e-8, grad=1e-9)
     return dict(ell=1e-5, sig2=1e-4, grad=1e-4)
+
+
+def ell_scale(prob, theta, ell_ref):
+    """Scale for the l_hat bar: the largest of |l_hat| and its four summands A, B'delta,
+    delta'C delta/2 and (n/m) sum d (Sec. 3.2). Rounding acts on the summands, so a relative bar on
+    an l_hat that nearly cancels is read against the largest summand."""
+    import numpy as np
+    d = np.asarray(theta, dtype=np.float64) - prob.theta_bar[None, :]
+    A = np.full(d.shape[0], prob.A)
+    Bd = d @ prob.B
+    qC = 0.5 * np.einsum("bi,ij,bj->b", d, prob.C, d)
+    rest = np.asarray(ell_ref) - A - Bd - qC
+    return np.max(np.abs(np.stack([np.asarray(ell_ref), A, Bd, qC, rest])), axis=0)

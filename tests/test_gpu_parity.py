@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import make_pair, oracle_problem, state_round, tol
+from gpu_common import ell_scale, make_pair, oracle_problem, state_round, tol
 from oracle import oracle as O
 from smc_workloads import small_glm
 
@@ -33,10 +33,13 @@ def _particles(prob, B, m, scale, x_dtype, seed=3):
     return th, u
 
 
-def _check_estimates(x_dtype, got, ref):
+def _check_estimates(x_dtype, got, ref, prob=None, theta=None):
     t = tol(x_dtype)
     ell, s2, g = got
-    np.testing.assert_allclose(ell, ref["ell"], rtol=t["ell"], atol=0)
+    if prob is None:
+        np.testing.assert_allclose(ell, ref["ell"], rtol=t["ell"], atol=0)
+    else:  # against the estimator's largest summand (it may nearly cancel)
+        assert np.all(np.abs(ell - ref["ell"]) <= t["ell"] * ell_scale(prob, theta, ref["ell"]))
     # sigma2_hat enters the log target additively (-a^2/2 sigma2_hat), so its error is held to its
     # own relative bar plus the bar of l_hat in the same units
     bound = t["sig2"] * np.max(np.abs(ref["sigma2"])) + t["ell"] * np.max(np.abs(ref["ell"]))
@@ -426,7 +429,9 @@ def test_edge_cases():
     th_o, u_o = O.init_particles(wl.seed, wl.N, wl.p, wl.m, wl.n, wl.prior_mean, wl.prior_var)
     ref = O.loglik_batch(prob, wl.m, wl.G, state_round(th_o, "bf16"), u_o, grad=False,
                          blocks=True)
-    np.testing.assert_allclose(ell.cpu().numpy(), ref["ell"], rtol=1e-5)
+    th_r = state_round(th_o, "bf16")
+    err = np.abs(ell.cpu().numpy() - ref["ell"])
+    assert np.all(err <= 1e-5 * ell_scale(prob, th_r, ref["ell"]))
     S().smc_free(ctx)
 
 
