@@ -144,6 +144,21 @@ int loglik_est(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, dou
 int loglik_grad(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, double a,
                 void *grad, double *ell, double *sigma2);
 
+/* Forward half of the differentiable estimator: l_hat and sigma2_hat as loglik_est, and for every
+ * row j of every particle the increment d_j = l(eta_j) - q_j(theta) and its eta-derivative
+ * r_j = l'(eta_j) - l'(eta_bar_j) - l''(eta_bar_j) x_j'(theta - theta_bar) (Sec. 3.2), saved for
+ * loglik_bwd. ell, sigma2: device [B] double; d_save, r_save: device [B, m] in the state type
+ * (caller-owned). Out-of-range indices return SMC_ERR_ARG. */
+int loglik_fwd(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, double *ell,
+               double *sigma2, void *d_save, void *r_save);
+
+/* Backward half: for upstream gradients g_ell, g_sig2 (device [B] double) of (l_hat, sigma2_hat),
+ * grad = g_ell (B + C delta + (n/m) sum_j r_j x_j) + g_sig2 (2 n^2/m^2) sum_j (d_j - dbar) r_j x_j
+ * (the exact derivative for fixed u; no prior term), from the values loglik_fwd saved at the same
+ * theta and u; rows are gathered again by u. grad: device [B, p] state type. */
+int loglik_bwd(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, const void *d_save,
+               const void *r_save, const double *g_ell, const double *g_sig2, void *grad);
+
 /* ------------------------------------------------------------------------------------------- */
 /* State access (for checkpointing, tests and host-resident callers)                             */
 /* ------------------------------------------------------------------------------------------- */

@@ -3,13 +3,15 @@
 The compute path is the CUDA library built from ``csrc/`` and declared in ``include/subsmc.h``;
 this package is its Python binding (``smc``) and build script (``build``).
 """
-from .smc import (Context, SubsampledSMC, loglik_est, loglik_grad, smc_autotune, smc_cv_moments,
+from .smc import (Context, SubsampledLoglik, SubsampledSMC, loglik_bwd, loglik_est, loglik_fwd,
+                  loglik_grad, smc_autotune, smc_cv_moments,
                   smc_free, smc_get_cache, smc_get_centre, smc_get_mass, smc_get_particles,
                   smc_get_status, smc_init, smc_launch_count, smc_move, smc_profile_enable,
                   smc_profile_read, smc_resample, smc_resample_noalloc,
                   smc_reweight, smc_set_particles, smc_set_scalars)
 
-__all__ = ["Context", "SubsampledSMC", "loglik_est", "loglik_grad", "smc_autotune",
+__all__ = ["Context", "SubsampledLoglik", "SubsampledSMC", "loglik_bwd", "loglik_est", "loglik_fwd",
+           "loglik_grad", "smc_autotune",
            "smc_cv_moments", "smc_free", "smc_get_cache", "smc_get_centre", "smc_get_mass",
            "smc_get_particles", "smc_get_status", "smc_init", "smc_launch_count", "smc_move",
            "smc_profile_enable", "smc_profile_read", "smc_resample_noalloc",

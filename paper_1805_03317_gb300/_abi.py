@@ -42,6 +42,8 @@ SIGNATURES = {
     "smc_move": (ctypes.c_int, [c_vp, c_i32, c_dp, c_dp]),
     "loglik_est": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "loglik_grad": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_d, c_vp, c_vp, c_vp]),
+    "loglik_fwd": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "loglik_bwd": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "smc_get_particles": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),
     "smc_set_particles": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),
     "smc_get_cache": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),

@@ -171,7 +171,7 @@ int hmc_launch(smc_ctx *c, const EstArgs &a) {
 }
 
 int est_launch(smc_ctx *c, int op, const EstArgs &a) {
-  ProfScope ps(c, op);
+  ProfScope ps(c, op >= 3 ? 0 : op);  // the autograd pair counts as estimator work
   c->launches += 1;
   if (c->x_dtype == SMC_F64) return est_launch_f64(op, c->tile, a, c->stream);
   if (c->x_dtype == SMC_F32) return est_launch_f32(op, c->tile, a, c->stream);
@@ -703,6 +703,47 @@ int loglik_grad(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, doub
                 double *ell, double *sigma2) {
   if (!grad) return fail(c, SMC_ERR_ARG, "grad is NULL");
   return estimate_impl(c, B, theta, u, a, grad, ell, sigma2);
+}
+
+int loglik_fwd(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, double *ell,
+               double *sigma2, void *d_save, void *r_save) {
+  if (!c) return SMC_ERR_ARG;
+  if (B < 0 || (B > 0 && (!theta || !u || !ell || !sigma2 || !d_save || !r_save)))
+    return fail(c, SMC_ERR_ARG, "bad loglik_fwd arguments");
+  EstArgs ea = base_args(c);
+  ea.B = B;
+  ea.theta = theta;
+  ea.u = u;
+  ea.ell = ell;
+  ea.sig2 = sigma2;
+  ea.dsave = d_save;
+  ea.rsave = r_save;
+  LAUNCH(c, est_launch(c, 3, ea), 0);
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  return check_err_bits(c, h);
+}
+
+int loglik_bwd(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, const void *d_save,
+               const void *r_save, const double *g_ell, const double *g_sig2, void *grad) {
+  if (!c) return SMC_ERR_ARG;
+  if (B < 0 || (B > 0 && (!theta || !u || !d_save || !r_save || !g_ell || !g_sig2 || !grad)))
+    return fail(c, SMC_ERR_ARG, "bad loglik_bwd arguments");
+  EstArgs ea = base_args(c);
+  ea.B = B;
+  ea.theta = theta;
+  ea.u = u;
+  ea.dsave = const_cast<void *>(d_save);
+  ea.rsave = const_cast<void *>(r_save);
+  ea.g_ell = g_ell;
+  ea.g_sig2 = g_sig2;
+  ea.grad = grad;
+  LAUNCH(c, est_launch(c, 4, ea), 0);
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  return check_err_bits(c, h);
 }
 
 int smc_get_particles(smc_ctx *c, void *theta, int32_t *u, double *W) {

@@ -32,6 +32,16 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Per-row traffic of the forward/backward pair behind the autograd binding. MODE 1 (forward):
+// d_j and r_j of every row are written to dsave/rsave [m]. MODE 2 (backward): no x'delta and no
+// family terms; row j's weight is r_j (c1 + c2 (d_j - dbar)) from the saved values, and the
+// gradient partials accumulate weight * x (g1 only).
+template <typename CT> struct RowIO {
+  CT *dsave = nullptr, *rsave = nullptr;
+  const CT *dsaved = nullptr, *rsaved = nullptr;
+  CT c1 = CT(0), c2 = CT(0), dbar = CT(0);
+};
+
 // Streamed rows. A warp takes its particle's rows 32 at a time (a sweep) and lane l owns row l of
 // the sweep. For the covariates the warp splits into 32/T groups of T lanes: group r covers rows
 // rT .. rT+T-1 of the sweep, and lane g of the group holds element slots g*CPL .. g*CPL+CPL-1 of
@@ -114,11 +124,11 @@ struct WarpEval {
   // over this lane's slots into g1, g2. Returns S = sum d and Q = sum d^2 on every lane; BLOCKS
   // also writes per-block (sum d, sum d^2) of the floor partition of the nrows rows into G blocks
   // to blk_out[2G].
-  template <bool GRAD, bool BLOCKS>
+  template <bool GRAD, bool BLOCKS, int MODE = 0>
   __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int64_t n,
                                        const int32_t *idx, int nrows, int fam, CT inv_s2, CT *g1,
                                        CT *g2, double *blk_out, int G, double &Ssum, double &Qsum,
-                                       DevState *st) const {
+                                       DevState *st, const RowIO<CT> &io = RowIO<CT>()) const {
     const int nsw = (nrows + 31) >> 5;
     // rows past the end copy the last row again (already on chip) and are masked out
     const int klast = nrows > 0 ? idx[nrows - 1] : 0;
@@ -192,6 +202,15 @@ struct WarpEval {
     };
     // d and r of the owned row of sweep s (stage b) at D, masked past the end; sums of d, d^2
     auto terms = [&](int s, int b, CT D, CT &d, CT &r) {
+      const int j = (s << 5) + lane;
+      if constexpr (MODE == 2) {  // weight of the row from the saved forward values
+        (void)D;
+        d = CT(0);
+        r = CT(0);
+        if (j < nrows && !((bad >> b) & 1u))
+          r = io.rsaved[j] * (io.c1 + io.c2 * (io.dsaved[j] - io.dbar));
+        return;
+      }
       const RowC<CT> c = *reinterpret_cast<const RowC<CT> *>(tail(b));
       switch (fam) {
         case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
@@ -199,10 +218,15 @@ struct WarpEval {
         case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
         default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
       }
-      const int j = (s << 5) + lane;
       if (j >= nrows || ((bad >> b) & 1u)) {
         d = CT(0);
         r = CT(0);
+      }
+      if constexpr (MODE == 1) {
+        if (j < nrows) {
+          io.dsave[j] = d;
+          io.rsave[j] = r;
+        }
       }
       if (BLOCKS) {  // block of row j: largest g with floor(g nrows / G) <= j
         const int r1 = min((s << 5) + 31, nrows - 1);
@@ -242,7 +266,7 @@ struct WarpEval {
         for (int v = 0; v < NV; ++v)
           SD::unpack(*reinterpret_cast<const uint4 *>(chunk(b, t, v)), &x[v * SD::VEC]);
         axpy_slots<CPL>(rt, x, g1);
-        axpy_slots<CPL>(drt, x, g2);
+        if constexpr (MODE != 2) axpy_slots<CPL>(drt, x, g2);
       }
     };
     fetch(0);
@@ -261,7 +285,7 @@ struct WarpEval {
       if (nsw > 0) {
         cp_async_wait<NST - 2>();  // sweep 0 has landed
         if (tail_in_chunks) __syncwarp();  // tails were copied by other lanes of the group
-        Dc = phase1(0);
+        if (MODE != 2) Dc = phase1(0);
       }
       for (int s = 0; s < nsw; ++s) {
         const int b = s % NST;
@@ -272,7 +296,7 @@ struct WarpEval {
         cp_async_wait<NST - 2>();  // sweep s+1 has landed
         if (tail_in_chunks) __syncwarp();
         CT Dn = CT(0);
-        if (s + 1 < nsw) Dn = phase1((s + 1) % NST);
+        if (MODE != 2 && s + 1 < nsw) Dn = phase1((s + 1) % NST);
         if (GRAD) phase2(b, r, d * r);
         Dc = Dn;
       }
@@ -283,7 +307,7 @@ struct WarpEval {
         cp_async_wait<NST - 1>();  // this lane's copies of sweep s have landed
         if (tail_in_chunks) __syncwarp();  // tails were copied by other lanes of the group
         const int b = s % NST;
-        const CT D = phase1(b);
+        const CT D = MODE == 2 ? CT(0) : phase1(b);
         CT d, r;
         terms(s, b, D, d, r);
         if (GRAD) {
@@ -338,11 +362,13 @@ template <typename CT> __device__ __forceinline__ CT ldg_ct(const void *p, int i
 // One evaluation of the estimator for the warp's particle at theta (in sm.th / sm.dl).
 // Reads rows of idx[0..m); GRAD: writes the target gradient to sm.g; BLOCKS: writes per-block
 // (sum d, sum d^2) to blk_out[G*2]. Returns l_hat and sigma2_hat on every lane.
-template <typename XT, int T, int CPL, int U, bool K, bool GRAD, bool BLOCKS>
+template <typename XT, int T, int CPL, int U, bool K, bool GRAD, bool BLOCKS, int MODE = 0>
 __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &W, const EstArgs &a,
                                               const int32_t *idx, WarpSmem<typename Store<XT>::CT> &sm,
                                               double temp, double *blk_out, double &ell,
-                                              double &sig2) {
+                                              double &sig2,
+                                              const RowIO<typename Store<XT>::CT> &io =
+                                                  RowIO<typename Store<XT>::CT>()) {
   using CT = typename Store<XT>::CT;
   const XT *Xp = reinterpret_cast<const XT *>(a.Xp);
   const CT inv_s2 = (CT)a.inv_s2;
@@ -350,8 +376,8 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &
 #pragma unroll
   for (int s = 0; s < CPL; ++s) g1[s] = g2[s] = CT(0);
   double S, Q;
-  W.template rows<GRAD, BLOCKS>(Xp, a.S, a.n, idx, a.m, a.fam, inv_s2, g1, g2, blk_out, a.G, S, Q,
-                                a.st);
+  W.template rows<GRAD, BLOCKS, MODE>(Xp, a.S, a.n, idx, a.m, a.fam, inv_s2, g1, g2, blk_out, a.G,
+                                      S, Q, a.st, io);
   const double nm = (double)a.n / (double)a.m;
   const double dbar = S / (double)a.m;
   if (GRAD) {
@@ -455,6 +481,93 @@ __global__ void __launch_bounds__(WARPS * 32) k_estimate(EstArgs a) {
     if (a.ell) a.ell[i] = ell;
     if (a.sig2) a.sig2[i] = sig2;
     if (!isfinite(ell) || !isfinite(sig2)) set_err(a.st, kErrNonFinite);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Forward/backward pair behind the autograd binding (Sec. 3.2 estimator, its exact gradient for
+// fixed u). Forward: l_hat and sigma2_hat as loglik_est, and per row d_j, r_j saved to
+// dsave/rsave [B, m]. Backward, for upstream gradients (g_l, g_s) of (l_hat, sigma2_hat):
+//   dL/dtheta = g_l (B + C delta) + sum_j r_j [g_l n/m + g_s 2 (n/m)^2 (d_j - dbar)] x_j
+// from the saved values and the rows gathered again by u (no family terms are re-evaluated).
+// ------------------------------------------------------------------------------------------------
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_fwdsave(EstArgs a) {
+  using CT = typename Store<XT>::CT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * WARPS + warp;
+  if (i >= a.B) return;
+  WarpEval<XT, T, CPL, U, K> W;
+  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
+  W.init(wbase, a.Yo);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), a.p, T * CPL);
+  const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * a.p;
+  for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
+  __syncwarp();
+  refresh_delta(W, a, sm);
+  RowIO<CT> io;
+  io.dsave = reinterpret_cast<CT *>(a.dsave) + (int64_t)i * a.m;
+  io.rsave = reinterpret_cast<CT *>(a.rsave) + (int64_t)i * a.m;
+  double ell, sig2;
+  eval_particle<XT, T, CPL, U, K, false, false, 1>(W, a, a.u + (int64_t)i * a.m, sm, 1.0, nullptr,
+                                                    ell, sig2, io);
+  if (W.lane == 0) {
+    a.ell[i] = ell;
+    a.sig2[i] = sig2;
+    if (!isfinite(ell) || !isfinite(sig2)) set_err(a.st, kErrNonFinite);
+  }
+}
+
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_backward(EstArgs a) {
+  using CT = typename Store<XT>::CT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * WARPS + warp;
+  if (i >= a.B) return;
+  WarpEval<XT, T, CPL, U, K> W;
+  const int p = a.p, m = a.m;
+  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(p);
+  W.init(wbase, a.Yo);
+  WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), p, T * CPL);
+  const CT *th = reinterpret_cast<const CT *>(a.theta) + (int64_t)i * p;
+  for (int c = W.lane; c < p; c += 32) sm.th[c] = th[c];
+  __syncwarp();
+  refresh_delta(W, a, sm);
+  RowIO<CT> io;
+  io.dsaved = reinterpret_cast<const CT *>(a.dsave) + (int64_t)i * m;
+  io.rsaved = reinterpret_cast<const CT *>(a.rsave) + (int64_t)i * m;
+  double sd = 0.0;
+  for (int j = W.lane; j < m; j += 32) sd += (double)io.dsaved[j];
+  sd = warp_sum(sd);
+  const double nm = (double)a.n / (double)m, gl = a.g_ell[i], gs = a.g_sig2[i];
+  io.c1 = (CT)(gl * nm);
+  io.c2 = (CT)(gs * 2.0 * nm * nm);
+  io.dbar = (CT)(sd / (double)m);
+  CT g1[CPL], g2[CPL];
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) g1[e] = g2[e] = CT(0);
+  double S_, Q_;
+  W.template rows<true, false, 2>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n,
+                                  a.u + (int64_t)i * m, m, a.fam, (CT)a.inv_s2, g1, g2, nullptr,
+                                  a.G, S_, Q_, a.st, io);
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+#pragma unroll
+    for (int o = T; o < 32; o <<= 1) g1[e] += __shfl_xor_sync(0xffffffffu, g1[e], o);
+  }
+  if (W.gb == 0) {
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) sm.G1[W.gl * CPL + e] = g1[e];
+  }
+  __syncwarp();
+  CT *gout = reinterpret_cast<CT *>(a.grad) + (int64_t)i * p;
+  const CT cgl = (CT)gl;
+  for (int c = W.lane; c < p; c += 32) {
+    CT cd = CT(0);
+    for (int k = 0; k < p; ++k) cd = fma(ldg_ct<CT>(a.C_ct, k * p + c), sm.dl[k], cd);
+    gout[c] = cgl * (ldg_ct<CT>(a.B_ct, c) + cd) + sm.G1[c];
   }
 }
 
@@ -636,10 +749,18 @@ inline int launch_tile(int op, const EstArgs &a, cudaStream_t s) {
     e = cudaFuncSetAttribute(k_upm<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_upm<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
-  } else {
+  } else if (op == 2) {
     e = cudaFuncSetAttribute(k_hmc<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_hmc<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
+  } else if (op == 3) {
+    e = cudaFuncSetAttribute(k_fwdsave<XT, T, CPL, U, WARPS, K>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_fwdsave<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_backward<XT, T, CPL, U, WARPS, K>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_backward<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
   }
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();

@@ -65,6 +65,9 @@ struct EstArgs {
   int32_t *unew;          // [B, maxblk] scratch for proposed block indices
   int maxblk;
   DevState *st;
+  // autograd pair: per-row d, r [B, m] (state type), upstream gradients of l_hat, sigma2_hat [B]
+  void *dsave, *rsave;
+  const double *g_ell, *g_sig2;
 };
 
 // Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots; NST
@@ -75,7 +78,8 @@ struct Tile {
 };
 
 // Launchers, one set per storage type (defined in est_f64.cu, est_f32.cu, est_bf16.cu).
-// op: 0 = plain estimator (optionally with gradient), 1 = u-update, 2 = HMC move.
+// op: 0 = plain estimator (optionally with gradient), 1 = u-update, 2 = HMC move,
+// 3 = estimator saving per-row d, r, 4 = backward from saved d, r.
 // Returns a cudaError_t; -1 if the tile id is not compiled for this storage type.
 int est_launch_f64(int op, int tile, const EstArgs &a, cudaStream_t s);
 int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s);

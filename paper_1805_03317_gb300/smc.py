@@ -130,6 +130,62 @@ def loglik_grad(ctx: Context, theta: torch.Tensor, u: torch.Tensor, a: float):
     return grad, ell, s2
 
 
+def loglik_fwd(ctx: Context, theta: torch.Tensor, u: torch.Tensor):
+    """l_hat, sigma2_hat [B] float64 and the per-row d, r [B, m] (state type) kept for loglik_bwd."""
+    B = theta.shape[0]
+    theta = theta.to(ctx.state_dtype).contiguous()
+    u = u.to(torch.int32).contiguous()
+    ell = torch.empty(B, dtype=torch.float64, device=theta.device)
+    s2 = torch.empty_like(ell)
+    d = torch.empty(B, ctx.m, dtype=ctx.state_dtype, device=theta.device)
+    r = torch.empty_like(d)
+    check(_abi.load().loglik_fwd(ctx.handle, B, _ptr(theta), _ptr(u), _ptr(ell), _ptr(s2), _ptr(d),
+                                 _ptr(r)), "loglik_fwd", ctx.handle)
+    return ell, s2, d, r
+
+
+def loglik_bwd(ctx: Context, theta: torch.Tensor, u: torch.Tensor, d: torch.Tensor,
+               r: torch.Tensor, g_ell: torch.Tensor, g_sig2: torch.Tensor):
+    """Gradient [B, p] (state type) of g_ell . l_hat + g_sig2 . sigma2_hat from saved d, r."""
+    theta = theta.to(ctx.state_dtype).contiguous()
+    u = u.to(torch.int32).contiguous()
+    d = d.contiguous()
+    r = r.contiguous()
+    ge = g_ell.to(device=theta.device, dtype=torch.float64).contiguous()
+    gs = g_sig2.to(device=theta.device, dtype=torch.float64).contiguous()
+    grad = torch.empty_like(theta)
+    check(_abi.load().loglik_bwd(ctx.handle, theta.shape[0], _ptr(theta), _ptr(u), _ptr(d),
+                                 _ptr(r), _ptr(ge), _ptr(gs), _ptr(grad)), "loglik_bwd", ctx.handle)
+    return grad
+
+
+class SubsampledLoglik(torch.autograd.Function):
+    """(l_hat, sigma2_hat) of the difference estimator as a differentiable function of theta for a
+    fixed subsample u (Sec. 3.2). The forward kernel saves each row's increment d_j and its
+    derivative r_j; the backward kernel gathers the particle's rows again by u and forms the exact
+    gradient from them (no tape through the estimator, no finite differences).
+    Usage: ell, s2 = SubsampledLoglik.apply(theta, u, ctx)."""
+
+    @staticmethod
+    def forward(fctx, theta, u, ctx):
+        ell, s2, d, r = loglik_fwd(ctx, theta.detach(), u)
+        fctx.save_for_backward(theta.detach(), u, d, r)
+        fctx.smc_ctx = ctx
+        fctx.in_dtype = theta.dtype
+        return ell, s2
+
+    @staticmethod
+    def backward(fctx, g_ell, g_sig2):
+        theta, u, d, r = fctx.saved_tensors
+        B = theta.shape[0]
+        if g_ell is None:
+            g_ell = torch.zeros(B, dtype=torch.float64, device=theta.device)
+        if g_sig2 is None:
+            g_sig2 = torch.zeros(B, dtype=torch.float64, device=theta.device)
+        grad = loglik_bwd(fctx.smc_ctx, theta, u, d, r, g_ell, g_sig2)
+        return grad.to(fctx.in_dtype), None, None
+
+
 def smc_get_particles(ctx: Context, theta=None, u=None, W=None):
     """Fill (or allocate on the context's device) theta [N,p], u [N,m] int32, W [N] float64."""
     dev = ctx.device

@@ -445,3 +445,74 @@ def test_bad_arguments_are_rejected():
         S().smc_init(X, y, "logistic", wl.prior_mean, -wl.prior_var, N=4, m=5, G=2, L=1, seed=1)
     with pytest.raises(S()._abi.SmcError):
         S().smc_init(X, y, "logistic", wl.prior_mean, wl.prior_var, N=4, m=5, G=2, L=0, seed=1)
+
+
+# ------------------------------------------------------------------------------------------------
+# Differentiable estimator: torch.autograd.Function over the forward/backward kernel pair
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("family", ["logistic", "poisson", "probit", "gaussian"])
+def test_autograd_backward_matches_finite_differences_fp64(family):
+    """FP64 storage: the backward kernel's gradient of a l_hat - a^2/2 sigma2_hat against central
+    differences of the forward kernel itself, at 32 random particles; and equal to the fused
+    loglik_grad kernel without its prior term."""
+    wl = _wl(family, "f64", p=6, n=3000, m=90, G=6)
+    prob, ctx = make_pair(wl)
+    th, u = _particles(prob, 32, wl.m, 0.05, "f64", seed=8)
+    a = 0.7
+    theta = torch.from_numpy(th).to(DEV).requires_grad_(True)
+    ut = torch.from_numpy(u).to(DEV)
+    ell, s2 = S().SubsampledLoglik.apply(theta, ut, ctx)
+    (a * ell - 0.5 * a * a * s2).sum().backward()
+    g = theta.grad.cpu().numpy()
+    h = 1e-5
+    fd = np.zeros_like(th)
+    for c in range(prob.p):
+        tp, tm = th.copy(), th.copy()
+        tp[:, c] += h
+        tm[:, c] -= h
+        ep, sp = S().loglik_est(ctx, torch.from_numpy(tp).to(DEV), ut)
+        em, sm_ = S().loglik_est(ctx, torch.from_numpy(tm).to(DEV), ut)
+        fp = (a * ep - 0.5 * a * a * sp).cpu().numpy()
+        fm = (a * em - 0.5 * a * a * sm_).cpu().numpy()
+        fd[:, c] = (fp - fm) / (2 * h)
+    scale = np.maximum(np.abs(fd).max(axis=1, keepdims=True), 1.0)
+    assert (np.abs(g - fd) / scale).max() < 1e-6
+    gk, _, _ = S().loglik_grad(ctx, theta.detach(), ut, a)
+    prior = -(th - prob.prior_mean) / prob.prior_var
+    np.testing.assert_allclose(g, gk.cpu().numpy() - prior, rtol=1e-9, atol=1e-9 * scale.max())
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("family", ["logistic", "poisson"])
+def test_autograd_backward_matches_oracle(family, x_dtype):
+    """FP32/BF16 storage: autograd gradient (upstream gradients a and -a^2/2) against the oracle's
+    FP64 gradient minus the prior, and against central differences of the oracle's l_hat and
+    sigma2_hat on the same stored values, at 32 random particles."""
+    wl = _wl(family, x_dtype, p=9, n=4000, m=150, G=10)
+    prob, ctx = make_pair(wl)
+    th, u = _particles(prob, 32, wl.m, 0.05, x_dtype, seed=9)
+    a = 0.8
+    theta = torch.from_numpy(th).to(DEV).float().requires_grad_(True)
+    ut = torch.from_numpy(u).to(DEV)
+    ell, s2 = S().SubsampledLoglik.apply(theta, ut, ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=a)
+    np.testing.assert_allclose(ell.detach().cpu().numpy(), ref["ell"], rtol=1e-5)
+    (a * ell - 0.5 * a * a * s2).sum().backward()
+    g = theta.grad.double().cpu().numpy()
+    prior = -(th - prob.prior_mean) / prob.prior_var
+    gref = ref["grad"] - prior
+    scale = np.maximum(np.abs(gref).max(axis=1, keepdims=True), 1.0)
+    assert (np.abs(g - gref) / scale).max() < 1e-4
+    h = 1e-6
+    fd = np.zeros_like(th)
+    for c in range(prob.p):
+        tp, tm = th.copy(), th.copy()
+        tp[:, c] += h
+        tm[:, c] -= h
+        rp = O.loglik_batch(prob, wl.m, wl.G, tp, u, grad=False)
+        rm = O.loglik_batch(prob, wl.m, wl.G, tm, u, grad=False)
+        fd[:, c] = ((a * rp["ell"] - 0.5 * a * a * rp["sigma2"])
+                    - (a * rm["ell"] - 0.5 * a * a * rm["sigma2"])) / (2 * h)
+    assert (np.abs(g - fd) / scale).max() < 1e-4
+    S().smc_free(ctx)
