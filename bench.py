@@ -50,6 +50,7 @@ def parse():
                     help="run only the HBM-bound gather leg and print its JSON (for profiling)")
     ap.add_argument("--gather-tile", type=int, default=0,
                     help="estimator tile hint for the gather leg (0: autotune)")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph stage timing")
     ap.add_argument("--no-gam", action="store_true",
                     help="skip the GAM gather leg (n=1e7, p=101; about 10-30 s of data generation)")
     ap.add_argument("--gam-n", type=int, default=10_000_000,
@@ -162,10 +163,14 @@ def run_stage(S, ctx, R):
     return a
 
 
-def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist):
+def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist, graph=False):
+    """Times `steps` stages after `warmup` untimed ones. graph: every stage is one smc_stage call
+    replaying a captured CUDA graph (captured during the warm-up), else the three calls
+    smc_reweight, smc_resample, smc_move with their host readbacks."""
     import torch
+    stage = (lambda: S.smc_stage(ctx, R, use_graph=True)) if graph else (lambda: run_stage(S, ctx, R))
     for _ in range(warmup):
-        run_stage(S, ctx, R)
+        stage()
     torch.cuda.synchronize()
     if dist:
         torch.distributed.barrier()
@@ -180,7 +185,7 @@ def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist):
     for k in range(steps):
         flush.add_(1)  # write a buffer larger than L2 between timed stages
         starts[k].record()
-        run_stage(S, ctx, R)
+        stage()
         ends[k].record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -350,6 +355,16 @@ def gpu_arm(args):
     e2e_value = per_stage * max(3, min(args.steps, 20)) * world / e2e_wall
     S.smc_free(ctx)
 
+    # the same stages (fresh context, same seed) with every stage replayed as one CUDA graph
+    graph = None
+    if not args.no_graph:
+        ctxg, _ = make_ctx(S, wl, dev, seed_offset=rank)
+        msg, _, lg, _ = timed_stages(S, ctxg, wl, R, args.steps, args.warmup, flush, dist, graph=True)
+        S.smc_free(ctxg)
+        graph = {"value": per_stage * args.steps * world / (msg / 1e3),
+                 "ms_per_step": msg / args.steps, "gpu_launches": lg,
+                 "note": "smc_stage with use_graph: one graph launch per stage, no host sync"}
+
     fp32 = None
     walls = {}
     if not args.no_compare and rank == 0:
@@ -411,6 +426,7 @@ def gpu_arm(args):
         "e2e": {"value": e2e_value, "unit": "grad-evals/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "fp32_storage": fp32,
+        "graph_stages": graph,
         "hbm_gather_leg": gather,
         "gam_gather_leg": gam,
         "smc_wall_time": walls,

@@ -129,6 +129,16 @@ int smc_resample(smc_ctx *ctx, int32_t *ancestors);
  * Host outputs (may be NULL): acceptance rates of the u and theta updates over these R moves. */
 int smc_move(smc_ctx *ctx, int32_t R, double *acc_u, double *acc_theta);
 
+/* One whole stage (Algorithm 2 (a)-(f)): smc_reweight, smc_resample and smc_move(R) with no host
+ * outputs and no host synchronisation. use_graph = 0 issues the launches one by one. use_graph = 1
+ * replays the stage as one CUDA graph: the first call at each of the two particle-buffer parities
+ * (resampling alternates between two buffers) and R captures it on a private stream, later calls
+ * launch the instantiated graph on the context's stream; the kernels then read the stage index
+ * from a device counter, so replays draw the same random numbers as the launch-by-launch path
+ * (results are bit-identical). Tracing events are not recorded inside graphs. smc_autotune drops
+ * the graphs. Errors inside the graph surface at the next call that reads the device state. */
+int smc_stage(smc_ctx *ctx, int32_t R, int32_t use_graph);
+
 /* ------------------------------------------------------------------------------------------- */
 /* The subsampled estimator on caller-supplied particles (Sec. 3.2, Eq. difference_estimator_logl)*/
 /* ------------------------------------------------------------------------------------------- */

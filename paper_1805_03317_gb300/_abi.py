@@ -40,6 +40,7 @@ SIGNATURES = {
     "smc_reweight": (ctypes.c_int, [c_vp, c_dp, c_dp, c_dp]),
     "smc_resample": (ctypes.c_int, [c_vp, c_vp]),
     "smc_move": (ctypes.c_int, [c_vp, c_i32, c_dp, c_dp]),
+    "smc_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
     "loglik_est": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "loglik_grad": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_d, c_vp, c_vp, c_vp]),
     "loglik_fwd": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -55,6 +55,16 @@ struct smc_ctx {
   bool prof_on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[6];
   std::vector<cudaEvent_t> ev_pool;
+  // CUDA graphs of one whole stage (smc_stage), one per buffer parity: the resampling gather
+  // alternates between the two particle buffers, so a stage captured at parity q replays correctly
+  // only at parity q. Kernels inside them read the stage index from the device counter.
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int g_R[2] = {0, 0};
+  int64_t g_launches[2] = {0, 0};
+  int parity = 0;             // 0: theta/u/ell/sig2/blk are the buffers allocated first
+  bool capturing = false;     // inside a stream capture: no tracing events
+  int stage_dev = 0;          // kernels read the stage index from the device counter
+  bool dev_stage_synced = false;  // the device counter equals stage
   // host mirrors
   int stage = 0, moves_in_stage = 0;
   int64_t launches = 0;
@@ -134,7 +144,7 @@ struct ProfScope {
   int group;
   cudaEvent_t a = nullptr;
   ProfScope(smc_ctx *c_, int g) : c(c_), group(g) {
-    if (c->prof_on) {
+    if (c->prof_on && !c->capturing) {
       a = take_event(c);
       cudaEventRecord(a, c->stream);
     }
@@ -147,6 +157,14 @@ struct ProfScope {
     }
   }
 };
+
+void drop_graphs(smc_ctx *c) {
+  for (int q = 0; q < 2; ++q) {
+    if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
+    c->gexec[q] = nullptr;
+    c->g_R[q] = 0;
+  }
+}
 
 int res_launch(smc_ctx *c, int tile, const EstArgs &a, bool dry) {
   if (c->x_dtype == SMC_F64) return res_launch_f64(tile, a, c->stream, c->sms, dry);
@@ -574,6 +592,7 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
 int smc_free(smc_ctx *c) {
   if (!c) return SMC_OK;
   cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
   for (void *q : c->allocs) cudaFree(q);
   for (auto &v : c->prof)
     for (auto &pr : v) {
@@ -592,6 +611,7 @@ const char *smc_last_error(const smc_ctx *c) {
 int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
   if (!c) return SMC_ERR_ARG;
   c->stage += 1;
+  if (!c->stage_dev) c->dev_stage_synced = false;
   c->moves_in_stage = 0;
   int nl = 0;
   int e;
@@ -627,7 +647,8 @@ int smc_resample(smc_ctx *c, int32_t *ancestors) {
   if (!c) return SMC_ERR_ARG;
   ProfScope ps(c, 5);
   LAUNCH(c,
-         resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->W, c->cum, c->anc,
+         resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->stage_dev, c->W,
+                  c->cum, c->anc,
                   c->theta, c->theta_alt, c->u, c->u_alt, c->ell, c->ell_alt, c->sig2,
                   c->sig2_alt, c->blk, c->blk_alt, c->logW, c->W, c->st, c->stream),
          3);
@@ -636,6 +657,7 @@ int smc_resample(smc_ctx *c, int32_t *ancestors) {
   std::swap(c->ell, c->ell_alt);
   std::swap(c->sig2, c->sig2_alt);
   std::swap(c->blk, c->blk_alt);
+  c->parity ^= 1;
   if (ancestors)
     CUDA_OK(c, cudaMemcpyAsync(ancestors, c->anc, sizeof(int32_t) * c->N, cudaMemcpyDefault,
                                c->stream));
@@ -659,6 +681,7 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     a.blk = c->blk;
     a.blk_prop = c->blk_prop;
     a.move = c->moves_in_stage + r;
+    a.stage_dev = c->stage_dev;
     LAUNCH(c, est_launch(c, 1, a), 0);
     LAUNCH(c, hmc_launch(c, a), 0);
   }
@@ -672,6 +695,87 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     if (acc_theta) *acc_theta = (double)h.acc_theta / ((double)c->N * R);
     return check_err_bits(c, h);
   }
+  return SMC_OK;
+}
+
+// The host-side effects of one stage, mirrored on a graph replay: stage counters, the resampling
+// buffer swap, the launch count.
+static void mirror_stage(smc_ctx *c, int R, int q) {
+  c->stage += 1;
+  c->moves_in_stage = R;
+  std::swap(c->theta, c->theta_alt);
+  std::swap(c->u, c->u_alt);
+  std::swap(c->ell, c->ell_alt);
+  std::swap(c->sig2, c->sig2_alt);
+  std::swap(c->blk, c->blk_alt);
+  c->parity ^= 1;
+  c->launches += c->g_launches[q];
+}
+
+static int stage_body(smc_ctx *c, int R) {
+  int r = smc_reweight(c, nullptr, nullptr, nullptr);
+  if (!r) r = smc_resample(c, nullptr);
+  if (!r) r = smc_move(c, R, nullptr, nullptr);
+  return r;
+}
+
+int smc_stage(smc_ctx *c, int32_t R, int32_t use_graph) {
+  if (!c) return SMC_ERR_ARG;
+  if (R < 1 || R > 256) return fail(c, SMC_ERR_ARG, "R must be in [1, 256]");
+  if (!use_graph) return stage_body(c, R);
+  if (!c->dev_stage_synced) {
+    LAUNCH(c, stage_set(c->st, c->stage, c->stream), 1);
+    c->dev_stage_synced = true;
+  }
+  const int q = c->parity;
+  if (c->gexec[q] && c->g_R[q] == R) {
+    CUDA_OK(c, cudaGraphLaunch(c->gexec[q], c->stream));
+    mirror_stage(c, R, q);
+    return SMC_OK;
+  }
+  if (c->gexec[q]) {
+    cudaGraphExecDestroy(c->gexec[q]);
+    c->gexec[q] = nullptr;
+  }
+  // Capture on a private stream (the legacy default stream cannot be captured). Capturing runs the
+  // stage's host code, which advances the host-side state as if the stage had run; the graph is
+  // launched right after, on the context's stream, so device and host agree again.
+  cudaStream_t cap;
+  CUDA_OK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaStream_t orig = c->stream;
+  const int64_t l0 = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return fail(c, SMC_ERR_CUDA, std::string("stage capture: ") + cudaGetErrorString(e));
+  }
+  c->stream = cap;
+  c->capturing = true;
+  c->stage_dev = 1;
+  int r = stage_advance(c->st, cap);
+  c->launches += 1;
+  if (!r) r = stage_body(c, R);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+  c->stream = orig;
+  c->capturing = false;
+  c->stage_dev = 0;
+  cudaStreamDestroy(cap);
+  if (r || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    c->dev_stage_synced = false;
+    if (r) return r;
+    return fail(c, SMC_ERR_CUDA, std::string("stage capture: ") + cudaGetErrorString(e2));
+  }
+  e = cudaGraphInstantiate(&c->gexec[q], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->gexec[q] = nullptr;
+    return fail(c, SMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  c->g_R[q] = R;
+  c->g_launches[q] = c->launches - l0;
+  CUDA_OK(c, cudaGraphLaunch(c->gexec[q], c->stream));
   return SMC_OK;
 }
 
@@ -859,6 +963,7 @@ int smc_set_scalars(smc_ctx *c, int32_t stage, double a, double eps, double log_
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->stage = stage;
   c->moves_in_stage = 0;
+  c->dev_stage_synced = false;
   return SMC_OK;
 }
 
@@ -938,6 +1043,7 @@ int smc_autotune(smc_ctx *c, int32_t *tile, int32_t *hmc_kernel) {
     }
   }
   c->res_tile = best_res;
+  drop_graphs(c);  // captured stages used the previous kernels
   CUDA_OK(c, cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   cudaEventDestroy(e0);

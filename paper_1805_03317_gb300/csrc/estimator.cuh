@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
   W.init(wbase, a.Yo);
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), a.p, slots);
-  const uint32_t smv = stage_move(a.stage, a.move);
+  const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const Stream sblk(a.seed, kUpmBlock, smv, (uint32_t)i);
   const Stream sidx(a.seed, kUpmIdx, smv, (uint32_t)i);
   const int g = (int)draw_index(sblk.draw(0), (uint64_t)a.G);
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(p);
   W.init(wbase, a.Yo);
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), p, slots);
-  const uint32_t smv = stage_move(a.stage, a.move);
+  const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const double temp = a.st->a;
   const CT eps = (CT)a.st->eps;
   CT *th_g = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;

@@ -67,6 +67,7 @@ struct EstArgs {
   DevState *st;
   // autograd pair: per-row d, r [B, m] (state type), upstream gradients of l_hat, sigma2_hat [B]
   void *dsave, *rsave;
+  int stage_dev;          // 1: the stage index comes from st->stage (graph replays), else stage
   const double *g_ell, *g_sig2;
 };
 
@@ -125,11 +126,15 @@ int weighted_moments(int is_f64, int N, int p, const double *W, const void *thet
                      double *partials, double *mean, double *Sigma, cudaStream_t s);
 int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double *chol,
                 void *Sigma_ct, void *Linv_ct, double *work, DevState *st, cudaStream_t s);
-int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, const double *W,
-             uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
+// stage_dev: 1 = the resampling draw's stage index comes from st->stage (graph replays).
+int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, int stage_dev,
+             const double *W, uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
              int32_t *u_out, const double *ell, double *ell_out, const double *sig2,
              double *sig2_out, const double *blk, double *blk_out, double *logW, double *Wout,
              DevState *st, cudaStream_t s);
+// Device stage counter used by graph replays: set it, or advance it by one (single-thread kernels).
+int stage_set(DevState *st, int stage, cudaStream_t s);
+int stage_advance(DevState *st, cudaStream_t s);
 int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_t s);
 int eps_update(int N, int R, DevState *st, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   const CT inv_s2 = (CT)a.inv_s2;
   const double nm = (double)a.n / (double)m, inv_m = 1.0 / (double)m;
   const CT ta = (CT)temp, ta2 = (CT)(temp * temp * nm * nm), tnm = (CT)(temp * nm);
-  const uint32_t smv = stage_move(a.stage, a.move);
+  const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const int fam = a.fam;
   const bool col = lane < p;
   // per-lane column constants (lane c holds column c)

@@ -913,7 +913,8 @@ int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads)
-    k_res_scan(int N, const double *W, uint64_t *cum, uint64_t seed, int stage, DevState *st) {
+    k_res_scan(int N, const double *W, uint64_t *cum, uint64_t seed, int stage, int stage_dev,
+               DevState *st) {
   __shared__ unsigned long long tot[kScanThreads];
   const int tid = threadIdx.x;
   const int per = (N + kScanThreads - 1) / kScanThreads;
@@ -935,7 +936,7 @@ __global__ void __launch_bounds__(kScanThreads)
   }
   if (tid == kScanThreads - 1) {
     const unsigned long long T = tot[kScanThreads - 1];
-    const Stream rs(seed, kResample, stage_move(stage, 0), 0u);
+    const Stream rs(seed, kResample, stage_move(stage_dev ? st->stage : stage, 0), 0u);
     const double U = draw_uniform(rs.draw(0));
     st->res_T = T;
     st->res_off = (unsigned long long)floor(U * (double)T);
@@ -991,12 +992,12 @@ __global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, con
   }
 }
 
-int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, const double *W,
-             uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
+int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, int stage_dev,
+             const double *W, uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
              int32_t *u_out, const double *ell, double *ell_out, const double *sig2,
              double *sig2_out, const double *blk, double *blk_out, double *logW, double *Wout,
              DevState *st, cudaStream_t s) {
-  k_res_scan<<<1, kScanThreads, 0, s>>>(N, W, cum, seed, stage, st);
+  k_res_scan<<<1, kScanThreads, 0, s>>>(N, W, cum, seed, stage, stage_dev, st);
   k_res_ancestors<<<(N + 255) / 256, 256, 0, s>>>(N, cum, anc, st);
   const int gw = (N * 32 + 255) / 256;
   const int grid = gw < 152 * 16 ? gw : 152 * 16;
@@ -1056,6 +1057,24 @@ __global__ void k_round_f32(int count, double *v) {
 int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s) {
   if (is_f64 || count <= 0) return 0;
   k_round_f32<<<(count + 255) / 256, 256, 0, s>>>(count, v);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace subsmc
+
+namespace subsmc {
+namespace {
+__global__ void k_stage_set(DevState *st, int stage) { st->stage = stage; }
+__global__ void k_stage_advance(DevState *st) { st->stage += 1; }
+}  // namespace
+
+int stage_set(DevState *st, int stage, cudaStream_t s) {
+  k_stage_set<<<1, 1, 0, s>>>(st, stage);
+  return (int)cudaGetLastError();
+}
+
+int stage_advance(DevState *st, cudaStream_t s) {
+  k_stage_advance<<<1, 1, 0, s>>>(st);
   return (int)cudaGetLastError();
 }
 

@@ -107,6 +107,13 @@ def smc_move(ctx: Context, R: int):
     return au.value, at.value
 
 
+def smc_stage(ctx: Context, R: int, use_graph: bool = True):
+    """One stage (reweight, resample, R moves) without host synchronisation; with use_graph the
+    stage is replayed as one CUDA graph after its first capture."""
+    check(_abi.load().smc_stage(ctx.handle, int(R), 1 if use_graph else 0), "smc_stage",
+          ctx.handle)
+
+
 def loglik_est(ctx: Context, theta: torch.Tensor, u: torch.Tensor):
     B = theta.shape[0]
     theta = theta.to(ctx.state_dtype).contiguous()
