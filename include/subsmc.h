@@ -82,6 +82,10 @@ typedef struct {
                              /* resident tile k-2                                                  */
   int32_t cv_kernel;         /* control-variate moments: 0 = automatic (tensor cores, tcgen05,     */
                              /* for BF16 storage with p <= 128; SIMT otherwise), 1 = SIMT          */
+  int32_t full_data;         /* 1: the comparison method of Sec. 4, full-data SMC: the cache holds  */
+                             /* the exact l(theta) (sigma2 = 0), smc_move runs HMC on the exact    */
+                             /* tempered posterior with loglik_full forces (no u update); BF16     */
+                             /* storage and p <= 64 only. 0: subsampling SMC                       */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */
@@ -153,6 +157,14 @@ int loglik_est(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, dou
  * (the HMC force of Algorithm 1 step 2). grad: device [B, p] state type; ell, sigma2 may be NULL. */
 int loglik_grad(smc_ctx *ctx, int32_t B, const void *theta, const int32_t *u, double a,
                 void *grad, double *ell, double *sigma2);
+
+/* Full-data log-likelihood, the comparison method of the paper's experiments (Sec. 4): for B
+ * particles, ell = sum_{k=1}^{n} l_k(x_k'theta) over all n rows (including the per-row constants)
+ * and grad = a * sum_k l'_k(x_k'theta) x_k + grad log p(theta). The linear predictor
+ * [B x p] . [p x n] and the gradient contraction [B x n] . [n x p] run on the tensor cores
+ * (tcgen05); needs BF16 storage and p <= 64 (else SMC_ERR_ARG). theta: device [B, p] float;
+ * ell: device [B] double or NULL; grad: device [B, p] float or NULL. Scratch is context-owned. */
+int loglik_full(smc_ctx *ctx, int32_t B, const void *theta, double a, double *ell, void *grad);
 
 /* Forward half of the differentiable estimator: l_hat and sigma2_hat as loglik_est, and for every
  * row j of every particle the increment d_j = l(eta_j) - q_j(theta) and its eta-derivative

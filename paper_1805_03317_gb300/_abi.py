@@ -28,7 +28,8 @@ class SmcProblem(ctypes.Structure):
 class SmcConfig(ctypes.Structure):
     _fields_ = [("N", c_i32), ("m", c_i32), ("G", c_i32), ("L", c_i32), ("ess_frac", c_d),
                 ("seed", c_u64), ("search_k", c_i32), ("search_rounds", c_i32), ("eps0", c_d),
-                ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32)]
+                ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
+                ("full_data", c_i32)]
 
 
 # name -> (restype, argtypes)
@@ -43,6 +44,7 @@ SIGNATURES = {
     "smc_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
     "loglik_est": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "loglik_grad": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_d, c_vp, c_vp, c_vp]),
+    "loglik_full": (ctypes.c_int, [c_vp, c_i32, c_vp, c_d, c_vp, c_vp]),
     "loglik_fwd": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "loglik_bwd": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "smc_get_particles": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),

@@ -65,6 +65,19 @@ struct smc_ctx {
   bool capturing = false;     // inside a stream capture: no tracing events
   int stage_dev = 0;          // kernels read the stage index from the device counter
   bool dev_stage_synced = false;  // the device counter equals stage
+  // full-data comparison (loglik_full): FP64 per-particle accumulators, timeout flag, constant
+  double *full_acc = nullptr;
+  int64_t full_cap = 0;
+  int *full_flag = nullptr;
+  double *full_const_d = nullptr;
+  double full_const = 0.0;
+  bool full_const_ready = false;
+  // full-data comparison SMC (smc_config.full_data): the moves use the exact log-likelihood
+  int full_data = 0;
+  void *fm_thp = nullptr, *fm_rho = nullptr, *fm_g = nullptr;
+  double *fm_ell = nullptr, *fm_h0 = nullptr;
+  cudaGraphExec_t fm_graph = nullptr;
+  int64_t fm_launches = 0;
   // host mirrors
   int stage = 0, moves_in_stage = 0;
   int64_t launches = 0;
@@ -370,7 +383,60 @@ int set_centre(smc_ctx *c) {
 }
 
 // Recompute the per-particle cache (l_hat, sigma2_hat, block sums) at the current particles.
+// Full-data log-likelihood (the comparison method): scratch, the theta-free constant (once), and
+// one evaluation without host synchronisation.
+int full_prepare(smc_ctx *c, int64_t B) {
+  if (c->x_dtype != SMC_BF16 || c->p > 64)
+    return fail(c, SMC_ERR_ARG, "the full-data kernel needs BF16 storage and p <= 64");
+  if (!c->full_const_ready) {
+    if (!c->full_flag) ALLOC(c, c->full_flag, 2 * sizeof(double));  // flag, then the constant
+    c->full_const_d = reinterpret_cast<double *>(c->full_flag) + 1;
+    LAUNCH(c,
+           full_loglik_const(c->Xp, c->n, c->S, c->Yo, c->fam, c->noise_sigma * c->noise_sigma,
+                             c->full_const_d, c->stream),
+           1);
+    CUDA_OK(c, cudaMemcpyAsync(&c->full_const, c->full_const_d, sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemsetAsync(c->full_flag, 0, sizeof(int), c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    c->full_const_ready = true;
+  }
+  const int64_t need = full_acc_doubles(c->n, c->p, (int)B, c->sms);
+  if (need > c->full_cap) {
+    ALLOC(c, c->full_acc, sizeof(double) * (size_t)need);
+    c->full_cap = need;
+  }
+  return SMC_OK;
+}
+
+int full_eval(smc_ctx *c, int B, const void *theta, double a, const double *a_dev,
+                     double *ell, void *grad) {
+  ProfScope ps(c, 0);
+  LAUNCH(c,
+         full_loglik(c->Xp, c->n, c->p, c->S, c->Yo, c->fam, c->noise_sigma * c->noise_sigma,
+                     theta, B, a, a_dev, c->full_const, c->mu_ct, c->ivar_ct, c->full_acc,
+                     c->full_flag, ell, grad, c->sms, c->stream),
+         2);
+  return SMC_OK;
+}
+
+int full_check_flag(smc_ctx *c) {
+  int flag = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&flag, c->full_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (flag) return fail(c, SMC_ERR_TIMEOUT, "full-data kernel: tensor-core wait timed out");
+  return SMC_OK;
+}
+
 int refresh_cache(smc_ctx *c) {
+  if (c->full_data) {  // the exact log-likelihood; no subsample variance
+    int r = full_prepare(c, c->N);
+    if (r) return r;
+    if ((r = full_eval(c, c->N, c->theta, 1.0, nullptr, c->ell, nullptr))) return r;
+    CUDA_OK(c, cudaMemsetAsync(c->sig2, 0, sizeof(double) * c->N, c->stream));
+    CUDA_OK(c, cudaMemsetAsync(c->blk, 0, sizeof(double) * c->N * c->G * 2, c->stream));
+    return SMC_OK;
+  }
   EstArgs a = base_args(c);
   a.B = c->N;
   a.theta = c->theta;
@@ -447,6 +513,13 @@ int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const dou
   if ((r = set_centre(c))) return r;
   // particles
   const size_t Np = (size_t)c->N * p, Nm = (size_t)c->N * c->m, NG = (size_t)c->N * c->G * 2;
+  if (c->full_data) {  // full-data move buffers: trajectory position, momentum, force, l, H0
+    ALLOC(c, c->fm_thp, cts * Np);
+    ALLOC(c, c->fm_rho, cts * Np);
+    ALLOC(c, c->fm_g, cts * Np);
+    ALLOC(c, c->fm_ell, sizeof(double) * c->N);
+    ALLOC(c, c->fm_h0, sizeof(double) * c->N);
+  }
   ALLOC(c, c->theta, cts * Np);
   ALLOC(c, c->theta_alt, cts * Np);
   ALLOC(c, c->grad_scratch, cts * Np);
@@ -555,6 +628,12 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->rounds = rounds;
   c->eps0 = cfg->eps0;
   c->cv_kernel = cfg->cv_kernel == 1 ? 1 : 0;
+  c->full_data = cfg->full_data ? 1 : 0;
+  if (c->full_data && (P->x_dtype != SMC_BF16 || P->p > 64)) {
+    g_init_error = "full_data needs BF16 storage and p <= 64";
+    delete c;
+    return SMC_ERR_ARG;
+  }
   c->tile = cfg->tile_hint > 0 ? cfg->tile_hint - 1 : default_tile(c);
   Tile tl[32];
   const int nt = est_tiles(c, tl, 32);
@@ -593,6 +672,7 @@ int smc_free(smc_ctx *c) {
   if (!c) return SMC_OK;
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
+  if (c->fm_graph) cudaGraphExecDestroy(c->fm_graph);
   for (void *q : c->allocs) cudaFree(q);
   for (auto &v : c->prof)
     for (auto &pr : v) {
@@ -664,12 +744,18 @@ int smc_resample(smc_ctx *c, int32_t *ancestors) {
   return SMC_OK;
 }
 
+static int full_moves(smc_ctx *c, int R);
+
 int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
   if (!c) return SMC_ERR_ARG;
   if (R < 1) return fail(c, SMC_ERR_ARG, "R must be >= 1");
   if (c->moves_in_stage + R > 256) return fail(c, SMC_ERR_ARG, "at most 256 moves per stage");
   CUDA_OK(c, cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream));
-  for (int r = 0; r < R; ++r) {
+  if (c->full_data) {
+    int r = full_moves(c, R);
+    if (r) return r;
+  }
+  for (int r = 0; r < (c->full_data ? 0 : R); ++r) {
     EstArgs a = base_args(c);
     a.B = c->N;
     a.theta = c->theta;
@@ -848,6 +934,91 @@ int loglik_bwd(smc_ctx *c, int32_t B, const void *theta, const int32_t *u, const
   int r = sync_state(c, &h);
   if (r) return r;
   return check_err_bits(c, h);
+}
+
+int loglik_full(smc_ctx *c, int32_t B, const void *theta, double a, double *ell, void *grad) {
+  if (!c) return SMC_ERR_ARG;
+  if (B < 0 || (B > 0 && !theta) || (!ell && !grad))
+    return fail(c, SMC_ERR_ARG, "bad loglik_full arguments");
+  int r = full_prepare(c, B);
+  if (r) return r;
+  if (B == 0) return SMC_OK;
+  if ((r = full_eval(c, B, theta, a, nullptr, ell, grad))) return r;
+  return full_check_flag(c);
+}
+
+// R HMC moves of the full-data comparison SMC: per move the momentum and H0, then the leapfrog
+// loop (L + 1 full-data evaluations with kicks and drifts between them; replayed as one CUDA
+// graph after its first capture), then the Metropolis-Hastings step with the exact l at the end
+// point. Inside a stage capture (smc_stage) the loop is captured inline instead.
+static int full_leapfrog(smc_ctx *c) {
+  const int N = c->N, p = c->p;
+  const double *adev = &c->st->a;
+  int r = full_eval(c, N, c->fm_thp, 0.0, adev, nullptr, c->fm_g);
+  if (r) return r;
+  for (int l = 0; l < c->L; ++l) {
+    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->st, 1, c->stream), 1);
+    if ((r = full_eval(c, N, c->fm_thp, 0.0, adev, c->fm_ell, c->fm_g))) return r;
+    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->st, 0, c->stream), 1);
+  }
+  return SMC_OK;
+}
+
+static int full_moves(smc_ctx *c, int R) {
+  const int N = c->N, p = c->p;
+  for (int q = 0; q < R; ++q) {
+    const int move = c->moves_in_stage + q;
+    LAUNCH(c,
+           full_move_begin(N, p, c->theta, c->fm_thp, c->fm_rho, c->Linv_ct, c->Sigma_ct, c->mu_ct,
+                           c->ivar_ct, c->ell, c->seed, c->stage, c->stage_dev, move, c->st,
+                           c->fm_h0, c->stream),
+           1);
+    if (c->capturing) {
+      int r = full_leapfrog(c);
+      if (r) return r;
+    } else {
+      if (!c->fm_graph) {  // capture the loop once (its buffers and sizes never change)
+        cudaStream_t cap;
+        CUDA_OK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaStream_t orig = c->stream;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+          cudaStreamDestroy(cap);
+          return fail(c, SMC_ERR_CUDA, std::string("leapfrog capture: ") + cudaGetErrorString(e));
+        }
+        c->stream = cap;
+        c->capturing = true;
+        const int64_t l0 = c->launches;
+        int r = full_leapfrog(c);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        c->stream = orig;
+        c->capturing = false;
+        cudaStreamDestroy(cap);
+        c->fm_launches = c->launches - l0;
+        c->launches = l0;
+        if (r || e != cudaSuccess || !g) {
+          if (g) cudaGraphDestroy(g);
+          if (r) return r;
+          return fail(c, SMC_ERR_CUDA, std::string("leapfrog capture: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&c->fm_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          c->fm_graph = nullptr;
+          return fail(c, SMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+      }
+      CUDA_OK(c, cudaGraphLaunch(c->fm_graph, c->stream));
+      c->launches += c->fm_launches;
+    }
+    LAUNCH(c,
+           full_move_accept(N, p, c->theta, c->fm_thp, c->fm_rho, c->Sigma_ct, c->mu_ct, c->ivar_ct,
+                            c->ell, c->fm_ell, c->fm_h0, c->seed, c->stage, c->stage_dev, move,
+                            c->st, c->stream),
+           1);
+  }
+  return SMC_OK;
 }
 
 int smc_get_particles(smc_ctx *c, void *theta, int32_t *u, double *W) {

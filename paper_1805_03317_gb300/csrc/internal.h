@@ -140,6 +140,32 @@ int eps_update(int N, int R, DevState *st, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);
 int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s);
 
+// Full-data log-likelihood on the tensor cores (full_mma.cu), BF16 storage, p <= 64: ell[B] =
+// sum_k l_k(theta_i) (+ lconst), grad[B, p] = a grad l + grad log prior (state type, may be null).
+// acc: FP64 scratch of full_acc_doubles(); flag: device int set to 1 if a wait timed out.
+// a_dev: device temperature (overrides a when not null).
+int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
+                const void *theta, int B, double a, const double *a_dev, double lconst,
+                const void *mu, const void *ivar, double *acc, int *flag, double *ell, void *grad,
+                int sms, cudaStream_t s);
+// Full-data HMC move pieces (state type float, p <= 64): momentum and H0; half kick (+ drift);
+// Metropolis-Hastings with the exact log-likelihood at the end point.
+int full_move_begin(int N, int p, const void *theta, void *thp, void *rho, const void *Linv,
+                    const void *Sigma, const void *mu, const void *ivar, const double *ell,
+                    uint64_t seed, int stage, int stage_dev, int move, const DevState *st,
+                    double *h0, cudaStream_t s);
+int full_move_kick(int N, int p, void *thp, void *rho, const void *g, const void *Sigma,
+                   const DevState *st, int drift, cudaStream_t s);
+int full_move_accept(int N, int p, void *theta, const void *thp, const void *rho,
+                     const void *Sigma, const void *mu, const void *ivar, double *ell,
+                     const double *ell_new, const double *h0, uint64_t seed, int stage,
+                     int stage_dev, int move, DevState *st, cudaStream_t s);
+// Doubles of FP64 scratch (acc) that full_loglik needs for B particles.
+int full_acc_doubles(int64_t n, int p, int B, int sms);
+// Sum over rows of the theta-free part of the log-density into *out (device double).
+int full_loglik_const(const void *Xp, int64_t n, int S, int Yo, int fam, double sigma2,
+                      double *out, cudaStream_t s);
+
 // Message returned by smc_last_error(NULL) (abi.cu).
 void set_global_error(const std::string &msg);
 

@@ -55,7 +55,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              m: int, G: int, L: int, seed: int, ess_frac: float = 0.5, noise_sigma: float = 1.0,
              theta_bar=None, search_k: int = 16, search_rounds: int = 10, eps0: float = 0.0,
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
-             stream=None) -> Context:
+             full_data: bool = False, stream=None) -> Context:
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -68,7 +68,8 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
     prob = SmcProblem(FAMILY[family], n, p, X.data_ptr(), DTYPE[x_dtype], X.stride(0),
                       y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma))
     cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
-                    search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel)
+                    search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
+                    1 if full_data else 0)
     tb = None
     tb_ptr = None
     if theta_bar is not None:
@@ -135,6 +136,18 @@ def loglik_grad(ctx: Context, theta: torch.Tensor, u: torch.Tensor, a: float):
     check(_abi.load().loglik_grad(ctx.handle, B, _ptr(theta), _ptr(u), float(a), _ptr(grad),
                                   _ptr(ell), _ptr(s2)), "loglik_grad", ctx.handle)
     return grad, ell, s2
+
+
+def loglik_full(ctx: Context, theta: torch.Tensor, a: float = 1.0):
+    """Full-data l(theta) [B] float64 and the gradient of a l + log p [B, p] float32 (tensor
+    cores; BF16 storage, p <= 64)."""
+    B = theta.shape[0]
+    theta = theta.to(torch.float32).contiguous()
+    ell = torch.empty(B, dtype=torch.float64, device=theta.device)
+    grad = torch.empty_like(theta)
+    check(_abi.load().loglik_full(ctx.handle, B, _ptr(theta), float(a), _ptr(ell), _ptr(grad)),
+          "loglik_full", ctx.handle)
+    return grad, ell
 
 
 def loglik_fwd(ctx: Context, theta: torch.Tensor, u: torch.Tensor):
