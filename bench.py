@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--gather-tile", type=int, default=0,
                     help="estimator tile hint for the gather leg (0: autotune)")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph stage timing")
+    ap.add_argument("--no-full", action="store_true",
+                    help="skip the full-data comparison leg (about 5 s)")
     ap.add_argument("--no-gam", action="store_true",
                     help="skip the GAM gather leg (n=1e7, p=101; about 10-30 s of data generation)")
     ap.add_argument("--gam-n", type=int, default=10_000_000,
@@ -58,6 +60,14 @@ def parse():
     ap.add_argument("--gam-only", action="store_true",
                     help="run only the GAM gather leg and print its JSON (for profiling)")
     return ap.parse_args()
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 def peaks():
@@ -279,6 +289,47 @@ def gather_leg(S, dev, hbm, wl=None, reps=20, stages=3, tile_hint=0):
                       "hmc_achieved_gbs": hmc_bytes / (ms_h / max(n_h, 1) / 1e3) / 1e9}}
 
 
+def full_data_leg(S, wl, dev, R, tc_peak, stages=2, reps=5):
+    """The comparison method (full-data SMC, exact log-likelihood) on the same workload: one
+    loglik_full evaluation over all N particles x n rows (the tcgen05 kernel), and `stages` full
+    SMC stages (reweight, resample, R HMC moves with L + 1 full-data evaluations each)."""
+    import torch
+    X, y = device_workload(wl, dev)
+    ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=1, G=1, L=wl.L,
+                     seed=wl.seed, ess_frac=0.5, theta_bar=None, full_data=True)
+    del X, y
+    th, _, _ = S.smc_get_particles(ctx)
+    for _ in range(2):
+        S.loglik_full(ctx, th, 1.0)
+    S.smc_profile_enable(ctx, True)
+    S.smc_profile_read(ctx, "estimate")
+    for _ in range(reps):
+        S.loglik_full(ctx, th, 1.0)
+    n_e, ms_e = S.smc_profile_read(ctx, "estimate")
+    per_eval = ms_e / max(n_e, 1)
+    S.smc_profile_enable(ctx, False)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(stages):
+        run_stage(S, ctx, R)
+    t1.record()
+    torch.cuda.synchronize()
+    ms_stage = t0.elapsed_time(t1) / stages
+    S.smc_free(ctx)
+    kp = (wl.p + 15) // 16 * 16
+    mma_flops = 2.0 * wl.N * wl.n * kp * (3 + 2)  # GEMM1: 3 theta terms; GEMM2: 2 l' terms
+    return {"kernel": "k_full_mma (eta = Theta X', family terms, l' X on tcgen05)",
+            "ms_per_eval": per_eval,
+            "particle_rows_per_s": wl.N * wl.n / (per_eval / 1e3),
+            "tensor_tflops": mma_flops / (per_eval / 1e3) / 1e12,
+            "tensor_peak_tflops": tc_peak,
+            "ms_per_stage": ms_stage,
+            "grad_evals_per_s": wl.N * wl.n * R * (wl.L + 1) / (ms_stage / 1e3),
+            "note": "bound by the per-element family terms (3 MUFU ops per particle-row), not the "
+                    "MMAs"}
+
+
 def gam_leg(S, dev, hbm, tile_hint=0, n=10_000_000):
     """The GAM workload (Gaussian response, sigma = 0.5, n = 1e7, p = 101 B-spline columns, BF16;
     N = 16384, m = 5000, L = 25) through the gather leg: 82M gathered rows per estimator call."""
@@ -378,6 +429,11 @@ def gpu_arm(args):
         walls = {"bf16": full_run(S, wl, dev, R), "fp32": full_run(S, wl32, dev, R)}
         del wl32
 
+    full = None
+    if not args.no_full and rank == 0:
+        full = full_data_leg(S, wl, dev, R, bf16_peak())
+        full["subsampling_speedup_per_stage"] = full["ms_per_stage"] / (ms / args.steps)
+
     gather = None
     if not args.no_gather and rank == 0:
         gather = gather_leg(S, dev, hbm)
@@ -427,6 +483,7 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": bo},
         "fp32_storage": fp32,
         "graph_stages": graph,
+        "full_data_comparison": full,
         "hbm_gather_leg": gather,
         "gam_gather_leg": gam,
         "smc_wall_time": walls,
