@@ -259,6 +259,34 @@ int smc_profile_read(smc_ctx *ctx, int32_t group, int64_t *launches, double *tot
 int smc_resample_noalloc(int32_t N, const double *W, uint64_t seed, int32_t stage,
                          int32_t *ancestors, void *stream);
 
+/* ------------------------------------------------------------------------------------------- */
+/* Batches of independent posteriors                                                             */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Many independent problems (uneven n and p; BF16 storage) stepped together. One context per
+ * problem, created as by smc_init with cfgs[q] (all on the same stream; the estimator tile is
+ * the narrowest compiled tile that covers the widest row, the HMC kernel the streamed one). */
+typedef struct smc_batch smc_batch;
+int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const smc_config *cfgs,
+                   void *stream);
+int smc_batch_free(smc_batch *b);
+const char *smc_batch_last_error(const smc_batch *b);
+/* The context of problem q (owned by the batch: do not free it), for the per-problem calls
+ * (smc_get_particles, smc_get_status, loglik_est, ...). */
+int smc_batch_context(smc_batch *b, int32_t q, smc_ctx **ctx);
+/* The batch's estimator tile as a tile_hint value. */
+int smc_batch_tile(const smc_batch *b, int32_t *tile_hint);
+int64_t smc_batch_launch_count(const smc_batch *b);
+/* One stage of every problem (Algorithm 2 (a)-(f)): reweight and resample per problem, then per
+ * move one u-update launch and one HMC trajectory launch over the particles of all problems
+ * together, then the step sizes. use_graph = 1: the whole batch stage is captured once per buffer
+ * parity and replayed as one CUDA graph (kernels read the stage index from device counters), with
+ * results bit-identical to use_graph = 0 and to stepping each problem alone with the same tile. */
+int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph);
+/* Time the batched HMC launch for every compiled tile that covers the widest row (on scratch
+ * copies; the state is unchanged) and keep the fastest; output: the tile as a tile_hint value. */
+int smc_batch_autotune(smc_batch *b, int32_t *tile_hint);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,15 @@ SIGNATURES = {
     "smc_resample": (ctypes.c_int, [c_vp, c_vp]),
     "smc_move": (ctypes.c_int, [c_vp, c_i32, c_dp, c_dp]),
     "smc_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
+    "smc_batch_init": (ctypes.c_int, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(SmcProblem),
+                                      ctypes.POINTER(SmcConfig), c_vp]),
+    "smc_batch_free": (ctypes.c_int, [c_vp]),
+    "smc_batch_last_error": (ctypes.c_char_p, [c_vp]),
+    "smc_batch_context": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    "smc_batch_tile": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i32)]),
+    "smc_batch_launch_count": (ctypes.c_int64, [c_vp]),
+    "smc_batch_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
+    "smc_batch_autotune": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i32)]),
     "loglik_est": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "loglik_grad": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_d, c_vp, c_vp, c_vp]),
     "loglik_full": (ctypes.c_int, [c_vp, c_i32, c_vp, c_d, c_vp, c_vp]),

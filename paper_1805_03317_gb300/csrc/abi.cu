@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -1246,6 +1247,363 @@ int smc_profile_read(smc_ctx *c, int32_t group, int64_t *launches, double *total
   if (launches) *launches = (int64_t)c->prof[group].size();
   if (total_ms) *total_ms = tot;
   c->prof[group].clear();
+  return SMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batches of independent posteriors (many problems of uneven n and p stepped together): one context
+// per problem, and per move one u-update launch and one HMC launch over all particles of all
+// problems (the kernels find each particle's problem from the prefix offsets).
+// ------------------------------------------------------------------------------------------------
+struct smc_batch {
+  int P = 0, tile = 0, total = 0, wstride = 0, Rcap = 0;
+  std::vector<smc_ctx *> ctx;
+  cudaStream_t stream = nullptr;
+  int *offsets_d = nullptr;
+  EstArgs *args_d = nullptr;  // [Rcap] x [P] arguments of the batched launches
+  std::vector<EstArgs> args_h;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  EstArgs *gargs[2] = {nullptr, nullptr};  // the argument arrays each graph reads
+  int gR[2] = {0, 0};
+  int64_t launches = 0;
+  std::string err;
+};
+
+static int bfail(smc_batch *b, int code, const std::string &msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+// Arguments of move `move` for problem context c; swapped: use the buffers the next resampling
+// will make current (for graphs built before the stage's host code runs).
+static EstArgs batch_move_args(smc_ctx *c, int move, bool swapped, int stage_dev) {
+  EstArgs a = base_args(c);
+  a.B = c->N;
+  a.theta = a.theta_out = swapped ? c->theta_alt : c->theta;
+  a.u = a.u_mut = swapped ? c->u_alt : c->u;
+  a.ell = swapped ? c->ell_alt : c->ell;
+  a.sig2 = swapped ? c->sig2_alt : c->sig2;
+  a.blk = swapped ? c->blk_alt : c->blk;
+  a.blk_prop = c->blk_prop;
+  a.move = move;
+  a.stage_dev = stage_dev;
+  return a;
+}
+
+static int batch_upload(smc_batch *b, int R, bool swapped, int stage_dev) {
+  if (R > b->Rcap) {
+    if (b->args_d) cudaFree(b->args_d);
+    b->args_d = nullptr;
+    if (cudaMalloc(&b->args_d, sizeof(EstArgs) * (size_t)R * b->P) != cudaSuccess)
+      return bfail(b, SMC_ERR_OOM, "batch argument array");
+    b->Rcap = R;
+  }
+  b->args_h.resize((size_t)R * b->P);
+  for (int r = 0; r < R; ++r)
+    for (int q = 0; q < b->P; ++q)
+      b->args_h[(size_t)r * b->P + q] =
+          batch_move_args(b->ctx[q], swapped ? r : b->ctx[q]->moves_in_stage + r, swapped,
+                          stage_dev);
+  // synchronous with respect to the host (pageable source), before any capture begins
+  if (cudaMemcpyAsync(b->args_d, b->args_h.data(), sizeof(EstArgs) * (size_t)R * b->P,
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return bfail(b, SMC_ERR_CUDA, "batch argument upload");
+  return SMC_OK;
+}
+
+static int batch_moves(smc_batch *b, int R) {
+  for (int r = 0; r < R; ++r) {
+    BatchArgs ba;
+    ba.probs = b->args_d + (size_t)r * b->P;
+    ba.offsets = b->offsets_d;
+    ba.nprob = b->P;
+    ba.total = b->total;
+    ba.wstride = b->wstride;
+    int e = est_launch_batch_bf16(1, b->tile, ba, b->stream);
+    if (!e) e = est_launch_batch_bf16(2, b->tile, ba, b->stream);
+    if (e) return bfail(b, SMC_ERR_CUDA, std::string("batched move: ") +
+                                             cudaGetErrorString((cudaError_t)e));
+    b->launches += 2;
+  }
+  return SMC_OK;
+}
+
+// The stage of every problem: reweight and resample per problem, R batched moves, step sizes.
+static int batch_stage_body(smc_batch *b, int R, bool args_ready) {
+  for (smc_ctx *c : b->ctx) {
+    int r = smc_reweight(c, nullptr, nullptr, nullptr);
+    if (!r) r = smc_resample(c, nullptr);
+    if (r) return bfail(b, r, c->err);
+    if (cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "accept counters");
+  }
+  if (!args_ready) {
+    int r = batch_upload(b, R, false, 0);
+    if (r) return r;
+  }
+  int r = batch_moves(b, R);
+  if (r) return r;
+  for (smc_ctx *c : b->ctx) {
+    c->moves_in_stage += R;
+    if (eps_update(c->N, R, c->st, c->stream)) return bfail(b, SMC_ERR_CUDA, "step size");
+  }
+  return SMC_OK;
+}
+
+int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const smc_config *cfgs,
+                   void *stream) {
+  if (!out || P < 1 || !probs || !cfgs) return SMC_ERR_ARG;
+  *out = nullptr;
+  // one estimator tile for the whole batch: the narrowest compiled BF16 tile covering every row
+  int need = 0;
+  for (int q = 0; q < P; ++q) {
+    if (probs[q].x_dtype != SMC_BF16) {
+      g_init_error = "batches need BF16 storage";
+      return SMC_ERR_ARG;
+    }
+    const int yo = ((probs[q].p * 2 + 15) / 16) * 8;
+    if (yo > need) need = yo;
+  }
+  Tile tl[32];
+  const int nt = est_tiles_bf16(tl, 32);
+  int tile = -1;
+  for (int t = 0; t < nt; ++t) {
+    if (tl[t].T * tl[t].CPL < need) continue;
+    const int wt = tl[t].T * tl[t].CPL, wb = tile < 0 ? 1 << 30 : tl[tile].T * tl[tile].CPL;
+    if (wt < wb || (wt == wb && tl[t].T < tl[tile].T)) tile = t;
+  }
+  if (tile < 0) {
+    g_init_error = "no compiled tile covers the batch's widest row";
+    return SMC_ERR_ARG;
+  }
+  smc_batch *b = new smc_batch();
+  b->P = P;
+  b->tile = tile;
+  b->stream = (cudaStream_t)stream;
+  std::vector<int> off(P);
+  for (int q = 0; q < P; ++q) {
+    smc_config cfg = cfgs[q];
+    cfg.tile_hint = tile + 1;
+    cfg.hmc_kernel = 1;  // the batched HMC launch is the streamed trajectory kernel
+    cfg.full_data = 0;
+    smc_ctx *c = nullptr;
+    const int r = smc_init(&c, &probs[q], &cfg, nullptr, stream);
+    if (r != SMC_OK) {
+      const std::string m = "problem " + std::to_string(q) + ": " + g_init_error;
+      smc_batch_free(b);
+      g_init_error = m;
+      return r;
+    }
+    b->ctx.push_back(c);
+    off[q] = b->total;
+    b->total += c->N;
+    const int ws = est_warp_smem_bf16(tile, c->p);
+    if (ws > b->wstride) b->wstride = ws;
+  }
+  if (cudaMalloc(&b->offsets_d, sizeof(int) * P) != cudaSuccess ||
+      cudaMemcpy(b->offsets_d, off.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess) {
+    smc_batch_free(b);
+    g_init_error = "batch offsets";
+    return SMC_ERR_OOM;
+  }
+  *out = b;
+  return SMC_OK;
+}
+
+int smc_batch_free(smc_batch *b) {
+  if (!b) return SMC_OK;
+  if (b->stream || !b->ctx.empty()) cudaStreamSynchronize(b->stream);
+  for (int q = 0; q < 2; ++q) {
+    if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
+    if (b->gargs[q]) cudaFree(b->gargs[q]);
+  }
+  for (smc_ctx *c : b->ctx) smc_free(c);
+  if (b->offsets_d) cudaFree(b->offsets_d);
+  if (b->args_d) cudaFree(b->args_d);
+  delete b;
+  return SMC_OK;
+}
+
+const char *smc_batch_last_error(const smc_batch *b) {
+  return b ? b->err.c_str() : g_init_error.c_str();
+}
+
+int smc_batch_context(smc_batch *b, int32_t q, smc_ctx **ctx) {
+  if (!b || !ctx || q < 0 || q >= b->P) return SMC_ERR_ARG;
+  *ctx = b->ctx[q];
+  return SMC_OK;
+}
+
+int smc_batch_tile(const smc_batch *b, int32_t *tile_hint) {
+  if (!b || !tile_hint) return SMC_ERR_ARG;
+  *tile_hint = b->tile + 1;
+  return SMC_OK;
+}
+
+int64_t smc_batch_launch_count(const smc_batch *b) {
+  if (!b) return 0;
+  int64_t n = b->launches;
+  for (smc_ctx *c : b->ctx) n += c->launches;
+  return n;
+}
+
+int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph) {
+  if (!b) return SMC_ERR_ARG;
+  if (R < 1 || R > 256) return bfail(b, SMC_ERR_ARG, "R must be in [1, 256]");
+  if (!use_graph) return batch_stage_body(b, R, false);
+  const int q = b->ctx[0]->parity;
+  for (smc_ctx *c : b->ctx) {
+    if (c->parity != q) return bfail(b, SMC_ERR_STATE, "batch problems out of step");
+    if (!c->dev_stage_synced) {
+      if (stage_set(c->st, c->stage, b->stream)) return bfail(b, SMC_ERR_CUDA, "stage counter");
+      c->dev_stage_synced = true;
+    }
+  }
+  if (!(b->gexec[q] && b->gR[q] == R)) {
+    if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
+    b->gexec[q] = nullptr;
+    if (b->gargs[q]) cudaFree(b->gargs[q]);
+    b->gargs[q] = nullptr;
+    // arguments of this parity's graph: the buffers after the stage's resampling, stage index
+    // from the device counters; kept in their own slot of the argument array
+    int r = batch_upload(b, R, true, 1);
+    if (r) return r;
+    EstArgs *keep = b->args_d;  // becomes this graph's argument array
+    b->gargs[q] = keep;
+    b->args_d = nullptr;
+    b->Rcap = 0;
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "capture stream");
+    cudaStream_t orig = b->stream;
+    cudaStreamSynchronize(orig);  // the argument upload has completed
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return bfail(b, SMC_ERR_CUDA, "batch capture");
+    }
+    b->stream = cap;
+    for (smc_ctx *c : b->ctx) {
+      c->stream = cap;
+      c->capturing = true;
+      c->stage_dev = 1;
+    }
+    b->args_d = keep;
+    b->Rcap = R;
+    r = 0;
+    for (smc_ctx *c : b->ctx)
+      if (!r && stage_advance(c->st, cap)) r = SMC_ERR_CUDA;
+    if (!r) r = batch_stage_body(b, R, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    b->stream = orig;
+    for (smc_ctx *c : b->ctx) {
+      c->stream = orig;
+      c->capturing = false;
+      c->stage_dev = 0;
+    }
+    cudaStreamDestroy(cap);
+    // the capture consumed this argument array: the next upload gets a fresh one
+    b->args_d = nullptr;
+    b->Rcap = 0;
+    if (r || e2 != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return r ? r : bfail(b, SMC_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e2));
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&b->gexec[q], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+      b->gexec[q] = nullptr;
+      return bfail(b, SMC_ERR_CUDA, "batch graph instantiate");
+    }
+    b->gR[q] = R;
+    if (cudaGraphLaunch(b->gexec[q], b->stream) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "batch graph launch");
+    return SMC_OK;  // capturing ran the host side of the stage; the launch runs its device side
+  }
+  if (cudaGraphLaunch(b->gexec[q], b->stream) != cudaSuccess)
+    return bfail(b, SMC_ERR_CUDA, "batch graph launch");
+  for (smc_ctx *c : b->ctx) {  // the host side of the replayed stage
+    c->stage += 1;
+    c->moves_in_stage = R;
+    std::swap(c->theta, c->theta_alt);
+    std::swap(c->u, c->u_alt);
+    std::swap(c->ell, c->ell_alt);
+    std::swap(c->sig2, c->sig2_alt);
+    std::swap(c->blk, c->blk_alt);
+    c->parity ^= 1;
+  }
+  return SMC_OK;
+}
+
+int smc_batch_autotune(smc_batch *b, int32_t *tile_hint) {
+  if (!b) return SMC_ERR_ARG;
+  int need = 0;
+  for (smc_ctx *c : b->ctx)
+    if (c->Sx > need) need = c->Sx;
+  Tile tl[32];
+  const int nt = est_tiles_bf16(tl, 32);
+  // scratch copies: the batched HMC runs on theta_alt, ell_alt, sig2_alt, blk_alt
+  b->args_h.resize(b->P);
+  for (int q = 0; q < b->P; ++q) {
+    smc_ctx *c = b->ctx[q];
+    if (cudaMemcpyAsync(c->theta_alt, c->theta, ct_size(c) * c->N * c->p, cudaMemcpyDeviceToDevice,
+                        b->stream) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "autotune copy");
+    EstArgs a = batch_move_args(c, 255, false, 0);
+    a.theta = a.theta_out = c->theta_alt;
+    a.ell = c->ell_alt;
+    a.sig2 = c->sig2_alt;
+    a.blk = c->blk_alt;
+    b->args_h[q] = a;
+  }
+  EstArgs *tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(EstArgs) * b->P) != cudaSuccess)
+    return bfail(b, SMC_ERR_OOM, "autotune arguments");
+  cudaMemcpyAsync(tmp, b->args_h.data(), sizeof(EstArgs) * b->P, cudaMemcpyHostToDevice, b->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = b->tile;
+  float best_ms = 1e30f;
+  for (int t = 0; t < nt; ++t) {
+    if (tl[t].T * tl[t].CPL < need) continue;
+    int ws = 0;
+    for (smc_ctx *c : b->ctx) ws = std::max(ws, est_warp_smem_bf16(t, c->p));
+    BatchArgs ba{tmp, b->offsets_d, b->P, b->total, ws};
+    float tot = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      ok = est_launch_batch_bf16(2, t, ba, b->stream) == 0;
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // the first run warms up
+    }
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tmp);
+  b->tile = best;
+  b->wstride = 0;
+  for (smc_ctx *c : b->ctx) {
+    b->wstride = std::max(b->wstride, est_warp_smem_bf16(best, c->p));
+    c->tile = best;
+    cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), b->stream);
+  }
+  for (int q = 0; q < 2; ++q) {  // graphs were built for the previous tile
+    if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
+    if (b->gargs[q]) cudaFree(b->gargs[q]);
+    b->gexec[q] = nullptr;
+    b->gargs[q] = nullptr;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, SMC_ERR_CUDA, "autotune");
+  if (tile_hint) *tile_hint = best + 1;
   return SMC_OK;
 }
 

@@ -441,6 +441,19 @@ __device__ __forceinline__ void refresh_delta(WarpEval<XT, T, CPL, U, K> &W, con
   W.load_slots(sm.dl, a.p, W.dl);
 }
 
+// Problem of global particle g: the last q with offsets[q] <= g (offsets ascending, offsets[0] = 0).
+__device__ __forceinline__ int batch_problem(const int *offsets, int nprob, int g) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(offsets + mid) <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Kernel 1: the plain estimator on caller particles (loglik_est / loglik_grad, cache refresh).
 // ------------------------------------------------------------------------------------------------
@@ -579,15 +592,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_backward(EstArgs a) {
 //   log r = a (n/m)(S_g* - S_g) - (a^2/2)(sigma2* - sigma2).
 // ------------------------------------------------------------------------------------------------
 template <typename XT, int T, int CPL, int U, int WARPS, bool K>
-__global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
+__device__ __forceinline__ void upm_body(const EstArgs &a, int i, unsigned char *wbase) {
   using CT = typename Store<XT>::CT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * WARPS + warp;
-  if (i >= a.B) return;
   WarpEval<XT, T, CPL, U, K> W;
   const int slots = T * CPL;
-  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p);
   W.init(wbase, a.Yo);
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), a.p, slots);
   const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
@@ -642,6 +650,28 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
     }
   }
 }
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * WARPS + warp;
+  if (i >= a.B) return;
+  upm_body<XT, T, CPL, U, WARPS, K>(a, i,
+                                  smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p));
+}
+// All particles of a batch of independent posteriors in one launch: the global warp index picks
+// the problem (offsets: first particle of each problem) and the particle within it; per-warp
+// shared memory has the batch's largest stride.
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_upm_batch(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * WARPS + warp;
+  if (g >= b.total) return;
+  const int q = batch_problem(b.offsets, b.nprob, g);
+  upm_body<XT, T, CPL, U, WARPS, K>(b.probs[q], g - b.offsets[q],
+                                  smem_raw + (size_t)warp * b.wstride);
+}
 
 // ------------------------------------------------------------------------------------------------
 // Kernel 3: one HMC move of theta given u (Algorithm 1 step 2), the whole trajectory in one launch.
@@ -651,16 +681,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
 // On acceptance theta, l_hat, sigma2_hat and the block sums at the end point replace the cache.
 // ------------------------------------------------------------------------------------------------
 template <typename XT, int T, int CPL, int U, int WARPS, bool K>
-__global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
+__device__ __forceinline__ void hmc_body(const EstArgs &a, int i, unsigned char *wbase) {
   using CT = typename Store<XT>::CT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * WARPS + warp;
-  if (i >= a.B) return;
   WarpEval<XT, T, CPL, U, K> W;
   const int slots = T * CPL;
   const int p = a.p;
-  unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(p);
   W.init(wbase, a.Yo);
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), p, slots);
   const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
@@ -730,6 +755,28 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
     }
   }
 }
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * WARPS + warp;
+  if (i >= a.B) return;
+  hmc_body<XT, T, CPL, U, WARPS, K>(a, i,
+                                  smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p));
+}
+// All particles of a batch of independent posteriors in one launch: the global warp index picks
+// the problem (offsets: first particle of each problem) and the particle within it; per-warp
+// shared memory has the batch's largest stride.
+template <typename XT, int T, int CPL, int U, int WARPS, bool K>
+__global__ void __launch_bounds__(WARPS * 32) k_hmc_batch(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * WARPS + warp;
+  if (g >= b.total) return;
+  const int q = batch_problem(b.offsets, b.nprob, g);
+  hmc_body<XT, T, CPL, U, WARPS, K>(b.probs[q], g - b.offsets[q],
+                                  smem_raw + (size_t)warp * b.wstride);
+}
 
 // ------------------------------------------------------------------------------------------------
 // Launch helpers
@@ -761,6 +808,26 @@ inline int launch_tile(int op, const EstArgs &a, cudaStream_t s) {
     e = cudaFuncSetAttribute(k_backward<XT, T, CPL, U, WARPS, K>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_backward<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(a);
+  }
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaGetLastError();
+}
+
+// Batched launch over all particles of a batch: op 1 = u-update, 2 = HMC move.
+template <typename XT, int T, int CPL, int U, int WARPS, bool K = false>
+inline int launch_tile_batch(int op, const BatchArgs &b, cudaStream_t s) {
+  const size_t smem = (size_t)WARPS * b.wstride;
+  const dim3 grid((b.total + WARPS - 1) / WARPS), block(WARPS * 32);
+  if (b.total <= 0) return 0;
+  cudaError_t e;
+  if (op == 1) {
+    e = cudaFuncSetAttribute(k_upm_batch<XT, T, CPL, U, WARPS, K>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_upm_batch<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(b);
+  } else {
+    e = cudaFuncSetAttribute(k_hmc_batch<XT, T, CPL, U, WARPS, K>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_hmc_batch<XT, T, CPL, U, WARPS, K><<<grid, block, smem, s>>>(b);
   }
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();

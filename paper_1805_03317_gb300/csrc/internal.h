@@ -71,6 +71,15 @@ struct EstArgs {
   const double *g_ell, *g_sig2;
 };
 
+// A batch of independent posteriors launched together: per-problem arguments (device array), the
+// first global particle of each problem (ascending, offsets[0] = 0), the particle total and the
+// per-warp shared-memory stride (the largest over the batch's problems).
+struct BatchArgs {
+  const EstArgs *probs;
+  const int *offsets;
+  int nprob, total, wstride;
+};
+
 // Tile shape of the estimator: T lanes share one row, each lane holds CPL element slots; NST
 // ring stages of streamed rows per warp (resident kernel: unused); warps per CTA; pipe: the
 // streamed kernels overlap the gradient partials of one sweep with x'delta of the next (NST >= 3).
@@ -85,6 +94,10 @@ struct Tile {
 int est_launch_f64(int op, int tile, const EstArgs &a, cudaStream_t s);
 int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s);
 int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s);
+// Batched u-update (op 1) or streamed HMC move (op 2) over all particles of a batch (BF16 storage);
+// per-warp shared-memory bytes of a tile for p covariates (0 for an unknown tile).
+int est_launch_batch_bf16(int op, int tile, const BatchArgs &b, cudaStream_t s);
+int est_warp_smem_bf16(int tile, int p);
 int est_tiles_f64(Tile *out, int cap);
 int est_tiles_f32(Tile *out, int cap);
 int est_tiles_bf16(Tile *out, int cap);

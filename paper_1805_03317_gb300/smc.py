@@ -34,16 +34,18 @@ class Context:
     """Owns one smc_ctx; the handle is passed to the module-level entry points."""
 
     def __init__(self, handle: ctypes.c_void_p, N: int, m: int, G: int, p: int, n: int,
-                 state_dtype: torch.dtype, device: torch.device, keepalive):
+                 state_dtype: torch.dtype, device: torch.device, keepalive, owned: bool = True):
         self.handle = handle
         self.N, self.m, self.G, self.p, self.n = N, m, G, p, n
         self.state_dtype = state_dtype
         self.device = device
         self._keepalive = keepalive
+        self.owned = owned  # False: a problem of a Batch, freed with the batch
 
     def __del__(self):
         try:
-            smc_free(self)
+            if self.owned:
+                smc_free(self)
         except Exception:
             pass
 
@@ -85,7 +87,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
 
 
 def smc_free(ctx: Context) -> None:
-    if ctx.handle:
+    if ctx.handle and ctx.owned:
         _abi.load().smc_free(ctx.handle)
         ctx.handle = ctypes.c_void_p()
 
@@ -344,3 +346,104 @@ def smc_resample_noalloc(W: torch.Tensor, seed: int, stage: int, ancestors: torc
         rc = _abi.load().smc_resample_noalloc(W.numel(), _ptr(W), int(seed) & ((1 << 64) - 1),
                                               int(stage), _ptr(ancestors), _stream_handle(stream))
     check(rc, "smc_resample_noalloc", None)
+
+
+# ------------------------------------------------------------------------------------------------
+# Batches of independent posteriors
+# ------------------------------------------------------------------------------------------------
+class Batch:
+    """Owns one smc_batch; `contexts` are its problems (for per-problem calls)."""
+
+    def __init__(self, handle, contexts, keepalive):
+        self.handle = handle
+        self.contexts = contexts
+        self._keepalive = keepalive
+
+    def __del__(self):
+        try:
+            smc_batch_free(self)
+        except Exception:
+            pass
+
+
+def _bcheck(code: int, where: str, handle) -> None:
+    if code != 0:
+        msg = _abi.load().smc_batch_last_error(handle)
+        raise _abi.SmcError(code, where, (msg or b"").decode(errors="replace"))
+
+
+def smc_batch_init(problems, stream=None) -> Batch:
+    """problems: list of dicts with X, y, family, prior_mean, prior_var and the smc_init settings
+    (N, m, G, L, seed; optional ess_frac, noise_sigma, eps0, search_k, search_rounds)."""
+    lib = _abi.load()
+    P = len(problems)
+    probs = (SmcProblem * P)()
+    cfgs = (SmcConfig * P)()
+    keep = []
+    meta = []
+    for q, d in enumerate(problems):
+        X = d["X"]
+        if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1 or X.dtype != torch.bfloat16:
+            raise ValueError("batch problems need 2-D CUDA BF16 X with unit column stride")
+        y = d["y"].to(device=X.device, dtype=torch.float32).contiguous()
+        n, p = X.shape
+        pm = np.ascontiguousarray(d["prior_mean"], dtype=np.float64)
+        pv = np.ascontiguousarray(d["prior_var"], dtype=np.float64)
+        probs[q] = SmcProblem(FAMILY[d["family"]], n, p, X.data_ptr(), DTYPE["bf16"], X.stride(0),
+                              y.data_ptr(), _dp(pm), _dp(pv), float(d.get("noise_sigma", 1.0)))
+        cfgs[q] = SmcConfig(d["N"], d["m"], d["G"], d["L"], float(d.get("ess_frac", 0.5)),
+                            int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
+                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 0)
+        keep += [y, pm, pv]
+        meta.append((d["N"], d["m"], d["G"], p, n, X.device))
+    handle = ctypes.c_void_p()
+    with torch.cuda.device(meta[0][5]):
+        rc = lib.smc_batch_init(ctypes.byref(handle), P, probs, cfgs, _stream_handle(stream))
+    _bcheck(rc, "smc_batch_init", None)
+    ctxs = []
+    for q in range(P):
+        h = ctypes.c_void_p()
+        _bcheck(lib.smc_batch_context(handle, q, ctypes.byref(h)), "smc_batch_context", handle)
+        N, m, G, p, n, dev = meta[q]
+        ctxs.append(Context(h, N, m, G, p, n, torch.float32, dev, None, owned=False))
+    return Batch(handle, ctxs, keep)
+
+
+def smc_batch_free(b: Batch) -> None:
+    if b.handle:
+        for c in b.contexts:
+            c.handle = ctypes.c_void_p()
+        _abi.load().smc_batch_free(b.handle)
+        b.handle = ctypes.c_void_p()
+
+
+def smc_batch_stage(b: Batch, R: int, use_graph: bool = True) -> None:
+    _bcheck(_abi.load().smc_batch_stage(b.handle, int(R), 1 if use_graph else 0),
+            "smc_batch_stage", b.handle)
+
+
+def smc_batch_autotune(b: Batch) -> int:
+    t = ctypes.c_int32()
+    _bcheck(_abi.load().smc_batch_autotune(b.handle, ctypes.byref(t)), "smc_batch_autotune",
+            b.handle)
+    return t.value
+
+
+def smc_batch_tile(b: Batch) -> int:
+    t = ctypes.c_int32()
+    _bcheck(_abi.load().smc_batch_tile(b.handle, ctypes.byref(t)), "smc_batch_tile", b.handle)
+    return t.value
+
+
+def smc_batch_launch_count(b: Batch) -> int:
+    return int(_abi.load().smc_batch_launch_count(b.handle))
+
+
+def smc_batch_context(b: Batch, q: int) -> Context:
+    """The context of problem q (owned by the batch)."""
+    return b.contexts[q]
+
+
+def smc_batch_last_error(b: Batch | None = None) -> str:
+    msg = _abi.load().smc_batch_last_error(b.handle if b is not None else None)
+    return (msg or b"").decode(errors="replace")

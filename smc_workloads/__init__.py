@@ -243,3 +243,37 @@ def gam_1e7(x_dtype: str = "bf16", n: int = 10_000_000, N: int = 16384, m: int =
         Xd = Xs.astype(np.float64) if upcast else None
     return Workload(f"gam-n{n}-p101-{x_dtype}", "gaussian", x_dtype, Xd, Xs, ys.astype(np.float64),
                     ys, np.zeros(p), np.full(p, 100.0), N, m, 10, 25, 5, seed, sigma, None)
+
+
+def batch_uneven(P: int = 64, N: int = 1024, G: int = 10, L: int = 20, R: int = 5,
+                 n_lo: float = 1e4, n_hi: float = 1e6, seed_offset: int = 0,
+                 upcast: bool = True) -> list:
+    """Batched uneven posteriors: P independent regressions, half logistic and half probit, n
+    log-uniform in [n_lo, n_hi], p uniform in {5, ..., 40} (intercept + N(0, 1) covariates),
+    theta_true ~ N(0, 0.3^2 I), prior N(0, 10 I); N particles each, m = ceil(0.001 n) clamped to
+    [100, 1000], G blocks, L leapfrog steps, R moves. X stored in BF16. Each problem has its own
+    seed (BASE_SEED + 3, then a per-problem stream). upcast=False leaves Workload.X as None."""
+    seed = BASE_SEED + 3 + seed_offset
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(P):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        p = int(rng.integers(5, 41))
+        fam = "logistic" if q % 2 == 0 else "probit"
+        m = int(min(1000, max(100, math.ceil(0.001 * n))))
+        prng = np.random.Generator(np.random.PCG64([seed, q]))
+        X = np.empty((n, p), dtype=np.float32)
+        X[:, 0] = 1.0
+        X[:, 1:] = prng.standard_normal((n, p - 1), dtype=np.float32)
+        theta = 0.3 * prng.standard_normal(p)
+        bits = round_to_bf16_bits(X)
+        del X
+        Xd = bf16_bits_to_f64(bits)
+        y = _respond(prng, fam, Xd @ theta)
+        if not upcast:
+            Xd = None
+        ys = y.astype(np.float32)
+        out.append(Workload(f"batch{q}-{fam}-n{n}-p{p}", fam, "bf16", Xd, bits, ys.astype(np.float64),
+                            ys, np.zeros(p), np.full(p, 10.0), N, m, G, L, R, seed * 1000 + q, 1.0,
+                            theta))
+    return out

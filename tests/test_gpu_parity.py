@@ -627,3 +627,56 @@ def test_full_data_graph_stages_are_bit_identical():
     assert S().smc_get_status(ca) == S().smc_get_status(cb)
     S().smc_free(ca)
     S().smc_free(cb)
+
+
+# ------------------------------------------------------------------------------------------------
+# Batches of independent posteriors of uneven n and p
+# ------------------------------------------------------------------------------------------------
+def _batch_problem_dicts(wls):
+    from gpu_common import device_arrays
+    out = []
+    for w in wls:
+        X, y = device_arrays(w)
+        out.append(dict(X=X, y=y, family=w.family, prior_mean=w.prior_mean, prior_var=w.prior_var,
+                        N=w.N, m=w.m, G=w.G, L=w.L, seed=w.seed))
+    return out
+
+
+def test_batch_stages_match_single_problems():
+    """One batched u-update and one batched HMC launch per move over all problems' particles
+    (plain and graph-replayed stages) gives bit-identical results to stepping each problem alone
+    with the same tile and the streamed trajectory kernel."""
+    from smc_workloads import batch_uneven
+    wls = batch_uneven(P=5, N=96, G=5, L=4, R=2, n_lo=2000, n_hi=20000)
+    b = S().smc_batch_init(_batch_problem_dicts(wls))
+    tile = S().smc_batch_tile(b)
+    singles = [make_pair(w, tile_hint=tile, hmc_kernel=1, theta_bar=None)[1] for w in wls]
+    for use_graph in [False, True, True, False, True, True]:
+        S().smc_batch_stage(b, 2, use_graph=use_graph)
+        for c in singles:
+            S().smc_reweight(c)
+            S().smc_resample(c)
+            S().smc_move(c, 2)
+    for q, c in enumerate(singles):
+        cb = S().smc_batch_context(b, q)
+        ta, ua, Wa = S().smc_get_particles(cb)
+        ts, us, Ws = S().smc_get_particles(c)
+        assert torch.equal(ta, ts) and torch.equal(ua, us) and torch.equal(Wa, Ws), q
+        assert S().smc_get_status(cb) == S().smc_get_status(c), q
+        S().smc_free(c)
+    S().smc_batch_free(b)
+
+
+def test_batch_autotune_leaves_state_unchanged():
+    from smc_workloads import batch_uneven
+    wls = batch_uneven(P=4, N=64, G=5, L=3, R=2, n_lo=2000, n_hi=10000, seed_offset=1)
+    b = S().smc_batch_init(_batch_problem_dicts(wls))
+    S().smc_batch_stage(b, 2, use_graph=False)
+    before = [S().smc_get_particles(S().smc_batch_context(b, q)) for q in range(4)]
+    tile = S().smc_batch_autotune(b)
+    assert tile >= 1
+    after = [S().smc_get_particles(S().smc_batch_context(b, q)) for q in range(4)]
+    for x, y_ in zip(before, after):
+        assert all(torch.equal(u, v) for u, v in zip(x, y_))
+    S().smc_batch_stage(b, 2, use_graph=True)
+    S().smc_batch_free(b)
