@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--gather-tile", type=int, default=0,
                     help="estimator tile hint for the gather leg (0: autotune)")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph stage timing")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched uneven-posteriors leg (64 problems)")
     ap.add_argument("--no-full", action="store_true",
                     help="skip the full-data comparison leg (about 5 s)")
     ap.add_argument("--no-gam", action="store_true",
@@ -330,6 +332,49 @@ def full_data_leg(S, wl, dev, R, tc_peak, stages=2, reps=5):
                     "MMAs"}
 
 
+def batch_leg(S, dev, P=64, stages=5, warmup=3):
+    """Batched uneven posteriors: 64 logistic/probit problems (n log-uniform in [1e4, 1e6], p in
+    5..40, N = 1024 each, m = clamp(ceil(n/1000), 100, 1000), G = 10, L = 20, R = 5), all
+    particles of all problems in one u-update and one HMC launch per move, the whole batch stage
+    replayed as one CUDA graph; tile from the batch autotuner."""
+    import torch
+    from smc_workloads import batch_uneven
+    t0 = time.perf_counter()
+    wls = batch_uneven(P=P, upcast=False)
+    gen_s = time.perf_counter() - t0
+    probs = []
+    for w in wls:
+        X, y = device_workload(w, dev)
+        probs.append(dict(X=X, y=y, family=w.family, prior_mean=w.prior_mean,
+                          prior_var=w.prior_var, N=w.N, m=w.m, G=w.G, L=w.L, seed=w.seed))
+    b = S.smc_batch_init(probs)
+    del probs
+    tile = S.smc_batch_autotune(b)
+    R = wls[0].R
+    per_stage = sum(w.N * w.m for w in wls) * R * (wls[0].L + 1)
+    out = {"workload": f"{P} problems: logistic/probit, n log-uniform [1e4, 1e6] "
+                       f"(total {sum(w.n for w in wls)} rows), p 5..40, N=1024 each, "
+                       f"m=clamp(n/1000,100,1000), G=10, L=20, R=5, X=bf16",
+           "tile": tile, "data_generation_s": round(gen_s, 1)}
+    for name, graph in (("graph", True), ("launches", False)):
+        for _ in range(warmup):
+            S.smc_batch_stage(b, R, use_graph=graph)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = S.smc_batch_launch_count(b)
+        e0.record()
+        for _ in range(stages):
+            S.smc_batch_stage(b, R, use_graph=graph)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / stages
+        out[name] = {"ms_per_stage": ms, "grad_evals_per_s": per_stage / (ms / 1e3),
+                     "launches_per_stage": (S.smc_batch_launch_count(b) - l0) / stages}
+    S.smc_batch_free(b)
+    return out
+
+
 def gam_leg(S, dev, hbm, tile_hint=0, n=10_000_000):
     """The GAM workload (Gaussian response, sigma = 0.5, n = 1e7, p = 101 B-spline columns, BF16;
     N = 16384, m = 5000, L = 25) through the gather leg: 82M gathered rows per estimator call."""
@@ -434,6 +479,10 @@ def gpu_arm(args):
         full = full_data_leg(S, wl, dev, R, bf16_peak())
         full["subsampling_speedup_per_stage"] = full["ms_per_stage"] / (ms / args.steps)
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_leg(S, dev)
+
     gather = None
     if not args.no_gather and rank == 0:
         gather = gather_leg(S, dev, hbm)
@@ -484,6 +533,7 @@ def gpu_arm(args):
         "fp32_storage": fp32,
         "graph_stages": graph,
         "full_data_comparison": full,
+        "batched_posteriors": batch,
         "hbm_gather_leg": gather,
         "gam_gather_leg": gam,
         "smc_wall_time": walls,

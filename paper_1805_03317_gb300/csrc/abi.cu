@@ -1265,6 +1265,7 @@ struct smc_batch {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   EstArgs *gargs[2] = {nullptr, nullptr};  // the argument arrays each graph reads
   int gR[2] = {0, 0};
+  int64_t glaunches[2] = {0, 0};  // kernel launches inside each graph
   int64_t launches = 0;
   std::string err;
 };
@@ -1481,6 +1482,8 @@ int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph) {
       cudaStreamDestroy(cap);
       return bfail(b, SMC_ERR_CUDA, "batch capture");
     }
+    int64_t l0 = b->launches;
+    for (smc_ctx *c : b->ctx) l0 += c->launches;
     b->stream = cap;
     for (smc_ctx *c : b->ctx) {
       c->stream = cap;
@@ -1516,12 +1519,18 @@ int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph) {
       return bfail(b, SMC_ERR_CUDA, "batch graph instantiate");
     }
     b->gR[q] = R;
+    {
+      int64_t nl = b->launches;
+      for (smc_ctx *c : b->ctx) nl += c->launches;
+      b->glaunches[q] = nl - l0;
+    }
     if (cudaGraphLaunch(b->gexec[q], b->stream) != cudaSuccess)
       return bfail(b, SMC_ERR_CUDA, "batch graph launch");
     return SMC_OK;  // capturing ran the host side of the stage; the launch runs its device side
   }
   if (cudaGraphLaunch(b->gexec[q], b->stream) != cudaSuccess)
     return bfail(b, SMC_ERR_CUDA, "batch graph launch");
+  b->launches += b->glaunches[q];
   for (smc_ctx *c : b->ctx) {  // the host side of the replayed stage
     c->stage += 1;
     c->moves_in_stage = R;
