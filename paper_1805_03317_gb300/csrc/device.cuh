@@ -205,8 +205,27 @@ __device__ __forceinline__ RowC<CT> row_consts(CT eb, CT y, CT inv_s2) {
   return c;
 }
 
+// Horner steps of the two cumulant-series chains at once (FP32: one packed FMA per step):
+// (pd, pr) = (pd, pr) * D + kappa * (1/k!, 1/(k-1)!).
+template <typename CT>
+__device__ __forceinline__ void horner2(CT &pd, CT &pr, CT D, CT kappa, double fd, double fr) {
+  pd = fma(pd, D, kappa * CT(fd));
+  pr = fma(pr, D, kappa * CT(fr));
+}
+template <>
+__device__ __forceinline__ void horner2<float>(float &pd, float &pr, float D, float kappa,
+                                               double fd, double fr) {
+  const float2 coef = __fmul2_rn(make_float2(kappa, kappa), make_float2((float)fd, (float)fr));
+  const float2 v = __ffma2_rn(make_float2(pd, pr), make_float2(D, D), coef);
+  pd = v.x;
+  pr = v.y;
+}
+
+// short4: the caller has checked |D| <= 1/20 for every lane of the warp (FP32 only); the
+// logistic series then stops at kappa_6 (truncation below 2e-8 of w|D|^3 and w D^2).
 template <int FAM, typename CT>
-__device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT &d, CT &r) {
+__device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT &d, CT &r,
+                                         bool short4 = false) {
   if (FAM == 0) {  // logistic: l = y*eta - log(1 + e^eta); y cancels from d and r
     const CT sb = c.c0, w = c.c1;
     // With K(D) = log(1 - s + s e^D), the cumulant generating function of Bernoulli(s), s = sigma(eta_bar):
@@ -215,6 +234,21 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
     // The series converges for |D| < pi; up to |D| = 1/4 (1/20 in FP64) terms to kappa_10 leave a
     // relative error below 1e-9 (1e-15). No transcendental, no division, no cancellation.
     constexpr CT kSmall = sizeof(CT) == 8 ? CT(0.05) : CT(0.25);
+    if (sizeof(CT) == 4 && short4) {
+      const CT q = CT(1) - CT(2) * sb;
+      const CT k3 = w * q;
+      const CT k4 = w * (CT(1) - CT(6) * w);
+      const CT k5 = k3 * (CT(1) - CT(12) * w);
+      const CT k6 = w * (CT(1) + w * (CT(-30) + CT(120) * w));
+      CT pd = k6 * CT(1.0 / 720.0), pr = k6 * CT(1.0 / 120.0);
+      horner2(pd, pr, D, k5, 1.0 / 120.0, 1.0 / 24.0);
+      horner2(pd, pr, D, k4, 1.0 / 24.0, 1.0 / 6.0);
+      horner2(pd, pr, D, k3, 1.0 / 6.0, 0.5);
+      const CT D2 = D * D;
+      d = -D2 * D * pd;
+      r = -D2 * pr;
+      return;
+    }
     if (fabs(D) <= kSmall) {
       const CT q = CT(1) - CT(2) * sb;
       const CT k3 = w * q;
@@ -226,22 +260,14 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
       const CT k9 = k3 * (CT(1) + w * (CT(-252) + w * (CT(5040) - CT(20160) * w)));
       const CT k10 =
           w * (CT(1) + w * (CT(-510) + w * (CT(17640) + w * (CT(-151200) + CT(362880) * w))));
-      CT pd = k10 * CT(1.0 / 3628800.0);
-      pd = fma(pd, D, k9 * CT(1.0 / 362880.0));
-      pd = fma(pd, D, k8 * CT(1.0 / 40320.0));
-      pd = fma(pd, D, k7 * CT(1.0 / 5040.0));
-      pd = fma(pd, D, k6 * CT(1.0 / 720.0));
-      pd = fma(pd, D, k5 * CT(1.0 / 120.0));
-      pd = fma(pd, D, k4 * CT(1.0 / 24.0));
-      pd = fma(pd, D, k3 * CT(1.0 / 6.0));
-      CT pr = k10 * CT(1.0 / 362880.0);
-      pr = fma(pr, D, k9 * CT(1.0 / 40320.0));
-      pr = fma(pr, D, k8 * CT(1.0 / 5040.0));
-      pr = fma(pr, D, k7 * CT(1.0 / 720.0));
-      pr = fma(pr, D, k6 * CT(1.0 / 120.0));
-      pr = fma(pr, D, k5 * CT(1.0 / 24.0));
-      pr = fma(pr, D, k4 * CT(1.0 / 6.0));
-      pr = fma(pr, D, k3 * CT(0.5));
+      CT pd = k10 * CT(1.0 / 3628800.0), pr = k10 * CT(1.0 / 362880.0);
+      horner2(pd, pr, D, k9, 1.0 / 362880.0, 1.0 / 40320.0);
+      horner2(pd, pr, D, k8, 1.0 / 40320.0, 1.0 / 5040.0);
+      horner2(pd, pr, D, k7, 1.0 / 5040.0, 1.0 / 720.0);
+      horner2(pd, pr, D, k6, 1.0 / 720.0, 1.0 / 120.0);
+      horner2(pd, pr, D, k5, 1.0 / 120.0, 1.0 / 24.0);
+      horner2(pd, pr, D, k4, 1.0 / 24.0, 1.0 / 6.0);
+      horner2(pd, pr, D, k3, 1.0 / 6.0, 0.5);
       const CT D2 = D * D;
       d = -D2 * D * pd;
       r = -D2 * pr;

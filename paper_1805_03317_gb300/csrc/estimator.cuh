@@ -212,8 +212,10 @@ struct WarpEval {
         return;
       }
       const RowC<CT> c = *reinterpret_cast<const RowC<CT> *>(tail(b));
+      // every lane evaluates a row here, so a warp vote is safe
+      const bool short4 = __all_sync(0xffffffffu, fabs(D) <= CT(0.05));
       switch (fam) {
-        case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
+        case 0: row_incr<0, CT>(c, D, inv_s2, d, r, short4); break;
         case 1: row_incr<1, CT>(c, D, inv_s2, d, r); break;
         case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
         default: row_incr<3, CT>(c, D, inv_s2, d, r); break;

@@ -680,3 +680,19 @@ def test_batch_autotune_leaves_state_unchanged():
         assert all(torch.equal(u, v) for u, v in zip(x, y_))
     S().smc_batch_stage(b, 2, use_graph=True)
     S().smc_batch_free(b)
+
+
+@pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("hmc_kernel", [0, 1])
+def test_short_logistic_series_near_centre(x_dtype, hmc_kernel):
+    """Particles close to the centre (every |x'(theta - theta_bar)| <= 1/20, so whole warps take the
+    four-term cumulant series): estimator, gradient and one HMC move against the oracle."""
+    wl = _wl("logistic", x_dtype, p=9, n=5000, N=64, m=150, G=5)
+    prob, ctx = make_pair(wl, hmc_kernel=hmc_kernel)
+    th, u = _particles(prob, 64, wl.m, 0.002, x_dtype, seed=12)
+    D = np.abs((prob.X[u] * (th - prob.theta_bar)[:, None, :]).sum(-1))
+    assert D.max() <= 0.05
+    g, ell, s2 = S().loglik_grad(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV), 0.9)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=0.9)
+    _check_estimates(x_dtype, (ell.cpu().numpy(), s2.cpu().numpy(), g.cpu().double().numpy()), ref)
+    S().smc_free(ctx)
