@@ -73,6 +73,8 @@ def lib():
             L.orc_cv_moments.argtypes = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp,
                                          ctypes.POINTER(c_d), _dp, _dp]
             L.orc_log_prior.argtypes = [c_i, _dp, _dp, _dp, ctypes.c_void_p]
+            L.orc_set_cv_order.argtypes = [c_i]
+            L.orc_set_cv_order.restype = None
             L.orc_log_prior.restype = c_d
             prob = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp, c_d, _dp, _dp, _dp, _dp, c_i, c_i]
             L.orc_loglik_batch.argtypes = prob + [c_i, _dp, _i64p, c_d, _dp, _dp,
@@ -180,6 +182,7 @@ class Problem:
     A: float = 0.0
     B: np.ndarray | None = None
     C: np.ndarray | None = None
+    cv_order: int = 2        # Taylor order of the control variates (2, or 1: first order)
 
     def __post_init__(self):
         self.X = np.ascontiguousarray(self.X, dtype=np.float64)
@@ -201,6 +204,7 @@ class Problem:
                                             self.sigma)
 
     def args(self, m, G):
+        lib().orc_set_cv_order(int(self.cv_order))  # read by the estimator calls that follow
         return (FAMILIES[self.family], self.n, self.p, self.X, self.y, self.sigma,
                 self.theta_bar, self.A, self.B, self.C, self.prior_mean, self.prior_var, m, G)
 

@@ -243,6 +243,12 @@ typedef struct {
 
 static int64_t block_start(int g, int m, int G) { return ((int64_t)g * m) / G; }
 
+/* Order of the Taylor control variate: 2 (q_k to second order, the paper's main estimator) or 1
+ * (first order: q_k = l_k(tb) + grad l_k(tb)'delta; Sec. 4's first-order variant). Process-wide;
+ * set by the Python front end before each call. */
+static int g_cv_order = 2;
+void orc_set_cv_order(int k) { g_cv_order = (k == 1) ? 1 : 2; }
+
 /* Difference estimator (Sec. 3.2, Eq. difference_estimator_logl) for one particle:
  *   l_hat = sum_k q_k(theta) + (n/m) sum_j [l_{u_j}(theta) - q_{u_j}(theta)]
  *   sigma2_hat = (n^2/m^2) sum_j (d_{u_j} - dbar)^2,  d_k = l_k - q_k
@@ -259,11 +265,12 @@ void orc_loglik_one(const orc_prob *P, const int64_t *u, const double *theta, do
   double *rvals = (double *)malloc(sizeof(double) * m);
   for (int c = 0; c < p; ++c) delta[c] = theta[c] - P->theta_bar[c];
 
-  /* sum_k q_k(theta) = A + B'delta + (1/2) delta'C delta */
+  /* sum_k q_k(theta) = A + B'delta + (1/2) delta'C delta (first order: A + B'delta) */
+  const double c2 = g_cv_order == 2 ? 1.0 : 0.0;
   double q_total = P->A;
   for (int r = 0; r < p; ++r) {
     q_total += P->B[r] * delta[r];
-    for (int c = 0; c < p; ++c) q_total += 0.5 * delta[r] * P->C[r * p + c] * delta[c];
+    for (int c = 0; c < p; ++c) q_total += c2 * 0.5 * delta[r] * P->C[r * p + c] * delta[c];
   }
 
   double dsum = 0.0;
@@ -275,10 +282,11 @@ void orc_loglik_one(const orc_prob *P, const int64_t *u, const double *theta, do
     orc_family(P->fam, eta_bar, P->y[u[j]], P->sigma, &lb, &d1b, &d2b);
     /* q_k(theta) = l_k(tb) + grad l_k(tb)'delta + delta' hess l_k(tb) delta / 2 */
     double xd = dot(x, delta, p);
-    double q = lb + d1b * xd + 0.5 * d2b * xd * xd;
+    double q = lb + d1b * xd + c2 * 0.5 * d2b * xd * xd;
     dvals[j] = l - q;
-    /* d/dtheta d_k = [l'(eta) - l'(eta_bar) - l''(eta_bar) x'delta] x_k */
-    rvals[j] = d1 - d1b - d2b * xd;
+    /* d/dtheta d_k = [l'(eta) - l'(eta_bar) - l''(eta_bar) x'delta] x_k (no last term at first
+     * order) */
+    rvals[j] = d1 - d1b - c2 * d2b * xd;
     dsum += dvals[j];
   }
   double dbar = dsum / m;
@@ -307,7 +315,7 @@ void orc_loglik_one(const orc_prob *P, const int64_t *u, const double *theta, do
     double *gs = (double *)calloc(p, sizeof(double));
     for (int r = 0; r < p; ++r) {
       gl[r] = P->B[r];
-      for (int c = 0; c < p; ++c) gl[r] += P->C[r * p + c] * delta[c];
+      for (int c = 0; c < p; ++c) gl[r] += c2 * P->C[r * p + c] * delta[c];
     }
     for (int j = 0; j < m; ++j) {
       const double *x = P->X + u[j] * p;

@@ -440,3 +440,47 @@ def test_smc_recovers_conjugate_posterior_and_log_marginal():
     assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
     assert abs(np.mean(errs)) < 0.15
     assert np.max(np.abs(errs)) < 0.6
+
+
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit"])
+def test_first_order_estimator_unbiased_and_its_gradient(fam):
+    """First-order control variates (q_k = l_k(tb) + grad l_k(tb)'delta): averaging l_hat over all
+    n^m index tuples gives l(theta) exactly, the printed sigma2_hat has expectation
+    (m-1)/m Var(l_hat), l_hat = A at the centre, and the force is the gradient of the target."""
+    n, m = 5, 3
+    prob = tiny_problem(fam, n=n, p=2, seed=11)
+    prob.cv_order = 1
+    theta = prob.theta_bar + np.array([0.4, -0.7])
+    us = np.array([[a, b, c] for a in range(n) for b in range(n) for c in range(n)],
+                  dtype=np.int64)
+    thetas = np.repeat(theta[None, :], us.shape[0], axis=0)
+    out = O.loglik_batch(prob, m, 1, thetas, us, a=1.0, grad=False)
+    exact = scipy_loglik(fam, prob.X, prob.y, theta, prob.sigma)
+    assert out["ell"].mean() == pytest.approx(exact, rel=1e-12)
+    assert out["sigma2"].mean() == pytest.approx((m - 1) / m * out["ell"].var(), rel=1e-10)
+    # first and second order differ (the check is not vacuous)
+    prob.cv_order = 2
+    out2 = O.loglik_batch(prob, m, 1, thetas, us, a=1.0, grad=False)
+    assert np.max(np.abs(out2["ell"] - out["ell"])) > 1e-6
+    prob.cv_order = 1
+    o = O.loglik_batch(prob, m, 1, prob.theta_bar[None, :], us[:1], a=1.0, grad=False)
+    assert o["ell"][0] == pytest.approx(prob.A, rel=1e-14)
+    prob2 = tiny_problem(fam, n=40, p=3, seed=4)
+    prob2.cv_order = 1
+    rng = np.random.default_rng(8)
+    mm, a = 12, 0.7
+    u = rng.integers(0, prob2.n, size=(1, mm)).astype(np.int64)
+    th = prob2.theta_bar + 0.5 * rng.standard_normal(prob2.p)
+
+    def target(t):
+        r = O.loglik_batch(prob2, mm, 3, t[None, :], u, a=a, grad=False)
+        return (a * r["ell"][0] - 0.5 * a * a * r["sigma2"][0]
+                + scipy_log_prior(t, prob2.prior_mean, prob2.prior_var))
+
+    g = O.loglik_batch(prob2, mm, 3, th[None, :], u, a=a)["grad"][0]
+    h = 1e-6
+    for c in range(prob2.p):
+        e = np.zeros(prob2.p)
+        e[c] = h
+        fd = (target(th + e) - target(th - e)) / (2 * h)
+        assert g[c] == pytest.approx(fd, rel=1e-6, abs=1e-6)
