@@ -82,6 +82,13 @@ typedef struct {
                              /* resident tile k-2                                                  */
   int32_t cv_kernel;         /* control-variate moments: 0 = automatic (tensor cores, tcgen05,     */
                              /* for BF16 storage with p <= 128; SIMT otherwise), 1 = SIMT          */
+  int32_t cv_order;          /* Taylor order of the control variates: 0 or 2 = second order (Sec. */
+                             /* 3.2), 1 = first order (q_k = l_k + grad l_k'delta at theta_bar)    */
+  int32_t cv_centre;         /* 0 = fixed centre (theta_bar given, else the posterior mode);       */
+                             /* 1 = re-centred every stage at the weighted particle mean (Alg. 2   */
+                             /* (d)): A, B, C, the row constants and every particle's l_hat,       */
+                             /* sigma2_hat are recomputed at the start of smc_reweight (this needs */
+                             /* host synchronisation, so smc_stage's graphs refuse it)             */
   int32_t full_data;         /* 1: the comparison method of Sec. 4, full-data SMC: the cache holds  */
                              /* the exact l(theta) (sigma2 = 0), smc_move runs HMC on the exact    */
                              /* tempered posterior with loglik_full forces (no u update); BF16     */

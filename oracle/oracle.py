@@ -340,6 +340,7 @@ class SMCConfig:
     rounds: int = 10
     eps0: float | None = None      # default 0.5 * p^(-1/4)
     max_stages: int = 1000
+    recentre: bool = False         # Algorithm 2 (d): theta_bar = the reweighted particle mean
 
 
 @dataclass
@@ -381,6 +382,8 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     mean, Sigma, Lc, rc = moments(W, st.thetas)
     if rc >= 0:  # a covariance that is not positive definite (e.g. N = 1) keeps the previous one
         st.Sigma, st.Lc = Sigma, Lc
+    if cfg.recentre:  # new control variates at the weighted mean: A, B, C once per stage (Sec. 3.2)
+        prob.set_centre(mean)
     U = uniform(r64(cfg.seed, TAG_RESAMPLE, stage_move(s, 0), 0, 0))
     anc = resample(W, U)
     st.thetas = st.thetas[anc].copy()

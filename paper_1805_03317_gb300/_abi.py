@@ -29,7 +29,7 @@ class SmcConfig(ctypes.Structure):
     _fields_ = [("N", c_i32), ("m", c_i32), ("G", c_i32), ("L", c_i32), ("ess_frac", c_d),
                 ("seed", c_u64), ("search_k", c_i32), ("search_rounds", c_i32), ("eps0", c_d),
                 ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
-                ("full_data", c_i32)]
+                ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32)]
 
 
 # name -> (restype, argtypes)

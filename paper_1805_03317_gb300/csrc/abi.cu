@@ -19,6 +19,7 @@ struct smc_ctx {
   cudaStream_t stream = nullptr;
   // problem
   int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0, cv_kernel = 0;
+  int cv_order = 2, cv_centre = 0;  // control-variate order; 1: re-centred every stage
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
@@ -257,6 +258,8 @@ EstArgs base_args(const smc_ctx *c) {
   a.fam = c->fam;
   a.inv_s2 = 1.0 / (c->noise_sigma * c->noise_sigma);
   a.A = c->A_h;
+  a.A_dev = c->cv_centre ? c->A_d : nullptr;
+  a.cv_order = c->cv_order;
   a.B_ct = c->B_ct;
   a.C_ct = c->C_ct;
   a.tb_ct = c->tb_ct;
@@ -363,20 +366,31 @@ int newton_map(smc_ctx *c, double *theta_d) {
   return SMC_OK;
 }
 
-// Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies,
-// and the per-row constants at the centre in every packed row's tail.
-int set_centre(smc_ctx *c) {
+// Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies
+// (C is zero in the copy the kernels read under first-order control variates), and the per-row
+// constants at the centre in every packed row's tail. Stream-ordered, no host synchronisation.
+int centre_kernels(smc_ctx *c) {
   const int p = c->p;
   LAUNCH(c, round_to_state_type(c->is_f64, p, c->tb_d, c->stream), c->is_f64 ? 0 : 1);
   int r = moments_at(c, c->tb_d, c->A_d, c->B_d, c->C_d);
   if (r) return r;
   LAUNCH(c, to_state_type(c->is_f64, p, c->tb_d, c->tb_ct, c->stream), 1);
   LAUNCH(c, to_state_type(c->is_f64, p, c->B_d, c->B_ct, c->stream), 1);
-  LAUNCH(c, to_state_type(c->is_f64, p * p, c->C_d, c->C_ct, c->stream), 1);
+  if (c->cv_order == 1) {
+    CUDA_OK(c, cudaMemsetAsync(c->C_ct, 0, (size_t)p * p * (c->is_f64 ? 8 : 4), c->stream));
+  } else {
+    LAUNCH(c, to_state_type(c->is_f64, p * p, c->C_d, c->C_ct, c->stream), 1);
+  }
   LAUNCH(c,
          row_consts(c->Xp, c->x_dtype, c->n, p, c->S, c->Yo, c->fam, c->tb_ct,
                     1.0 / (c->noise_sigma * c->noise_sigma), c->stream),
          1);
+  return SMC_OK;
+}
+
+int set_centre(smc_ctx *c) {
+  int r = centre_kernels(c);
+  if (r) return r;
   CUDA_OK(c, cudaMemcpyAsync(&c->A_h, c->A_d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   if (!isfinite(c->A_h)) return fail(c, SMC_ERR_NONFINITE, "A(theta_bar) is not finite");
@@ -629,6 +643,13 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->rounds = rounds;
   c->eps0 = cfg->eps0;
   c->cv_kernel = cfg->cv_kernel == 1 ? 1 : 0;
+  if (cfg->cv_order < 0 || cfg->cv_order > 2 || cfg->cv_centre < 0 || cfg->cv_centre > 1) {
+    g_init_error = "cv_order must be 0, 1 or 2 and cv_centre 0 or 1";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  c->cv_order = cfg->cv_order == 1 ? 1 : 2;
+  c->cv_centre = cfg->cv_centre;
   c->full_data = cfg->full_data ? 1 : 0;
   if (c->full_data && (P->x_dtype != SMC_BF16 || P->p > 64)) {
     g_init_error = "full_data needs BF16 storage and p <= 64";
@@ -713,6 +734,16 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
     r = set_mass(c);
   }
   if (r) return r;
+  if (c->cv_centre && !c->full_data) {
+    // Algorithm 2 (d): the control variates move to the reweighted particle mean; the cached
+    // l_hat, sigma2_hat and block sums are re-estimated under them before the moves compare
+    // proposals with them. A non-finite A surfaces through the estimates' error bits.
+    ProfScope ps(c, 4);
+    CUDA_OK(c, cudaMemcpyAsync(c->tb_d, c->mean_d, sizeof(double) * c->p,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    if ((r = centre_kernels(c))) return r;
+    if ((r = refresh_cache(c))) return r;
+  }
   if (a_next || log_z_inc || ess) {
     DevState h;
     if ((r = sync_state(c, &h))) return r;

@@ -303,6 +303,36 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
   }
 }
 
+// l''(eta_bar) of a row from its stored constants.
+template <int FAM, typename CT> __device__ __forceinline__ CT row_l2(const RowC<CT> &c, CT inv_s2) {
+  if (FAM == 0) return -c.c1;
+  if (FAM == 2) return -c.c0;
+  if (FAM == 3) return -inv_s2;
+  return -c.c2 * (c.c0 + c.c2);
+}
+// First-order control variates: d and r of the second-order forms plus the second-order term,
+// d1 = d2 + l''(eta_bar) D^2 / 2, r1 = r2 + l''(eta_bar) D.
+template <typename CT> __device__ __forceinline__ void to_first_order(CT l2, CT D, CT &d, CT &r) {
+  d = fma(CT(0.5) * l2 * D, D, d);
+  r = fma(l2, D, r);
+}
+__device__ __forceinline__ float row_l2_any(int fam, const RowC<float> &c, float inv_s2) {
+  switch (fam) {
+    case 0: return row_l2<0, float>(c, inv_s2);
+    case 1: return row_l2<1, float>(c, inv_s2);
+    case 2: return row_l2<2, float>(c, inv_s2);
+    default: return row_l2<3, float>(c, inv_s2);
+  }
+}
+__device__ __forceinline__ double row_l2_any(int fam, const RowC<double> &c, double inv_s2) {
+  switch (fam) {
+    case 0: return row_l2<0, double>(c, inv_s2);
+    case 1: return row_l2<1, double>(c, inv_s2);
+    case 2: return row_l2<2, double>(c, inv_s2);
+    default: return row_l2<3, double>(c, inv_s2);
+  }
+}
+
 template <int FAM, typename CT>
 __device__ __forceinline__ void row_terms(CT eb, CT D, CT y, CT inv_s2, CT &d, CT &r) {
   row_incr<FAM, CT>(row_consts<FAM, CT>(eb, y, inv_s2), D, inv_s2, d, r);

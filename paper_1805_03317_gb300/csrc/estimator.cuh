@@ -128,7 +128,8 @@ struct WarpEval {
   __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int64_t n,
                                        const int32_t *idx, int nrows, int fam, CT inv_s2, CT *g1,
                                        CT *g2, double *blk_out, int G, double &Ssum, double &Qsum,
-                                       DevState *st, const RowIO<CT> &io = RowIO<CT>()) const {
+                                       DevState *st, const RowIO<CT> &io = RowIO<CT>(),
+                                       int cv1 = 0) const {
     const int nsw = (nrows + 31) >> 5;
     // rows past the end copy the last row again (already on chip) and are masked out
     const int klast = nrows > 0 ? idx[nrows - 1] : 0;
@@ -220,6 +221,7 @@ struct WarpEval {
         case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
         default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
       }
+      if (cv1) to_first_order(row_l2_any(fam, c, inv_s2), D, d, r);
       if (j >= nrows || ((bad >> b) & 1u)) {
         d = CT(0);
         r = CT(0);
@@ -379,7 +381,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &
   for (int s = 0; s < CPL; ++s) g1[s] = g2[s] = CT(0);
   double S, Q;
   W.template rows<GRAD, BLOCKS, MODE>(Xp, a.S, a.n, idx, a.m, a.fam, inv_s2, g1, g2, blk_out, a.G,
-                                      S, Q, a.st, io);
+                                      S, Q, a.st, io, a.cv_order == 1);
   const double nm = (double)a.n / (double)a.m;
   const double dbar = S / (double)a.m;
   if (GRAD) {
@@ -418,7 +420,7 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &
     }
   }
   qlin = warp_sum(qlin);
-  ell = a.A + qlin + nm * S;
+  ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + qlin + nm * S;
   sig2 = nm * nm * (Q - S * S / (double)a.m);
   __syncwarp();
 }
@@ -619,7 +621,8 @@ __device__ __forceinline__ void upm_body(const EstArgs &a, int i, unsigned char 
   refresh_delta(W, a, sm);
   double Sg, Qg;
   W.template rows<false, false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n, unew, nb, a.fam,
-                                (CT)a.inv_s2, nullptr, nullptr, nullptr, 0, Sg, Qg, a.st);
+                                (CT)a.inv_s2, nullptr, nullptr, nullptr, 0, Sg, Qg, a.st,
+                                RowIO<CT>(), a.cv_order == 1);
   double *blk = a.blk + (int64_t)i * a.G * 2;
   // totals over blocks from the cache (lanes over blocks)
   double St = 0.0, Qt = 0.0;

@@ -41,6 +41,7 @@ struct EstArgs {
   int p, S, Yo, m, G, fam;
   double inv_s2;   // Gaussian family: 1/sigma^2
   double A;        // sum_k l_k(theta_bar)
+  const double *A_dev;  // when set, A is read from here (a centre that moves every stage)
   const void *B_ct, *C_ct, *tb_ct;  // B [p], C [p,p] (symmetric), theta_bar [p]
   const void *mu_ct, *ivar_ct;      // prior mean, 1/prior variance [p]
   double log_prior_const;           // -0.5 * sum log(2 pi v)
@@ -68,6 +69,8 @@ struct EstArgs {
   // autograd pair: per-row d, r [B, m] (state type), upstream gradients of l_hat, sigma2_hat [B]
   void *dsave, *rsave;
   int stage_dev;          // 1: the stage index comes from st->stage (graph replays), else stage
+  int cv_order;           // 1: first-order control variates (row increments without the
+                          //    second-order term; C is zero in the state-type copy), else 2
   const double *g_ell, *g_sig2;
 };
 

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   const CT ta = (CT)temp, ta2 = (CT)(temp * temp * nm * nm), tnm = (CT)(temp * nm);
   const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const int fam = a.fam;
+  const int cv1 = a.cv_order == 1;
   const bool col = lane < p;
   // per-lane column constants (lane c holds column c)
   const CT Bc = col ? ldg_ct<CT>(a.B_ct, lane) : CT(0);
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
           case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
           default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
         }
+        if (cv1) to_first_order(row_l2_any(fam, c, inv_s2), D, d, r);
         axpy_slots<CPL>(r, x, v);
         axpy_slots<CPL>(d * r, x, v + CPL);
         sd += d;
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
             S2 += (double)rd[2 * w + 1];
           }
         }
-        ell = a.A + (double)qlin + nm * S1;
+        ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + (double)qlin + nm * S1;
         sig = nm * nm * (S2 - S1 * S1 * inv_m);
       }
       buf ^= 1;

@@ -57,7 +57,8 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              m: int, G: int, L: int, seed: int, ess_frac: float = 0.5, noise_sigma: float = 1.0,
              theta_bar=None, search_k: int = 16, search_rounds: int = 10, eps0: float = 0.0,
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
-             full_data: bool = False, stream=None) -> Context:
+             cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
+             stream=None) -> Context:
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -71,7 +72,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
                       y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma))
     cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
                     search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
-                    1 if full_data else 0)
+                    int(cv_order), int(cv_centre), 1 if full_data else 0)
     tb = None
     tb_ptr = None
     if theta_bar is not None:
@@ -393,7 +394,8 @@ def smc_batch_init(problems, stream=None) -> Batch:
                               y.data_ptr(), _dp(pm), _dp(pv), float(d.get("noise_sigma", 1.0)))
         cfgs[q] = SmcConfig(d["N"], d["m"], d["G"], d["L"], float(d.get("ess_frac", 0.5)),
                             int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
-                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 0)
+                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 2, 0,
+                            0)
         keep += [y, pm, pv]
         meta.append((d["N"], d["m"], d["G"], p, n, X.device))
     handle = ctypes.c_void_p()

@@ -1,0 +1,198 @@
+"""GPU parity for the control-variate variants: first-order control variates (Sec. 4's Experiment
+4: q_k without the second-order term) and per-stage re-centring of theta_bar at the reweighted
+particle mean (Algorithm 2 (d)), through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import ell_scale, make_pair, state_round, tol
+from oracle import oracle as O
+from smc_workloads import small_glm
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def S():
+    import paper_1805_03317_gb300 as pkg
+    return pkg
+
+
+def _wl(family, x_dtype, p=7, n=5000, N=64, m=77, G=5, seed=11):
+    kw = dict(x_scale=0.3) if family == "poisson" else {}
+    return small_glm(family, n=n, p=p, N=N, m=m, G=G, L=4, x_dtype=x_dtype, seed=seed, **kw)
+
+
+def _check(x_dtype, prob, th, got, ref):
+    t = tol(x_dtype)
+    ell, s2, g = got
+    assert np.all(np.abs(ell - ref["ell"]) <= t["ell"] * ell_scale(prob, th, ref["ell"]))
+    bound = t["sig2"] * np.max(np.abs(ref["sigma2"])) + t["ell"] * np.max(np.abs(ref["ell"]))
+    assert np.max(np.abs(s2 - ref["sigma2"])) <= bound
+    if g is not None:
+        gs = np.maximum(np.max(np.abs(ref["grad"]), axis=1, keepdims=True), 1.0)
+        assert (np.abs(g - ref["grad"]) / gs).max() <= t["grad"]
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("family", ["logistic", "poisson", "gaussian", "probit"])
+@pytest.mark.parametrize("hint", [0, 3, 7, 10])
+def test_first_order_estimator_and_gradient_match_oracle(family, x_dtype, hint):
+    wl = _wl(family, x_dtype)
+    try:
+        prob, ctx = make_pair(wl, tile_hint=hint, cv_order=1)
+    except S()._abi.SmcError as e:
+        if e.code == -1 and hint > 0:
+            pytest.skip("tile not compiled for this storage type or too narrow")
+        raise
+    prob.cv_order = 1
+    rng = np.random.default_rng(3)
+    th = state_round(prob.theta_bar + 0.1 * rng.standard_normal((37, prob.p)), x_dtype)
+    u = rng.integers(0, prob.n, size=(37, wl.m)).astype(np.int64)
+    g, ell, s2 = S().loglik_grad(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                                 0.8)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=0.8)
+    _check(x_dtype, prob, th, (ell.cpu().numpy(), s2.cpu().numpy(), g.cpu().double().numpy()),
+           ref)
+    # the second-order estimates differ at this spread (the first-order path is not a no-op)
+    prob.cv_order = 2
+    ref2 = O.loglik_batch(prob, wl.m, wl.G, th, u, a=0.8, grad=False)
+    assert np.max(np.abs(ref2["sigma2"] - ref["sigma2"])) > 1e-3 * np.max(ref["sigma2"])
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("family", ["logistic", "poisson"])
+def test_first_order_autograd_matches_oracle(family, x_dtype):
+    """The autograd pair under first-order control variates (the saved d, r carry the first-order
+    residuals; C is zero): gradient against the oracle's target gradient minus the prior and
+    against central differences of the oracle's l_hat and sigma2_hat."""
+    wl = _wl(family, x_dtype, p=9, n=4000, m=150, G=10)
+    prob, ctx = make_pair(wl, cv_order=1)
+    prob.cv_order = 1
+    rng = np.random.default_rng(9)
+    th = state_round(prob.theta_bar + 0.05 * rng.standard_normal((32, prob.p)), x_dtype)
+    u = rng.integers(0, prob.n, size=(32, wl.m)).astype(np.int64)
+    a = 0.8
+    theta = torch.from_numpy(th).to(DEV).float().requires_grad_(True)
+    ell, s2 = S().SubsampledLoglik.apply(theta, torch.from_numpy(u).to(DEV), ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, a=a)
+    np.testing.assert_allclose(ell.detach().cpu().numpy(), ref["ell"], rtol=1e-5)
+    (a * ell - 0.5 * a * a * s2).sum().backward()
+    g = theta.grad.double().cpu().numpy()
+    gref = ref["grad"] + (th - prob.prior_mean) / prob.prior_var
+    scale = np.maximum(np.abs(gref).max(axis=1, keepdims=True), 1.0)
+    assert (np.abs(g - gref) / scale).max() < 1e-4
+    h = 1e-6
+    fd = np.zeros_like(th)
+    for c in range(prob.p):
+        tp, tm = th.copy(), th.copy()
+        tp[:, c] += h
+        tm[:, c] -= h
+        rp = O.loglik_batch(prob, wl.m, wl.G, tp, u, grad=False)
+        rm = O.loglik_batch(prob, wl.m, wl.G, tm, u, grad=False)
+        fd[:, c] = ((a * rp["ell"] - 0.5 * a * a * rp["sigma2"])
+                    - (a * rm["ell"] - 0.5 * a * a * rm["sigma2"])) / (2 * h)
+    assert (np.abs(g - fd) / scale).max() < 1e-4
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("order", [2, 1])
+def test_recentring_stage_matches_oracle(x_dtype, order):
+    """One reweighting with re-centring: theta_bar becomes the reweighted mean (rounded to the
+    storage type), A, B, C are the full-data sums there, and the cached l_hat, sigma2_hat of every
+    particle are the estimates under the new control variates."""
+    wl = _wl("logistic", x_dtype, N=300, m=40, G=4)
+    prob, ctx = make_pair(wl, cv_order=order, cv_centre=1)
+    prob.cv_order = order
+    rng = np.random.default_rng(5)
+    shift = 0.1 * rng.standard_normal(wl.p)  # a cloud away from the initial centre
+    th = state_round(prob.theta_bar + shift + 0.05 * rng.standard_normal((wl.N, wl.p)), x_dtype)
+    u = rng.integers(0, wl.n, size=(wl.N, wl.m)).astype(np.int64)
+    W = rng.random(wl.N) ** 3
+    W /= W.sum()
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    S().smc_set_scalars(ctx, 4, 0.2, 0.3, 0.0)
+    a_new, _, _ = S().smc_reweight(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)  # reweighting uses the old centre
+    ra, _, rW, _, _ = O.reweight(np.log(W), ref["ell"], ref["sigma2"], 0.2, 0.5)
+    assert a_new == pytest.approx(ra, rel=1e-12 if x_dtype == "f64" else 1e-5)
+    mean, _, _, _ = O.moments(rW, th)
+    tb_want = state_round(mean, x_dtype)
+    tb, A, B, C = S().smc_get_centre(ctx)
+    if x_dtype == "f64":
+        np.testing.assert_allclose(tb, tb_want, rtol=1e-12, atol=1e-14)
+    else:
+        np.testing.assert_array_equal(tb, tb_want)
+    prob.set_centre(tb_want)
+    assert A == pytest.approx(prob.A, rel=1e-10)
+    np.testing.assert_allclose(B, prob.B, rtol=1e-9, atol=1e-9 * np.abs(prob.B).max())
+    ctol = 1e-10 if x_dtype == "f64" else 2e-6  # C: FP32 tile sums for FP32/BF16 storage
+    np.testing.assert_allclose(C, prob.C, rtol=ctol, atol=ctol * 1e-2 * np.abs(prob.C).max())
+    ell, s2, _ = S().smc_get_cache(ctx)
+    ref_new = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)
+    _check(x_dtype, prob, th, (ell.cpu().numpy(), s2.cpu().numpy(), None), ref_new)
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("hmc_kernel", [0, 1])
+@pytest.mark.parametrize("order", [2, 1])
+def test_recentred_smc_run_matches_oracle_fp64(order, hmc_kernel):
+    """A whole FP64 run from a centre at the prior mean, re-centred every stage: temperatures,
+    log Z, subsample indices (bit-exact) and particles follow the oracle."""
+    wl = small_glm("logistic", n=4000, p=4, N=128, m=50, G=5, L=6, R=2, x_dtype="f64", seed=21)
+    prob, ctx = make_pair(wl, theta_bar=np.zeros(wl.p), hmc_kernel=hmc_kernel, cv_order=order,
+                          cv_centre=1)
+    prob.cv_order = order
+    cfg = O.SMCConfig(N=wl.N, m=wl.m, G=wl.G, L=wl.L, R=wl.R, seed=wl.seed, tau=0.5,
+                      recentre=True)
+    st_o = O.smc_run(prob, cfg)
+    runner = S().SubsampledSMC.__new__(S().SubsampledSMC)
+    runner.ctx, runner.history = ctx, []
+    st = runner.run(wl.R)
+    assert st["stage"] == st_o.stage
+    np.testing.assert_allclose([h["a"] for h in runner.history], [h["a"] for h in st_o.history],
+                               rtol=1e-9)
+    assert st["log_z"] == pytest.approx(st_o.log_z, abs=1e-7)
+    th, u, _ = S().smc_get_particles(ctx)
+    np.testing.assert_array_equal(u.cpu().numpy(), st_o.us)
+    np.testing.assert_allclose(th.cpu().numpy(), st_o.thetas, rtol=1e-7, atol=1e-9)
+    tb, _, _, _ = S().smc_get_centre(ctx)
+    np.testing.assert_allclose(tb, prob.theta_bar, rtol=1e-9, atol=1e-12)
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("hmc_kernel", [0, 1])
+def test_recentred_graph_stages_are_bit_identical(hmc_kernel):
+    """Re-centring needs no host synchronisation, so graph-captured stages carry it: replayed
+    graphs give the same particles, cache and centre as launch-by-launch stages."""
+    wl = _wl("logistic", "bf16", p=7, n=6000, N=300, m=77, G=5)
+    _, ca = make_pair(wl, theta_bar=np.zeros(7), hmc_kernel=hmc_kernel, cv_order=1, cv_centre=1)
+    _, cb = make_pair(wl, theta_bar=np.zeros(7), hmc_kernel=hmc_kernel, cv_order=1, cv_centre=1)
+    for use_graph in [True, True, True, False, True, True]:
+        S().smc_stage(ca, 2, use_graph=use_graph)
+        S().smc_reweight(cb)
+        S().smc_resample(cb)
+        S().smc_move(cb, 2)
+    ta, ua, Wa = S().smc_get_particles(ca)
+    tb_, ub, Wb = S().smc_get_particles(cb)
+    assert torch.equal(ta, tb_) and torch.equal(ua, ub) and torch.equal(Wa, Wb)
+    assert S().smc_get_status(ca) == S().smc_get_status(cb)
+    ea, qa, _ = S().smc_get_cache(ca)
+    eb, qb, _ = S().smc_get_cache(cb)
+    assert torch.equal(ea, eb) and torch.equal(qa, qb)
+    ca_c, cb_c = S().smc_get_centre(ca), S().smc_get_centre(cb)
+    assert np.array_equal(ca_c[0], cb_c[0]) and ca_c[1] == cb_c[1]
+    assert not np.array_equal(ca_c[0], np.zeros(7))
+    S().smc_free(ca)
+    S().smc_free(cb)
+
+
+def test_bad_cv_settings_are_rejected():
+    wl = _wl("logistic", "f32")
+    for kw in (dict(cv_order=3), dict(cv_centre=2), dict(cv_order=-1)):
+        with pytest.raises(S()._abi.SmcError):
+            make_pair(wl, **kw)
