@@ -85,14 +85,25 @@ typedef struct {
   int32_t cv_order;          /* Taylor order of the control variates: 0 or 2 = second order (Sec. */
                              /* 3.2), 1 = first order (q_k = l_k + grad l_k'delta at theta_bar)    */
   int32_t cv_centre;         /* 0 = fixed centre (theta_bar given, else the posterior mode);       */
-                             /* 1 = re-centred every stage at the weighted particle mean (Alg. 2   */
-                             /* (d)): A, B, C, the row constants and every particle's l_hat,       */
-                             /* sigma2_hat are recomputed at the start of smc_reweight (this needs */
-                             /* host synchronisation, so smc_stage's graphs refuse it)             */
+                             /* 1 = re-centred every stage as in Alg. 2 (d): after the reweighting */
+                             /* theta_bar = sum_i W_i theta_i, then A, B, C, the row constants and */
+                             /* every particle's cached l_hat, sigma2_hat are recomputed there     */
+                             /* before resampling and the moves;                                   */
+                             /* 2 = re-centred at the start of every stage, at the weighted mean   */
+                             /* of the current cloud, and the cache recomputed before reweighting. */
+                             /* Both are stream-ordered (no host sync; graph stages carry them)    */
   int32_t full_data;         /* 1: the comparison method of Sec. 4, full-data SMC: the cache holds  */
                              /* the exact l(theta) (sigma2 = 0), smc_move runs HMC on the exact    */
                              /* tempered posterior with loglik_full forces (no u update); BF16     */
                              /* storage and p <= 64 only. 0: subsampling SMC                       */
+  int32_t resampling;        /* 0 = systematic (one uniform per stage); 1 = multinomial, one       */
+                             /* uniform per offspring (the paper's scheme, Sec. 2.2). Both act on  */
+                             /* integer weights floor(W_i 2^40) and are exact                      */
+  int32_t grid_points;       /* 0 = the K-ary bracket search for the next temperature; S >= 2 =    */
+                             /* the paper's grid rule (Sec. 2.3): the increment is the point of a   */
+                             /* geometric grid of S values over [(1-a) 10^-E, 1-a] whose ESS is    */
+                             /* closest to ess_frac * N (ties: the smaller increment)              */
+  double grid_decades;       /* E of the grid, > 0; 0 -> 16                                        */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */

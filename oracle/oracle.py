@@ -93,6 +93,10 @@ def lib():
             L.orc_moments.argtypes = [c_i, c_i, _dp, _dp, _dp, _dp, _dp]
             L.orc_moments.restype = c_i
             L.orc_resample.argtypes = [c_i, _dp, c_d, _i32p]
+            L.orc_resample_multinomial.argtypes = [c_i, _dp, _dp, _i32p]
+            L.orc_reweight_grid.argtypes = [c_i, _dp, _dp, _dp, _dp, c_d, c_d, c_i, c_d,
+                                            ctypes.POINTER(c_d), ctypes.POINTER(c_d)]
+            L.orc_reweight_grid.restype = c_d
             L.orc_num_threads.restype = c_i
             _lib = L
     return _lib
@@ -299,6 +303,18 @@ def reweight(logW, ell, sig2, a, tau, K=16, rounds=10):
     return float(a_new), lw, W, lz.value, ess.value
 
 
+def reweight_grid(logW, ell, sig2, a, tau, S=1024, decades=16.0):
+    """The paper's grid rule (Sec. 2.3) on S geometric increments; same returns as reweight."""
+    lw = np.array(logW, dtype=np.float64)
+    W = np.zeros_like(lw)
+    lz = ctypes.c_double()
+    ess = ctypes.c_double()
+    a_new = lib().orc_reweight_grid(len(lw), lw, W, np.ascontiguousarray(ell, np.float64),
+                                    np.ascontiguousarray(sig2, np.float64), a, tau, S, decades,
+                                    ctypes.byref(lz), ctypes.byref(ess))
+    return float(a_new), lw, W, lz.value, ess.value
+
+
 def cholesky(S):
     S = np.ascontiguousarray(S, np.float64)
     Lc = np.zeros_like(S)
@@ -323,6 +339,21 @@ def resample(W, U):
     return anc
 
 
+def resample_multinomial(W, U):
+    """Multinomial resampling (Sec. 2.2): U[i] is offspring i's uniform."""
+    W = np.ascontiguousarray(W, np.float64)
+    anc = np.zeros(W.shape[0], dtype=np.int32)
+    lib().orc_resample_multinomial(W.shape[0], W, np.ascontiguousarray(U, np.float64), anc)
+    return anc
+
+
+def multinomial_uniforms(seed, stage, N):
+    """Offspring i's uniform: the second 64-bit draw of its block in the stage's resampling
+    stream (the first draw of offspring 0 is the systematic scheme's U)."""
+    return np.array([uniform(r64(seed, TAG_RESAMPLE, stage_move(stage, 0), i, 1))
+                     for i in range(N)])
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
 
@@ -340,7 +371,13 @@ class SMCConfig:
     rounds: int = 10
     eps0: float | None = None      # default 0.5 * p^(-1/4)
     max_stages: int = 1000
-    recentre: bool = False         # Algorithm 2 (d): theta_bar = the reweighted particle mean
+    recentre: int = 0              # 1: Algorithm 2 (d), theta_bar = the reweighted particle mean
+                                   # after the reweighting; 2: the weighted mean of the current
+                                   # cloud at the start of the stage, estimates refreshed before
+                                   # the reweighting
+    resampling: str = "systematic"  # or "multinomial" (the paper's scheme)
+    grid_points: int = 0           # > 0: the paper's grid rule for the temperature (Sec. 2.3)
+    grid_decades: float = 16.0
 
 
 @dataclass
@@ -377,15 +414,26 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     (d) weighted moments and mass matrix, (e) resampling, (f) R moves of Algorithm 1."""
     st.stage += 1
     s = st.stage
-    a_new, logW, W, lz, ess = reweight(st.logW, st.ell, st.sig2, st.a, cfg.tau, cfg.K,
-                                       cfg.rounds)
+    if cfg.recentre == 2:  # centre at the current cloud; the cache follows the new estimator
+        mean0, _, _, _ = moments(st.W, st.thetas)
+        prob.set_centre(mean0)
+        out = loglik_batch(prob, cfg.m, cfg.G, st.thetas, st.us, a=st.a, grad=False)
+        st.ell, st.sig2 = out["ell"], out["sigma2"]
+    if cfg.grid_points > 0:
+        a_new, logW, W, lz, ess = reweight_grid(st.logW, st.ell, st.sig2, st.a, cfg.tau,
+                                                cfg.grid_points, cfg.grid_decades)
+    else:
+        a_new, logW, W, lz, ess = reweight(st.logW, st.ell, st.sig2, st.a, cfg.tau, cfg.K,
+                                           cfg.rounds)
     mean, Sigma, Lc, rc = moments(W, st.thetas)
     if rc >= 0:  # a covariance that is not positive definite (e.g. N = 1) keeps the previous one
         st.Sigma, st.Lc = Sigma, Lc
-    if cfg.recentre:  # new control variates at the weighted mean: A, B, C once per stage (Sec. 3.2)
+    if cfg.recentre == 1:  # new control variates at the weighted mean: A, B, C once per stage
         prob.set_centre(mean)
-    U = uniform(r64(cfg.seed, TAG_RESAMPLE, stage_move(s, 0), 0, 0))
-    anc = resample(W, U)
+    if cfg.resampling == "multinomial":
+        anc = resample_multinomial(W, multinomial_uniforms(cfg.seed, s, cfg.N))
+    else:
+        anc = resample(W, uniform(r64(cfg.seed, TAG_RESAMPLE, stage_move(s, 0), 0, 0)))
     st.thetas = st.thetas[anc].copy()
     st.us = st.us[anc].copy()
     st.a = a_new

@@ -27,8 +27,10 @@
  *   - sigma2_hat_m is implemented as printed, (n^2/m^2) * sum_j (d_j - dbar)^2.
  *   - the HMC force is the exact gradient of a*l_hat - a^2/2*sigma2_hat + log p(theta) for fixed u.
  *   - u blocks are the contiguous floor partitions [floor(g*m/G), floor((g+1)*m/G)).
- *   - resampling is systematic, on weights quantised to integers floor(W_i * 2^40).
- *   - the tempering increment is found by a K-ary refinement of a bracket (K=2 is bisection).
+ *   - resampling is systematic, on weights quantised to integers floor(W_i * 2^40); the paper's
+ *     multinomial scheme is the alternative, on the same integer weights.
+ *   - the tempering increment is found by a K-ary refinement of a bracket (K=2 is bisection), or
+ *     by the paper's grid rule on a geometric grid of increments.
  *
  * Parity status per function: every exported function is pinned by the CPU tests (brute force,
  * enumeration, closed forms, published Philox vectors); see the test files.
@@ -542,6 +544,41 @@ double orc_reweight(int N, double *logW, double *W, const double *ell, const dou
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The paper's grid rule for the next temperature (Sec. 2.3): ESS is evaluated at S grid points   */
+/* and the point whose ESS is closest to tau*N is taken. Reading for the grid, which the paper    */
+/* leaves open: increments D_s = (1-a) * 10^(-E*(S-1-s)/(S-1)), s = 0..S-1 (geometric, the last   */
+/* point 1-a itself), scanned in ascending order so that a tie keeps the smaller increment.       */
+/* Outputs as for orc_reweight.                                                                    */
+/* ------------------------------------------------------------------------------------------ */
+double orc_reweight_grid(int N, double *logW, double *W, const double *ell, const double *sig2,
+                         double a, double tau, int S, double E, double *log_z_inc, double *ess) {
+  double target = tau * (double)N;
+  double Dmax = 1.0 - a;
+  double best = INFINITY, D = Dmax;
+  for (int s = 0; s < S; ++s) {
+    double Ds = (s == S - 1) ? Dmax : Dmax * pow(10.0, -E * (double)(S - 1 - s) / (double)(S - 1));
+    double dist = fabs(orc_ess_at(N, logW, ell, sig2, a, Ds) - target);
+    if (dist < best) {
+      best = dist;
+      D = Ds;
+    }
+  }
+  double a_new = (D == Dmax) ? 1.0 : a + D;
+  double *lw = (double *)malloc(sizeof(double) * N);
+  for (int i = 0; i < N; ++i)
+    lw[i] = logW[i] + D * ell[i] - 0.5 * ((a + D) * (a + D) - a * a) * sig2[i];
+  double lse_new = lse(lw, N), lse_old = lse(logW, N);
+  *log_z_inc = lse_new - lse_old;
+  *ess = orc_ess_at(N, logW, ell, sig2, a, D);
+  for (int i = 0; i < N; ++i) {
+    logW[i] = lw[i] - lse_new;
+    W[i] = exp(logW[i]);
+  }
+  free(lw);
+  return a_new;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Weighted particle moments and the mass matrix (Algorithm 2 step (d)): mean = sum_i W_i theta_i, */
 /* Sigma = sum_i W_i (theta_i - mean)(theta_i - mean)', and its lower Cholesky factor; if the      */
 /* factorisation fails, jitter 1e-10*tr(Sigma)/p (times 10 per retry) is added to the diagonal.    */
@@ -608,6 +645,33 @@ void orc_resample(int N, const double *W, double U, int32_t *anc) {
   int j = 0;
   for (int i = 0; i < N; ++i) {
     uint64_t pos = ((uint64_t)i * T + off) / (uint64_t)N;
+    while (cum[j] <= pos) ++j;
+    anc[i] = j;
+  }
+  free(cum);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Multinomial resampling, the paper's scheme (Sec. 2.2): N independent draws from the weights.   */
+/* On the same integer weights as above, offspring i takes position min(floor(U_i*T), T-1), with  */
+/* its own uniform U_i, and its ancestor is the first j whose inclusive cumulative sum exceeds it */
+/* (the inverse of the quantised CDF).                                                             */
+/* ------------------------------------------------------------------------------------------ */
+void orc_resample_multinomial(int N, const double *W, const double *U, int32_t *anc) {
+  uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * N);
+  uint64_t T = 0;
+  for (int i = 0; i < N; ++i) {
+    T += (uint64_t)floor(W[i] * 0x1.0p40);
+    cum[i] = T;
+  }
+  for (int i = 0; i < N; ++i) {
+    if (T == 0) {
+      anc[i] = i;
+      continue;
+    }
+    uint64_t pos = (uint64_t)floor(U[i] * (double)T);
+    if (pos > T - 1) pos = T - 1;
+    int j = 0;
     while (cum[j] <= pos) ++j;
     anc[i] = j;
   }

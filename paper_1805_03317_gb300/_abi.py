@@ -29,7 +29,8 @@ class SmcConfig(ctypes.Structure):
     _fields_ = [("N", c_i32), ("m", c_i32), ("G", c_i32), ("L", c_i32), ("ess_frac", c_d),
                 ("seed", c_u64), ("search_k", c_i32), ("search_rounds", c_i32), ("eps0", c_d),
                 ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
-                ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32)]
+                ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32),
+                ("resampling", c_i32), ("grid_points", c_i32), ("grid_decades", c_d)]
 
 
 # name -> (restype, argtypes)

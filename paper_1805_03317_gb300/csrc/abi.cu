@@ -19,7 +19,10 @@ struct smc_ctx {
   cudaStream_t stream = nullptr;
   // problem
   int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0, cv_kernel = 0;
-  int cv_order = 2, cv_centre = 0;  // control-variate order; 1: re-centred every stage
+  int cv_order = 2, cv_centre = 0;  // control-variate order; re-centring (0 none, 1, 2)
+  int multinomial = 0;              // resampling scheme (0 systematic, 1 multinomial)
+  int grid_points = 0;              // > 0: grid temperature rule with this many points
+  double grid_decades = 16.0;
   int64_t n = 0;
   double noise_sigma = 1.0;
   std::vector<double> mu_h, var_h;
@@ -643,13 +646,24 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->rounds = rounds;
   c->eps0 = cfg->eps0;
   c->cv_kernel = cfg->cv_kernel == 1 ? 1 : 0;
-  if (cfg->cv_order < 0 || cfg->cv_order > 2 || cfg->cv_centre < 0 || cfg->cv_centre > 1) {
-    g_init_error = "cv_order must be 0, 1 or 2 and cv_centre 0 or 1";
+  if (cfg->cv_order < 0 || cfg->cv_order > 2 || cfg->cv_centre < 0 || cfg->cv_centre > 2) {
+    g_init_error = "cv_order must be 0, 1 or 2 and cv_centre 0, 1 or 2";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  if (cfg->resampling < 0 || cfg->resampling > 1 || cfg->grid_points < 0 ||
+      cfg->grid_points == 1 || cfg->grid_points > (1 << 16) || !(cfg->grid_decades >= 0.0) ||
+      cfg->grid_decades > 300.0) {
+    g_init_error = "resampling must be 0 or 1, grid_points 0 or in [2, 65536], grid_decades in "
+                   "[0, 300]";
     delete c;
     return SMC_ERR_ARG;
   }
   c->cv_order = cfg->cv_order == 1 ? 1 : 2;
   c->cv_centre = cfg->cv_centre;
+  c->multinomial = cfg->resampling;
+  c->grid_points = cfg->grid_points;
+  c->grid_decades = cfg->grid_decades > 0.0 ? cfg->grid_decades : 16.0;
   c->full_data = cfg->full_data ? 1 : 0;
   if (c->full_data && (P->x_dtype != SMC_BF16 || P->p > 64)) {
     g_init_error = "full_data needs BF16 storage and p <= 64";
@@ -710,6 +724,18 @@ const char *smc_last_error(const smc_ctx *c) {
   return c ? c->err.c_str() : g_init_error.c_str();
 }
 
+// Re-centre the control variates at the weighted particle mean in c->mean_d (Alg. 2 (d)): A, B,
+// C and the row constants there, then every particle's l_hat, sigma2_hat and block sums under the
+// new control variates, so that the next comparisons of estimates use one estimator. A non-finite
+// A surfaces through the estimates' error bits. Stream-ordered, no host synchronisation.
+static int recentre(smc_ctx *c) {
+  CUDA_OK(c, cudaMemcpyAsync(c->tb_d, c->mean_d, sizeof(double) * c->p, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  int r = centre_kernels(c);
+  if (!r) r = refresh_cache(c);
+  return r;
+}
+
 int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
   if (!c) return SMC_ERR_ARG;
   c->stage += 1;
@@ -717,9 +743,19 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
   c->moves_in_stage = 0;
   int nl = 0;
   int e;
+  if (c->cv_centre == 2 && !c->full_data) {  // centre at the current cloud, then reweight
+    ProfScope ps(c, 4);
+    LAUNCH(c,
+           weighted_moments(c->is_f64, c->N, c->p, c->W, c->theta, c->part, c->mean_d,
+                            c->Sigma_raw, c->stream),
+           4);
+    const int r0 = recentre(c);
+    if (r0) return r0;
+  }
   {
     ProfScope ps(c, 3);
-    e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->st, c->part,
+    e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->grid_points,
+                 c->grid_decades, c->st, c->part,
                  &nl, c->stream);
   }
   c->launches += nl;
@@ -734,15 +770,9 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
     r = set_mass(c);
   }
   if (r) return r;
-  if (c->cv_centre && !c->full_data) {
-    // Algorithm 2 (d): the control variates move to the reweighted particle mean; the cached
-    // l_hat, sigma2_hat and block sums are re-estimated under them before the moves compare
-    // proposals with them. A non-finite A surfaces through the estimates' error bits.
+  if (c->cv_centre == 1 && !c->full_data) {  // Algorithm 2 (d): centre at the reweighted mean
     ProfScope ps(c, 4);
-    CUDA_OK(c, cudaMemcpyAsync(c->tb_d, c->mean_d, sizeof(double) * c->p,
-                               cudaMemcpyDeviceToDevice, c->stream));
-    if ((r = centre_kernels(c))) return r;
-    if ((r = refresh_cache(c))) return r;
+    if ((r = recentre(c))) return r;
   }
   if (a_next || log_z_inc || ess) {
     DevState h;
@@ -759,7 +789,8 @@ int smc_resample(smc_ctx *c, int32_t *ancestors) {
   if (!c) return SMC_ERR_ARG;
   ProfScope ps(c, 5);
   LAUNCH(c,
-         resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->stage_dev, c->W,
+         resample(c->is_f64, c->N, c->p, c->m, c->G, c->seed, c->stage, c->stage_dev,
+                  c->multinomial, c->W,
                   c->cum, c->anc,
                   c->theta, c->theta_alt, c->u, c->u_alt, c->ell, c->ell_alt, c->sig2,
                   c->sig2_alt, c->blk, c->blk_alt, c->logW, c->W, c->st, c->stream),

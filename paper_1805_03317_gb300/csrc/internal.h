@@ -17,6 +17,7 @@ struct DevState {
   double ess;        // ESS at the chosen increment
   double eps;        // leapfrog step
   double lo, hi, dmax, D;  // temperature search bracket
+  double best_dist, best_D;  // grid search: the point whose ESS is closest to the target so far
   double lse_new, lse_old, lse_new2;
   int stage;
   int search_done;
@@ -135,15 +136,21 @@ int axpy_vec(int p, const double *x, double t, const double *s, double *out, cud
 int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, const double *mu,
                    const double *var, void *theta, int32_t *u, double *logW, double *W,
                    cudaStream_t s);
+// grid_points > 0: the paper's grid rule (Sec. 2.3): the increment is the point of a geometric grid
+// of grid_points values over [(1 - a) 10^-grid_decades, 1 - a] whose ESS is closest to tau N;
+// otherwise the K-ary bracket search of `rounds` rounds.
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
-             int K, int rounds, DevState *st, double *partials, int *launches, cudaStream_t s);
+             int K, int rounds, int grid_points, double grid_decades, DevState *st,
+             double *partials, int *launches, cudaStream_t s);
 int reweight_scratch_doubles();
 int weighted_moments(int is_f64, int N, int p, const double *W, const void *theta,
                      double *partials, double *mean, double *Sigma, cudaStream_t s);
 int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double *chol,
                 void *Sigma_ct, void *Linv_ct, double *work, DevState *st, cudaStream_t s);
 // stage_dev: 1 = the resampling draw's stage index comes from st->stage (graph replays).
+// multinomial: 1 = one uniform per offspring (multinomial), else one per stage (systematic).
 int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, int stage_dev,
+             int multinomial,
              const double *W, uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
              int32_t *u_out, const double *ell, double *ell_out, const double *sig2,
              double *sig2_out, const double *blk, double *blk_out, double *logW, double *Wout,

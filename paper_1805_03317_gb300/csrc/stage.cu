@@ -471,11 +471,16 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 constexpr int kRwThreads = 32, kMaxK = 32, kRwMaxBlocks = 152;  // final kernels: one warp
 constexpr int kSwWarps = 4;  // search kernels: warps per block, lanes = candidates
 
-// Candidates of a search round. Round 0 evaluates the K - 1 interior points of [0, 1 - a] and
-// the end point 1 - a itself (the test "ESS(1 - a) >= tau N" of the rule); later rounds evaluate
-// the K - 1 interior points lo + (hi - lo) k / K of the current bracket.
-__device__ __forceinline__ int candidates(const DevState *st, int K, int round, double &lo,
-                                          double &hi) {
+// Candidates of a search round. Bracket search (S = 0): round 0 evaluates the K - 1 interior
+// points of [0, 1 - a] and the end point 1 - a itself (the test "ESS(1 - a) >= tau N" of the
+// rule); later rounds evaluate the K - 1 interior points lo + (hi - lo) k / K of the current
+// bracket. Grid (S > 0): round r evaluates grid points rK .. rK + K - 1 (ascending).
+__device__ __forceinline__ int candidates(const DevState *st, int K, int round, int S,
+                                          double &lo, double &hi) {
+  if (S > 0) {
+    lo = hi = st->dmax;
+    return min(K, S - round * K);
+  }
   lo = round == 0 ? 0.0 : st->lo;
   hi = round == 0 ? st->dmax : st->hi;
   return round == 0 ? K : K - 1;
@@ -483,15 +488,21 @@ __device__ __forceinline__ int candidates(const DevState *st, int K, int round, 
 __device__ __forceinline__ double candidate(double lo, double hi, int K, int k) {
   return k == K - 1 ? hi : lo + (hi - lo) * (k + 1) / K;
 }
+// Grid point s of S: (1 - a) 10^(-E (S - 1 - s) / (S - 1)); the last point is 1 - a exactly.
+__device__ __forceinline__ double grid_point(double dmax, int S, double E, int s) {
+  if (s >= S - 1) return dmax;
+  return dmax * pow(10.0, -E * (double)(S - 1 - s) / (double)(S - 1));
+}
 
 // Per-block table of the round's candidates: D_k and h_k = ((a + D_k)^2 - a^2) / 2, so that
 // lw_i(D_k) = log W_i + D_k l_hat_i - h_k sigma2_hat_i.
-__device__ __forceinline__ int load_candidates(const DevState *st, int K, int round, double *Dk,
-                                               double *hk, double &lo, double &hi) {
-  const int ncand = candidates(st, K, round, lo, hi);
+__device__ __forceinline__ int load_candidates(const DevState *st, int K, int round, int S,
+                                               double E, double *Dk, double *hk, double &lo,
+                                               double &hi) {
+  const int ncand = candidates(st, K, round, S, lo, hi);
   const double a = st->a;
   for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
-    const double D = candidate(lo, hi, K, k);
+    const double D = S > 0 ? grid_point(st->dmax, S, E, round * K + k) : candidate(lo, hi, K, k);
     Dk[k] = D;
     hk[k] = 0.5 * ((a + D) * (a + D) - a * a);
   }
@@ -504,13 +515,13 @@ __device__ __forceinline__ int load_candidates(const DevState *st, int K, int ro
 // particle loads are broadcasts), so the candidates' chains run side by side.
 __global__ void __launch_bounds__(kSwWarps * 32)
     k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
-                 int round, DevState *st, double *pmax, double *gmax) {
+                 int round, int S, double E, DevState *st, double *pmax, double *gmax) {
   __shared__ double Dk[kMaxK], hk[kMaxK];
   __shared__ double wmax[kSwWarps][kMaxK];
   __shared__ bool is_last;
   if (st->search_done) return;  // uniform across the grid
   double lo, hi;
-  const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
+  const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
@@ -552,14 +563,14 @@ __global__ void __launch_bounds__(kSwWarps * 32)
 // ESS < tau N.
 __global__ void __launch_bounds__(kSwWarps * 32)
     k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
-                 int K, int round, int last_round, DevState *st, const double *gmax,
-                 double *psum) {
+                 int K, int round, int last_round, int S, double E, DevState *st,
+                 const double *gmax, double *psum) {
   __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK];
   __shared__ double wsum[kSwWarps][kMaxK][2];
   __shared__ bool is_last;
   if (st->search_done) return;
   double lo, hi;
-  const int ncand = load_candidates(st, K, round, Dk, hk, lo, hi);
+  const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
@@ -610,6 +621,21 @@ __global__ void __launch_bounds__(kSwWarps * 32)
   const int ninner = round == 0 ? K - 1 : ncand;  // interior points (round 0 adds the end point)
   for (int k = 0; k < ncand; ++k)
     if (!(ess_k[k] == ess_k[k])) atomicOr(&st->err, kErrNonFinite);
+  if (S > 0) {  // grid rule: the closest ESS so far wins; ties keep the smaller increment
+    for (int k = 0; k < ncand; ++k) {
+      const double dist = fabs(ess_k[k] - target);
+      if (dist < st->best_dist) {
+        st->best_dist = dist;
+        st->best_D = Dk[k];
+      }
+    }
+    if (round == last_round) {
+      st->D = st->best_D;
+      st->search_done = 1;
+    }
+    st->ticket = 0;
+    return;
+  }
   if (round == 0 && ess_k[K - 1] >= target) {  // ESS(1 - a) >= target: go straight to a = 1
     st->D = st->dmax;
     st->search_done = 1;
@@ -731,12 +757,20 @@ __global__ void k_search_begin(DevState *st) {
   st->lo = 0.0;
   st->hi = st->dmax;
   st->D = 0.0;
+  st->best_dist = INFINITY;
+  st->best_D = st->dmax;
   st->search_done = 0;
   st->ticket = 0;
 }
 
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
-             int K, int rounds, DevState *st, double *partials, int *launches, cudaStream_t s) {
+             int K, int rounds, int grid_points, double grid_decades, DevState *st,
+             double *partials, int *launches, cudaStream_t s) {
+  if (grid_points > 0) {  // the grid in rounds of kMaxK points
+    if (grid_points < 2 || !(grid_decades > 0.0)) return (int)cudaErrorInvalidValue;
+    K = kMaxK;
+    rounds = (grid_points + kMaxK - 1) / kMaxK;
+  }
   if (K < 2 || K > kMaxK) return (int)cudaErrorInvalidValue;
   int nb = (N + kRwThreads - 1) / kRwThreads;
   if (nb > kRwMaxBlocks) nb = kRwMaxBlocks;
@@ -749,9 +783,10 @@ int reweight(int N, const double *ell, const double *sig2, double *logW, double 
   k_search_begin<<<1, 1, 0, s>>>(st);
   ++count;
   for (int r = 0; r < rounds; ++r) {
-    k_search_max<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, K, r, st, pmax, gmax);
-    k_search_sum<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1, st,
-                                               gmax, psum);
+    k_search_max<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, K, r, grid_points,
+                                               grid_decades, st, pmax, gmax);
+    k_search_sum<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1,
+                                               grid_points, grid_decades, st, gmax, psum);
     count += 2;
   }
   k_final_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, pmax, gmax);
@@ -906,9 +941,11 @@ int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double
 }
 
 // ------------------------------------------------------------------------------------------------
-// Systematic resampling (Algorithm 2 (e)) on integer weights w_i = floor(W_i 2^40): inclusive
-// prefix sums cum (exact), T = cum[N-1], offset floor(U T) with U from the stage's resampling
-// stream, position i = floor((i T + offset) / N), ancestor = first j with cum[j] > position.
+// Resampling (Algorithm 2 (e)) on integer weights w_i = floor(W_i 2^40): inclusive prefix sums
+// cum (exact), T = cum[N-1]. Systematic: offset floor(U T) with U from the stage's resampling
+// stream, position i = floor((i T + offset) / N). Multinomial (the paper's scheme, Sec. 2.2):
+// position i = min(floor(U_i T), T - 1) with U_i from offspring i's own draw. Either way the
+// ancestor is the first j with cum[j] > position.
 // ------------------------------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 
@@ -943,14 +980,23 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-__global__ void k_res_ancestors(int N, const uint64_t *cum, int32_t *anc, const DevState *st) {
+__global__ void k_res_ancestors(int N, const uint64_t *cum, int32_t *anc, const DevState *st,
+                                uint64_t seed, int stage, int stage_dev, int multinomial) {
   const unsigned long long T = st->res_T, off = st->res_off;
+  const uint32_t sm = stage_move(stage_dev ? st->stage : stage, 0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (T == 0) {
       anc[i] = i;
       continue;
     }
-    const unsigned long long pos = ((unsigned long long)i * T + off) / (unsigned long long)N;
+    unsigned long long pos;
+    if (multinomial) {
+      const double Ui = draw_uniform(Stream(seed, kResample, sm, (uint32_t)i).draw(1));
+      pos = (unsigned long long)floor(Ui * (double)T);
+      if (pos > T - 1) pos = T - 1;
+    } else {
+      pos = ((unsigned long long)i * T + off) / (unsigned long long)N;
+    }
     int lo = 0, hi = N - 1;  // first j with cum[j] > pos; cum[N-1] = T > pos
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -993,12 +1039,13 @@ __global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, con
 }
 
 int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, int stage_dev,
-             const double *W, uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
+             int multinomial, const double *W, uint64_t *cum, int32_t *anc, const void *theta, void *theta_out, const int32_t *u,
              int32_t *u_out, const double *ell, double *ell_out, const double *sig2,
              double *sig2_out, const double *blk, double *blk_out, double *logW, double *Wout,
              DevState *st, cudaStream_t s) {
   k_res_scan<<<1, kScanThreads, 0, s>>>(N, W, cum, seed, stage, stage_dev, st);
-  k_res_ancestors<<<(N + 255) / 256, 256, 0, s>>>(N, cum, anc, st);
+  k_res_ancestors<<<(N + 255) / 256, 256, 0, s>>>(N, cum, anc, st, seed, stage, stage_dev,
+                                                   multinomial);
   const int gw = (N * 32 + 255) / 256;
   const int grid = gw < 152 * 16 ? gw : 152 * 16;
   if (is_f64)

@@ -303,6 +303,41 @@ def test_bisection_and_16ary_agree():
     assert a2 == pytest.approx(a16, rel=1e-11, abs=1e-14)
 
 
+def _ess_numpy(logW, ell, sig2, a, D):
+    lw = logW + D * ell - 0.5 * ((a + D) ** 2 - a ** 2) * sig2
+    return float(np.exp(2 * special.logsumexp(lw) - special.logsumexp(2 * lw)))
+
+
+@pytest.mark.parametrize("a", [0.0, 0.2, 0.9])
+def test_grid_rule_takes_the_point_closest_to_the_target(a):
+    """The paper's rule (Sec. 2.3): among the grid points the increment whose ESS is closest to
+    the target. The grid and the ESS are rebuilt here with numpy and scipy's logsumexp."""
+    logW, ell, sig2 = _weights_case(seed=5)
+    N, tau, S, E = logW.size, 0.8, 257, 12.0
+    a_new, lw, W, lz, ess = O.reweight_grid(logW, ell, sig2, a, tau, S, E)
+    dmax = 1.0 - a
+    grid = dmax * np.power(10.0, -E * (S - 1 - np.arange(S)) / (S - 1))
+    grid[-1] = dmax
+    dist = np.array([abs(_ess_numpy(logW, ell, sig2, a, D) - tau * N) for D in grid])
+    best = int(np.argmin(dist))
+    D = dmax if a_new == 1.0 else a_new - a
+    assert D == pytest.approx(grid[best], rel=1e-13)
+    assert ess == pytest.approx(_ess_numpy(logW, ell, sig2, a, D), rel=1e-9)
+    # the grid is fine enough here that the chosen ESS is near the target (not just the closest)
+    assert abs(ess - tau * N) < 0.02 * N
+    inc = D * ell - 0.5 * ((a + D) ** 2 - a ** 2) * sig2
+    assert lz == pytest.approx(special.logsumexp(logW + inc) - special.logsumexp(logW), rel=1e-12)
+    np.testing.assert_allclose(W, np.exp(logW + inc - special.logsumexp(logW + inc)), rtol=1e-9)
+
+
+def test_grid_rule_takes_one_when_every_point_is_above_the_target():
+    N = 100
+    logW = np.full(N, -math.log(N))
+    ell = np.full(N, -10.0) + 1e-3 * np.arange(N)
+    a_new, _, _, _, ess = O.reweight_grid(logW, ell, np.zeros(N), 0.4, 0.8, 64, 8.0)
+    assert a_new == 1.0 and ess > 0.99 * N
+
+
 # ----------------------------------------------------------------------------------------------
 # Moments, mass matrix and resampling (Algorithm 2 (d)-(e))
 # ----------------------------------------------------------------------------------------------
@@ -335,6 +370,47 @@ def test_resampling_invariants():
     one = np.zeros(N)
     one[17] = 1.0
     np.testing.assert_array_equal(O.resample(one, 0.25), np.full(N, 17))
+
+
+def test_multinomial_resampling_is_the_inverse_quantised_cdf():
+    """Multinomial resampling (Sec. 2.2): each offspring inverts the CDF of the integer weights at
+    its own uniform (rebuilt here with numpy's searchsorted); counts over many replications follow
+    the multinomial law (mean N w, variance N w (1 - w)), unlike systematic resampling."""
+    rng = np.random.default_rng(12)
+    N = 211
+    W = rng.random(N) ** 4
+    W /= W.sum()
+    wq = np.floor(W * 2.0 ** 40).astype(np.uint64)
+    cum = np.cumsum(wq)
+    T = int(cum[-1])
+    U = rng.random(N)
+    U[:3] = [0.0, 0.5, 1.0 - 2.0 ** -53]
+    anc = O.resample_multinomial(W, U)
+    pos = np.minimum(np.floor(U * float(T)).astype(np.uint64), np.uint64(T - 1))
+    np.testing.assert_array_equal(anc, np.searchsorted(cum, pos, side="right"))
+    reps = 3000
+    counts = np.zeros((reps, N))
+    for r in range(reps):
+        counts[r] = np.bincount(O.resample_multinomial(W, rng.random(N)), minlength=N)
+    q = wq / float(T)
+    mean, var = counts.mean(axis=0), counts.var(axis=0)
+    assert np.all(np.abs(mean - N * q) < 5 * np.sqrt(N * q * (1 - q) / reps) + 1e-12)
+    big = N * q > 2
+    np.testing.assert_allclose(var[big], (N * q * (1 - q))[big], rtol=0.25)
+    one = np.zeros(N)
+    one[17] = 1.0
+    np.testing.assert_array_equal(O.resample_multinomial(one, rng.random(N)), np.full(N, 17))
+    np.testing.assert_array_equal(O.resample_multinomial(np.zeros(N), rng.random(N)), np.arange(N))
+
+
+def test_multinomial_uniforms_are_the_second_draw_of_each_offspring_block():
+    seed, stage, N = 77, 5, 9
+    U = O.multinomial_uniforms(seed, stage, N)
+    for i in range(N):
+        out = O.philox4x32_10([0, i, O.stage_move(stage, 0), O.TAG_RESAMPLE],
+                              [seed & 0xFFFFFFFF, seed >> 32])
+        r = (int(out[3]) << 32) | int(out[2])
+        assert U[i] == (r >> 11) * 2.0 ** -53
 
 
 # ----------------------------------------------------------------------------------------------
@@ -486,7 +562,8 @@ def test_first_order_estimator_unbiased_and_its_gradient(fam):
         assert g[c] == pytest.approx(fd, rel=1e-6, abs=1e-6)
 
 
-def test_recentred_smc_gaussian_matches_fixed_centre():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_recentred_smc_gaussian_matches_fixed_centre(mode):
     """Algorithm 2 (d) moves theta_bar to the reweighted particle mean every stage. For the
     Gaussian family the second-order expansion is exact, so l_hat does not depend on the centre:
     a run started from a poor centre and re-centred every stage must follow the fixed-centre run
@@ -496,7 +573,7 @@ def test_recentred_smc_gaussian_matches_fixed_centre():
     cfg = O.SMCConfig(N=256, m=8, G=2, L=6, R=2, seed=5, tau=0.5)
     st0 = O.smc_run(prob, cfg)
     prob.set_centre(np.zeros(prob.p))
-    cfg_r = O.SMCConfig(N=256, m=8, G=2, L=6, R=2, seed=5, tau=0.5, recentre=True)
+    cfg_r = O.SMCConfig(N=256, m=8, G=2, L=6, R=2, seed=5, tau=0.5, recentre=mode)
     st1 = O.smc_run(prob, cfg_r)
     assert st1.stage == st0.stage
     assert st1.log_z == pytest.approx(st0.log_z, abs=1e-8)
@@ -529,8 +606,8 @@ def _logistic_quadrature(seed=2, n=400):
     return prob, mean, sd, logml
 
 
-@pytest.mark.parametrize("order", [2, 1])
-def test_recentred_logistic_smc_against_quadrature(order):
+@pytest.mark.parametrize("order,mode", [(2, 1), (1, 1), (2, 2)])
+def test_recentred_logistic_smc_against_quadrature(order, mode):
     """Subsampled SMC re-centred every stage (Algorithm 2 (d)), from a centre at the prior mean,
     with second- or first-order control variates (Sec. 4's Experiment 4): the log marginal
     likelihood and the posterior mean agree with grid quadrature. Four seeded runs are averaged."""
@@ -539,7 +616,7 @@ def test_recentred_logistic_smc_against_quadrature(order):
     errs, means = [], []
     for seed in range(1, 5):
         prob.set_centre(np.zeros(2))
-        cfg = O.SMCConfig(N=1024, m=40, G=4, L=8, R=3, seed=seed, tau=0.5, recentre=True)
+        cfg = O.SMCConfig(N=1024, m=40, G=4, L=8, R=3, seed=seed, tau=0.5, recentre=mode)
         st = O.smc_run(prob, cfg)
         assert st.a == 1.0
         errs.append(st.log_z - logml)
@@ -547,3 +624,24 @@ def test_recentred_logistic_smc_against_quadrature(order):
         assert np.all(np.abs(prob.theta_bar - mean) < 0.5 * sd)
     assert np.all(np.abs(np.mean(means, axis=0) - mean) < 0.1 * sd)
     assert abs(np.mean(errs)) < 0.2
+
+
+def test_paper_settings_recover_conjugate_posterior_and_log_marginal():
+    """The paper's own settings together: ESS target 0.8N by the grid rule, multinomial
+    resampling, control variates re-centred every stage (Algorithm 2 as printed). Averaged over
+    six seeded runs on the conjugate Gaussian model, against the closed forms."""
+    prob, mu, S, logml = _conjugate()
+    errs, means = [], []
+    for seed in range(1, 7):
+        prob.set_centre(np.zeros(prob.p))
+        cfg = O.SMCConfig(N=1024, m=8, G=2, L=8, R=3, seed=seed, tau=0.8, recentre=1,
+                          resampling="multinomial", grid_points=512, grid_decades=16.0)
+        st = O.smc_run(prob, cfg)
+        assert st.a == 1.0
+        assert all(abs(h["ess"] - 0.8 * cfg.N) < 0.05 * cfg.N for h in st.history[:-1])
+        errs.append(st.log_z - logml)
+        means.append(st.thetas.mean(axis=0))
+    sd = np.sqrt(np.diag(S))
+    assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
+    assert abs(np.mean(errs)) < 0.15
+
