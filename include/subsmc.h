@@ -40,9 +40,16 @@ typedef enum {
 } smc_status;
 
 /* Per-row likelihood families l_k(theta) = log p(y_k | x_k' theta) (Sec. 3.1, Eq. likelihood).
- * Logistic: Sec. 4.2 (Experiment 1); Poisson with log link: Sec. 4.3 (Experiment 2);
- * Gaussian response with known sd and probit: used by the synthetic workloads. */
-typedef enum { SMC_LOGISTIC = 0, SMC_PROBIT = 1, SMC_POISSON = 2, SMC_GAUSSIAN = 3 } smc_family;
+ * Logistic: Sec. 4.2 (Experiment 1); Poisson with log link and Student-t regression (errors
+ * t_nu with scale s): Sec. 4.3 (Experiment 2); Gaussian response with known sd and probit: used by
+ * the synthetic workloads. */
+typedef enum {
+  SMC_LOGISTIC = 0,
+  SMC_PROBIT = 1,
+  SMC_POISSON = 2,
+  SMC_GAUSSIAN = 3,
+  SMC_STUDENT_T = 4
+} smc_family;
 
 /* Storage type of the covariate matrix X. */
 typedef enum { SMC_F64 = 0, SMC_F32 = 1, SMC_BF16 = 2 } smc_dtype;
@@ -61,7 +68,10 @@ typedef struct {
                              /* Read only inside smc_init.                                        */
   const double *prior_mean;  /* host [p]                                                          */
   const double *prior_var;   /* host [p], every entry > 0                                         */
-  double noise_sigma;        /* Gaussian family: known response sd (> 0); ignored otherwise       */
+  double noise_sigma;        /* Gaussian family: known response sd (> 0); Student-t: the error    */
+                             /* scale s (> 0); ignored otherwise                                  */
+  double dof;                /* Student-t: degrees of freedom nu (> 0; the paper's nu = 5);      */
+                             /* ignored otherwise                                                 */
 } smc_problem;
 
 /* Run settings. The paper's tuning knobs (Sec. 3.4, Sec. 4.1): M particles, m, G, the ESS target,

@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-FAMILIES = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3}
+FAMILIES = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3, "student_t": 4}
 TAG_INIT_THETA, TAG_INIT_U, TAG_UPM_BLOCK, TAG_UPM_IDX = 1, 2, 3, 4
 TAG_MOMENTUM, TAG_MH_THETA, TAG_MH_U, TAG_RESAMPLE = 5, 6, 7, 8
 
@@ -75,6 +75,8 @@ def lib():
             L.orc_log_prior.argtypes = [c_i, _dp, _dp, _dp, ctypes.c_void_p]
             L.orc_set_cv_order.argtypes = [c_i]
             L.orc_set_cv_order.restype = None
+            L.orc_set_dof.argtypes = [c_d]
+            L.orc_set_dof.restype = None
             L.orc_log_prior.restype = c_d
             prob = [c_i, c_i64, c_i, _dp, _dp, c_d, _dp, c_d, _dp, _dp, _dp, _dp, c_i, c_i]
             L.orc_loglik_batch.argtypes = prob + [c_i, _dp, _i64p, c_d, _dp, _dp,
@@ -136,14 +138,17 @@ def normal(seed, tag, sm, particle, j) -> float:
 # ----------------------------------------------------------------------------------------------
 # Model pieces
 # ----------------------------------------------------------------------------------------------
-def family(fam: str, eta: float, y: float, sigma: float = 1.0):
+def family(fam: str, eta: float, y: float, sigma: float = 1.0, dof: float = 5.0):
+    """l, l', l'' of one row; sigma: Gaussian sd or Student-t scale, dof: Student-t nu."""
+    lib().orc_set_dof(float(dof))
     l, d1, d2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().orc_family(FAMILIES[fam], eta, y, sigma, ctypes.byref(l), ctypes.byref(d1),
                      ctypes.byref(d2))
     return l.value, d1.value, d2.value
 
 
-def full_loglik(fam, X, y, theta, sigma=1.0, grad=True):
+def full_loglik(fam, X, y, theta, sigma=1.0, grad=True, dof=5.0):
+    lib().orc_set_dof(float(dof))
     X = np.ascontiguousarray(X, dtype=np.float64)
     n, p = X.shape
     ell = ctypes.c_double()
@@ -154,7 +159,8 @@ def full_loglik(fam, X, y, theta, sigma=1.0, grad=True):
     return (ell.value, g) if grad else ell.value
 
 
-def cv_moments(fam, X, y, theta_bar, sigma=1.0):
+def cv_moments(fam, X, y, theta_bar, sigma=1.0, dof=5.0):
+    lib().orc_set_dof(float(dof))
     X = np.ascontiguousarray(X, dtype=np.float64)
     n, p = X.shape
     A = ctypes.c_double()
@@ -187,6 +193,7 @@ class Problem:
     B: np.ndarray | None = None
     C: np.ndarray | None = None
     cv_order: int = 2        # Taylor order of the control variates (2, or 1: first order)
+    dof: float = 5.0         # Student-t degrees of freedom (sigma is then the error scale)
 
     def __post_init__(self):
         self.X = np.ascontiguousarray(self.X, dtype=np.float64)
@@ -205,27 +212,42 @@ class Problem:
     def set_centre(self, theta_bar):
         self.theta_bar = np.ascontiguousarray(theta_bar, np.float64)
         self.A, self.B, self.C = cv_moments(self.family, self.X, self.y, self.theta_bar,
-                                            self.sigma)
+                                            self.sigma, self.dof)
 
     def args(self, m, G):
         lib().orc_set_cv_order(int(self.cv_order))  # read by the estimator calls that follow
+        lib().orc_set_dof(float(self.dof))
         return (FAMILIES[self.family], self.n, self.p, self.X, self.y, self.sigma,
                 self.theta_bar, self.A, self.B, self.C, self.prior_mean, self.prior_var, m, G)
 
 
 def newton_map(prob: Problem, iters: int = 50, tol: float = 1e-10):
     """Posterior mode (full data + prior) by Newton's method with step halving; the
-    control-variate centre of the workloads (a fixed reading of Sec. 3.2's theta_bar)."""
+    control-variate centre of the workloads (a fixed reading of Sec. 3.2's theta_bar). Where the
+    negative Hessian is not positive definite (a log-density that is not concave, as the
+    Student-t one far from the mode) lam I is added, lam = 1e-8 max|diag| times 10 per retry,
+    which keeps the step an ascent direction (Levenberg 1944)."""
     theta = prob.prior_mean.copy()
 
+    def damped_step(H, g):
+        M = -H
+        lam, scale = 0.0, max(np.max(np.abs(np.diag(M))), 1e-300)
+        for _ in range(40):
+            try:
+                Lc = np.linalg.cholesky(M + lam * np.eye(M.shape[0]))
+                return np.linalg.solve(Lc.T, np.linalg.solve(Lc, g))
+            except np.linalg.LinAlgError:
+                lam = 1e-8 * scale if lam == 0.0 else 10.0 * lam
+        raise np.linalg.LinAlgError("no damping made the Newton matrix positive definite")
+
     def logpost(t):
-        A, B, C = cv_moments(prob.family, prob.X, prob.y, t, prob.sigma)
+        A, B, C = cv_moments(prob.family, prob.X, prob.y, t, prob.sigma, prob.dof)
         lp, gp = log_prior(t, prob.prior_mean, prob.prior_var)
         return A + lp, B + gp, C - np.diag(1.0 / prob.prior_var)
 
     f, g, H = logpost(theta)
     for _ in range(iters):
-        step = np.linalg.solve(-H, g)
+        step = damped_step(H, g)
         t = 1.0
         while True:
             cand = theta + t * step

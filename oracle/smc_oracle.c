@@ -43,7 +43,12 @@
 #include <omp.h>
 #endif
 
-enum { FAM_LOGISTIC = 0, FAM_PROBIT = 1, FAM_POISSON = 2, FAM_GAUSSIAN = 3 };
+enum { FAM_LOGISTIC = 0, FAM_PROBIT = 1, FAM_POISSON = 2, FAM_GAUSSIAN = 3, FAM_STUDENT_T = 4 };
+
+/* Degrees of freedom nu of the Student-t family (Sec. 4.3: nu = 5). Process-wide; set by the Python
+ * front end before each call, like the control-variate order below. */
+static double g_dof = 5.0;
+void orc_set_dof(double nu) { g_dof = nu; }
 enum {
   TAG_INIT_THETA = 1, TAG_INIT_U = 2, TAG_UPM_BLOCK = 3, TAG_UPM_IDX = 4,
   TAG_MOMENTUM = 5, TAG_MH_THETA = 6, TAG_MH_U = 7, TAG_RESAMPLE = 8
@@ -161,6 +166,16 @@ void orc_family(int fam, double eta, double y, double sigma, double *l, double *
       *d2 = -1.0 / s2;
       break;
     }
+    case FAM_STUDENT_T: {
+      /* y = eta + s*e, e ~ t_nu (Sec. 4.3): l = log Gamma((nu+1)/2) - log Gamma(nu/2)
+       * - log(nu pi s^2)/2 - (nu+1)/2 log(1 + (y - eta)^2 / (nu s^2)) */
+      double nu = g_dof, s2 = sigma * sigma, r = y - eta, q = nu * s2 + r * r;
+      *l = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(3.14159265358979323846 * nu * s2) -
+           0.5 * (nu + 1.0) * log(q / (nu * s2));
+      *d1 = (nu + 1.0) * r / q;
+      *d2 = (nu + 1.0) * (r * r - nu * s2) / (q * q);
+      break;
+    }
     case FAM_PROBIT: {
       /* l = log Phi(s*eta), s = 2y - 1 */
       double s = 2.0 * y - 1.0, z = s * eta, lp, lam;
@@ -236,7 +251,7 @@ typedef struct {
   int p;
   const double *X; /* [n,p] */
   const double *y; /* [n]   */
-  double sigma;    /* Gaussian noise sd */
+  double sigma;    /* Gaussian noise sd, Student-t scale */
   const double *theta_bar, *B, *C;
   double A;
   const double *prior_mu, *prior_var;

@@ -15,14 +15,14 @@ c_dp = ctypes.POINTER(ctypes.c_double)
 c_ip = ctypes.POINTER(ctypes.c_int32)
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_CUDA, SMC_ERR_NONFINITE, SMC_ERR_TIMEOUT, SMC_ERR_OOM = 0, -1, -2, -3, -4, -5
-FAMILY = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3}
+FAMILY = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3, "student_t": 4}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
 
 
 class SmcProblem(ctypes.Structure):
     _fields_ = [("family", c_i32), ("n", c_i64), ("p", c_i32), ("X", c_vp), ("x_dtype", c_i32),
                 ("x_ld", c_i64), ("y", c_vp), ("prior_mean", c_dp), ("prior_var", c_dp),
-                ("noise_sigma", c_d)]
+                ("noise_sigma", c_d), ("dof", c_d)]
 
 
 class SmcConfig(ctypes.Structure):

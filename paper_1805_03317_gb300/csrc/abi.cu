@@ -24,7 +24,8 @@ struct smc_ctx {
   int grid_points = 0;              // > 0: grid temperature rule with this many points
   double grid_decades = 16.0;
   int64_t n = 0;
-  double noise_sigma = 1.0;
+  double noise_sigma = 1.0;  // Gaussian sd or Student-t scale (1 for the other families)
+  double dof = 0.0;          // Student-t degrees of freedom
   std::vector<double> mu_h, var_h;
   double log_prior_const = 0.0;
   // configuration
@@ -300,7 +301,7 @@ int check_err_bits(smc_ctx *c, const DevState &h) {
 int moments_at(smc_ctx *c, const double *theta_d, double *A_out, double *B_out, double *C_out) {
   LAUNCH(c,
          cv_moments(c->Xp, c->x_dtype, c->n, c->p, c->S, c->Yo, c->fam,
-                    c->noise_sigma * c->noise_sigma, theta_d, c->part,
+                    c->noise_sigma * c->noise_sigma, c->dof, theta_d, c->part,
                     cv_moments_blocks(c->p), A_out, B_out, C_out, c->cv_kernel, c->stream),
          2);
   return SMC_OK;
@@ -386,7 +387,7 @@ int centre_kernels(smc_ctx *c) {
   }
   LAUNCH(c,
          row_consts(c->Xp, c->x_dtype, c->n, p, c->S, c->Yo, c->fam, c->tb_ct,
-                    1.0 / (c->noise_sigma * c->noise_sigma), c->stream),
+                    1.0 / (c->noise_sigma * c->noise_sigma), c->dof, c->stream),
          1);
   return SMC_OK;
 }
@@ -411,7 +412,7 @@ int full_prepare(smc_ctx *c, int64_t B) {
     c->full_const_d = reinterpret_cast<double *>(c->full_flag) + 1;
     LAUNCH(c,
            full_loglik_const(c->Xp, c->n, c->S, c->Yo, c->fam, c->noise_sigma * c->noise_sigma,
-                             c->full_const_d, c->stream),
+                             c->dof, c->full_const_d, c->stream),
            1);
     CUDA_OK(c, cudaMemcpyAsync(&c->full_const, c->full_const_d, sizeof(double),
                                cudaMemcpyDeviceToHost, c->stream));
@@ -432,7 +433,7 @@ int full_eval(smc_ctx *c, int B, const void *theta, double a, const double *a_de
   ProfScope ps(c, 0);
   LAUNCH(c,
          full_loglik(c->Xp, c->n, c->p, c->S, c->Yo, c->fam, c->noise_sigma * c->noise_sigma,
-                     theta, B, a, a_dev, c->full_const, c->mu_ct, c->ivar_ct, c->full_acc,
+                     c->dof, theta, B, a, a_dev, c->full_const, c->mu_ct, c->ivar_ct, c->full_acc,
                      c->full_flag, ell, grad, c->sms, c->stream),
          2);
   return SMC_OK;
@@ -595,7 +596,6 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   if (!out) return fail(nullptr, SMC_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!P || !cfg) return fail(nullptr, SMC_ERR_ARG, "problem or config is NULL");
-  if (P->family < 0 || P->family > 3) return fail(nullptr, SMC_ERR_ARG, "unknown family");
   if (P->x_dtype < 0 || P->x_dtype > 2) return fail(nullptr, SMC_ERR_ARG, "unknown x_dtype");
   if (P->n < 1 || P->n > 0x7fffffffLL) return fail(nullptr, SMC_ERR_ARG, "n must be in [1, 2^31)");
   if (P->p < 1 || P->p > 126) return fail(nullptr, SMC_ERR_ARG, "p must be in [1, 126]");
@@ -605,8 +605,12 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   for (int k = 0; k < P->p; ++k)
     if (!(P->prior_var[k] > 0) || !isfinite(P->prior_mean[k]))
       return fail(nullptr, SMC_ERR_ARG, "prior variances must be > 0 and means finite");
-  if (P->family == SMC_GAUSSIAN && !(P->noise_sigma > 0))
-    return fail(nullptr, SMC_ERR_ARG, "Gaussian family needs noise_sigma > 0");
+  if (P->family < SMC_LOGISTIC || P->family > SMC_STUDENT_T)
+    return fail(nullptr, SMC_ERR_ARG, "unknown family");
+  if ((P->family == SMC_GAUSSIAN || P->family == SMC_STUDENT_T) && !(P->noise_sigma > 0))
+    return fail(nullptr, SMC_ERR_ARG, "Gaussian and Student-t families need noise_sigma > 0");
+  if (P->family == SMC_STUDENT_T && !(P->dof > 0 && P->dof < 1e6))
+    return fail(nullptr, SMC_ERR_ARG, "Student-t family needs dof in (0, 1e6)");
   if (cfg->N < 1 || cfg->N >= (1 << 23)) return fail(nullptr, SMC_ERR_ARG, "N must be in [1, 2^23)");
   if (cfg->m < 1 || cfg->G < 1 || cfg->G > cfg->m)
     return fail(nullptr, SMC_ERR_ARG, "need m >= 1 and 1 <= G <= m");
@@ -632,7 +636,9 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->Sx = c->Yo;  // streamed tiles cover the covariate vectors; tails travel separately
   c->n = P->n;
   c->p = P->p;
-  c->noise_sigma = P->family == SMC_GAUSSIAN ? P->noise_sigma : 1.0;
+  c->noise_sigma =
+      (P->family == SMC_GAUSSIAN || P->family == SMC_STUDENT_T) ? P->noise_sigma : 1.0;
+  c->dof = P->family == SMC_STUDENT_T ? P->dof : 0.0;
   c->mu_h.assign(P->prior_mean, P->prior_mean + P->p);
   c->var_h.assign(P->prior_var, P->prior_var + P->p);
   for (int k = 0; k < P->p; ++k) c->log_prior_const += -0.5 * log(6.283185307179586 * c->var_h[k]);

@@ -132,8 +132,9 @@ __device__ __forceinline__ int unit_off(int k, int c) { return c * kStrip + (k >
 
 template <int FAM>
 __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64_t n, int p, int S,
-                                                  int Yo, double s2, const double *theta,
-                                                  double *part, int N, int ncols) {
+                                                  int Yo, double s2, double nu,
+                                                  const double *theta, double *part, int N,
+                                                  int ncols) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nvx = (p + 7) / 8;   // 16-byte units of covariates per row
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
         }
         const double eta = ((ep[0] + ep[1]) + (ep[2] + ep[3])) + ((ep[4] + ep[5]) + (ep[6] + ep[7]));
         const RowC<float> *tl = reinterpret_cast<const RowC<float> *>(Xp + (r0 + k) * S + Yo);
-        row_value<FAM>(eta, (double)__ldg(&tl->y), s2, l, d1, d2);
+        row_value<FAM>(eta, (double)__ldg(&tl->y), s2, nu, l, d1, d2);
       }
       Aacc += l;
       lps[k] = d1;
@@ -324,7 +325,7 @@ size_t cv_mma_smem(int p, int N) {
 }
 
 template <int FAM>
-int launch_fam(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, double s2,
+int launch_fam(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, double s2, double nu,
                const double *theta, double *part, int maxblocks, int *nblocks, cudaStream_t s) {
   const int N = ((p + 15) / 16) * 16;
   const size_t smem = cv_mma_smem(p, N);
@@ -346,7 +347,7 @@ int launch_fam(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, double 
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
   *nblocks = (int)grid;
-  k_cv_mma<FAM><<<(int)grid, kRows, smem, s>>>(Xp, n, p, S, Yo, s2, theta, part, N, cols);
+  k_cv_mma<FAM><<<(int)grid, kRows, smem, s>>>(Xp, n, p, S, Yo, s2, nu, theta, part, N, cols);
   return (int)cudaGetLastError();
 }
 
@@ -355,15 +356,17 @@ int launch_fam(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, double 
 // Partials of A, B, C for BF16 storage with p <= 128 on the tensor cores; writes the number of
 // partial blocks used to *nblocks. Returns a cudaError_t (cudaErrorInvalidValue if p > 128).
 int cv_moments_mma(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
-                   const double *theta, double *partials, int maxblocks, int *nblocks,
+                   double nu, const double *theta, double *partials, int maxblocks, int *nblocks,
                    cudaStream_t s) {
   if (p < 1 || p > kM) return (int)cudaErrorInvalidValue;
   const __nv_bfloat16 *X = (const __nv_bfloat16 *)Xp;
+  const double v = nu;
   switch (fam) {
-    case 0: return launch_fam<0>(X, n, p, S, Yo, sigma2, theta, partials, maxblocks, nblocks, s);
-    case 1: return launch_fam<1>(X, n, p, S, Yo, sigma2, theta, partials, maxblocks, nblocks, s);
-    case 2: return launch_fam<2>(X, n, p, S, Yo, sigma2, theta, partials, maxblocks, nblocks, s);
-    default: return launch_fam<3>(X, n, p, S, Yo, sigma2, theta, partials, maxblocks, nblocks, s);
+    case 0: return launch_fam<0>(X, n, p, S, Yo, sigma2, v, theta, partials, maxblocks, nblocks, s);
+    case 1: return launch_fam<1>(X, n, p, S, Yo, sigma2, v, theta, partials, maxblocks, nblocks, s);
+    case 2: return launch_fam<2>(X, n, p, S, Yo, sigma2, v, theta, partials, maxblocks, nblocks, s);
+    case 3: return launch_fam<3>(X, n, p, S, Yo, sigma2, v, theta, partials, maxblocks, nblocks, s);
+    default: return launch_fam<4>(X, n, p, S, Yo, sigma2, v, theta, partials, maxblocks, nblocks, s);
   }
 }
 

@@ -170,21 +170,28 @@ template <typename CT> __device__ __forceinline__ void log_phi_(CT z, CT &lp, CT
 }
 
 // Trajectory-invariant per-row constants: they depend on eta_bar = x'theta_bar and y only, so they
-// are computed once per centre and stored in the row's tail. row_terms = row_incr(row_consts(...)).
+// are computed once per centre and stored in the row's tail; row_incr(row_consts(...)) gives d, r.
 //   logistic: c0 = sigma(eta_bar), c1 = c0 (1 - c0), c2 = eta_bar
 //   Poisson:  c0 = e^eta_bar
 //   Gaussian: c0 = y - eta_bar
 //   probit:   c0 = z_bar = s eta_bar (s = 2y - 1), c1 = log Phi(z_bar), c2 = lambda(z_bar)
+//   Student-t: c0 = r_bar = y - eta_bar, c1 = 1 / (nu s^2 + r_bar^2), c2 = nu + 1
 template <typename CT> struct alignas(16) RowC {
   CT c0, c1, c2, y;
 };
 
+// nu: degrees of freedom of the Student-t family (unused by the others).
 template <int FAM, typename CT>
-__device__ __forceinline__ RowC<CT> row_consts(CT eb, CT y, CT inv_s2) {
+__device__ __forceinline__ RowC<CT> row_consts(CT eb, CT y, CT inv_s2, CT nu = CT(0)) {
   RowC<CT> c;
   c.c0 = c.c1 = c.c2 = CT(0);
   c.y = y;
-  if (FAM == 0) {
+  if (FAM == 4) {
+    const CT rb = y - eb;
+    c.c0 = rb;
+    c.c1 = CT(1) / fma(rb, rb, nu / inv_s2);
+    c.c2 = nu + CT(1);
+  } else if (FAM == 0) {
     const CT sb = sigmoid_(eb);
     c.c0 = sb;
     c.c1 = sb * (CT(1) - sb);
@@ -284,6 +291,32 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
       r = sb - sigmoid_(eb + D) + w * D;
     }
     d = -L1 + sb * D + CT(0.5) * w * D * D;
+  } else if (FAM == 4) {  // Student-t: l = const - (nu+1)/2 log(nu s^2 + (y - eta)^2)
+    // With r = r_bar - D, q = nu s^2 + r^2 = q_bar (1 + w), w = (D^2 - 2 r_bar D) b, b = 1/q_bar:
+    //   l - l_bar = -(nu+1)/2 log1p(w); its first two Taylor terms in D are -(nu+1)/2 (a D +
+    //   (b - a^2/2) D^2) with a = -2 r_bar b, so
+    //   d = -(nu+1)/2 [L3(w) - a b D^3 - b^2 D^4 / 2],  L3(w) = log1p(w) - w + w^2/2,
+    //   r = -(nu+1) b^2 D^2 [r_bar (3 - 4 r_bar^2 b) + (2 r_bar^2 b - 1) D] / (1 + w),
+    // both free of the cancellation of the printed definitions. L3 = w^3 sum_j (-w)^j / (j + 3)
+    // by its series for small |w| (terms w^3 .. w^14: the remainder is below 2e-8 of w^3/3 for
+    // |w| <= 1/4 in FP32, below 1e-16 for |w| <= 1/20 in FP64), else directly.
+    const CT rb = c.c0, b = c.c1, nu1 = c.c2;
+    const CT w = (D * D - CT(2) * rb * D) * b;
+    constexpr CT kSmall = sizeof(CT) == 8 ? CT(0.05) : CT(0.25);
+    CT L3;
+    if (fabs(w) <= kSmall) {
+      CT s = CT(1.0 / 14.0);
+#pragma unroll
+      for (int k = 13; k >= 3; --k) s = fma(s, -w, CT(1.0 / k));
+      L3 = w * w * w * s;
+    } else {
+      L3 = log1p(w) - w + CT(0.5) * w * w;
+    }
+    const CT a = CT(-2) * rb * b, D2 = D * D;
+    d = CT(-0.5) * nu1 * (L3 - a * b * D2 * D - CT(0.5) * b * b * D2 * D2);
+    const CT rb2b = rb * rb * b;
+    r = -nu1 * b * b * D2 * fma(fma(CT(2), rb2b, CT(-1)), D, rb * (CT(3) - CT(4) * rb2b)) /
+        (CT(1) + w);
   } else if (FAM == 2) {  // Poisson: d = -e^eb tail3(D), r = -e^eb tail2(D)
     const CT t3 = exp_tail<CT, 3>(D);  // e^D - 1 - D - D^2/2; e^D - 1 - D = t3 + D^2/2
     d = -c.c0 * t3;
@@ -308,6 +341,7 @@ template <int FAM, typename CT> __device__ __forceinline__ CT row_l2(const RowC<
   if (FAM == 0) return -c.c1;
   if (FAM == 2) return -c.c0;
   if (FAM == 3) return -inv_s2;
+  if (FAM == 4) return c.c2 * c.c1 * fma(CT(2) * c.c0 * c.c0, c.c1, CT(-1));
   return -c.c2 * (c.c0 + c.c2);
 }
 // First-order control variates: d and r of the second-order forms plus the second-order term,
@@ -321,7 +355,8 @@ __device__ __forceinline__ float row_l2_any(int fam, const RowC<float> &c, float
     case 0: return row_l2<0, float>(c, inv_s2);
     case 1: return row_l2<1, float>(c, inv_s2);
     case 2: return row_l2<2, float>(c, inv_s2);
-    default: return row_l2<3, float>(c, inv_s2);
+    case 3: return row_l2<3, float>(c, inv_s2);
+    default: return row_l2<4, float>(c, inv_s2);
   }
 }
 __device__ __forceinline__ double row_l2_any(int fam, const RowC<double> &c, double inv_s2) {
@@ -329,20 +364,23 @@ __device__ __forceinline__ double row_l2_any(int fam, const RowC<double> &c, dou
     case 0: return row_l2<0, double>(c, inv_s2);
     case 1: return row_l2<1, double>(c, inv_s2);
     case 2: return row_l2<2, double>(c, inv_s2);
-    default: return row_l2<3, double>(c, inv_s2);
+    case 3: return row_l2<3, double>(c, inv_s2);
+    default: return row_l2<4, double>(c, inv_s2);
   }
 }
 
-template <int FAM, typename CT>
-__device__ __forceinline__ void row_terms(CT eb, CT D, CT y, CT inv_s2, CT &d, CT &r) {
-  row_incr<FAM, CT>(row_consts<FAM, CT>(eb, y, inv_s2), D, inv_s2, d, r);
-}
-
-// Full per-row value and derivatives at eta (used by the moment kernel, FP64).
+// Full per-row value and derivatives at eta (used by the moment kernel, FP64). s2: the Gaussian
+// variance or the Student-t squared scale; nu: the Student-t degrees of freedom.
 template <int FAM>
-__device__ __forceinline__ void row_value(double eta, double y, double s2, double &l, double &d1,
-                                          double &d2) {
-  if (FAM == 0) {
+__device__ __forceinline__ void row_value(double eta, double y, double s2, double nu, double &l,
+                                          double &d1, double &d2) {
+  if (FAM == 4) {
+    const double r = y - eta, q = fma(r, r, nu * s2);
+    l = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(3.14159265358979323846 * nu * s2) -
+        0.5 * (nu + 1.0) * log1p(r * r / (nu * s2));
+    d1 = (nu + 1.0) * r / q;
+    d2 = (nu + 1.0) * (r * r - nu * s2) / (q * q);
+  } else if (FAM == 0) {
     const double s = sigmoid_(eta);
     l = y * eta - softplus_(eta);
     d1 = y - s;

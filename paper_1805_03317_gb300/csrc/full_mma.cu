@@ -109,11 +109,16 @@ __device__ __forceinline__ float bfv(uint32_t b) { return __uint_as_float(b << 1
 // of kStrip bytes, 8-index core matrices of 128 bytes, 16 bytes per index.
 __device__ __forceinline__ int uoff(int t, int q) { return q * kStrip + (t >> 3) * 128 + (t & 7) * 16; }
 
-// theta-dependent part of l_k and its eta-derivative, FP32 (the per-row constants of the Poisson
-// and Gaussian log-densities are added once per particle by the finishing kernel).
+// theta-dependent part of l_k and its eta-derivative, FP32 (the per-row constants of the Poisson,
+// Gaussian and Student-t log-densities are added once per particle by the finishing kernel).
 template <int FAM>
-__device__ __forceinline__ void fam_terms(float eta, float y, float inv_s2, float &l, float &d1) {
-  if (FAM == 0) {  // logistic: y eta - softplus(eta), y - sigma(eta)
+__device__ __forceinline__ void fam_terms(float eta, float y, float inv_s2, float nu, float &l,
+                                          float &d1) {
+  if (FAM == 4) {  // Student-t: -(nu+1)/2 log(1 + r^2 / (nu s^2)), (nu+1) r / (nu s^2 + r^2)
+    const float r = y - eta, z = r * r * inv_s2;
+    l = -0.5f * (nu + 1.f) * log1pf(z / nu);
+    d1 = __fdividef((nu + 1.f) * r * inv_s2, nu + z);
+  } else if (FAM == 0) {  // logistic: y eta - softplus(eta), y - sigma(eta)
     const float e = __expf(-fabsf(eta));
     const float inv = __fdividef(1.f, 1.f + e);
     l = y * eta - (fmaxf(eta, 0.f) + __logf(1.f + e));
@@ -166,7 +171,8 @@ constexpr int kThreads = 256;
 
 template <int FAM>
 __global__ void __launch_bounds__(kThreads) k_full_mma(
-    const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, float inv_s2, const float *theta,
+    const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, float inv_s2, float nu,
+    const float *theta,
     int B, int ntile_p, int nchunk, int64_t chunk_rows, double *acc, int Kp, int Np, int *flag) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_full_mma(
           for (int e = 0; e < 16; ++e) {
             float l = 0.f;
             d[e] = 0.f;
-            if (fast || (live && t0 + c0 + e < r1)) fam_terms<FAM>(v[e], yy[e], inv_s2, l, d[e]);
+            if (fast || (live && t0 + c0 + e < r1)) fam_terms<FAM>(v[e], yy[e], inv_s2, nu, l, d[e]);
             ls += l;
           }
           lsum += (double)ls;
@@ -392,16 +398,21 @@ __global__ void k_full_finish(int B, int p, int nchunk, const double *acc, doubl
   }
 }
 
-// Sum over rows of the theta-free part of the log-density: -lgamma(y + 1) (Poisson) or
-// -log(2 pi sigma^2) / 2 (Gaussian); FP64, per-block partial sums added atomically.
+// Sum over rows of the theta-free part of the log-density: -lgamma(y + 1) (Poisson),
+// -log(2 pi sigma^2) / 2 (Gaussian) or lgamma((nu+1)/2) - lgamma(nu/2) - log(nu pi s^2) / 2
+// (Student-t); FP64, per-block partial sums added atomically.
 __global__ void k_full_const(const __nv_bfloat16 *Xp, int64_t n, int S, int Yo, int fam, double s2,
-                             double *out) {
+                             double nu, double *out) {
+  const double tc = fam == 4 ? lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) -
+                                   0.5 * log(3.14159265358979323846 * nu * s2)
+                             : 0.0;
   double t = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const double y = (double)reinterpret_cast<const RowC<float> *>(Xp + k * S + Yo)->y;
     if (fam == 2) t -= lgamma(y + 1.0);
     if (fam == 3) t -= 0.5 * log(6.283185307179586476925286766559 * s2);
+    if (fam == 4) t += tc;
   }
   t = warp_sum(t);
   if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(out, t);
@@ -427,7 +438,7 @@ int full_chunks(int64_t n, int B, int sms, int64_t *chunk_rows_out) {
 }
 
 template <int FAM>
-int launch_full(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, float inv_s2,
+int launch_full(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, float inv_s2, float nu,
                 const float *theta, int B, double *acc, int *flag, int sms, cudaStream_t s) {
   const int Kp = ((p + 15) / 16) * 16, Np = ((p + 15) / 16) * 16;
   const size_t smem = full_smem(Kp);
@@ -448,8 +459,8 @@ int launch_full(const __nv_bfloat16 *Xp, int64_t n, int p, int S, int Yo, float 
   const int nchunk = full_chunks(n, B, sms, &chunk_rows);
   const int items = ntile * nchunk;
   const int grid = items < slots ? items : slots;
-  k_full_mma<FAM><<<grid, kThreads, smem, s>>>(Xp, n, p, S, Yo, inv_s2, theta, B, ntile, nchunk,
-                                         chunk_rows, acc, Kp, Np, flag);
+  k_full_mma<FAM><<<grid, kThreads, smem, s>>>(Xp, n, p, S, Yo, inv_s2, nu, theta, B, ntile,
+                                               nchunk, chunk_rows, acc, Kp, Np, flag);
   return (int)cudaGetLastError();
 }
 
@@ -459,16 +470,16 @@ int full_acc_doubles(int64_t n, int p, int B, int sms) {
   return full_chunks(n, B, sms, nullptr) * B * (p + 1);
 }
 
-int full_loglik_const(const void *Xp, int64_t n, int S, int Yo, int fam, double sigma2,
+int full_loglik_const(const void *Xp, int64_t n, int S, int Yo, int fam, double sigma2, double nu,
                       double *out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess) return (int)e;
-  if (fam != 2 && fam != 3) return 0;
-  k_full_const<<<152 * 4, 256, 0, s>>>((const __nv_bfloat16 *)Xp, n, S, Yo, fam, sigma2, out);
+  if (fam != 2 && fam != 3 && fam != 4) return 0;
+  k_full_const<<<152 * 4, 256, 0, s>>>((const __nv_bfloat16 *)Xp, n, S, Yo, fam, sigma2, nu, out);
   return (int)cudaGetLastError();
 }
 
-int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
+int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2, double nu,
                 const void *theta, int B, double a, const double *a_dev, double lconst,
                 const void *mu, const void *ivar, double *acc, int *flag, double *ell, void *grad,
                 int sms, cudaStream_t s) {
@@ -477,13 +488,14 @@ int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double
   // every (chunk, live particle) slot of acc is written by exactly one CTA item
   const __nv_bfloat16 *X = (const __nv_bfloat16 *)Xp;
   const float *th = (const float *)theta;
-  const float i2 = (float)(1.0 / sigma2);
+  const float i2 = (float)(1.0 / sigma2), v = (float)nu;
   int r;
   switch (fam) {
-    case 0: r = launch_full<0>(X, n, p, S, Yo, i2, th, B, acc, flag, sms, s); break;
-    case 1: r = launch_full<1>(X, n, p, S, Yo, i2, th, B, acc, flag, sms, s); break;
-    case 2: r = launch_full<2>(X, n, p, S, Yo, i2, th, B, acc, flag, sms, s); break;
-    default: r = launch_full<3>(X, n, p, S, Yo, i2, th, B, acc, flag, sms, s); break;
+    case 0: r = launch_full<0>(X, n, p, S, Yo, i2, v, th, B, acc, flag, sms, s); break;
+    case 1: r = launch_full<1>(X, n, p, S, Yo, i2, v, th, B, acc, flag, sms, s); break;
+    case 2: r = launch_full<2>(X, n, p, S, Yo, i2, v, th, B, acc, flag, sms, s); break;
+    case 3: r = launch_full<3>(X, n, p, S, Yo, i2, v, th, B, acc, flag, sms, s); break;
+    default: r = launch_full<4>(X, n, p, S, Yo, i2, v, th, B, acc, flag, sms, s); break;
   }
   if (r) return r;
   const int64_t tot = (int64_t)B * (p + 1);

@@ -40,7 +40,7 @@ struct EstArgs {
   const void *Xp;  // packed rows [n, S]: x in [0, p), the RowC tail {c0, c1, c2, y} at element Yo
   int64_t n;
   int p, S, Yo, m, G, fam;
-  double inv_s2;   // Gaussian family: 1/sigma^2
+  double inv_s2;   // Gaussian family: 1/sigma^2; Student-t: 1/scale^2
   double A;        // sum_k l_k(theta_bar)
   const double *A_dev;  // when set, A is read from here (a centre that moves every stage)
   const void *B_ct, *C_ct, *tb_ct;  // B [p], C [p,p] (symmetric), theta_bar [p]
@@ -121,13 +121,14 @@ int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const vo
               int S, int Yo, cudaStream_t s);
 // Rewrites the constants c0..c2 in every packed row's tail for the centre tb_ct (state type).
 int row_consts(void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, const void *tb_ct,
-               double inv_s2, cudaStream_t s);
+               double inv_s2, double nu, cudaStream_t s);
 // mode 0: tensor cores (cv_mma.cu) for BF16 storage with p <= 128, SIMT otherwise; mode 1: SIMT.
+// sigma2: Gaussian variance or Student-t squared scale; nu: Student-t degrees of freedom.
 int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
-               const double *theta, double *partials, int nblocks, double *A, double *B,
-               double *C, int mode, cudaStream_t s);
+               double nu, const double *theta, double *partials, int nblocks, double *A,
+               double *B, double *C, int mode, cudaStream_t s);
 int cv_moments_mma(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
-                   const double *theta, double *partials, int maxblocks, int *nblocks,
+                   double nu, const double *theta, double *partials, int maxblocks, int *nblocks,
                    cudaStream_t s);
 int cv_moments_blocks(int p);
 int newton_step(int p, const double *theta, const double *B, const double *C, const double *mu,
@@ -167,7 +168,7 @@ int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s);
 // sum_k l_k(theta_i) (+ lconst), grad[B, p] = a grad l + grad log prior (state type, may be null).
 // acc: FP64 scratch of full_acc_doubles(); flag: device int set to 1 if a wait timed out.
 // a_dev: device temperature (overrides a when not null).
-int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2,
+int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double sigma2, double nu,
                 const void *theta, int B, double a, const double *a_dev, double lconst,
                 const void *mu, const void *ivar, double *acc, int *flag, double *ell, void *grad,
                 int sms, cudaStream_t s);
@@ -186,7 +187,7 @@ int full_move_accept(int N, int p, void *theta, const void *thp, const void *rho
 // Doubles of FP64 scratch (acc) that full_loglik needs for B particles.
 int full_acc_doubles(int64_t n, int p, int B, int sms);
 // Sum over rows of the theta-free part of the log-density into *out (device double).
-int full_loglik_const(const void *Xp, int64_t n, int S, int Yo, int fam, double sigma2,
+int full_loglik_const(const void *Xp, int64_t n, int S, int Yo, int fam, double sigma2, double nu,
                       double *out, cudaStream_t s);
 
 // Message returned by smc_last_error(NULL) (abi.cu).

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
           case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
           case 1: row_incr<1, CT>(c, D, inv_s2, d, r); break;
           case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
-          default: row_incr<3, CT>(c, D, inv_s2, d, r); break;
+          case 3: row_incr<3, CT>(c, D, inv_s2, d, r); break;
+          default: row_incr<4, CT>(c, D, inv_s2, d, r); break;
         }
         if (cv1) to_first_order(row_l2_any(fam, c, inv_s2), D, d, r);
         axpy_slots<CPL>(r, x, v);

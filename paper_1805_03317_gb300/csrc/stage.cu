@@ -83,7 +83,8 @@ int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const vo
 // eta_bar = x'theta_bar in column order and rewrites c0..c2 of the row's tail (device.cuh).
 template <typename XT, int FAM>
 __global__ void k_row_consts(XT *Xp, int64_t n, int p, int S, int Yo,
-                             const typename Store<XT>::CT *tb, typename Store<XT>::CT inv_s2) {
+                             const typename Store<XT>::CT *tb, typename Store<XT>::CT inv_s2,
+                             typename Store<XT>::CT nu) {
   using SD = Store<XT>;
   using CT = typename SD::CT;
   const int nvx = Yo * (int)sizeof(XT) / 16;
@@ -101,33 +102,37 @@ __global__ void k_row_consts(XT *Xp, int64_t n, int p, int S, int Yo,
       }
     }
     RowC<CT> *tl = reinterpret_cast<RowC<CT> *>(row + Yo);
-    *tl = row_consts<FAM, CT>(eb, tl->y, inv_s2);
+    *tl = row_consts<FAM, CT>(eb, tl->y, inv_s2, nu);
   }
 }
 
 template <typename XT>
 int launch_row_consts(XT *Xp, int64_t n, int p, int S, int Yo, int fam, const void *tb,
-                      double inv_s2, cudaStream_t s) {
+                      double inv_s2, double nu, cudaStream_t s) {
   using CT = typename Store<XT>::CT;
   const int64_t need = (n + 255) / 256;
   const int grid = (int)(need < 152 * 16 ? need : 152 * 16);
   const CT *t = (const CT *)tb;
-  const CT i2 = (CT)inv_s2;
+  const CT i2 = (CT)inv_s2, v = (CT)nu;
   switch (fam) {
-    case 0: k_row_consts<XT, 0><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
-    case 1: k_row_consts<XT, 1><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
-    case 2: k_row_consts<XT, 2><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
-    default: k_row_consts<XT, 3><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2); break;
+    case 0: k_row_consts<XT, 0><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2, v); break;
+    case 1: k_row_consts<XT, 1><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2, v); break;
+    case 2: k_row_consts<XT, 2><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2, v); break;
+    case 3: k_row_consts<XT, 3><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2, v); break;
+    default: k_row_consts<XT, 4><<<grid, 256, 0, s>>>(Xp, n, p, S, Yo, t, i2, v); break;
   }
   return (int)cudaGetLastError();
 }
 
 int row_consts(void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, const void *tb_ct,
-               double inv_s2, cudaStream_t s) {
+               double inv_s2, double nu, cudaStream_t s) {
   if (n <= 0) return 0;
-  if (x_dtype == 0) return launch_row_consts<double>((double *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
-  if (x_dtype == 1) return launch_row_consts<float>((float *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
-  return launch_row_consts<__nv_bfloat16>((__nv_bfloat16 *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, s);
+  if (x_dtype == 0)
+    return launch_row_consts<double>((double *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, nu, s);
+  if (x_dtype == 1)
+    return launch_row_consts<float>((float *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, nu, s);
+  return launch_row_consts<__nv_bfloat16>((__nv_bfloat16 *)Xp, n, p, S, Yo, fam, tb_ct, inv_s2, nu,
+                                          s);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -159,7 +164,8 @@ template <typename XT> __device__ __forceinline__ double packed_y(const XT *row,
 template <typename XT, int MAXQ>
 __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_t n, int p, int S,
                                                             int Yo, int fam, double s2,
-                                                            const double *theta, double *part) {
+                                                            double nu, const double *theta,
+                                                            double *part) {
   using AT = typename std::conditional<sizeof(XT) == 8, double, float>::type;
   extern __shared__ double sh[];
   double *ths = sh;                                   // [p]
@@ -210,10 +216,11 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_partials(const XT *Xp, int64_
         for (int c = 0; c < p; ++c) eta = fma((double)xs[tid * p + c], ths[c], eta);
         const double y = packed_y<XT>(Xp + k * S, Yo);
         switch (fam) {
-          case 0: row_value<0>(eta, y, s2, l, d1, d2); break;
-          case 1: row_value<1>(eta, y, s2, l, d1, d2); break;
-          case 2: row_value<2>(eta, y, s2, l, d1, d2); break;
-          default: row_value<3>(eta, y, s2, l, d1, d2); break;
+          case 0: row_value<0>(eta, y, s2, nu, l, d1, d2); break;
+          case 1: row_value<1>(eta, y, s2, nu, l, d1, d2); break;
+          case 2: row_value<2>(eta, y, s2, nu, l, d1, d2); break;
+          case 3: row_value<3>(eta, y, s2, nu, l, d1, d2); break;
+          default: row_value<4>(eta, y, s2, nu, l, d1, d2); break;
         }
       }
       d1s[tid] = d1;
@@ -275,25 +282,27 @@ __global__ void k_cv_reduce(const double *part, int nblk, int p, double *A, doub
 
 template <typename XT, int MAXQ>
 cudaError_t launch_cv_q(int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n, int p,
-                        int S, int Yo, int fam, double s2, const double *theta, double *part) {
+                        int S, int Yo, int fam, double s2, double nu, const double *theta,
+                        double *part) {
   cudaError_t e = cudaFuncSetAttribute(k_cv_partials<XT, MAXQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_cv_partials<XT, MAXQ><<<nblocks, kCvThreads, smem, s>>>(Xp, n, p, S, Yo, fam, s2, theta,
-                                                            part);
+  k_cv_partials<XT, MAXQ><<<nblocks, kCvThreads, smem, s>>>(Xp, n, p, S, Yo, fam, s2, nu,
+                                                            theta, part);
   return cudaGetLastError();
 }
 
 // Pair slots per thread: the smallest compiled count that covers p(p+1)/2 pairs.
 template <typename XT>
 cudaError_t launch_cv(int need, int nblocks, size_t smem, cudaStream_t s, const XT *Xp, int64_t n,
-                      int p, int S, int Yo, int fam, double s2, const double *theta, double *part) {
-  if (need <= 1) return launch_cv_q<XT, 1>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
-  if (need <= 2) return launch_cv_q<XT, 2>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
-  if (need <= 4) return launch_cv_q<XT, 4>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
-  if (need <= 8) return launch_cv_q<XT, 8>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
-  if (need <= 16) return launch_cv_q<XT, 16>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
-  return launch_cv_q<XT, 32>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, theta, part);
+                      int p, int S, int Yo, int fam, double s2, double nu, const double *theta,
+                      double *part) {
+  if (need <= 1) return launch_cv_q<XT, 1>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
+  if (need <= 2) return launch_cv_q<XT, 2>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
+  if (need <= 4) return launch_cv_q<XT, 4>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
+  if (need <= 8) return launch_cv_q<XT, 8>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
+  if (need <= 16) return launch_cv_q<XT, 16>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
+  return launch_cv_q<XT, 32>(nblocks, smem, s, Xp, n, p, S, Yo, fam, s2, nu, theta, part);
 }
 
 int cv_moments_blocks(int p) {
@@ -302,11 +311,12 @@ int cv_moments_blocks(int p) {
 }
 
 int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int fam, double sigma2,
-               const double *theta, double *partials, int nblocks, double *A, double *B,
+               double nu, const double *theta, double *partials, int nblocks, double *A, double *B,
                double *C, int mode, cudaStream_t s) {
   if (mode == 0 && x_dtype == 2 && p <= 128) {
     int used = 0;
-    const int e = cv_moments_mma(Xp, n, p, S, Yo, fam, sigma2, theta, partials, nblocks, &used, s);
+    const int e =
+        cv_moments_mma(Xp, n, p, S, Yo, fam, sigma2, nu, theta, partials, nblocks, &used, s);
     if (e != 0) return e;
     const int width = 1 + p + p * (p + 1) / 2;
     k_cv_reduce<<<(width + 7) / 8, 256, 0, s>>>(partials, used, p, A, B, C);
@@ -319,13 +329,13 @@ int cv_moments(const void *Xp, int x_dtype, int64_t n, int p, int S, int Yo, int
   cudaError_t e;
   if (x_dtype == 0)
     e = launch_cv<double>(need, nblocks, smem, s, (const double *)Xp, n, p, S, Yo, fam, sigma2,
-                          theta, partials);
+                          nu, theta, partials);
   else if (x_dtype == 1)
-    e = launch_cv<float>(need, nblocks, smem, s, (const float *)Xp, n, p, S, Yo, fam, sigma2,
+    e = launch_cv<float>(need, nblocks, smem, s, (const float *)Xp, n, p, S, Yo, fam, sigma2, nu,
                          theta, partials);
   else
     e = launch_cv<__nv_bfloat16>(need, nblocks, smem, s, (const __nv_bfloat16 *)Xp, n, p, S, Yo,
-                                 fam, sigma2, theta, partials);
+                                 fam, sigma2, nu, theta, partials);
   if (e != cudaSuccess) return (int)e;
   const int width = 1 + p + p * (p + 1) / 2;
   k_cv_reduce<<<(width + 7) / 8, 256, 0, s>>>(partials, nblocks, p, A, B, C);
@@ -375,13 +385,25 @@ __global__ void k_newton_step(int p, const double *theta, const double *B, const
   __shared__ int flag;
   double *g = M + p * p;
   const int tid = threadIdx.x;
-  for (int e = tid; e < p * p; e += blockDim.x) {
-    const int i = e / p, k = e % p;
-    M[e] = -C[e] + (i == k ? 1.0 / var[i] : 0.0);
-  }
   for (int c = tid; c < p; c += blockDim.x) g[c] = B[c] - (theta[c] - mu[c]) / var[c];
-  __syncthreads();
-  const bool ok = chol_block(M, p, &flag);
+  // M = -C + diag(1/var) + lam I. A log-density that is not concave (Student-t far from the mode)
+  // can leave M indefinite; lam = 1e-8 max|diag| (times 10 per retry) then keeps the step an
+  // ascent direction (Levenberg's damping). Uniform across the block: every thread sees the same
+  // factorisation outcome.
+  double scale = 0.0;
+  for (int i = 0; i < p; ++i) scale = fmax(scale, fabs(-C[i * p + i] + 1.0 / var[i]));
+  if (!(scale > 0.0)) scale = 1e-300;
+  double lam = 0.0;
+  bool ok = false;
+  for (int tries = 0; tries < 40 && !ok; ++tries) {
+    for (int e = tid; e < p * p; e += blockDim.x) {
+      const int i = e / p, k = e % p;
+      M[e] = -C[e] + (i == k ? 1.0 / var[i] + lam : 0.0);
+    }
+    __syncthreads();
+    ok = chol_block(M, p, &flag);
+    lam = lam == 0.0 ? 1e-8 * scale : 10.0 * lam;
+  }
   if (!ok) {
     if (tid == 0) *info = 1;
     return;

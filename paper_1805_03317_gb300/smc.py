@@ -56,6 +56,7 @@ class Context:
 # ------------------------------------------------------------------------------------------------
 def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_var, *, N: int,
              m: int, G: int, L: int, seed: int, ess_frac: float = 0.5, noise_sigma: float = 1.0,
+             dof: float = 5.0,
              theta_bar=None, search_k: int = 16, search_rounds: int = 10, eps0: float = 0.0,
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
              cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
@@ -71,7 +72,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
     pm = np.ascontiguousarray(prior_mean, dtype=np.float64)
     pv = np.ascontiguousarray(prior_var, dtype=np.float64)
     prob = SmcProblem(FAMILY[family], n, p, X.data_ptr(), DTYPE[x_dtype], X.stride(0),
-                      y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma))
+                      y.data_ptr(), _dp(pm), _dp(pv), float(noise_sigma), float(dof))
     cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
                     search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
                     int(cv_order), int(cv_centre), 1 if full_data else 0,
@@ -394,7 +395,8 @@ def smc_batch_init(problems, stream=None) -> Batch:
         pm = np.ascontiguousarray(d["prior_mean"], dtype=np.float64)
         pv = np.ascontiguousarray(d["prior_var"], dtype=np.float64)
         probs[q] = SmcProblem(FAMILY[d["family"]], n, p, X.data_ptr(), DTYPE["bf16"], X.stride(0),
-                              y.data_ptr(), _dp(pm), _dp(pv), float(d.get("noise_sigma", 1.0)))
+                              y.data_ptr(), _dp(pm), _dp(pv), float(d.get("noise_sigma", 1.0)),
+                              float(d.get("dof", 5.0)))
         cfgs[q] = SmcConfig(d["N"], d["m"], d["G"], d["L"], float(d.get("ess_frac", 0.5)),
                             int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
                             d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 2, 0,

@@ -50,6 +50,7 @@ class Workload:
     seed: int
     sigma: float = 1.0
     theta_true: np.ndarray | None = None
+    dof: float = 5.0       # Student-t degrees of freedom (sigma is then the error scale)
 
     @property
     def n(self) -> int:
@@ -75,7 +76,7 @@ def _store(X: np.ndarray, y: np.ndarray, x_dtype: str, upcast: bool = True):
     raise ValueError(x_dtype)
 
 
-def _respond(rng, family: str, eta: np.ndarray, sigma: float = 1.0) -> np.ndarray:
+def _respond(rng, family: str, eta: np.ndarray, sigma: float = 1.0, dof: float = 5.0) -> np.ndarray:
     if family == "logistic":
         return (rng.random(eta.shape[0]) < 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
     if family == "probit":
@@ -85,13 +86,15 @@ def _respond(rng, family: str, eta: np.ndarray, sigma: float = 1.0) -> np.ndarra
         return rng.poisson(np.exp(eta)).astype(np.float64)
     if family == "gaussian":
         return eta + sigma * rng.standard_normal(eta.shape[0])
+    if family == "student_t":
+        return eta + sigma * rng.standard_t(dof, size=eta.shape[0])
     raise ValueError(family)
 
 
 def small_glm(family: str = "logistic", n: int = 2000, p: int = 5, N: int = 64, m: int = 50,
               G: int = 5, L: int = 5, R: int = 2, x_dtype: str = "f64", seed: int = 1,
               sigma: float = 0.5, theta_scale: float = 0.5, prior_var: float = 10.0,
-              x_scale: float = 1.0) -> Workload:
+              x_scale: float = 1.0, dof: float = 5.0) -> Workload:
     """Small seeded GLM (intercept + iid N(0, x_scale^2) covariates) for parity and pin tests."""
     rng = np.random.Generator(np.random.PCG64(seed))
     X = np.empty((n, p))
@@ -99,10 +102,10 @@ def small_glm(family: str = "logistic", n: int = 2000, p: int = 5, N: int = 64, 
     X[:, 1:] = x_scale * rng.standard_normal((n, p - 1))
     theta = theta_scale * rng.standard_normal(p)
     Xs64, Xs, _, _ = _store(X, np.zeros(n), x_dtype)
-    y = _respond(rng, family, Xs64 @ theta, sigma)
+    y = _respond(rng, family, Xs64 @ theta, sigma, dof)
     Xd, Xs, yd, ys = _store(X, y, x_dtype)
     return Workload(f"small-{family}", family, x_dtype, Xd, Xs, yd, ys, np.zeros(p),
-                    np.full(p, prior_var), N, m, G, L, R, seed, sigma, theta)
+                    np.full(p, prior_var), N, m, G, L, R, seed, sigma, theta, dof)
 
 
 def logistic_1e4(seed_offset: int = 0) -> Workload:
@@ -142,6 +145,25 @@ def logistic_1e6(x_dtype: str = "bf16", n: int = 1_000_000) -> Workload:
     Xd, Xs, yd, ys = _store(X, y, x_dtype)
     return Workload(f"logistic-n1e6-p20-{x_dtype}", "logistic", x_dtype, Xd, Xs, yd, ys,
                     np.zeros(p), np.full(p, 10.0), 4096, 1000, 10, 20, 5, seed, 1.0, theta)
+
+
+def student_t_5e5(x_dtype: str = "bf16", n: int = 500_000, N: int = 4096, L: int = 20) -> Workload:
+    """Student-t regression of the paper's Experiment 2 (Sec. 4.3) in shape: n=500,000, p=50
+    covariates with unit variances and pairwise correlation 0.9 (x = sqrt(0.9) z0 + sqrt(0.1) z_j),
+    theta_true ~ U(-5, 5), errors t_5 with unit scale, prior N(0, 10 I); m = 1250 (sample
+    fraction 0.0025), G = 100, R = 5. X stored as BF16 (or FP32)."""
+    seed = BASE_SEED + 5
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = 50
+    z0 = rng.standard_normal(n)
+    X = (math.sqrt(0.9) * z0[:, None] + math.sqrt(0.1) * rng.standard_normal((n, p))).astype(
+        np.float32)
+    theta = rng.uniform(-5.0, 5.0, p)
+    Xs64, _, _, _ = _store(X, np.zeros(n), x_dtype)
+    y = _respond(rng, "student_t", Xs64 @ theta, 1.0, 5.0)
+    Xd, Xs, yd, ys = _store(X, y, x_dtype)
+    return Workload(f"student-t-n5e5-p50-{x_dtype}", "student_t", x_dtype, Xd, Xs, yd, ys,
+                    np.zeros(p), np.full(p, 10.0), N, 1250, 100, L, 5, seed, 1.0, theta, 5.0)
 
 
 def poisson_5e6(x_dtype: str = "bf16", n: int = 5_000_000, upcast: bool = True) -> Workload:

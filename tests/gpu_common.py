@@ -22,7 +22,8 @@ def state_round(v, x_dtype):
 
 
 def oracle_problem(wl, theta_bar=None):
-    prob = O.Problem(wl.family, wl.X, wl.y, wl.prior_mean, wl.prior_var, sigma=wl.sigma)
+    prob = O.Problem(wl.family, wl.X, wl.y, wl.prior_mean, wl.prior_var, sigma=wl.sigma,
+                     dof=wl.dof)
     tb = O.newton_map(prob) if theta_bar is None else np.asarray(theta_bar, np.float64)
     prob.set_centre(state_round(tb, wl.x_dtype))
     return prob
@@ -32,7 +33,7 @@ def make_pair(wl, theta_bar=None, tile_hint=0, **kw):
     import paper_1805_03317_gb300 as S
     prob = oracle_problem(wl, theta_bar)
     X, y = device_arrays(wl)
-    args = dict(N=wl.N, m=wl.m, G=wl.G, L=wl.L, seed=wl.seed, noise_sigma=wl.sigma,
+    args = dict(N=wl.N, m=wl.m, G=wl.G, L=wl.L, seed=wl.seed, noise_sigma=wl.sigma, dof=wl.dof,
                 theta_bar=prob.theta_bar, tile_hint=tile_hint)
     args.update(kw)
     ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, **args)

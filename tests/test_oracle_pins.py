@@ -29,6 +29,8 @@ def scipy_loglik_rows(fam, eta, y, sigma=1.0):
         return stats.norm.logpdf(y, loc=eta, scale=sigma)
     if fam == "probit":
         return special.log_ndtr((2 * y - 1) * eta)
+    if fam == "student_t":
+        return stats.t.logpdf(y, df=5.0, loc=eta, scale=sigma)
     raise ValueError(fam)
 
 
@@ -51,6 +53,8 @@ def tiny_problem(fam, n=7, p=3, seed=3, sigma=0.7):
         y = (rng.random(n) < special.ndtr(eta)).astype(float)
     elif fam == "poisson":
         y = rng.poisson(np.exp(eta)).astype(float)
+    elif fam == "student_t":
+        y = eta + sigma * rng.standard_t(5.0, size=n)
     else:
         y = eta + sigma * rng.standard_normal(n)
     prob = O.Problem(fam, X, y, np.zeros(p), np.full(p, 3.0), sigma=sigma)
@@ -106,11 +110,11 @@ def test_box_muller_normals_moments():
 # ----------------------------------------------------------------------------------------------
 # Families (Sec. 3.1) against scipy, derivatives against finite differences
 # ----------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("fam", ["logistic", "poisson", "gaussian", "probit"])
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "gaussian", "probit", "student_t"])
 def test_family_logdensity_and_derivatives(fam):
     sigma = 0.7
     ys = {"logistic": [0.0, 1.0], "probit": [0.0, 1.0], "poisson": [0.0, 1.0, 4.0, 17.0],
-          "gaussian": [-1.3, 0.0, 2.5]}[fam]
+          "gaussian": [-1.3, 0.0, 2.5], "student_t": [-1.3, 0.0, 2.5, 40.0]}[fam]
     etas = np.linspace(-6, 6, 25)
     if fam == "probit":
         etas = np.concatenate([etas, [-40.0, -12.0, -5.5, 8.0, 30.0]])
@@ -134,7 +138,7 @@ def test_erfcx_continued_fraction():
 # ----------------------------------------------------------------------------------------------
 # Control-variate moments (Sec. 3.2)
 # ----------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("fam", ["logistic", "poisson", "gaussian", "probit"])
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "gaussian", "probit", "student_t"])
 def test_cv_moments_against_full_likelihood(fam):
     prob = tiny_problem(fam)
     tb = prob.theta_bar
@@ -152,7 +156,7 @@ def test_cv_moments_against_full_likelihood(fam):
     np.testing.assert_allclose(prob.C, prob.C.T, rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit"])
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit", "student_t"])
 def test_moment_identity_sum_of_row_control_variates(fam):
     """sum_k q_k(theta) built row by row equals A + B'delta + delta'C delta/2 (Sec. 3.2)."""
     prob = tiny_problem(fam, n=9)
@@ -170,7 +174,7 @@ def test_moment_identity_sum_of_row_control_variates(fam):
 # ----------------------------------------------------------------------------------------------
 # Difference estimator (Eq. difference_estimator_logl) and variance estimate
 # ----------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit"])
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit", "student_t"])
 def test_estimator_unbiased_by_enumeration(fam):
     """Averaging l_hat over all n^m equally likely index tuples gives l(theta) exactly; and the
     printed sigma2_hat has expectation (m-1)/m * Var(l_hat) (sampling with replacement)."""
@@ -188,7 +192,7 @@ def test_estimator_unbiased_by_enumeration(fam):
     assert var > 1e-6  # the check above is not vacuous
 
 
-@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit"])
+@pytest.mark.parametrize("fam", ["logistic", "poisson", "probit", "student_t"])
 def test_target_gradient_finite_difference(fam):
     """The HMC force is the gradient of a*l_hat - a^2/2*sigma2_hat + log p(theta) for fixed u."""
     prob = tiny_problem(fam, n=40, p=3, seed=4)
@@ -644,4 +648,35 @@ def test_paper_settings_recover_conjugate_posterior_and_log_marginal():
     sd = np.sqrt(np.diag(S))
     assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
     assert abs(np.mean(errs)) < 0.15
+
+
+def test_student_t_newton_reaches_the_mode_from_a_non_concave_start():
+    """Student-t regression (Sec. 4.3) far from the mode has an indefinite Hessian; the damped
+    Newton steps still end at a stationary point of the log posterior that is a maximum (the
+    gradient rebuilt from scipy's log-density by finite differences, the Hessian negative
+    definite), and the plain posterior mode found by scipy's optimiser agrees."""
+    from scipy import optimize
+    rng = np.random.default_rng(21)
+    n, p = 400, 3
+    X = np.column_stack([np.ones(n), rng.standard_normal((n, p - 1))])
+    theta = np.array([6.0, -4.0, 5.0])  # residuals of ~8 at the prior mean: l'' > 0 there
+    y = X @ theta + 0.8 * rng.standard_t(5.0, size=n)
+    prob = O.Problem("student_t", X, y, np.zeros(p), np.full(p, 10.0), sigma=0.8, dof=5.0)
+    _, _, C0 = O.cv_moments("student_t", X, y, np.zeros(p), 0.8, 5.0)
+    assert np.max(np.linalg.eigvalsh(-C0 + np.eye(p) / 10.0)) > 0  # some curvature is wrong-signed
+    assert np.min(np.linalg.eigvalsh(-C0 + np.eye(p) / 10.0)) < 0
+    mode = O.newton_map(prob)
+
+    def neg_logpost(t):
+        return -(scipy_loglik("student_t", X, y, t, 0.8)
+                 + scipy_log_prior(t, prob.prior_mean, prob.prior_var))
+
+    h = 1e-6
+    g = np.array([(neg_logpost(mode + h * e) - neg_logpost(mode - h * e)) / (2 * h)
+                  for e in np.eye(p)])
+    assert np.max(np.abs(g)) < 1e-4
+    _, _, C = O.cv_moments("student_t", X, y, mode, 0.8, 5.0)
+    assert np.max(np.linalg.eigvalsh(C - np.eye(p) / 10.0)) < 0
+    ref = optimize.minimize(neg_logpost, mode + 0.3, method="BFGS", options={"gtol": 1e-9})
+    np.testing.assert_allclose(mode, ref.x, atol=1e-5)
 
