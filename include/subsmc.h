@@ -148,11 +148,12 @@ const char *smc_last_error(const smc_ctx *ctx);
  * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS. */
 int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
 
-/* Step (e): systematic resampling with the current weights, carrying theta, u and the cached
- * estimates; then W = 1/N. Weights are quantised to w_i = floor(W_i 2^40); with T = sum w_i and one
- * uniform U per stage, position i = floor((i T + floor(U T)) / N) selects the first particle whose
- * cumulative integer weight exceeds it, so the ancestors are exact and independent of summation order.
- * ancestors: device [N] int32 or NULL. */
+/* Step (e): resampling with the current weights, carrying theta, u and the cached estimates; then
+ * W = 1/N. Weights are quantised to w_i = floor(W_i 2^40), T = sum w_i. Systematic (default): one
+ * uniform U per stage, position i = floor((i T + floor(U T)) / N). Multinomial (smc_config.resampling
+ * = 1, Sec. 2.2): offspring i's own uniform U_i, position min(floor(U_i T), T - 1). The ancestor is
+ * the first particle whose cumulative integer weight exceeds the position, so the ancestors are
+ * exact and independent of summation order. ancestors: device [N] int32 or NULL. */
 int smc_resample(smc_ctx *ctx, int32_t *ancestors);
 
 /* Step (f): R Markov moves of Algorithm 1 at the current temperature, each a block pseudo-marginal
@@ -160,6 +161,18 @@ int smc_resample(smc_ctx *ctx, int32_t *ancestors);
  * step adapts: eps *= clip(exp(theta_acceptance - 0.65), 0.5, 2).
  * Host outputs (may be NULL): acceptance rates of the u and theta updates over these R moves. */
 int smc_move(smc_ctx *ctx, int32_t R, double *acc_u, double *acc_theta);
+
+/* Step (f) with the number of moves tuned as the paper does (Sec. 3.4, after Buchholz et al.): moves
+ * of Algorithm 1 one at a time until the particles have decorrelated from the cloud they started
+ * from. After each move rho_c = the correlation across particles of component c between the
+ * starting and the current cloud; the moves stop once the ceil(quantile * p)-th smallest rho_c is
+ * <= rho_max (the paper: 90% of the components below a threshold), or after R_max moves. The step
+ * size then adapts as in smc_move over the moves made. Synchronises with the host after every move
+ * (not usable inside smc_stage's graphs).
+ * R_max: 1 .. 256 minus the moves already made this stage; rho_max in [-1, 1]; quantile in (0, 1].
+ * Host outputs (may be NULL): the number of moves made and the acceptance rates over them. */
+int smc_move_adaptive(smc_ctx *ctx, int32_t R_max, double rho_max, double quantile,
+                      int32_t *R_used, double *acc_u, double *acc_theta);
 
 /* One whole stage (Algorithm 2 (a)-(f)): smc_reweight, smc_resample and smc_move(R) with no host
  * outputs and no host synchronisation. use_graph = 0 issues the launches one by one. use_graph = 1

@@ -400,6 +400,7 @@ class SMCConfig:
     resampling: str = "systematic"  # or "multinomial" (the paper's scheme)
     grid_points: int = 0           # > 0: the paper's grid rule for the temperature (Sec. 2.3)
     grid_decades: float = 16.0
+    adaptive: tuple | None = None  # (R_max, rho_max, quantile): moves until decorrelated
 
 
 @dataclass
@@ -417,6 +418,25 @@ class SMCState:
     Sigma: np.ndarray | None = None   # mass-matrix inverse of the last stage (prior covariance at first)
     Lc: np.ndarray | None = None
     history: list = field(default_factory=list)
+
+
+def componentwise_correlation(th0, th):
+    """Correlation across particles of each component between two clouds (a component with no
+    spread in either cloud counts as 1)."""
+    d0 = th0 - th0.mean(axis=0)
+    d1 = th - th.mean(axis=0)
+    xx, yy, xy = (d0 * d0).sum(axis=0), (d1 * d1).sum(axis=0), (d0 * d1).sum(axis=0)
+    ok = (xx > 0) & (yy > 0)
+    return np.where(ok, xy / np.sqrt(np.where(ok, xx * yy, 1.0)), 1.0)
+
+
+def decorrelated(th0, th, rho_max, quantile):
+    """The adaptive-R rule (Sec. 3.4, after Buchholz et al.): the ceil(quantile p)-th smallest
+    componentwise correlation between the starting and the current cloud is at most rho_max."""
+    rho = np.sort(componentwise_correlation(th0, th))
+    p = rho.shape[0]
+    k = min(max(math.ceil(quantile * p) - 1, 0), p - 1)
+    return bool(rho[k] <= rho_max)
 
 
 def smc_init(prob: Problem, cfg: SMCConfig) -> SMCState:
@@ -463,15 +483,23 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     st.logW = np.full(cfg.N, -math.log(cfg.N))
     st.W = np.exp(st.logW)
     acc_u = acc_t = 0
-    for r in range(cfg.R):
-        acc_u += int(upm_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.thetas, st.us).sum())
-        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, r, st.a, st.eps, cfg.L, st.Sigma,
+    R_max = cfg.R if cfg.adaptive is None else int(cfg.adaptive[0])
+    th0 = st.thetas.copy()
+    R = 0
+    while R < R_max:
+        acc_u += int(upm_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.thetas, st.us).sum())
+        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.eps, cfg.L, st.Sigma,
                               st.Lc, st.thetas, st.us).sum())
+        R += 1
+        if cfg.adaptive is not None:
+            _, rho_max, q = cfg.adaptive
+            if decorrelated(th0, st.thetas, rho_max, q):
+                break
     out = loglik_batch(prob, cfg.m, cfg.G, st.thetas, st.us, a=st.a, grad=False)
     st.ell, st.sig2 = out["ell"], out["sigma2"]
-    rate = acc_t / float(cfg.N * cfg.R)
+    rate = acc_t / float(cfg.N * R)
     st.history.append(dict(stage=s, a=st.a, ess=ess, log_z_inc=lz, eps=st.eps,
-                           acc_u=acc_u / float(cfg.N * cfg.R), acc_theta=rate))
+                           acc_u=acc_u / float(cfg.N * R), acc_theta=rate, R=R))
     st.eps = st.eps * min(2.0, max(0.5, math.exp(rate - 0.65)))
     return st
 

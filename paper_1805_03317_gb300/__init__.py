@@ -6,7 +6,8 @@ this package is its Python binding (``smc``) and build script (``build``).
 from .smc import (Batch, Context, SubsampledLoglik, SubsampledSMC, loglik_bwd, loglik_est, loglik_fwd,
                   loglik_full, loglik_grad, smc_autotune, smc_cv_moments,
                   smc_free, smc_get_cache, smc_get_centre, smc_get_mass, smc_get_particles,
-                  smc_get_status, smc_init, smc_launch_count, smc_move, smc_profile_enable,
+                  smc_get_status, smc_init, smc_launch_count, smc_move, smc_move_adaptive,
+                  smc_profile_enable,
                   smc_profile_read, smc_resample, smc_resample_noalloc,
                   smc_reweight, smc_set_particles, smc_set_scalars, smc_stage, smc_batch_init,
                   smc_batch_free, smc_batch_stage, smc_batch_autotune, smc_batch_tile,
@@ -18,5 +19,6 @@ __all__ = ["Batch", "smc_batch_init", "smc_batch_free", "smc_batch_stage", "smc_
            "loglik_full", "loglik_grad", "smc_autotune",
            "smc_cv_moments", "smc_free", "smc_get_cache", "smc_get_centre", "smc_get_mass",
            "smc_get_particles", "smc_get_status", "smc_init", "smc_launch_count", "smc_move",
+           "smc_move_adaptive",
            "smc_profile_enable", "smc_profile_read", "smc_resample_noalloc",
            "smc_resample", "smc_reweight", "smc_set_particles", "smc_set_scalars", "smc_stage"]

@@ -42,6 +42,7 @@ SIGNATURES = {
     "smc_reweight": (ctypes.c_int, [c_vp, c_dp, c_dp, c_dp]),
     "smc_resample": (ctypes.c_int, [c_vp, c_vp]),
     "smc_move": (ctypes.c_int, [c_vp, c_i32, c_dp, c_dp]),
+    "smc_move_adaptive": (ctypes.c_int, [c_vp, c_i32, c_d, c_d, c_ip, c_dp, c_dp]),
     "smc_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
     "smc_batch_init": (ctypes.c_int, [ctypes.POINTER(c_vp), c_i32, ctypes.POINTER(SmcProblem),
                                       ctypes.POINTER(SmcConfig), c_vp]),

@@ -43,6 +43,8 @@ struct smc_ctx {
   void *tb_ct = nullptr, *B_ct = nullptr, *C_ct = nullptr;
   double A_h = 0.0;
   void *theta = nullptr, *theta_alt = nullptr, *grad_scratch = nullptr;
+  void *theta0 = nullptr;    // adaptive moves: the cloud at the start of the stage's moves
+  double *rho_d = nullptr;   // adaptive moves: componentwise correlations [p]
   int32_t *u = nullptr, *u_alt = nullptr, *unew = nullptr, *anc = nullptr;
   int maxblk = 1;
   double *logW = nullptr, *W = nullptr;
@@ -851,6 +853,72 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     return check_err_bits(c, h);
   }
   return SMC_OK;
+}
+
+// Moves until the particles have decorrelated from the cloud they started the stage's moves from
+// (the number of moves R tuned as in Buchholz et al., cited in Sec. 3.4): after each move the
+// componentwise correlations rho_c between the starting and the current cloud are formed, and the
+// moves stop once the quantile-q order statistic of rho_1..rho_p (the ceil(q p)-th smallest) is at
+// most rho_max, or after R_max moves. The step-size rule then sees the acceptance over the moves
+// made. Reads the correlations on the host after every move.
+int smc_move_adaptive(smc_ctx *c, int32_t R_max, double rho_max, double quantile,
+                      int32_t *R_used, double *acc_u, double *acc_theta) {
+  if (!c) return SMC_ERR_ARG;
+  if (R_max < 1 || c->moves_in_stage + R_max > 256)
+    return fail(c, SMC_ERR_ARG, "R_max must be >= 1, at most 256 moves per stage");
+  if (!(rho_max >= -1.0 && rho_max <= 1.0) || !(quantile > 0.0 && quantile <= 1.0))
+    return fail(c, SMC_ERR_ARG, "rho_max must be in [-1, 1] and quantile in (0, 1]");
+  if (c->capturing) return fail(c, SMC_ERR_ARG, "adaptive moves cannot be graph-captured");
+  const int N = c->N, p = c->p;
+  const size_t tbytes = (size_t)N * p * (c->is_f64 ? sizeof(double) : sizeof(float));
+  if (!c->theta0) {
+    ALLOC(c, c->theta0, tbytes);
+    ALLOC(c, c->rho_d, sizeof(double) * p);
+  }
+  CUDA_OK(c, cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(c->theta0, c->theta, tbytes, cudaMemcpyDeviceToDevice, c->stream));
+  int kq = (int)ceil(quantile * p) - 1;
+  kq = kq < 0 ? 0 : (kq >= p ? p - 1 : kq);
+  std::vector<double> rho(p);
+  int R = 0;
+  while (R < R_max) {
+    if (c->full_data) {
+      int r = full_moves(c, 1);
+      if (r) return r;
+    } else {
+      EstArgs a = base_args(c);
+      a.B = N;
+      a.theta = c->theta;
+      a.theta_out = c->theta;
+      a.u = c->u;
+      a.u_mut = c->u;
+      a.ell = c->ell;
+      a.sig2 = c->sig2;
+      a.blk = c->blk;
+      a.blk_prop = c->blk_prop;
+      a.move = c->moves_in_stage;
+      a.stage_dev = c->stage_dev;
+      LAUNCH(c, est_launch(c, 1, a), 0);
+      LAUNCH(c, hmc_launch(c, a), 0);
+    }
+    c->moves_in_stage += 1;
+    R += 1;
+    LAUNCH(c, autocorr(c->is_f64, N, p, c->theta0, c->theta, c->rho_d, c->stream), 1);
+    CUDA_OK(c, cudaMemcpyAsync(rho.data(), c->rho_d, sizeof(double) * p, cudaMemcpyDeviceToHost,
+                               c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    std::vector<double> sorted(rho);
+    std::sort(sorted.begin(), sorted.end());
+    if (sorted[kq] <= rho_max) break;
+  }
+  LAUNCH(c, eps_update(N, R, c->st, c->stream), 1);
+  if (R_used) *R_used = R;
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  if (acc_u) *acc_u = (double)h.acc_u / ((double)N * R);
+  if (acc_theta) *acc_theta = (double)h.acc_theta / ((double)N * R);
+  return check_err_bits(c, h);
 }
 
 // The host-side effects of one stage, mirrored on a graph replay: stage counters, the resampling

@@ -161,6 +161,8 @@ int stage_set(DevState *st, int stage, cudaStream_t s);
 int stage_advance(DevState *st, cudaStream_t s);
 int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_t s);
 int eps_update(int N, int R, DevState *st, cudaStream_t s);
+// rho[c] = correlation across the N particles of component c of clouds a and b (state type).
+int autocorr(int is_f64, int N, int p, const void *a, const void *b, double *rho, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);
 int round_to_state_type(int is_f64, int count, double *v, cudaStream_t s);
 

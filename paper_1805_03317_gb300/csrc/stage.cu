@@ -1106,6 +1106,53 @@ int eps_update(int N, int R, DevState *st, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+// Componentwise correlation across particles between two clouds (the stage's starting cloud and
+// the current one), for the adaptive number of moves: one block per component, FP64, two passes
+// (means, then centred sums), fixed reduction order. A component with no spread in either cloud
+// gets correlation 1.
+constexpr int kAcThreads = 256;
+__device__ __forceinline__ double block_sum_fixed(double v, double *sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kAcThreads / 32; ++w) t += sh[w];
+  return t;
+}
+template <typename CT>
+__global__ void __launch_bounds__(kAcThreads)
+    k_autocorr(int N, int p, const CT *a, const CT *b, double *rho) {
+  __shared__ double sh[kAcThreads / 32];
+  const int c = blockIdx.x;
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < N; i += kAcThreads) {
+    sa += (double)a[(int64_t)i * p + c];
+    sb += (double)b[(int64_t)i * p + c];
+  }
+  const double ma = block_sum_fixed(sa, sh) / N;
+  const double mb = block_sum_fixed(sb, sh) / N;
+  double xx = 0.0, yy = 0.0, xy = 0.0;
+  for (int i = threadIdx.x; i < N; i += kAcThreads) {
+    const double dx = (double)a[(int64_t)i * p + c] - ma, dy = (double)b[(int64_t)i * p + c] - mb;
+    xx = fma(dx, dx, xx);
+    yy = fma(dy, dy, yy);
+    xy = fma(dx, dy, xy);
+  }
+  xx = block_sum_fixed(xx, sh);
+  yy = block_sum_fixed(yy, sh);
+  xy = block_sum_fixed(xy, sh);
+  if (threadIdx.x == 0) rho[c] = (xx > 0.0 && yy > 0.0) ? xy / sqrt(xx * yy) : 1.0;
+}
+int autocorr(int is_f64, int N, int p, const void *a, const void *b, double *rho, cudaStream_t s) {
+  if (is_f64)
+    k_autocorr<double><<<p, kAcThreads, 0, s>>>(N, p, (const double *)a, (const double *)b, rho);
+  else
+    k_autocorr<float><<<p, kAcThreads, 0, s>>>(N, p, (const float *)a, (const float *)b, rho);
+  return (int)cudaGetLastError();
+}
+
 template <typename CT> __global__ void k_convert(int count, const double *src, CT *dst) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
     dst[i] = (CT)src[i];

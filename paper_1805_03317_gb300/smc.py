@@ -115,6 +115,16 @@ def smc_move(ctx: Context, R: int):
     return au.value, at.value
 
 
+def smc_move_adaptive(ctx: Context, R_max: int, rho_max: float = 0.1, quantile: float = 0.9):
+    """Moves until the quantile of the componentwise start-to-current correlations is at most
+    rho_max (or R_max moves); returns (moves made, u acceptance, theta acceptance)."""
+    r, au, at = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    check(_abi.load().smc_move_adaptive(ctx.handle, int(R_max), float(rho_max), float(quantile),
+                                        ctypes.byref(r), ctypes.byref(au), ctypes.byref(at)),
+          "smc_move_adaptive", ctx.handle)
+    return r.value, au.value, at.value
+
+
 def smc_stage(ctx: Context, R: int, use_graph: bool = True):
     """One stage (reweight, resample, R moves) without host synchronisation; with use_graph the
     stage is replayed as one CUDA graph after its first capture."""
@@ -318,17 +328,22 @@ class SubsampledSMC:
         self.ctx = smc_init(X, y, family, prior_mean, prior_var, **kw)
         self.history = []
 
-    def stage(self, R: int) -> dict:
+    def stage(self, R: int, adaptive=None) -> dict:
+        """One stage with R moves, or with adaptive = (R_max, rho_max, quantile) the adaptive
+        number of moves (smc_move_adaptive)."""
         a, lz, ess = smc_reweight(self.ctx)
         smc_resample(self.ctx)
-        au, at = smc_move(self.ctx, R)
-        rec = {"a": a, "log_z_inc": lz, "ess": ess, "acc_u": au, "acc_theta": at}
+        if adaptive is None:
+            au, at = smc_move(self.ctx, R)
+        else:
+            R, au, at = smc_move_adaptive(self.ctx, *adaptive)
+        rec = {"a": a, "log_z_inc": lz, "ess": ess, "acc_u": au, "acc_theta": at, "R": R}
         self.history.append(rec)
         return rec
 
-    def run(self, R: int, max_stages: int = 1000) -> dict:
+    def run(self, R: int, max_stages: int = 1000, adaptive=None) -> dict:
         while smc_get_status(self.ctx)["a"] < 1.0 and len(self.history) < max_stages:
-            self.stage(R)
+            self.stage(R, adaptive)
         return smc_get_status(self.ctx)
 
     def particles(self):

@@ -324,3 +324,43 @@ def test_bad_stage_settings_are_rejected():
             make_pair(wl, **kw)
     with pytest.raises(KeyError):
         make_pair(wl, resampling="stratified")
+
+
+# ------------------------------------------------------------------------------------------------
+# Adaptive number of moves (Sec. 3.4, after Buchholz et al.)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("hmc_kernel", [0, 1])
+@pytest.mark.parametrize("rho_max", [0.3, 0.05])
+def test_adaptive_moves_run_matches_oracle_fp64(rho_max, hmc_kernel):
+    """A whole FP64 run with the adaptive number of moves: the same move count at every stage as
+    the oracle, indices bit-exact, temperatures and log Z."""
+    wl = small_glm("logistic", n=4000, p=4, N=128, m=50, G=5, L=6, R=1, x_dtype="f64", seed=29)
+    prob, ctx = make_pair(wl, hmc_kernel=hmc_kernel)
+    ad = (30, rho_max, 0.9)
+    cfg = O.SMCConfig(N=wl.N, m=wl.m, G=wl.G, L=wl.L, R=1, seed=wl.seed, tau=0.5, adaptive=ad)
+    st_o = O.smc_run(prob, cfg)
+    runner = S().SubsampledSMC.__new__(S().SubsampledSMC)
+    runner.ctx, runner.history = ctx, []
+    st = runner.run(1, adaptive=ad)
+    assert [h["R"] for h in runner.history] == [h["R"] for h in st_o.history]
+    assert max(h["R"] for h in runner.history) > 1
+    np.testing.assert_allclose([h["a"] for h in runner.history], [h["a"] for h in st_o.history],
+                               rtol=1e-9)
+    assert st["log_z"] == pytest.approx(st_o.log_z, abs=1e-7)
+    th, u, _ = S().smc_get_particles(ctx)
+    np.testing.assert_array_equal(u.cpu().numpy(), st_o.us)
+    np.testing.assert_allclose(th.cpu().numpy(), st_o.thetas, rtol=1e-7, atol=1e-9)
+    S().smc_free(ctx)
+
+
+def test_adaptive_moves_full_data_and_bad_arguments():
+    wl = small_glm("logistic", n=3000, p=5, N=256, m=20, G=2, L=6, x_dtype="bf16", seed=3)
+    _, ctx = make_pair(wl, full_data=True)
+    S().smc_reweight(ctx)
+    S().smc_resample(ctx)
+    R, au, at = S().smc_move_adaptive(ctx, 12, 0.2, 0.9)
+    assert 1 <= R <= 12 and au == 0.0 and 0.0 < at <= 1.0
+    for bad in ((0, 0.1, 0.9), (300, 0.1, 0.9), (5, 1.5, 0.9), (5, 0.1, 0.0)):
+        with pytest.raises(S()._abi.SmcError):
+            S().smc_move_adaptive(ctx, *bad)
+    S().smc_free(ctx)

@@ -680,3 +680,43 @@ def test_student_t_newton_reaches_the_mode_from_a_non_concave_start():
     ref = optimize.minimize(neg_logpost, mode + 0.3, method="BFGS", options={"gtol": 1e-9})
     np.testing.assert_allclose(mode, ref.x, atol=1e-5)
 
+
+
+def test_componentwise_correlation_and_the_adaptive_rule():
+    """The adaptive number of moves (Sec. 3.4): correlations against numpy's corrcoef, and the
+    rule reads the ceil(q p)-th smallest of them."""
+    rng = np.random.default_rng(30)
+    th0 = rng.standard_normal((500, 6))
+    th = 0.3 * th0 + rng.standard_normal((500, 6)) * np.linspace(0.1, 3.0, 6)
+    rho = O.componentwise_correlation(th0, th)
+    for c in range(6):
+        assert rho[c] == pytest.approx(np.corrcoef(th0[:, c], th[:, c])[0, 1], rel=1e-12)
+    srt = np.sort(rho)
+    # q = 0.9 with p = 6: the 6th smallest (the largest); q = 0.5: the 3rd smallest
+    assert O.decorrelated(th0, th, srt[5], 0.9) and not O.decorrelated(th0, th, srt[4], 0.9)
+    assert O.decorrelated(th0, th, srt[2], 0.5) and not O.decorrelated(th0, th, srt[1], 0.5)
+    flat = th.copy()
+    flat[:, 0] = 1.0  # no spread: counts as still correlated
+    assert O.componentwise_correlation(th0, flat)[0] == 1.0
+
+
+def test_adaptive_moves_recover_conjugate_posterior():
+    """Runs whose move counts follow the adaptive rule recover the conjugate posterior and log
+    marginal likelihood (seed-averaged); a lower threshold needs at least as many moves."""
+    prob, mu, S, logml = _conjugate()
+    prob.set_centre(mu)
+    errs, means, Rs = [], [], {0.5: [], 0.05: []}
+    for seed in range(1, 7):
+        for rho_max in (0.5, 0.05):
+            cfg = O.SMCConfig(N=1024, m=8, G=2, L=8, R=1, seed=seed, tau=0.5,
+                              adaptive=(40, rho_max, 0.9))
+            st = O.smc_run(prob, cfg)
+            Rs[rho_max] += [h["R"] for h in st.history]
+            if rho_max == 0.05:
+                errs.append(st.log_z - logml)
+                means.append(st.thetas.mean(axis=0))
+    assert np.mean(Rs[0.05]) > np.mean(Rs[0.5]) >= 1.0
+    assert 1 <= min(Rs[0.05]) and max(Rs[0.05]) <= 40
+    sd = np.sqrt(np.diag(S))
+    assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
+    assert abs(np.mean(errs)) < 0.15
