@@ -114,6 +114,11 @@ typedef struct {
                              /* geometric grid of S values over [(1-a) 10^-E, 1-a] whose ESS is    */
                              /* closest to ess_frac * N (ties: the smaller increment)              */
   double grid_decades;       /* E of the grid, > 0; 0 -> 16                                        */
+  int32_t theta_move;        /* Markov move of theta given u (Algorithm 1 step 2, Sec. 4.2's         */
+                             /* comparison): 0 = HMC with L leapfrog steps (L = 1 is MALA);         */
+                             /* 1 = random-walk Metropolis, theta* = theta + eps * Lc z with Sigma  */
+                             /* = Lc Lc' the particle covariance, one estimator pass per move, the  */
+                             /* step size steered to acceptance 0.234 (HMC: 0.65). Subsampling only */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */

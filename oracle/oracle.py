@@ -85,6 +85,8 @@ def lib():
             L.orc_upm_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, _dp, _i64p, _i32p]
             L.orc_hmc_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, c_i, _dp, _dp, _dp,
                                               _i64p, _i32p]
+            L.orc_rw_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, _dp, _dp, _i64p,
+                                             _i32p]
             L.orc_ess_at.argtypes = [c_i, _dp, _dp, _dp, c_d, c_d]
             L.orc_ess_at.restype = c_d
             L.orc_reweight.argtypes = [c_i, _dp, _dp, _dp, _dp, c_d, c_d, c_i, c_i,
@@ -307,6 +309,16 @@ def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us):
     return acc
 
 
+def rw_move(prob, m, G, seed, stage, move, a, eps, Lc, thetas, us):
+    """Random-walk Metropolis move of theta given u, proposal N(theta, eps^2 Lc Lc')."""
+    N = thetas.shape[0]
+    acc = np.zeros(N, dtype=np.int32)
+    lib().orc_rw_move(*prob.args(m, G), N, seed, stage_move(stage, move), a, eps,
+                      np.ascontiguousarray(Lc, np.float64), thetas,
+                      np.ascontiguousarray(us, np.int64), acc)
+    return acc
+
+
 def ess_at(logW, ell, sig2, a, D):
     return float(lib().orc_ess_at(len(logW), np.ascontiguousarray(logW, np.float64),
                                   np.ascontiguousarray(ell, np.float64),
@@ -401,6 +413,7 @@ class SMCConfig:
     grid_points: int = 0           # > 0: the paper's grid rule for the temperature (Sec. 2.3)
     grid_decades: float = 16.0
     adaptive: tuple | None = None  # (R_max, rho_max, quantile): moves until decorrelated
+    theta_move: str = "hmc"        # or "rw": random-walk Metropolis (Sec. 4.2's comparison)
 
 
 @dataclass
@@ -488,8 +501,12 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     R = 0
     while R < R_max:
         acc_u += int(upm_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.thetas, st.us).sum())
-        acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.eps, cfg.L, st.Sigma,
-                              st.Lc, st.thetas, st.us).sum())
+        if cfg.theta_move == "rw":
+            acc_t += int(rw_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.eps, st.Lc,
+                                 st.thetas, st.us).sum())
+        else:
+            acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.eps, cfg.L,
+                                  st.Sigma, st.Lc, st.thetas, st.us).sum())
         R += 1
         if cfg.adaptive is not None:
             _, rho_max, q = cfg.adaptive
@@ -500,7 +517,8 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
     rate = acc_t / float(cfg.N * R)
     st.history.append(dict(stage=s, a=st.a, ess=ess, log_z_inc=lz, eps=st.eps,
                            acc_u=acc_u / float(cfg.N * R), acc_theta=rate, R=R))
-    st.eps = st.eps * min(2.0, max(0.5, math.exp(rate - 0.65)))
+    target = 0.234 if cfg.theta_move == "rw" else 0.65  # acceptance the step size is steered to
+    st.eps = st.eps * min(2.0, max(0.5, math.exp(rate - target)))
     return st
 
 

@@ -491,6 +491,41 @@ void orc_hmc_move(int fam, int64_t n, int p, const double *X, const double *y, d
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Random-walk Metropolis move of theta given u (the RW kernel of Sec. 4.2's comparison):         */
+/*   theta* = theta + eps * Lc z,  z ~ N(0, I) (the momentum stream's normals), Sigma = Lc Lc',    */
+/*   accepted when log U < log target(theta*) - log target(theta) (U from the theta-MH stream).   */
+/* ------------------------------------------------------------------------------------------ */
+void orc_rw_move(int fam, int64_t n, int p, const double *X, const double *y, double sigma,
+                 const double *tb, double A, const double *B, const double *C, const double *pm,
+                 const double *pv, int m, int G, int N, uint64_t seed, uint32_t stage_move,
+                 double a, double eps, const double *Lc, double *thetas, const int64_t *us,
+                 int *accepted) {
+  orc_prob P = make_prob(fam, n, p, X, y, sigma, tb, A, B, C, pm, pv, m, G);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < N; ++i) {
+    double *theta0 = thetas + (int64_t)i * p;
+    const int64_t *u = us + (int64_t)i * m;
+    double *z = (double *)malloc(sizeof(double) * p);
+    double *th = (double *)malloc(sizeof(double) * p);
+    for (int c = 0; c < p; ++c)
+      z[c] = orc_normal(seed, TAG_MOMENTUM, stage_move, (uint32_t)i, (uint64_t)c);
+    for (int r = 0; r < p; ++r) {
+      double s = 0.0;
+      for (int c = 0; c <= r; ++c) s += Lc[r * p + c] * z[c];
+      th[r] = theta0[r] + eps * s;
+    }
+    double lt0 = log_target(&P, u, theta0, a, NULL);
+    double lt1 = log_target(&P, u, th, a, NULL);
+    double U = orc_uniform(orc_r64(seed, TAG_MH_THETA, stage_move, (uint32_t)i, 0));
+    int acc = log(U) < lt1 - lt0;
+    if (acc) memcpy(theta0, th, sizeof(double) * p);
+    accepted[i] = acc;
+    free(z);
+    free(th);
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Reweighting with an adaptively chosen temperature (Sec. 2.2, Sec. 3.3, Algorithm 2 (b)-(c)).   */
 /*   lw_i(D) = log W_i + D*l_hat_i - ((a+D)^2 - a^2)/2 * sigma2_hat_i                               */
 /*   ESS(D)  = (sum_i e^{lw_i})^2 / sum_i e^{2 lw_i}                                                */

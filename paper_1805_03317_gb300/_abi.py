@@ -30,7 +30,8 @@ class SmcConfig(ctypes.Structure):
                 ("seed", c_u64), ("search_k", c_i32), ("search_rounds", c_i32), ("eps0", c_d),
                 ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
                 ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32),
-                ("resampling", c_i32), ("grid_points", c_i32), ("grid_decades", c_d)]
+                ("resampling", c_i32), ("grid_points", c_i32), ("grid_decades", c_d),
+                ("theta_move", c_i32)]
 
 
 # name -> (restype, argtypes)

@@ -21,6 +21,7 @@ struct smc_ctx {
   int fam = 0, x_dtype = 0, is_f64 = 0, esz = 8, S = 0, Sx = 0, Yo = 0, p = 0, cv_kernel = 0;
   int cv_order = 2, cv_centre = 0;  // control-variate order; re-centring (0 none, 1, 2)
   int multinomial = 0;              // resampling scheme (0 systematic, 1 multinomial)
+  int rw = 0;                       // theta move: 0 HMC, 1 random-walk Metropolis
   int grid_points = 0;              // > 0: grid temperature rule with this many points
   double grid_decades = 16.0;
   int64_t n = 0;
@@ -203,7 +204,7 @@ int res_tiles(const smc_ctx *c, Tile *out, int cap) {
 int hmc_launch(smc_ctx *c, const EstArgs &a) {
   ProfScope ps(c, 2);
   c->launches += 1;
-  if (c->res_tile >= 0) return res_launch(c, c->res_tile, a, false);
+  if (c->res_tile >= 0 && !c->rw) return res_launch(c, c->res_tile, a, false);
   if (c->x_dtype == SMC_F64) return est_launch_f64(2, c->tile, a, c->stream);
   if (c->x_dtype == SMC_F32) return est_launch_f32(2, c->tile, a, c->stream);
   return est_launch_bf16(2, c->tile, a, c->stream);
@@ -266,6 +267,7 @@ EstArgs base_args(const smc_ctx *c) {
   a.A = c->A_h;
   a.A_dev = c->cv_centre ? c->A_d : nullptr;
   a.cv_order = c->cv_order;
+  a.rw = c->rw;
   a.B_ct = c->B_ct;
   a.C_ct = c->C_ct;
   a.tb_ct = c->tb_ct;
@@ -670,6 +672,12 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->cv_order = cfg->cv_order == 1 ? 1 : 2;
   c->cv_centre = cfg->cv_centre;
   c->multinomial = cfg->resampling;
+  if (cfg->theta_move < 0 || cfg->theta_move > 1 || (cfg->theta_move == 1 && cfg->full_data)) {
+    g_init_error = "theta_move must be 0 (HMC) or 1 (random walk; subsampling only)";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  c->rw = cfg->theta_move;
   c->grid_points = cfg->grid_points;
   c->grid_decades = cfg->grid_decades > 0.0 ? cfg->grid_decades : 16.0;
   c->full_data = cfg->full_data ? 1 : 0;
@@ -843,7 +851,7 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     LAUNCH(c, hmc_launch(c, a), 0);
   }
   c->moves_in_stage += R;
-  LAUNCH(c, eps_update(c->N, R, c->st, c->stream), 1);
+  LAUNCH(c, eps_update(c->N, R, c->st, c->stream, c->rw ? 0.234 : 0.65), 1);
   if (acc_u || acc_theta) {
     DevState h;
     int r = sync_state(c, &h);
@@ -911,7 +919,7 @@ int smc_move_adaptive(smc_ctx *c, int32_t R_max, double rho_max, double quantile
     std::sort(sorted.begin(), sorted.end());
     if (sorted[kq] <= rho_max) break;
   }
-  LAUNCH(c, eps_update(N, R, c->st, c->stream), 1);
+  LAUNCH(c, eps_update(N, R, c->st, c->stream, c->rw ? 0.234 : 0.65), 1);
   if (R_used) *R_used = R;
   DevState h;
   int r = sync_state(c, &h);
@@ -1482,7 +1490,8 @@ static int batch_stage_body(smc_batch *b, int R, bool args_ready) {
   if (r) return r;
   for (smc_ctx *c : b->ctx) {
     c->moves_in_stage += R;
-    if (eps_update(c->N, R, c->st, c->stream)) return bfail(b, SMC_ERR_CUDA, "step size");
+    if (eps_update(c->N, R, c->st, c->stream, c->rw ? 0.234 : 0.65))
+      return bfail(b, SMC_ERR_CUDA, "step size");
   }
   return SMC_OK;
 }

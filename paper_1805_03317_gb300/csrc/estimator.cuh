@@ -718,14 +718,53 @@ __device__ __forceinline__ void hmc_body(const EstArgs &a, int i, unsigned char 
     }
     return 0.5 * warp_sum(k);
   };
+  const int32_t *idx = a.u + (int64_t)i * a.m;
+  double *bprop = a.blk_prop + (int64_t)i * a.G * 2;
+  if (a.rw) {  // random-walk Metropolis: theta* = theta + eps Sigma rho ~ N(theta, eps^2 Sigma)
+    for (int r = W.lane; r < p; r += 32) {
+      CT acc = CT(0);
+      for (int c = 0; c < p; ++c) acc = fma(ldg_ct<CT>(a.Sigma_ct, c * p + r), sm.rho[c], acc);
+      sm.v[r] = acc;
+    }
+    __syncwarp();
+    for (int c = W.lane; c < p; c += 32) {  // sm.v keeps the proposal itself
+      sm.v[c] = fma(eps, sm.v[c], sm.th[c]);
+      sm.th[c] = sm.v[c];
+    }
+    __syncwarp();
+    refresh_delta(W, a, sm);
+    double ell1, sig1;
+    eval_particle<XT, T, CPL, U, K, false, true>(W, a, idx, sm, temp, bprop, ell1, sig1);
+    // the current state's estimates are the cache (same u); the momentum is not changed, so
+    // the kinetic terms cancel and the MH ratio is the ratio of the targets
+    const double lp1 = log_prior_warp<CT>(a, sm.th);
+    __syncwarp();
+    for (int c = W.lane; c < p; c += 32) sm.th[c] = th_g[c];
+    __syncwarp();
+    const double lp0 = log_prior_warp<CT>(a, sm.th);
+    const double ell0 = a.ell[i], sig0 = a.sig2[i];
+    const double t1 = temp * ell1 - 0.5 * temp * temp * sig1 + lp1;
+    const double t0 = temp * ell0 - 0.5 * temp * temp * sig0 + lp0;
+    const Stream smh(a.seed, kMhTheta, smv, (uint32_t)i);
+    const double Uu = draw_uniform(smh.draw(0));
+    if (log(Uu) < t1 - t0) {  // false when t1 is NaN: the move is rejected
+      for (int c = W.lane; c < p; c += 32) th_g[c] = sm.v[c];
+      double *blk = a.blk + (int64_t)i * a.G * 2;
+      for (int h = W.lane; h < 2 * a.G; h += 32) blk[h] = bprop[h];
+      if (W.lane == 0) {
+        a.ell[i] = ell1;
+        a.sig2[i] = sig1;
+        atomicAdd(&a.st->acc_theta, 1ull);
+      }
+    }
+    return;
+  }
   const double kin0 = kinetic();
   refresh_delta(W, a, sm);
-  const int32_t *idx = a.u + (int64_t)i * a.m;
   double ell0, sig0;
   eval_particle<XT, T, CPL, U, K, true, false>(W, a, idx, sm, temp, nullptr, ell0, sig0);
   const double H0 = -(temp * ell0 - 0.5 * temp * temp * sig0 + log_prior_warp<CT>(a, sm.th)) + kin0;
   double ell1 = ell0, sig1 = sig0;
-  double *bprop = a.blk_prop + (int64_t)i * a.G * 2;
   for (int l = 0; l < a.L; ++l) {
     for (int c = W.lane; c < p; c += 32) sm.rho[c] += CT(0.5) * eps * sm.g[c];
     __syncwarp();

@@ -70,6 +70,7 @@ struct EstArgs {
   // autograd pair: per-row d, r [B, m] (state type), upstream gradients of l_hat, sigma2_hat [B]
   void *dsave, *rsave;
   int stage_dev;          // 1: the stage index comes from st->stage (graph replays), else stage
+  int rw;                 // theta move: 0 = HMC (L leapfrog steps), 1 = random-walk Metropolis
   int cv_order;           // 1: first-order control variates (row increments without the
                           //    second-order term; C is zero in the state-type copy), else 2
   const double *g_ell, *g_sig2;
@@ -160,7 +161,8 @@ int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, i
 int stage_set(DevState *st, int stage, cudaStream_t s);
 int stage_advance(DevState *st, cudaStream_t s);
 int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_t s);
-int eps_update(int N, int R, DevState *st, cudaStream_t s);
+// eps *= clip(exp(acceptance - target), 0.5, 2) over the last R moves.
+int eps_update(int N, int R, DevState *st, cudaStream_t s, double target = 0.65);
 // rho[c] = correlation across the N particles of component c of clouds a and b (state type).
 int autocorr(int is_f64, int N, int p, const void *a, const void *b, double *rho, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);

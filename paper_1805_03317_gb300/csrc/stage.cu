@@ -1096,13 +1096,13 @@ int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_
   return (int)cudaGetLastError();
 }
 
-__global__ void k_eps_update(int N, int R, DevState *st) {
+__global__ void k_eps_update(int N, int R, double target, DevState *st) {
   const double rate = (double)st->acc_theta / ((double)N * (double)R);
-  const double f = exp(rate - 0.65);
+  const double f = exp(rate - target);
   st->eps *= f < 0.5 ? 0.5 : (f > 2.0 ? 2.0 : f);
 }
-int eps_update(int N, int R, DevState *st, cudaStream_t s) {
-  k_eps_update<<<1, 1, 0, s>>>(N, R, st);
+int eps_update(int N, int R, DevState *st, cudaStream_t s, double target) {
+  k_eps_update<<<1, 1, 0, s>>>(N, R, target, st);
   return (int)cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ from ._abi import DTYPE, FAMILY, SmcConfig, SmcProblem, check
 
 _TORCH_X = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16"}
 RESAMPLING = {"systematic": 0, "multinomial": 1}
+THETA_MOVE = {"hmc": 0, "rw": 1}
 
 
 def _ptr(t):
@@ -61,7 +62,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
              cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
              resampling: str = "systematic", grid_points: int = 0, grid_decades: float = 0.0,
-             stream=None) -> Context:
+             theta_move: str = "hmc", stream=None) -> Context:
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -76,7 +77,8 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
     cfg = SmcConfig(N, m, G, L, float(ess_frac), int(seed) & ((1 << 64) - 1), search_k,
                     search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
                     int(cv_order), int(cv_centre), 1 if full_data else 0,
-                    RESAMPLING[resampling], int(grid_points), float(grid_decades))
+                    RESAMPLING[resampling], int(grid_points), float(grid_decades),
+                    THETA_MOVE[theta_move])
     tb = None
     tb_ptr = None
     if theta_bar is not None:
@@ -416,7 +418,8 @@ def smc_batch_init(problems, stream=None) -> Batch:
                             int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
                             d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 2, 0,
                             0, RESAMPLING[d.get("resampling", "systematic")],
-                            int(d.get("grid_points", 0)), float(d.get("grid_decades", 0.0)))
+                            int(d.get("grid_points", 0)), float(d.get("grid_decades", 0.0)),
+                            THETA_MOVE[d.get("theta_move", "hmc")])
         keep += [y, pm, pv]
         meta.append((d["N"], d["m"], d["G"], p, n, X.device))
     handle = ctypes.c_void_p()

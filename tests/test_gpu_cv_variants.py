@@ -364,3 +364,59 @@ def test_adaptive_moves_full_data_and_bad_arguments():
         with pytest.raises(S()._abi.SmcError):
             S().smc_move_adaptive(ctx, *bad)
     S().smc_free(ctx)
+
+
+# ------------------------------------------------------------------------------------------------
+# Random-walk Metropolis theta move (Sec. 4.2's comparison of move kernels)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("x_dtype", ["f64", "f32", "bf16"])
+def test_rw_move_matches_oracle(x_dtype):
+    wl = _wl("logistic", x_dtype, p=7, N=300, m=77, G=5)
+    prob, ctx = make_pair(wl, theta_move="rw")
+    rng = np.random.default_rng(5)
+    th = state_round(prob.theta_bar + 0.02 * rng.standard_normal((wl.N, wl.p)), x_dtype)
+    u = rng.integers(0, wl.n, size=(wl.N, wl.m)).astype(np.int64)
+    W = rng.random(wl.N) ** 3
+    W /= W.sum()
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    S().smc_set_scalars(ctx, 2, 0.3, 0.5, 0.0)
+    a, _, _ = S().smc_reweight(ctx)
+    acc_u, acc_t = S().smc_move(ctx, 1)
+    th_g, u_g, _ = S().smc_get_particles(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)
+    ra, _, rW, _, _ = O.reweight(np.log(W), ref["ell"], ref["sigma2"], 0.3, 0.5)
+    _, _, Lc, _ = O.moments(rW, th)
+    th_o, u_o = th.copy(), u.copy()
+    au = O.upm_move(prob, wl.m, wl.G, wl.seed, 3, 0, ra, th_o, u_o)
+    at = O.rw_move(prob, wl.m, wl.G, wl.seed, 3, 0, ra, 0.5, Lc, th_o, u_o)
+    assert 0.05 < at.mean() < 0.95  # both outcomes occur
+    if x_dtype == "f64":
+        np.testing.assert_array_equal(u_g.cpu().numpy(), u_o)
+        assert acc_u == pytest.approx(au.mean()) and acc_t == pytest.approx(at.mean())
+        np.testing.assert_allclose(th_g.cpu().numpy(), th_o, rtol=1e-9, atol=1e-11)
+    else:  # MH decisions may differ only where the FP64 log ratio is within FP32 rounding
+        same = np.all(np.abs(th_g.cpu().numpy() - th_o) <= 1e-4 * (np.abs(th_o) + 1e-3), axis=1)
+        assert same.mean() > 0.97
+        assert abs(acc_t - at.mean()) < 0.03
+    S().smc_free(ctx)
+
+
+@pytest.mark.parametrize("hmc_kernel", [0, 1])
+def test_rw_smc_run_matches_oracle_fp64(hmc_kernel):
+    wl = small_glm("logistic", n=4000, p=4, N=128, m=50, G=5, L=1, R=4, x_dtype="f64", seed=33)
+    prob, ctx = make_pair(wl, hmc_kernel=hmc_kernel, theta_move="rw", eps0=1.0)
+    cfg = O.SMCConfig(N=wl.N, m=wl.m, G=wl.G, L=1, R=wl.R, seed=wl.seed, tau=0.5,
+                      theta_move="rw", eps0=1.0)
+    st_o = O.smc_run(prob, cfg)
+    runner = S().SubsampledSMC.__new__(S().SubsampledSMC)
+    runner.ctx, runner.history = ctx, []
+    st = runner.run(wl.R)
+    assert st["stage"] == st_o.stage
+    np.testing.assert_allclose([h["acc_theta"] for h in runner.history],
+                               [h["acc_theta"] for h in st_o.history], rtol=1e-12)
+    assert st["log_z"] == pytest.approx(st_o.log_z, abs=1e-7)
+    th, u, _ = S().smc_get_particles(ctx)
+    np.testing.assert_array_equal(u.cpu().numpy(), st_o.us)
+    np.testing.assert_allclose(th.cpu().numpy(), st_o.thetas, rtol=1e-7, atol=1e-9)
+    S().smc_free(ctx)

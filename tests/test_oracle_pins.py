@@ -720,3 +720,49 @@ def test_adaptive_moves_recover_conjugate_posterior():
     sd = np.sqrt(np.diag(S))
     assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
     assert abs(np.mean(errs)) < 0.15
+
+
+def test_rw_move_proposal_and_invariance():
+    """Random-walk Metropolis (Sec. 4.2's RW kernel): at a tiny step every proposal
+    theta + eps Lc z is accepted (z rebuilt from the momentum stream's normals); started at exact
+    conjugate posterior draws with Sigma the posterior covariance, the moves keep them N(mu, S)."""
+    prob, mu, S, _ = _conjugate()
+    prob.set_centre(mu)
+    Lc = np.linalg.cholesky(S)
+    N, m, seed, stage = 64, 5, 13, 2
+    rng = np.random.default_rng(1)
+    th = mu + rng.standard_normal((N, prob.p)) @ Lc.T
+    us = rng.integers(0, prob.n, size=(N, m)).astype(np.int64)
+    th1 = th.copy()
+    acc = O.rw_move(prob, m, 1, seed, stage, 0, 1.0, 1e-6, Lc, th1, us)
+    assert acc.all()
+    for i in range(N):
+        z = np.array([O.normal(seed, O.TAG_MOMENTUM, O.stage_move(stage, 0), i, c)
+                      for c in range(prob.p)])
+        np.testing.assert_allclose(th1[i], th[i] + 1e-6 * Lc @ z, rtol=0, atol=1e-15)
+    N = 4000
+    th = mu + rng.standard_normal((N, prob.p)) @ Lc.T
+    us = rng.integers(0, prob.n, size=(N, m)).astype(np.int64)
+    rates = []
+    for r in range(6):
+        rates.append(O.rw_move(prob, m, 1, seed, stage, r, 1.0, 2.38 / math.sqrt(prob.p), Lc, th,
+                               us).mean())
+    assert 0.15 < np.mean(rates) < 0.6
+    z = np.linalg.solve(Lc, (th - mu).T).T
+    assert np.all(np.abs(z.mean(axis=0)) < 4 / math.sqrt(N))
+    assert np.all(np.abs(z.var(axis=0) - 1.0) < 5 * math.sqrt(2.0 / N))
+
+
+def test_rw_smc_recovers_conjugate_posterior():
+    prob, mu, S, logml = _conjugate()
+    prob.set_centre(mu)
+    errs, means = [], []
+    for seed in range(1, 7):
+        cfg = O.SMCConfig(N=1024, m=8, G=2, L=1, R=8, seed=seed, tau=0.5, theta_move="rw",
+                          eps0=1.0)
+        st = O.smc_run(prob, cfg)
+        errs.append(st.log_z - logml)
+        means.append(st.thetas.mean(axis=0))
+    sd = np.sqrt(np.diag(S))
+    assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
+    assert abs(np.mean(errs)) < 0.15
