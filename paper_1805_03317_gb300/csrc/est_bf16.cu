@@ -1,6 +1,5 @@
 // Estimator kernels for bf16 storage of X: one instantiation per compiled tile shape.
 #include "estimator.cuh"
-#include "resident.cuh"
 
 namespace subsmc {
 namespace {
@@ -34,24 +33,6 @@ int est_launch_bf16(int op, int tile, const EstArgs &a, cudaStream_t s) {
   }
 }
 
-int est_launch_batch_bf16(int op, int tile, const BatchArgs &b, cudaStream_t s) {
-  switch (tile) {
-    case 0: return launch_tile_batch<XT, 1, 8, 3, 4>(op, b, s);
-    case 1: return launch_tile_batch<XT, 2, 8, 3, 4>(op, b, s);
-    case 2: return launch_tile_batch<XT, 4, 8, 2, 4>(op, b, s);
-    case 3: return launch_tile_batch<XT, 2, 16, 2, 4>(op, b, s);
-    case 4: return launch_tile_batch<XT, 4, 16, 2, 4>(op, b, s);
-    case 5: return launch_tile_batch<XT, 8, 8, 2, 4>(op, b, s);
-    case 6: return launch_tile_batch<XT, 8, 8, 3, 4>(op, b, s);
-    case 7: return launch_tile_batch<XT, 8, 16, 2, 4>(op, b, s);
-    case 8: return launch_tile_batch<XT, 16, 8, 2, 4>(op, b, s);
-    case 9: return launch_tile_batch<XT, 4, 8, 3, 4, true>(op, b, s);
-    case 10: return launch_tile_batch<XT, 4, 16, 3, 4, true>(op, b, s);
-    case 11: return launch_tile_batch<XT, 8, 8, 3, 4, true>(op, b, s);
-    default: return -1;
-  }
-}
-
 int est_warp_smem_bf16(int tile, int p) {
   switch (tile) {
     case 0: return warp_smem_bytes<XT, 1, 8, 3>(p);
@@ -67,29 +48,6 @@ int est_warp_smem_bf16(int tile, int p) {
     case 10: return warp_smem_bytes<XT, 4, 16, 3>(p);
     case 11: return warp_smem_bytes<XT, 8, 8, 3>(p);
     default: return 0;
-  }
-}
-
-namespace {
-const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
-                          {1, 24, 1, 8}};
-}  // namespace
-
-int res_tiles_bf16(Tile *out, int cap) {
-  const int n = (int)(sizeof(kResTiles) / sizeof(kResTiles[0]));
-  for (int i = 0; i < n && i < cap; ++i) out[i] = kResTiles[i];
-  return n;
-}
-
-int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry) {
-  switch (tile) {
-    case 0: return launch_res<XT, 8, 4>(a, s, sms, dry);
-    case 1: return launch_res<XT, 16, 4>(a, s, sms, dry);
-    case 2: return launch_res<XT, 24, 4>(a, s, sms, dry);
-    case 3: return launch_res<XT, 32, 4>(a, s, sms, dry);
-    case 4: return launch_res<XT, 16, 8>(a, s, sms, dry);
-    case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
-    default: return -1;
   }
 }
 

@@ -1,0 +1,30 @@
+// Resident-trajectory HMC kernels for bf16 storage of X: one instantiation per compiled tile.
+// A translation unit of its own so that the library's sources compile in parallel.
+#include "resident.cuh"
+
+namespace subsmc {
+namespace {
+using XT = __nv_bfloat16;
+const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
+                          {1, 24, 1, 8}};
+}  // namespace
+
+int res_tiles_bf16(Tile *out, int cap) {
+  const int n = (int)(sizeof(kResTiles) / sizeof(kResTiles[0]));
+  for (int i = 0; i < n && i < cap; ++i) out[i] = kResTiles[i];
+  return n;
+}
+
+int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry) {
+  switch (tile) {
+    case 0: return launch_res<XT, 8, 4>(a, s, sms, dry);
+    case 1: return launch_res<XT, 16, 4>(a, s, sms, dry);
+    case 2: return launch_res<XT, 24, 4>(a, s, sms, dry);
+    case 3: return launch_res<XT, 32, 4>(a, s, sms, dry);
+    case 4: return launch_res<XT, 16, 8>(a, s, sms, dry);
+    case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
+    default: return -1;
+  }
+}
+
+}  // namespace subsmc

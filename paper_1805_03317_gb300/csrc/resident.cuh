@@ -169,25 +169,30 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
 #pragma unroll
       for (int s = 0; s < 2 * CPL; ++s) v[s] = CT(0);
       CT sd = CT(0), sd2 = CT(0);
-      for (int j = warp * 32 + lane; j < m; j += WARPS * 32) {
-        CT x[CPL];
-        load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
-        const CT D = dot_slots<CPL>(x, dr);
-        const RowC<CT> c = cst[j];
-        CT d, r;
-        switch (fam) {
-          case 0: row_incr<0, CT>(c, D, inv_s2, d, r); break;
-          case 1: row_incr<1, CT>(c, D, inv_s2, d, r); break;
-          case 2: row_incr<2, CT>(c, D, inv_s2, d, r); break;
-          case 3: row_incr<3, CT>(c, D, inv_s2, d, r); break;
-          default: row_incr<4, CT>(c, D, inv_s2, d, r); break;
+      // the row loop, specialised per family (the dispatch is taken once per pass, not per row)
+      auto row_loop = [&](auto famc) {
+        constexpr int F = decltype(famc)::value;
+        for (int j = warp * 32 + lane; j < m; j += WARPS * 32) {
+          CT x[CPL];
+          load_res_row<XT, CPL>(rows + (size_t)j * P.rb, x);
+          const CT D = dot_slots<CPL>(x, dr);
+          const RowC<CT> c = cst[j];
+          CT d, r;
+          row_incr<F, CT>(c, D, inv_s2, d, r);
+          if (cv1) to_first_order(row_l2<F, CT>(c, inv_s2), D, d, r);
+          axpy_slots<CPL>(r, x, v);
+          axpy_slots<CPL>(d * r, x, v + CPL);
+          sd += d;
+          sd2 = fma(d, d, sd2);
+          if (final) dv[j] = d;
         }
-        if (cv1) to_first_order(row_l2_any(fam, c, inv_s2), D, d, r);
-        axpy_slots<CPL>(r, x, v);
-        axpy_slots<CPL>(d * r, x, v + CPL);
-        sd += d;
-        sd2 = fma(d, d, sd2);
-        if (final) dv[j] = d;
+      };
+      switch (fam) {
+        case 0: row_loop(std::integral_constant<int, 0>{}); break;
+        case 1: row_loop(std::integral_constant<int, 1>{}); break;
+        case 2: row_loop(std::integral_constant<int, 2>{}); break;
+        case 3: row_loop(std::integral_constant<int, 3>{}); break;
+        default: row_loop(std::integral_constant<int, 4>{}); break;
       }
       int base = 0;
       reduce_scatter<2 * CPL, 16, CT>(v, lane, base);
