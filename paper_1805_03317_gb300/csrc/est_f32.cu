@@ -31,7 +31,7 @@ int est_launch_f32(int op, int tile, const EstArgs &a, cudaStream_t s) {
 
 namespace {
 const Tile kResTiles[] = {{1, 8, 1, 4, 0}, {1, 16, 1, 4, 0}, {1, 24, 1, 4, 0}, {1, 32, 1, 4, 0},
-                          {1, 16, 1, 8, 0}, {1, 24, 1, 8, 0}};
+                          {1, 16, 1, 8, 0}, {1, 24, 1, 8, 0}, {1, 20, 1, 4, 0}, {1, 12, 1, 4, 0}};
 }  // namespace
 
 int res_tiles_f32(Tile *out, int cap) {
@@ -48,6 +48,8 @@ int res_launch_f32(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry
     case 3: return launch_res<XT, 32, 4>(a, s, sms, dry);
     case 4: return launch_res<XT, 16, 8>(a, s, sms, dry);
     case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
+    case 6: return launch_res<XT, 20, 4>(a, s, sms, dry);
+    case 7: return launch_res<XT, 12, 4>(a, s, sms, dry);
     default: return -1;
   }
 }

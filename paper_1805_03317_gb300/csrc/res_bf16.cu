@@ -6,7 +6,7 @@ namespace subsmc {
 namespace {
 using XT = __nv_bfloat16;
 const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
-                          {1, 24, 1, 8}};
+                          {1, 24, 1, 8}, {1, 20, 1, 4}, {1, 12, 1, 4}};
 }  // namespace
 
 int res_tiles_bf16(Tile *out, int cap) {
@@ -23,6 +23,8 @@ int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dr
     case 3: return launch_res<XT, 32, 4>(a, s, sms, dry);
     case 4: return launch_res<XT, 16, 8>(a, s, sms, dry);
     case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
+    case 6: return launch_res<XT, 20, 4>(a, s, sms, dry);
+    case 7: return launch_res<XT, 12, 4>(a, s, sms, dry);
     default: return -1;
   }
 }

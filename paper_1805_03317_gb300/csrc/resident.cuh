@@ -18,7 +18,8 @@ namespace subsmc {
 // Shared-memory plan of one CTA.
 struct ResPlan {
   int rb;    // bytes per resident row (covariates only): an odd multiple of 16 (conflict-free LDS.128)
-  int nvec;  // 16-byte vectors of covariates per row
+  int nvec;  // 16-byte vectors of covariates per row (copied from the packed row)
+  int nvl;   // 16-byte vectors the tile's CPL slots read (>= nvec; the extra ones are zero-filled)
   int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, total;
 };
 
@@ -27,9 +28,10 @@ inline __host__ __device__ int round16(int v) { return (v + 15) & ~15; }
 template <typename CT>
 inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   ResPlan P;
-  const int xb = round16(p * esz);
+  const int xb = round16(p * esz), xl = round16(cpl * esz);
   P.nvec = xb / 16;
-  P.rb = ((xb / 16) % 2 == 0) ? xb + 16 : xb;
+  P.nvl = xl / 16;
+  P.rb = ((xl / 16) % 2 == 0) ? xl + 16 : xl;
   int off = m * P.rb;
   P.off_consts = off;
   off = round16(off + m * (int)sizeof(RowC<CT>));
@@ -53,15 +55,24 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// CPL covariate slots of a resident row; CPL need not be a multiple of the 16-byte vector width
+// (the row holds whole vectors, zero-padded, and the unused tail of the last one is dropped).
 template <typename XT, int CPL>
 __device__ __forceinline__ void load_res_row(const unsigned char *row,
                                              typename Store<XT>::CT *x) {
   using SD = Store<XT>;
-  constexpr int NV = CPL / SD::VEC;
+  using CT = typename SD::CT;
+  constexpr int NV = CPL / SD::VEC, REM = CPL % SD::VEC;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const uint4 w = *reinterpret_cast<const uint4 *>(row + 16 * v);
     SD::unpack(w, x + v * SD::VEC);
+  }
+  if constexpr (REM > 0) {
+    CT t[SD::VEC];
+    SD::unpack(*reinterpret_cast<const uint4 *>(row + 16 * NV), t);
+#pragma unroll
+    for (int e = 0; e < REM; ++e) x[NV * SD::VEC + e] = t[e];
   }
 }
 
@@ -109,20 +120,22 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     const int32_t *u = a.u + (int64_t)i * m;
     __syncthreads();  // the previous particle is finished with shared memory
     // 1. gather x_{u_j} and the row's constants at the centre (its tail) with 16-byte copies;
-    // invalid indices are flagged and their rows zeroed
+    // invalid indices are flagged and their rows zeroed. Vectors the tile reads beyond the row's
+    // covariates (a tile wider than p) are zero-filled.
     constexpr int NTV = (int)sizeof(RowC<CT>) / 16;
-    const int nvr = P.nvec + NTV;
+    const int nvr = P.nvl + NTV;
     for (int t = tid; t < m * nvr; t += blockDim.x) {
       const int j = t / nvr, q = t - j * nvr;
       const int k = u[j];
-      unsigned char *dst = q < P.nvec ? rows + (size_t)j * P.rb + 16 * q
-                                      : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvec);
-      if (k < 0 || (int64_t)k >= a.n) {
+      unsigned char *dst = q < P.nvl ? rows + (size_t)j * P.rb + 16 * q
+                                     : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvl);
+      const int qs = q < P.nvl ? q : P.nvec + (q - P.nvl);  // 16-byte vector of the packed row
+      if (k < 0 || (int64_t)k >= a.n || (q >= P.nvec && q < P.nvl)) {
         *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        if (q == 0) set_err(a.st, kErrIndex);
+        if (q == 0 && (k < 0 || (int64_t)k >= a.n)) set_err(a.st, kErrIndex);
         continue;
       }
-      cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * q);
+      cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * qs);
     }
     cp_async_wait_all();
     // 2. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
