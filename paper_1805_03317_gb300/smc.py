@@ -396,7 +396,8 @@ def _bcheck(code: int, where: str, handle) -> None:
 
 def smc_batch_init(problems, stream=None) -> Batch:
     """problems: list of dicts with X, y, family, prior_mean, prior_var and the smc_init settings
-    (N, m, G, L, seed; optional ess_frac, noise_sigma, eps0, search_k, search_rounds)."""
+    (N, m, G, L, seed; optional ess_frac, noise_sigma, dof, eps0, search_k, search_rounds,
+    cv_order, cv_centre, resampling, grid_points, grid_decades, theta_move)."""
     lib = _abi.load()
     P = len(problems)
     probs = (SmcProblem * P)()
@@ -416,8 +417,9 @@ def smc_batch_init(problems, stream=None) -> Batch:
                               float(d.get("dof", 5.0)))
         cfgs[q] = SmcConfig(d["N"], d["m"], d["G"], d["L"], float(d.get("ess_frac", 0.5)),
                             int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
-                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0, 2, 0,
-                            0, RESAMPLING[d.get("resampling", "systematic")],
+                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0,
+                            int(d.get("cv_order", 2)), int(d.get("cv_centre", 0)), 0,
+                            RESAMPLING[d.get("resampling", "systematic")],
                             int(d.get("grid_points", 0)), float(d.get("grid_decades", 0.0)),
                             THETA_MOVE[d.get("theta_move", "hmc")])
         keep += [y, pm, pv]

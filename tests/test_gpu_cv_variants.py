@@ -420,3 +420,48 @@ def test_rw_smc_run_matches_oracle_fp64(hmc_kernel):
     np.testing.assert_array_equal(u.cpu().numpy(), st_o.us)
     np.testing.assert_allclose(th.cpu().numpy(), st_o.thetas, rtol=1e-7, atol=1e-9)
     S().smc_free(ctx)
+
+
+def test_batch_with_mixed_options_matches_single_problems():
+    """A batch whose problems mix the options (Student-t and logistic families, first-order and
+    re-centred control variates, multinomial resampling with the grid rule, random-walk moves):
+    batched stages give bit-identical results to stepping each problem alone."""
+    from gpu_common import device_arrays
+    opts = [dict(family="student_t", cv_order=1),
+            dict(family="logistic", cv_centre=1),
+            dict(family="poisson", resampling="multinomial", grid_points=256, ess_frac=0.8),
+            dict(family="probit", theta_move="rw", cv_centre=2)]
+    wls, dicts = [], []
+    for q, o in enumerate(opts):
+        kw = dict(x_scale=0.3) if o["family"] == "poisson" else {}
+        w = small_glm(o["family"], n=3000 + 700 * q, p=5 + 2 * q, N=96, m=40 + 9 * q, G=4, L=4,
+                      x_dtype="bf16", seed=40 + q, **kw)
+        wls.append(w)
+        X, y = device_arrays(w)
+        d = dict(X=X, y=y, family=w.family, prior_mean=w.prior_mean, prior_var=w.prior_var,
+                 N=w.N, m=w.m, G=w.G, L=w.L, seed=w.seed, noise_sigma=w.sigma, dof=w.dof)
+        d.update({k: v for k, v in o.items() if k != "family"})
+        dicts.append(d)
+    b = S().smc_batch_init(dicts)
+    tile = S().smc_batch_tile(b)
+    singles = []
+    for q, (w, o) in enumerate(zip(wls, opts)):
+        kw = {k: v for k, v in o.items() if k != "family"}
+        # the same centre as the batch's problem (the device's Newton mode; an independently
+        # found mode can round to another FP32 value)
+        tb = S().smc_get_centre(S().smc_batch_context(b, q))[0]
+        singles.append(make_pair(w, tile_hint=tile, hmc_kernel=1, theta_bar=tb, **kw)[1])
+    for use_graph in [False, True, True, False]:
+        S().smc_batch_stage(b, 2, use_graph=use_graph)
+        for c in singles:
+            S().smc_reweight(c)
+            S().smc_resample(c)
+            S().smc_move(c, 2)
+    for q, c in enumerate(singles):
+        cb = S().smc_batch_context(b, q)
+        ta, ua, Wa = S().smc_get_particles(cb)
+        ts, us, Ws = S().smc_get_particles(c)
+        assert torch.equal(ta, ts) and torch.equal(ua, us) and torch.equal(Wa, Ws), q
+        assert S().smc_get_status(cb) == S().smc_get_status(c), q
+        S().smc_free(c)
+    S().smc_batch_free(b)

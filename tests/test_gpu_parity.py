@@ -651,7 +651,10 @@ def test_batch_stages_match_single_problems():
     wls = batch_uneven(P=5, N=96, G=5, L=4, R=2, n_lo=2000, n_hi=20000)
     b = S().smc_batch_init(_batch_problem_dicts(wls))
     tile = S().smc_batch_tile(b)
-    singles = [make_pair(w, tile_hint=tile, hmc_kernel=1, theta_bar=None)[1] for w in wls]
+    # the singles take the batch problems' centres (the device's Newton modes)
+    singles = [make_pair(w, tile_hint=tile, hmc_kernel=1,
+                         theta_bar=S().smc_get_centre(S().smc_batch_context(b, q))[0])[1]
+               for q, w in enumerate(wls)]
     for use_graph in [False, True, True, False, True, True]:
         S().smc_batch_stage(b, 2, use_graph=use_graph)
         for c in singles:
