@@ -342,6 +342,57 @@ def full_data_leg(S, wl, dev, R, tc_peak, stages=2, reps=5):
                     "MMAs"}
 
 
+def precision_leg(S, dev, R=5, seeds=3, n=1_000_000, p=20, max_stages=400):
+    """Mixed precision against FP32 storage at equal accuracy: a conjugate Gaussian linear model of
+    the headline shape (n = 1e6, p = 20, N = 4096, m = 1000, L = 20; sigma = 0.5, prior N(0, 10 I)),
+    where the second-order control variate is exact, so each storage type has a closed-form
+    posterior mean and log marginal likelihood on its own stored values. Complete SMC runs
+    (init to a = 1) in BF16 and FP32 storage, timed, with their errors against those closed forms
+    (several seeds: the errors are Monte Carlo error)."""
+    import torch
+    from smc_workloads import small_glm
+    out = {}
+    for x_dtype in ("bf16", "f32"):
+        wl = small_glm("gaussian", n=n, p=p, N=4096, m=1000, G=10, L=20, R=R, x_dtype=x_dtype,
+                       seed=11, sigma=0.5, theta_scale=0.3, prior_var=10.0)
+        X, y, s2, tau2 = wl.X, wl.y, wl.sigma ** 2, 10.0
+        XtX = X.T @ X
+        Sinv = XtX / s2 + np.eye(p) / tau2
+        mu = np.linalg.solve(Sinv, X.T @ y / s2)
+        sd = np.sqrt(np.diag(np.linalg.inv(Sinv)))
+        logdet = np.linalg.slogdet(np.eye(p) + tau2 * XtX / s2)[1]
+        logml = (-0.5 * n * math.log(2 * math.pi * s2) - 0.5 * logdet
+                 - (y @ y - y @ X @ mu) / (2 * s2))
+        walls, lz_err, mean_err, stages = [], [], [], []
+        for s in range(seeds):
+            Xd, yd = device_workload(wl, dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = S.smc_init(Xd, yd, "gaussian", wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m,
+                             G=wl.G, L=wl.L, seed=100 + s, ess_frac=0.5, noise_sigma=wl.sigma,
+                             theta_bar=None)
+            k, a = 0, 0.0
+            while a < 1.0 and k < max_stages:
+                a = run_stage(S, ctx, R)
+                k += 1
+            th, _, W = S.smc_get_particles(ctx)
+            mean = (th.double() * W[:, None]).sum(0).cpu().numpy()
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+            lz_err.append(S.smc_get_status(ctx)["log_z"] - logml)
+            mean_err.append(float(np.max(np.abs(mean - mu) / sd)))
+            stages.append(k)
+            S.smc_free(ctx)
+            del Xd, yd
+        out[x_dtype] = {"wall_s_mean": float(np.mean(walls)), "stages": stages,
+                        "log_z_minus_closed_form": [round(e, 4) for e in lz_err],
+                        "post_mean_err_max_sd": [round(e, 4) for e in mean_err]}
+    out["bf16_speedup"] = out["f32"]["wall_s_mean"] / out["bf16"]["wall_s_mean"]
+    out["workload"] = (f"gaussian n={n} p={p} N=4096 m=1000 G=10 L=20 R={R}, sigma=0.5, "
+                       f"prior N(0,10I); wall time includes init (packing, Newton centre)")
+    return out
+
+
 def student_t_leg(S, dev, R=5, max_stages=200, N=280):
     """Sec. 4.3's Student-t comparison in the paper's shape (n = 5e5, p = 50 correlated
     covariates, t_5 errors, m = 1250, G = 100; the paper's M = 280 particles, L = 20, BF16 X): a
@@ -522,6 +573,7 @@ def gpu_arm(args):
         del wl32
         # the paper's own stage settings (Algorithm 2 as printed): ESS target 0.8N by the grid
         # rule, multinomial resampling, control variates re-centred every stage, R tuned per stage
+        walls["conjugate_bf16_vs_fp32"] = precision_leg(S, dev, R)
         walls["bf16_paper_settings"] = full_run(
             S, wl, dev, R, adaptive=(30, 0.1, 0.9), ess_frac=0.8, grid_points=1024,
             resampling="multinomial", cv_centre=1)

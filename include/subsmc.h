@@ -119,6 +119,10 @@ typedef struct {
                              /* 1 = random-walk Metropolis, theta* = theta + eps * Lc z with Sigma  */
                              /* = Lc Lc' the particle covariance, one estimator pass per move, the  */
                              /* step size steered to acceptance 0.234 (HMC: 0.65). Subsampling only */
+  double eps_jitter;         /* HMC: particle i's trajectory uses step eps * U_i, U_i uniform on    */
+                             /* [1 - j, 1 + j] (second word of its theta-MH Philox block); random   */
+                             /* steps break near-periodic trajectories of a fixed eps L (Neal 2011, */
+                             /* cited in Sec. 1). j < 0.9; 0 -> 0.3; negative -> a fixed step       */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */

@@ -83,8 +83,8 @@ def lib():
                                                   ctypes.c_void_p, ctypes.c_void_p]
             L.orc_init.argtypes = [c_u64, c_i, c_i, c_i, c_i64, _dp, _dp, _dp, _i64p]
             L.orc_upm_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, _dp, _i64p, _i32p]
-            L.orc_hmc_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, c_i, _dp, _dp, _dp,
-                                              _i64p, _i32p]
+            L.orc_hmc_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, c_d, c_i, _dp, _dp,
+                                              _dp, _i64p, _i32p]
             L.orc_rw_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, _dp, _dp, _i64p,
                                              _i32p]
             L.orc_ess_at.argtypes = [c_i, _dp, _dp, _dp, c_d, c_d]
@@ -300,10 +300,12 @@ def upm_move(prob, m, G, seed, stage, move, a, thetas, us):
     return acc
 
 
-def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us):
+def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us, jitter=0.3):
+    """HMC move of theta given u (Algorithm 1 step 2); jitter > 0: each particle's step size is
+    uniform on eps [1 - jitter, 1 + jitter]."""
     N = thetas.shape[0]
     acc = np.zeros(N, dtype=np.int32)
-    lib().orc_hmc_move(*prob.args(m, G), N, seed, stage_move(stage, move), a, eps, L,
+    lib().orc_hmc_move(*prob.args(m, G), N, seed, stage_move(stage, move), a, eps, jitter, L,
                        np.ascontiguousarray(Sigma, np.float64), np.ascontiguousarray(Lc, np.float64),
                        thetas, np.ascontiguousarray(us, np.int64), acc)
     return acc
@@ -414,6 +416,7 @@ class SMCConfig:
     grid_decades: float = 16.0
     adaptive: tuple | None = None  # (R_max, rho_max, quantile): moves until decorrelated
     theta_move: str = "hmc"        # or "rw": random-walk Metropolis (Sec. 4.2's comparison)
+    eps_jitter: float = 0.3        # HMC: per-particle step size uniform on eps [1 -+ jitter]
 
 
 @dataclass
@@ -506,7 +509,7 @@ def smc_stage(prob: Problem, cfg: SMCConfig, st: SMCState):
                                  st.thetas, st.us).sum())
         else:
             acc_t += int(hmc_move(prob, cfg.m, cfg.G, cfg.seed, s, R, st.a, st.eps, cfg.L,
-                                  st.Sigma, st.Lc, st.thetas, st.us).sum())
+                                  st.Sigma, st.Lc, st.thetas, st.us, cfg.eps_jitter).sum())
         R += 1
         if cfg.adaptive is not None:
             _, rho_max, q = cfg.adaptive

@@ -441,8 +441,8 @@ void orc_upm_move(int fam, int64_t n, int p, const double *X, const double *y, d
 void orc_hmc_move(int fam, int64_t n, int p, const double *X, const double *y, double sigma,
                   const double *tb, double A, const double *B, const double *C, const double *pm,
                   const double *pv, int m, int G, int N, uint64_t seed, uint32_t stage_move,
-                  double a, double eps, int Lsteps, const double *Sigma, const double *Lc,
-                  double *thetas, const int64_t *us, int *accepted) {
+                  double a, double eps, double jitter, int Lsteps, const double *Sigma,
+                  const double *Lc, double *thetas, const int64_t *us, int *accepted) {
   orc_prob P = make_prob(fam, n, p, X, y, sigma, tb, A, B, C, pm, pv, m, G);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int i = 0; i < N; ++i) {
@@ -468,15 +468,23 @@ void orc_hmc_move(int fam, int64_t n, int p, const double *X, const double *y, d
     double lt0 = log_target(&P, u, th, a, g);
     double H0 = -lt0 + kin0;
     double lt = lt0;
+    /* the particle's step size, uniform on [eps (1 - jitter), eps (1 + jitter)] (the second word
+       of its theta-MH block): a random step size breaks the near-periodic trajectories of a fixed
+       eps L on near-Gaussian targets (Neal 2011) */
+    double eps_i = eps;
+    if (jitter > 0.0) {
+      double Uj = orc_uniform(orc_r64(seed, TAG_MH_THETA, stage_move, (uint32_t)i, 1));
+      eps_i = eps * (1.0 - jitter + 2.0 * jitter * Uj);
+    }
     for (int l = 0; l < Lsteps; ++l) {
-      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps * g[c];
+      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps_i * g[c];
       for (int r = 0; r < p; ++r) {
         v[r] = 0.0;
         for (int c = 0; c < p; ++c) v[r] += Sigma[r * p + c] * rho[c];
       }
-      for (int c = 0; c < p; ++c) th[c] += eps * v[c];
+      for (int c = 0; c < p; ++c) th[c] += eps_i * v[c];
       lt = log_target(&P, u, th, a, g);
-      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps * g[c];
+      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps_i * g[c];
     }
     double kin1 = 0.0;
     for (int r = 0; r < p; ++r)

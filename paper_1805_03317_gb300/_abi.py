@@ -31,7 +31,7 @@ class SmcConfig(ctypes.Structure):
                 ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
                 ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32),
                 ("resampling", c_i32), ("grid_points", c_i32), ("grid_decades", c_d),
-                ("theta_move", c_i32)]
+                ("theta_move", c_i32), ("eps_jitter", c_d)]
 
 
 # name -> (restype, argtypes)

@@ -22,6 +22,7 @@ struct smc_ctx {
   int cv_order = 2, cv_centre = 0;  // control-variate order; re-centring (0 none, 1, 2)
   int multinomial = 0;              // resampling scheme (0 systematic, 1 multinomial)
   int rw = 0;                       // theta move: 0 HMC, 1 random-walk Metropolis
+  double eps_jitter = 0.3;          // HMC step-size jitter (0: fixed step)
   int grid_points = 0;              // > 0: grid temperature rule with this many points
   double grid_decades = 16.0;
   int64_t n = 0;
@@ -85,6 +86,7 @@ struct smc_ctx {
   int full_data = 0;
   void *fm_thp = nullptr, *fm_rho = nullptr, *fm_g = nullptr;
   double *fm_ell = nullptr, *fm_h0 = nullptr;
+  float *fm_eps = nullptr;  // per-particle step sizes of the current move
   cudaGraphExec_t fm_graph = nullptr;
   int64_t fm_launches = 0;
   // host mirrors
@@ -268,6 +270,7 @@ EstArgs base_args(const smc_ctx *c) {
   a.A_dev = c->cv_centre ? c->A_d : nullptr;
   a.cv_order = c->cv_order;
   a.rw = c->rw;
+  a.eps_jitter = c->eps_jitter;
   a.B_ct = c->B_ct;
   a.C_ct = c->C_ct;
   a.tb_ct = c->tb_ct;
@@ -542,6 +545,7 @@ int init_impl(smc_ctx *c, const smc_problem *P, const smc_config *cfg, const dou
     ALLOC(c, c->fm_g, cts * Np);
     ALLOC(c, c->fm_ell, sizeof(double) * c->N);
     ALLOC(c, c->fm_h0, sizeof(double) * c->N);
+    ALLOC(c, c->fm_eps, sizeof(float) * c->N);
   }
   ALLOC(c, c->theta, cts * Np);
   ALLOC(c, c->theta_alt, cts * Np);
@@ -678,6 +682,12 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
     return SMC_ERR_ARG;
   }
   c->rw = cfg->theta_move;
+  if (!(cfg->eps_jitter < 0.9)) {
+    g_init_error = "eps_jitter must be below 0.9 (0: 0.3; negative: a fixed step size)";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  c->eps_jitter = cfg->eps_jitter == 0.0 ? 0.3 : (cfg->eps_jitter < 0.0 ? 0.0 : cfg->eps_jitter);
   c->grid_points = cfg->grid_points;
   c->grid_decades = cfg->grid_decades > 0.0 ? cfg->grid_decades : 16.0;
   c->full_data = cfg->full_data ? 1 : 0;
@@ -1102,9 +1112,13 @@ static int full_leapfrog(smc_ctx *c) {
   int r = full_eval(c, N, c->fm_thp, 0.0, adev, nullptr, c->fm_g);
   if (r) return r;
   for (int l = 0; l < c->L; ++l) {
-    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->st, 1, c->stream), 1);
+    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->fm_eps, 1,
+                             c->stream),
+           1);
     if ((r = full_eval(c, N, c->fm_thp, 0.0, adev, c->fm_ell, c->fm_g))) return r;
-    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->st, 0, c->stream), 1);
+    LAUNCH(c, full_move_kick(N, p, c->fm_thp, c->fm_rho, c->fm_g, c->Sigma_ct, c->fm_eps, 0,
+                             c->stream),
+           1);
   }
   return SMC_OK;
 }
@@ -1116,7 +1130,7 @@ static int full_moves(smc_ctx *c, int R) {
     LAUNCH(c,
            full_move_begin(N, p, c->theta, c->fm_thp, c->fm_rho, c->Linv_ct, c->Sigma_ct, c->mu_ct,
                            c->ivar_ct, c->ell, c->seed, c->stage, c->stage_dev, move, c->st,
-                           c->fm_h0, c->stream),
+                           c->fm_h0, c->eps_jitter, c->fm_eps, c->stream),
            1);
     if (c->capturing) {
       int r = full_leapfrog(c);

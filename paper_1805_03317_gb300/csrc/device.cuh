@@ -62,6 +62,16 @@ __device__ __forceinline__ int64_t draw_index(uint64_t r, uint64_t n) {
 __device__ __forceinline__ double draw_uniform(uint64_t r) {
   return (double)(r >> 11) * 0x1.0p-53;
 }
+// Particle i's HMC step size: eps times a uniform on [1 - jitter, 1 + jitter] taken from the
+// second 64-bit word of its theta-MH block (the first is the MH uniform). A random step size
+// breaks the near-periodic trajectories that a fixed eps L gives on near-Gaussian targets.
+__device__ __forceinline__ double jittered_eps(double eps, double jitter, uint64_t seed,
+                                               uint32_t sm, uint32_t i) {
+  if (!(jitter > 0.0)) return eps;
+  const double U = draw_uniform(Stream(seed, kMhTheta, sm, i).draw(1));
+  return eps * (1.0 - jitter + 2.0 * jitter * U);
+}
+
 // Box-Muller (1958) on one Philox block: u1 in (0,1], u2 in [0,1).
 __device__ __forceinline__ void box_muller(uint64_t ra, uint64_t rb, double &z0, double &z1) {
   const double u1 = (double)((ra >> 11) + 1) * 0x1.0p-53;

@@ -696,7 +696,9 @@ __device__ __forceinline__ void hmc_body(const EstArgs &a, int i, unsigned char 
   WarpSmem<CT> sm(reinterpret_cast<CT *>(wbase + WarpEval<XT, T, CPL, U, K>::RING), p, slots);
   const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const double temp = a.st->a;
-  const CT eps = (CT)a.st->eps;
+  // random walk: the proposal scale itself; HMC: the particle's (jittered) step size
+  const CT eps = a.rw ? (CT)a.st->eps
+                      : (CT)jittered_eps(a.st->eps, a.eps_jitter, a.seed, smv, (uint32_t)i);
   CT *th_g = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
   for (int c = W.lane; c < p; c += 32) sm.th[c] = th_g[c];
   // momentum: z ~ N(0, I) in sm.v, rho = Linv' z  (rho_r = sum_c Linv[c, r] z_c, c >= r)

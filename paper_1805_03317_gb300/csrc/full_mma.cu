@@ -550,11 +550,14 @@ __device__ __forceinline__ double log_prior_cols(const float *th, const float *m
 __global__ void k_fm_begin(int N, int p, const float *theta, float *thp, float *rho,
                            const float *Linv, const float *Sigma, const float *mu,
                            const float *ivar, const double *ell, uint64_t seed, int stage,
-                           int stage_dev, int move, const DevState *st, double *h0) {
+                           int stage_dev, int move, const DevState *st, double *h0,
+                           double jitter, float *eps_out) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= N) return;
-  const Stream smom(seed, kMomentum, stage_move(stage_dev ? st->stage : stage, move), (uint32_t)i);
+  const uint32_t sm = stage_move(stage_dev ? st->stage : stage, move);
+  if (lane == 0) eps_out[i] = (float)jittered_eps(st->eps, jitter, seed, sm, (uint32_t)i);
+  const Stream smom(seed, kMomentum, sm, (uint32_t)i);
   Cols z{0.f, 0.f};
   if (lane < p) z.v0 = (float)stream_normal(smom, (uint32_t)lane);
   if (lane + 32 < p) z.v1 = (float)stream_normal(smom, (uint32_t)(lane + 32));
@@ -573,13 +576,14 @@ __global__ void k_fm_begin(int N, int p, const float *theta, float *thp, float *
   if (lane == 0) h0[i] = -(st->a * ell[i] + lp) + kin;
 }
 
-// rho += eps/2 g; then, if drift, theta += eps Sigma rho.
+// rho += eps_i/2 g; then, if drift, theta += eps_i Sigma rho (eps_i: the particle's step size,
+// written by k_fm_begin).
 __global__ void k_fm_kick(int N, int p, float *thp, float *rho, const float *g, const float *Sigma,
-                          const DevState *st, int drift) {
+                          const float *eps_i, int drift) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= N) return;
-  const float eps = (float)st->eps;
+  const float eps = eps_i[i];
   float *r = rho + (int64_t)i * p;
   const float *gi = g + (int64_t)i * p;
   Cols x{0.f, 0.f};
@@ -626,18 +630,18 @@ __global__ void k_fm_accept(int N, int p, float *theta, const float *thp, const 
 int full_move_begin(int N, int p, const void *theta, void *thp, void *rho, const void *Linv,
                     const void *Sigma, const void *mu, const void *ivar, const double *ell,
                     uint64_t seed, int stage, int stage_dev, int move, const DevState *st,
-                    double *h0, cudaStream_t s) {
+                    double *h0, double jitter, float *eps_out, cudaStream_t s) {
   k_fm_begin<<<(N * 32 + 255) / 256, 256, 0, s>>>(
       N, p, (const float *)theta, (float *)thp, (float *)rho, (const float *)Linv,
       (const float *)Sigma, (const float *)mu, (const float *)ivar, ell, seed, stage, stage_dev,
-      move, st, h0);
+      move, st, h0, jitter, eps_out);
   return (int)cudaGetLastError();
 }
 
 int full_move_kick(int N, int p, void *thp, void *rho, const void *g, const void *Sigma,
-                   const DevState *st, int drift, cudaStream_t s) {
+                   const float *eps_i, int drift, cudaStream_t s) {
   k_fm_kick<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, p, (float *)thp, (float *)rho,
-                                                   (const float *)g, (const float *)Sigma, st,
+                                                   (const float *)g, (const float *)Sigma, eps_i,
                                                    drift);
   return (int)cudaGetLastError();
 }

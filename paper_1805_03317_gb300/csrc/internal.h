@@ -71,6 +71,7 @@ struct EstArgs {
   void *dsave, *rsave;
   int stage_dev;          // 1: the stage index comes from st->stage (graph replays), else stage
   int rw;                 // theta move: 0 = HMC (L leapfrog steps), 1 = random-walk Metropolis
+  double eps_jitter;      // HMC: particle step sizes uniform on eps [1 - j, 1 + j] (0: fixed)
   int cv_order;           // 1: first-order control variates (row increments without the
                           //    second-order term; C is zero in the state-type copy), else 2
   const double *g_ell, *g_sig2;
@@ -178,12 +179,14 @@ int full_loglik(const void *Xp, int64_t n, int p, int S, int Yo, int fam, double
                 int sms, cudaStream_t s);
 // Full-data HMC move pieces (state type float, p <= 64): momentum and H0; half kick (+ drift);
 // Metropolis-Hastings with the exact log-likelihood at the end point.
+// full_move_begin also writes each particle's (jittered) step size to eps_out [N], which the
+// kicks of its trajectory read.
 int full_move_begin(int N, int p, const void *theta, void *thp, void *rho, const void *Linv,
                     const void *Sigma, const void *mu, const void *ivar, const double *ell,
                     uint64_t seed, int stage, int stage_dev, int move, const DevState *st,
-                    double *h0, cudaStream_t s);
+                    double *h0, double jitter, float *eps_out, cudaStream_t s);
 int full_move_kick(int N, int p, void *thp, void *rho, const void *g, const void *Sigma,
-                   const DevState *st, int drift, cudaStream_t s);
+                   const float *eps_i, int drift, cudaStream_t s);
 int full_move_accept(int N, int p, void *theta, const void *thp, const void *rho,
                      const void *Sigma, const void *mu, const void *ivar, double *ell,
                      const double *ell_new, const double *h0, uint64_t seed, int stage,

@@ -95,7 +95,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   CT *Cs = reinterpret_cast<CT *>(smem + P.off_mat);  // [CPL, CPL] zero-padded
   CT *Sgs = Cs + CPL * CPL;                            // [CPL, CPL] zero-padded
   const double temp = a.st->a;
-  const CT eps = (CT)a.st->eps;
   const CT inv_s2 = (CT)a.inv_s2;
   const double nm = (double)a.n / (double)m, inv_m = 1.0 / (double)m;
   const CT ta = (CT)temp, ta2 = (CT)(temp * temp * nm * nm), tnm = (CT)(temp * nm);
@@ -140,6 +139,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     cp_async_wait_all();
     // 2. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
     CT *thg = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
+    const CT eps = (CT)jittered_eps(a.st->eps, a.eps_jitter, a.seed, smv, (uint32_t)i);
     if (warp == 0) {
       const Stream smom(a.seed, kMomentum, smv, (uint32_t)i);
       CT z = col ? (CT)stream_normal(smom, (uint32_t)lane) : CT(0);

@@ -62,7 +62,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
              cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
              resampling: str = "systematic", grid_points: int = 0, grid_decades: float = 0.0,
-             theta_move: str = "hmc", stream=None) -> Context:
+             theta_move: str = "hmc", eps_jitter: float = 0.0, stream=None) -> Context:
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -78,7 +78,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
                     search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
                     int(cv_order), int(cv_centre), 1 if full_data else 0,
                     RESAMPLING[resampling], int(grid_points), float(grid_decades),
-                    THETA_MOVE[theta_move])
+                    THETA_MOVE[theta_move], float(eps_jitter))
     tb = None
     tb_ptr = None
     if theta_bar is not None:
@@ -421,7 +421,8 @@ def smc_batch_init(problems, stream=None) -> Batch:
                             int(d.get("cv_order", 2)), int(d.get("cv_centre", 0)), 0,
                             RESAMPLING[d.get("resampling", "systematic")],
                             int(d.get("grid_points", 0)), float(d.get("grid_decades", 0.0)),
-                            THETA_MOVE[d.get("theta_move", "hmc")])
+                            THETA_MOVE[d.get("theta_move", "hmc")],
+                            float(d.get("eps_jitter", 0.0)))
         keep += [y, pm, pv]
         meta.append((d["N"], d["m"], d["G"], p, n, X.device))
     handle = ctypes.c_void_p()
