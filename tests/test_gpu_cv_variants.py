@@ -465,3 +465,51 @@ def test_batch_with_mixed_options_matches_single_problems():
         assert S().smc_get_status(cb) == S().smc_get_status(c), q
         S().smc_free(c)
     S().smc_batch_free(b)
+
+
+@pytest.mark.parametrize("scheme", ["systematic", "multinomial"])
+def test_resampling_edge_weights(scheme):
+    """One-hot weights send every offspring to that particle; a weight vector with tiny entries
+    (below 2^-40, quantised to zero) never selects them."""
+    N = 97
+    wl = _wl("logistic", "f64", N=N, m=9, G=3)
+    prob, ctx = make_pair(wl, resampling=scheme)
+    rng = np.random.default_rng(2)
+    th = prob.theta_bar + 0.1 * rng.standard_normal((N, wl.p))
+    u = rng.integers(0, wl.n, size=(N, wl.m)).astype(np.int64)
+    for W in (np.eye(N)[41], np.where(np.arange(N) % 3 == 0, 1.0, 1e-14)):
+        W = W / W.sum()
+        S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                              torch.from_numpy(W).to(DEV))
+        S().smc_set_scalars(ctx, 5, 0.5, 0.3, 0.0)
+        anc = torch.empty(N, dtype=torch.int32, device=DEV)
+        S().smc_resample(ctx, anc)
+        a = anc.cpu().numpy()
+        if scheme == "multinomial":
+            ref = O.resample_multinomial(W, O.multinomial_uniforms(wl.seed, 5, N))
+        else:
+            ref = O.resample(W, O.uniform(O.r64(wl.seed, O.TAG_RESAMPLE, O.stage_move(5, 0), 0, 0)))
+        np.testing.assert_array_equal(a, ref)
+        assert np.all(W[a] > 1e-12)
+    S().smc_free(ctx)
+
+
+def test_grid_rule_with_two_points_and_full_step():
+    """grid_points = 2: the candidates are (1 - a) 10^-E and 1 - a; the rule takes the one whose
+    ESS is closer to the target, as the oracle does."""
+    wl = _wl("logistic", "f64", N=300, m=40, G=4)
+    prob, ctx = make_pair(wl, grid_points=2, grid_decades=3.0, ess_frac=0.8)
+    rng = np.random.default_rng(5)
+    th = prob.theta_bar + 0.05 * rng.standard_normal((wl.N, wl.p))
+    u = rng.integers(0, wl.n, size=(wl.N, wl.m)).astype(np.int64)
+    W = np.full(wl.N, 1.0 / wl.N)
+    S().smc_set_particles(ctx, torch.from_numpy(th).to(DEV), torch.from_numpy(u).to(DEV),
+                          torch.from_numpy(W).to(DEV))
+    S().smc_set_scalars(ctx, 3, 0.4, 0.3, 0.0)
+    a_new, _, ess = S().smc_reweight(ctx)
+    ref = O.loglik_batch(prob, wl.m, wl.G, th, u, grad=False)
+    ra, _, _, _, ress = O.reweight_grid(np.log(W), ref["ell"], ref["sigma2"], 0.4, 0.8, 2, 3.0)
+    assert a_new == pytest.approx(ra, rel=1e-12)
+    assert a_new in (pytest.approx(1.0), pytest.approx(0.4 + 0.6e-3, rel=1e-12))
+    assert ess == pytest.approx(ress, rel=1e-9)
+    S().smc_free(ctx)
