@@ -490,10 +490,15 @@ def gam_leg(S, dev, hbm, tile_hint=0, n=10_000_000):
     return out
 
 
-def e2e_stages(S, ctx, wl, R, steps):
-    """Same stages through the public API with the particle state resident on the host: each step
-    copies theta, u, W in from pinned host memory and the new cloud back out."""
+def e2e_stages(S, ctx, wl, R, steps, warmup):
+    """The timed region's stages again, from a fresh context with the same seed (so the same
+    stage range as the device-timed value: warm-up stages untimed, then `steps` stages), through
+    the public API with the particle state resident on the host: each timed step copies theta, u,
+    W in from pinned host memory (smc_set_particles, which also re-estimates the cache) and the
+    new cloud back out."""
     import torch
+    for _ in range(warmup):
+        run_stage(S, ctx, R)
     th, u, W = S.smc_get_particles(ctx)
     th_h = th.cpu().pin_memory()
     u_h = u.cpu().pin_memory()
@@ -550,9 +555,11 @@ def gpu_arm(args):
     bytes_launch = units * bytes_row
     shares = {g: round(v[1] / ms, 4) for g, v in prof.items() if v[0]}
 
-    e2e_wall, bi, bo = e2e_stages(S, ctx, wl, R, max(3, min(args.steps, 20)))
-    e2e_value = per_stage * max(3, min(args.steps, 20)) * world / e2e_wall
     S.smc_free(ctx)
+    ctxe, _ = make_ctx(S, wl, dev, seed_offset=rank)
+    e2e_wall, bi, bo = e2e_stages(S, ctxe, wl, R, args.steps, args.warmup)
+    e2e_value = per_stage * args.steps * world / e2e_wall
+    S.smc_free(ctxe)
 
     # the same stages (fresh context, same seed) with every stage replayed as one CUDA graph
     graph = None
