@@ -148,12 +148,17 @@ const char *smc_last_error(const smc_ctx *ctx);
 /* ------------------------------------------------------------------------------------------- */
 
 /* Steps (a)-(d): advance the stage counter; choose the next temperature a_s so that the ESS of the
- * new weights stays at ess_frac*N (Sec. 2.2; K-ary refinement of a bracket, Algorithm 2 (b));
+ * new weights stays at ess_frac*N (Sec. 2.2; K-ary refinement of a bracket, Algorithm 2 (b); or,
+ * with smc_config.grid_points > 0, the grid point whose ESS is closest to ess_frac*N, Sec. 2.3);
  * reweight with w_i = W_i exp((a_s - a_{s-1}) l_hat_i - (a_s^2 - a_{s-1}^2) sigma2_hat_i / 2)
  * (Sec. 3.3) and normalise in FP64; accumulate log Z_s/Z_{s-1} (Sec. 3.5); form the weighted
  * particle covariance Sigma and its Cholesky factor for the HMC mass matrix H = Sigma^{-1}
  * (jitter 1e-10 tr(Sigma)/p, x10 per retry, up to 12 retries; if Sigma stays singular, e.g. for a
  * single particle, the previous stage's mass matrix is kept; at the start it is the prior covariance).
+ * With smc_config.cv_centre = 1 the control variates then move to the reweighted particle mean
+ * (Algorithm 2 (d)); with cv_centre = 2 they move to the current weighted mean before the
+ * reweighting. Either way A, B, C, the row constants and every particle's cached l_hat and
+ * sigma2_hat are recomputed, stream-ordered (no host synchronisation).
  * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS. */
 int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
 
@@ -166,8 +171,10 @@ int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
 int smc_resample(smc_ctx *ctx, int32_t *ancestors);
 
 /* Step (f): R Markov moves of Algorithm 1 at the current temperature, each a block pseudo-marginal
- * update of u (Eq. acc_prop_u) followed by an HMC move of theta given u. Afterwards the leapfrog
- * step adapts: eps *= clip(exp(theta_acceptance - 0.65), 0.5, 2).
+ * update of u (Eq. acc_prop_u) followed by an HMC move of theta given u (each particle's
+ * trajectory with its jittered step, smc_config.eps_jitter) or, with theta_move = 1, a random-walk
+ * Metropolis move. Afterwards the step adapts: eps *= clip(exp(theta_acceptance - t), 0.5, 2),
+ * t = 0.65 for HMC and 0.234 for the random walk.
  * Host outputs (may be NULL): acceptance rates of the u and theta updates over these R moves. */
 int smc_move(smc_ctx *ctx, int32_t R, double *acc_u, double *acc_theta);
 
