@@ -52,3 +52,31 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_abi, "_lib", None)
     with pytest.raises(ImportError):
         _abi.load()
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of `fields` of `struct` as the C compiler lays out include/subsmc.h."""
+    import subprocess
+    import tempfile
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = ('#include <stdio.h>\n#include <stddef.h>\n#include "subsmc.h"\nint main(void) {\n'
+           + "\n".join(lines) + "\nreturn 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("struct", ["smc_problem", "smc_config"])
+def test_binding_structs_match_the_c_layout(struct):
+    """The ctypes mirrors of the configuration structs have the C sizes and field offsets (a
+    field added on one side only would silently shift every later field)."""
+    from paper_1805_03317_gb300 import _abi
+    cls = {"smc_problem": _abi.SmcProblem, "smc_config": _abi.SmcConfig}[struct]
+    names = [f[0] for f in cls._fields_]
+    size, offsets = _c_layout(struct, names)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, n).offset for n in names] == offsets
