@@ -80,3 +80,15 @@ def test_binding_structs_match_the_c_layout(struct):
     size, offsets = _c_layout(struct, names)
     assert ctypes.sizeof(cls) == size
     assert [getattr(cls, n).offset for n in names] == offsets
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every binding signature passes as many arguments as the header's prototype declares."""
+    from paper_1805_03317_gb300 import _abi
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "subsmc.h")).read(),
+                 flags=re.S)
+    protos = dict(re.findall(r"([a-z_0-9]+)\s*\(([^;{)]*)\)\s*;", src))
+    for name, (_, argtypes) in _abi.SIGNATURES.items():
+        params = protos[name].strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(argtypes) == n, (name, len(argtypes), n)
