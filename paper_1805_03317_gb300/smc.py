@@ -323,6 +323,17 @@ def smc_profile_read(ctx: Context, group) -> tuple[int, float]:
 # ------------------------------------------------------------------------------------------------
 # Convenience wrapper
 # ------------------------------------------------------------------------------------------------
+def stage_log_line(rec: dict, status: dict) -> str:
+    """One JSON line for a stage: the stage record (temperature, ESS, log-evidence increment,
+    acceptance rates, moves) with the context's status after it (stage index, log Z, step)."""
+    import json
+    out = {"stage": int(status["stage"]), "a": float(rec["a"]), "ess": float(rec["ess"]),
+           "log_z_inc": float(rec["log_z_inc"]), "log_z": float(status["log_z"]),
+           "acc_u": float(rec["acc_u"]), "acc_theta": float(rec["acc_theta"]),
+           "moves": int(rec["R"]), "eps": float(status["eps"])}
+    return json.dumps(out)
+
+
 class SubsampledSMC:
     """Likelihood-annealed subsampling SMC (Algorithm 2) on one GPU."""
 
@@ -343,9 +354,18 @@ class SubsampledSMC:
         self.history.append(rec)
         return rec
 
-    def run(self, R: int, max_stages: int = 1000, adaptive=None) -> dict:
-        while smc_get_status(self.ctx)["a"] < 1.0 and len(self.history) < max_stages:
-            self.stage(R, adaptive)
+    def run(self, R: int, max_stages: int = 1000, adaptive=None, log_path=None) -> dict:
+        """Stages until a = 1. log_path: append one JSON line per stage (stage index, temperature,
+        ESS, log-evidence increment and running total, acceptance rates, moves, step size)."""
+        log = open(log_path, "a") if log_path else None
+        try:
+            while smc_get_status(self.ctx)["a"] < 1.0 and len(self.history) < max_stages:
+                rec = self.stage(R, adaptive)
+                if log is not None:
+                    log.write(stage_log_line(rec, smc_get_status(self.ctx)) + "\n")
+        finally:
+            if log is not None:
+                log.close()
         return smc_get_status(self.ctx)
 
     def particles(self):

@@ -92,3 +92,14 @@ def test_binding_argument_counts_match_the_header():
         params = protos[name].strip()
         n = 0 if params in ("", "void") else params.count(",") + 1
         assert len(argtypes) == n, (name, len(argtypes), n)
+
+
+def test_stage_log_line_is_one_json_record():
+    import json
+    from paper_1805_03317_gb300.smc import stage_log_line
+    rec = {"a": 0.25, "log_z_inc": -3.5, "ess": 2048.0, "acc_u": 0.4, "acc_theta": 0.7, "R": 5}
+    line = stage_log_line(rec, {"stage": 7, "a": 0.25, "log_z": -12.0, "eps": 0.1})
+    assert "\n" not in line
+    d = json.loads(line)
+    assert d == {"stage": 7, "a": 0.25, "ess": 2048.0, "log_z_inc": -3.5, "log_z": -12.0,
+                 "acc_u": 0.4, "acc_theta": 0.7, "moves": 5, "eps": 0.1}
