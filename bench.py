@@ -208,10 +208,22 @@ def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist, graph=False):
     prof = {g: S.smc_profile_read(ctx, g) for g in S.smc.PROFILE_GROUPS}
     S.smc_profile_enable(ctx, False)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     return ms, wall, launches, prof
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The largest of every rank's value (the timing rule: the job's time is its slowest rank)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank processes units_per_step per step (replicas, weak scaling);
+    ms is the slowest rank's time for the steps."""
+    return units_per_step * steps * world / (ms / 1e3)
 
 
 def full_run(S, wl, dev, R, max_stages=400, adaptive=None, **kw):
@@ -538,7 +550,7 @@ def gpu_arm(args):
     ms, wall, launches, prof = timed_stages(S, ctx, wl, R, args.steps, args.warmup, flush, dist)
     clocks = sampler.stop()
     per_stage = grad_evals_per_stage(wl, R)
-    value = per_stage * args.steps * world / (ms / 1e3)
+    value = job_throughput(per_stage, args.steps, world, ms)
 
     # roofline of the dominant kernel, the HMC trajectory with the subsample resident in shared
     # memory. It reads X once per trajectory and then runs L+1 estimator passes out of shared
