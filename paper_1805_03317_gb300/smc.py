@@ -63,6 +63,19 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
              resampling: str = "systematic", grid_points: int = 0, grid_decades: float = 0.0,
              theta_move: str = "hmc", eps_jitter: float = 0.0, stream=None) -> Context:
+    """Create a context (Algorithm 2 step 1) on X's device; the fields mirror smc_problem and
+    smc_config in include/subsmc.h.
+
+    X: [n, p] CUDA tensor (float64, float32 or bfloat16 storage), y: [n]. family: "logistic",
+    "probit", "poisson", "gaussian" (known sd noise_sigma) or "student_t" (dof, scale
+    noise_sigma). N particles, subsample size m, G blocks of u, L leapfrog steps, seed of the
+    counter-based random streams, ESS target ess_frac * N. theta_bar: control-variate centre
+    (None: the posterior mode by Newton's method on the device). Options of the paper: cv_order
+    (2 or 1), cv_centre (0 fixed, 1 re-centred after each reweighting as in Algorithm 2, 2 before
+    it), resampling ("systematic" or "multinomial"), grid_points / grid_decades (the grid
+    temperature rule), theta_move ("hmc" or "rw"), eps_jitter (0: 0.3; negative: fixed step),
+    full_data (the full-data comparison method). Tuning: search_k, search_rounds, eps0, tile_hint,
+    hmc_kernel, cv_kernel (0 = automatic)."""
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
