@@ -3,8 +3,9 @@
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this module. It compiles ``smc_oracle.c`` with the host C compiler into ``oracle/_build`` and
 wraps it with ctypes; the SMC driver loop below follows Algorithm 2 of the paper step by step
-(reweight with an adaptive temperature, weighted moments and mass matrix, resample, R moves of
-Algorithm 1), calling the C routines for each step. Nothing here touches the CUDA library.
+(reweight with an adaptive temperature, weighted moments and mass matrix, re-centring of the
+control variates when asked, resample, R moves of Algorithm 1 or moves until the cloud has
+decorrelated), calling the C routines for each step. Nothing here touches the CUDA library.
 """
 from __future__ import annotations
 

@@ -15,7 +15,9 @@
  *   - the annealed likelihood estimator and the extended target        (Sec. 3.1, Eqs. tempered_likelihood_estimator,
  *                                                                       extended_target_at_sequence_p)
  *   - the block pseudo-marginal update of u and its MH ratio           (Algorithm 1 step 1, Eq. acc_prop_u)
- *   - the HMC move of theta given u                                    (Algorithm 1 step 2)
+ *   - the HMC move of theta given u, or a random-walk move             (Algorithm 1 step 2; Sec. 4.2)
+ *   - first-order control variates                                     (Sec. 4, Experiment 4)
+ *   - the Student-t regression family                                  (Sec. 4.3)
  *   - reweighting, ESS, tempering search, log marginal likelihood      (Sec. 2.2-2.3, Sec. 3.3, Sec. 3.5, Algorithm 2)
  *   - weighted moments / mass matrix and resampling                    (Algorithm 2 steps (d)-(e))
  *
@@ -31,6 +33,9 @@
  *     multinomial scheme is the alternative, on the same integer weights.
  *   - the tempering increment is found by a K-ary refinement of a bracket (K=2 is bisection), or
  *     by the paper's grid rule on a geometric grid of increments.
+ *   - each particle's HMC step is eps times a uniform on [1 - j, 1 + j] (j = 0.3 by default), drawn
+ *     from the second word of its theta-MH Philox block; the random-walk scale is eps itself.
+ *   - the Newton search for the posterior mode damps a Hessian that is not negative definite.
  *
  * Parity status per function: every exported function is pinned by the CPU tests (brute force,
  * enumeration, closed forms, published Philox vectors); see the test files.
