@@ -766,3 +766,68 @@ def test_rw_smc_recovers_conjugate_posterior():
     sd = np.sqrt(np.diag(S))
     assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
     assert abs(np.mean(errs)) < 0.15
+
+
+def _prior_only_case(seed=17, N=40):
+    prob = tiny_problem("logistic", n=30, p=3, seed=6)
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((3, 3))
+    Sigma = A @ A.T + 0.5 * np.eye(3)
+    Lc = np.linalg.cholesky(Sigma)
+    th = prob.prior_mean + rng.standard_normal((N, 3)) * 2.0
+    us = rng.integers(0, prob.n, size=(N, 4)).astype(np.int64)
+    return prob, Sigma, Lc, th, us
+
+
+def _log_prior(t, prob):
+    return float(np.sum(-0.5 * (t - prob.prior_mean) ** 2 / prob.prior_var
+                        - 0.5 * np.log(2 * np.pi * prob.prior_var)))
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.3])
+def test_hmc_move_at_zero_temperature_matches_a_direct_leapfrog(jitter):
+    """At a = 0 the target is the prior alone, so the whole HMC move can be rebuilt in numpy from
+    its definition: momentum rho = Lc^-T z (z the momentum stream's normals), the particle's step
+    eps (1 - j + 2 j U) with U its theta-MH block's second word, L leapfrog steps under the
+    prior's force, H = -log p(theta) + rho' Sigma rho / 2, accept when log U0 < H0 - H1 (U0 the
+    first word). Accept decisions and end points agree with the oracle's move."""
+    prob, Sigma, Lc, th, us = _prior_only_case()
+    seed, stage, move, eps, L = 23, 4, 1, 1.2, 7
+    sm = O.stage_move(stage, move)
+    th_o = th.copy()
+    acc = O.hmc_move(prob, 4, 2, seed, stage, move, 0.0, eps, L, Sigma, Lc, th_o, us,
+                     jitter=jitter)
+    for i in range(th.shape[0]):
+        z = np.array([O.normal(seed, O.TAG_MOMENTUM, sm, i, c) for c in range(3)])
+        rho = np.linalg.solve(Lc.T, z)
+        e = eps
+        if jitter > 0:
+            e = eps * (1 - jitter + 2 * jitter * O.uniform(O.r64(seed, O.TAG_MH_THETA, sm, i, 1)))
+        t = th[i].copy()
+        force = lambda x: -(x - prob.prior_mean) / prob.prior_var
+        H0 = -_log_prior(t, prob) + 0.5 * rho @ Sigma @ rho
+        for _ in range(L):
+            rho = rho + 0.5 * e * force(t)
+            t = t + e * (Sigma @ rho)
+            rho = rho + 0.5 * e * force(t)
+        H1 = -_log_prior(t, prob) + 0.5 * rho @ Sigma @ rho
+        ok = math.log(O.uniform(O.r64(seed, O.TAG_MH_THETA, sm, i, 0))) < H0 - H1
+        assert bool(acc[i]) == ok, i
+        np.testing.assert_allclose(th_o[i], t if ok else th[i], rtol=1e-12, atol=1e-12)
+    assert 0 < acc.sum() < th.shape[0]  # both outcomes are exercised at this step
+
+
+def test_rw_move_at_zero_temperature_matches_its_definition():
+    prob, Sigma, Lc, th, us = _prior_only_case(seed=3)
+    seed, stage, move, eps = 31, 2, 0, 1.3
+    sm = O.stage_move(stage, move)
+    th_o = th.copy()
+    acc = O.rw_move(prob, 4, 2, seed, stage, move, 0.0, eps, Lc, th_o, us)
+    for i in range(th.shape[0]):
+        z = np.array([O.normal(seed, O.TAG_MOMENTUM, sm, i, c) for c in range(3)])
+        t = th[i] + eps * Lc @ z
+        ok = (math.log(O.uniform(O.r64(seed, O.TAG_MH_THETA, sm, i, 0)))
+              < _log_prior(t, prob) - _log_prior(th[i], prob))
+        assert bool(acc[i]) == ok, i
+        np.testing.assert_allclose(th_o[i], t if ok else th[i], rtol=1e-12, atol=1e-12)
+    assert 0 < acc.sum() < th.shape[0]
