@@ -831,3 +831,19 @@ def test_rw_move_at_zero_temperature_matches_its_definition():
         assert bool(acc[i]) == ok, i
         np.testing.assert_allclose(th_o[i], t if ok else th[i], rtol=1e-12, atol=1e-12)
     assert 0 < acc.sum() < th.shape[0]
+
+
+def test_initial_particles_follow_the_prior_and_p_of_u():
+    """Algorithm 2 step 1: theta ~ N(prior mean, diag(prior var)) and u iid uniform on {0..n-1}."""
+    N, p, m, n = 20000, 3, 6, 17
+    mu, var = np.array([0.5, -2.0, 0.0]), np.array([0.25, 4.0, 10.0])
+    th, us = O.init_particles(5, N, p, m, n, mu, var)
+    se = np.sqrt(var / N)
+    assert np.all(np.abs(th.mean(axis=0) - mu) < 5 * se)
+    assert np.all(np.abs(th.var(axis=0) / var - 1.0) < 5 * math.sqrt(2.0 / N))
+    assert np.abs(np.corrcoef(th.T)[np.triu_indices(p, 1)]).max() < 5 / math.sqrt(N)
+    counts = np.bincount(us.ravel(), minlength=n)
+    assert us.min() >= 0 and us.max() < n
+    assert stats.chisquare(counts).pvalue > 1e-4
+    # different particles and different slots draw independently
+    assert abs(np.corrcoef(us[:, 0], us[:, 1])[0, 1]) < 5 / math.sqrt(N)
