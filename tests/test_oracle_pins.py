@@ -847,3 +847,20 @@ def test_initial_particles_follow_the_prior_and_p_of_u():
     assert stats.chisquare(counts).pvalue > 1e-4
     # different particles and different slots draw independently
     assert abs(np.corrcoef(us[:, 0], us[:, 1])[0, 1]) < 5 / math.sqrt(N)
+
+
+def test_singular_particle_covariance_gets_the_documented_jitter():
+    """A cloud on a line has a singular covariance: the diagonal receives 1e-10 tr/p, times 10
+    per retry, cumulatively, until the Cholesky factorisation succeeds."""
+    rng = np.random.default_rng(4)
+    N, p = 200, 3
+    t = rng.standard_normal(N)
+    th = np.outer(t, [1.0, -2.0, 0.5]) + np.array([0.3, 0.1, -0.2])
+    W = np.full(N, 1.0 / N)
+    mean, S, Lc, rc = O.moments(W, th)
+    S0 = np.cov(th.T, aweights=W, ddof=0)
+    assert rc >= 1
+    jit0 = 1e-10 * np.trace(S0) / p
+    added = jit0 * sum(10.0 ** k for k in range(rc))
+    np.testing.assert_allclose(S - S0, added * np.eye(p), rtol=1e-6, atol=1e-15)
+    np.testing.assert_allclose(Lc @ Lc.T, S, rtol=1e-9, atol=1e-12 * np.abs(S).max())
