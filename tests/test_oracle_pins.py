@@ -902,3 +902,20 @@ def test_smc_log_marginal_on_the_plain_logistic_workload_against_importance_samp
         errs.append(st.log_z - ref)
     assert abs(np.mean(errs)) < 0.15, errs
     assert np.max(np.abs(errs)) < 0.7, errs
+
+
+def test_hmc_at_zero_temperature_keeps_prior_draws_prior_distributed():
+    """a = 0: the extended target is the prior (times p(u)); moves started from prior draws leave
+    the cloud distributed as the prior (moments within Monte Carlo error)."""
+    prob = tiny_problem("poisson", n=40, p=3, seed=2)
+    N, m = 6000, 5
+    mu, var = prob.prior_mean, prob.prior_var
+    th, us = O.init_particles(8, N, 3, m, prob.n, mu, var)
+    S = np.diag(var)
+    Lc = np.linalg.cholesky(S)
+    for r in range(3):
+        O.upm_move(prob, m, 1, 8, 1, r, 0.0, th, us)
+        O.hmc_move(prob, m, 1, 8, 1, r, 0.0, 0.8, 6, S, Lc, th, us)
+    z = (th - mu) / np.sqrt(var)
+    assert np.all(np.abs(z.mean(axis=0)) < 5 / math.sqrt(N))
+    assert np.all(np.abs(z.var(axis=0) - 1.0) < 5 * math.sqrt(2.0 / N))
