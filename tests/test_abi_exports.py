@@ -103,3 +103,30 @@ def test_stage_log_line_is_one_json_record():
     d = json.loads(line)
     assert d == {"stage": 7, "a": 0.25, "ess": 2048.0, "log_z_inc": -3.5, "log_z": -12.0,
                  "acc_u": 0.4, "acc_theta": 0.7, "moves": 5, "eps": 0.1}
+
+
+def test_runner_loop_and_stage_log_with_a_fake_context(tmp_path, monkeypatch):
+    """SubsampledSMC.run's host loop (no GPU: the library calls are replaced by fakes): stages
+    until a = 1 and one JSON line per stage in the log."""
+    import json
+    from paper_1805_03317_gb300 import smc
+    state = {"a": 0.0, "stage": 0, "log_z": 0.0, "eps": 0.5}
+
+    def fake_reweight(ctx):
+        state["stage"] += 1
+        state["a"] = min(1.0, state["a"] + 0.4)
+        state["log_z"] += -1.0
+        return state["a"], -1.0, 100.0
+
+    monkeypatch.setattr(smc, "smc_reweight", fake_reweight)
+    monkeypatch.setattr(smc, "smc_resample", lambda ctx: None)
+    monkeypatch.setattr(smc, "smc_move", lambda ctx, R: (0.5, 0.7))
+    monkeypatch.setattr(smc, "smc_get_status", lambda ctx: dict(state))
+    runner = smc.SubsampledSMC.__new__(smc.SubsampledSMC)
+    runner.ctx, runner.history = object(), []
+    log = tmp_path / "stages.jsonl"
+    st = runner.run(3, log_path=str(log))
+    assert st["a"] == 1.0 and len(runner.history) == 3
+    lines = [json.loads(s) for s in log.read_text().splitlines()]
+    assert [d["stage"] for d in lines] == [1, 2, 3] and lines[-1]["log_z"] == -3.0
+    assert all(d["moves"] == 3 for d in lines)
