@@ -4,14 +4,19 @@
 // copy of the data (WarpEval below: 32 rows per sweep, one row owned per lane, covariates split
 // over groups of T lanes). Per row the warp forms D = x'(theta - theta_bar), evaluates the
 // increment-form terms d and r (device.cuh) from the row's stored constants at the centre, and
-// accumulates
-//   sum d, sum d^2                 (per block of u when the block cache is refreshed)
-//   sum r x, sum d r x             (gradient partials, kept in registers)
+// accumulates, with e = d - K for a warp-uniform shift K (the d of the particle's first row),
+//   sum e, sum e^2                 (per block of u when the block cache is refreshed)
+//   sum r x, sum e r x             (gradient partials, kept in registers)
 // which give (Sec. 3.2, Eq. difference_estimator_logl)
-//   l_hat      = A + B'delta + delta'C delta/2 + (n/m) sum d
-//   sigma2_hat = (n^2/m^2) (sum d^2 - (sum d)^2/m)
-//   grad       = a (B + C delta + (n/m) sum r x) - a^2 (n^2/m^2)(sum d r x - dbar sum r x) - (theta-mu)/v
+//   l_hat      = A + B'delta + delta'C delta/2 + (n/m)(sum e + m K)
+//   sigma2_hat = (n^2/m^2) (sum e^2 - (sum e)^2/m)            (clamped at 0)
+//   grad       = a (B + C delta + (n/m) sum r x) - a^2 (n^2/m^2)(sum e r x - ebar sum r x) - (theta-mu)/v
 // The last line is the exact gradient of a*l_hat - a^2/2*sigma2_hat + log p(theta) for fixed u.
+// The shift makes the one-pass variance stable (shifted data, Chan, Golub & LeVeque 1983): far
+// from the centre the d_j share a large mean, and sum d^2 - (sum d)^2/m taken directly would
+// cancel in FP32; sum e^2 - (sum e)^2/m only loses (ebar/sd(d))^2, and ebar is O(sd(d)). Block
+// sums of the cache keep the exact FP64 (sum d, sum d^2) form, rebuilt from the shifted FP32
+// sums per block: sum d = sum e + n_g K, sum d^2 = sum e^2 + 2 K sum e + n_g K^2.
 #pragma once
 
 #include "device.cuh"
@@ -124,12 +129,15 @@ struct WarpEval {
   // over this lane's slots into g1, g2. Returns S = sum d and Q = sum d^2 on every lane; BLOCKS
   // also writes per-block (sum d, sum d^2) of the floor partition of the nrows rows into G blocks
   // to blk_out[2G].
+  // The sums are of e = d - K (returned in Ksh, warp-uniform: the d of row 0), so
+  // Ssum = sum e and Qsum = sum e^2; g2 accumulates e r x. BLOCKS writes the unshifted FP64 block
+  // sums (sum d, sum d^2) rebuilt from the shifted ones.
   template <bool GRAD, bool BLOCKS, int MODE = 0>
   __device__ __forceinline__ void rows(const XT *__restrict__ Xp, int S, int64_t n,
                                        const int32_t *idx, int nrows, int fam, CT inv_s2, CT *g1,
                                        CT *g2, double *blk_out, int G, double &Ssum, double &Qsum,
-                                       DevState *st, const RowIO<CT> &io = RowIO<CT>(),
-                                       int cv1 = 0) const {
+                                       double &Ksh, DevState *st,
+                                       const RowIO<CT> &io = RowIO<CT>(), int cv1 = 0) const {
     const int nsw = (nrows + 31) >> 5;
     // rows past the end copy the last row again (already on chip) and are masked out
     const int klast = nrows > 0 ? idx[nrows - 1] : 0;
@@ -182,9 +190,18 @@ struct WarpEval {
       __syncwarp();
     }
     CT sd = CT(0), sd2 = CT(0);
-    double cs = 0.0, cq = 0.0;  // BLOCKS: sums of the open block cg
+    double cs = 0.0, cq = 0.0;  // BLOCKS: shifted sums of the open block cg
     int cg = -1;
+    CT K = CT(0);               // shift of the sums: d of row 0 (set at sweep 0)
     Ssum = Qsum = 0.0;
+    // close block g: its unshifted FP64 sums from the shifted ones
+    auto close_block = [&](int g) {
+      const double ng = (double)((int)(((int64_t)(g + 1) * nrows) / G) -
+                                 (int)(((int64_t)g * nrows) / G));
+      const double k = (double)K;
+      blk_out[2 * g] = fma(ng, k, cs);
+      blk_out[2 * g + 1] = cq + k * fma(ng, k, 2.0 * cs);
+    };
     // partial x'delta of the group's T rows over this lane's slots, reduce-scattered: the full D of
     // the row this lane owns
     auto phase1 = [&](int b) -> CT {
@@ -223,7 +240,8 @@ struct WarpEval {
         default: row_incr<4, CT>(c, D, inv_s2, d, r); break;
       }
       if (cv1) to_first_order(row_l2_any(fam, c, inv_s2), D, d, r);
-      if (j >= nrows || ((bad >> b) & 1u)) {
+      const bool valid = j < nrows && !((bad >> b) & 1u);
+      if (!valid) {
         d = CT(0);
         r = CT(0);
       }
@@ -233,6 +251,8 @@ struct WarpEval {
           io.rsave[j] = r;
         }
       }
+      if (s == 0) K = __shfl_sync(0xffffffffu, d, 0);  // every lane is here at sweep 0
+      d = valid ? d - K : CT(0);  // from here on d holds e = d - K
       if (BLOCKS) {  // block of row j: largest g with floor(g nrows / G) <= j
         const int r1 = min((s << 5) + 31, nrows - 1);
         const int gA = (int)(((unsigned)((s << 5) + 1) * (unsigned)G - 1u) / (unsigned)nrows);
@@ -243,10 +263,7 @@ struct WarpEval {
           const CT bs = warp_sum(gj == g ? d : CT(0));
           const CT bq = warp_sum(gj == g ? d * d : CT(0));
           if (g != cg) {
-            if (cg >= 0 && lane == 0) {
-              blk_out[2 * cg] = cs;
-              blk_out[2 * cg + 1] = cq;
-            }
+            if (cg >= 0 && lane == 0) close_block(cg);
             cg = g;
             cs = cq = 0.0;
           }
@@ -325,14 +342,12 @@ struct WarpEval {
     }
     cp_async_wait<0>();
     if (BLOCKS) {
-      if (cg >= 0 && lane == 0) {
-        blk_out[2 * cg] = cs;
-        blk_out[2 * cg + 1] = cq;
-      }
+      if (cg >= 0 && lane == 0) close_block(cg);
     } else {
       Ssum = warp_sum((double)sd);
       Qsum = warp_sum((double)sd2);
     }
+    Ksh = (double)K;
   }
 };
 
@@ -380,11 +395,11 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &
   CT g1[CPL], g2[CPL];
 #pragma unroll
   for (int s = 0; s < CPL; ++s) g1[s] = g2[s] = CT(0);
-  double S, Q;
+  double S, Q, Ks;  // sums of e = d - Ks and e^2, and the shift Ks
   W.template rows<GRAD, BLOCKS, MODE>(Xp, a.S, a.n, idx, a.m, a.fam, inv_s2, g1, g2, blk_out, a.G,
-                                      S, Q, a.st, io, a.cv_order == 1);
+                                      S, Q, Ks, a.st, io, a.cv_order == 1);
   const double nm = (double)a.n / (double)a.m;
-  const double dbar = S / (double)a.m;
+  const double dbar = S / (double)a.m;  // mean of e (the gradient partials hold e r x)
   if (GRAD) {
     // reduce the gradient partials over the row slots of the warp
 #pragma unroll
@@ -421,8 +436,8 @@ __device__ __forceinline__ void eval_particle(const WarpEval<XT, T, CPL, U, K> &
     }
   }
   qlin = warp_sum(qlin);
-  ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + qlin + nm * S;
-  sig2 = nm * nm * (Q - S * S / (double)a.m);
+  ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + qlin + nm * fma((double)a.m, Ks, S);
+  sig2 = nm * nm * fmax(0.0, Q - S * S / (double)a.m);
   __syncwarp();
 }
 
@@ -566,10 +581,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_backward(EstArgs a) {
   CT g1[CPL], g2[CPL];
 #pragma unroll
   for (int e = 0; e < CPL; ++e) g1[e] = g2[e] = CT(0);
-  double S_, Q_;
+  double S_, Q_, K_;
   W.template rows<true, false, 2>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n,
                                   a.u + (int64_t)i * m, m, a.fam, (CT)a.inv_s2, g1, g2, nullptr,
-                                  a.G, S_, Q_, a.st, io);
+                                  a.G, S_, Q_, K_, a.st, io);
 #pragma unroll
   for (int e = 0; e < CPL; ++e) {
 #pragma unroll
@@ -620,10 +635,12 @@ __device__ __forceinline__ void upm_body(const EstArgs &a, int i, unsigned char 
   for (int c = W.lane; c < a.p; c += 32) sm.th[c] = th[c];
   __syncwarp();
   refresh_delta(W, a, sm);
-  double Sg, Qg;
+  double Se, Qe, Ks;
   W.template rows<false, false>(reinterpret_cast<const XT *>(a.Xp), a.S, a.n, unew, nb, a.fam,
-                                (CT)a.inv_s2, nullptr, nullptr, nullptr, 0, Sg, Qg, a.st,
+                                (CT)a.inv_s2, nullptr, nullptr, nullptr, 0, Se, Qe, Ks, a.st,
                                 RowIO<CT>(), a.cv_order == 1);
+  // the new block's FP64 (sum d, sum d^2) from the shifted sums of e = d - Ks
+  const double Sg = fma((double)nb, Ks, Se), Qg = Qe + Ks * fma((double)nb, Ks, 2.0 * Se);
   double *blk = a.blk + (int64_t)i * a.G * 2;
   // totals over blocks from the cache (lanes over blocks)
   double St = 0.0, Qt = 0.0;
@@ -639,7 +656,7 @@ __device__ __forceinline__ void upm_body(const EstArgs &a, int i, unsigned char 
   const double Sn = St - Sold + Sg, Qn = Qt - Qold + Qg;
   const double ell0 = a.ell[i], sig0 = a.sig2[i];
   const double ell1 = ell0 + nm * (Sg - Sold);
-  const double sig1 = nm * nm * (Qn - Sn * Sn / (double)a.m);
+  const double sig1 = nm * nm * fmax(0.0, Qn - Sn * Sn / (double)a.m);
   const double log_r = temp * (ell1 - ell0) - 0.5 * temp * temp * (sig1 - sig0);
   const Stream smh(a.seed, kMhU, smv, (uint32_t)i);
   const double Uu = draw_uniform(smh.draw(0));

@@ -9,6 +9,13 @@
 // gradient and runs the leapfrog update itself, with theta, rho and the gradient held one column
 // per lane, so no warp waits for another between passes. One CTA handles one particle at a time
 // and loops over particles (persistent grid).
+//
+// Sums over rows are of e_j = d_j - K with a CTA-uniform shift K near the subsample mean of d: the
+// cached mean for the first pass, then the previous pass's mean (shifted data: Chan, Golub &
+// LeVeque 1983). sigma2_hat = (n/m)^2 (sum e^2 - (sum e)^2/m) then stays accurate in FP32 partial
+// sums where the d_j share a large mean (particles far from the centre), and the gradient's
+// sum (d_j - dbar) r_j x_j is formed as sum e_j r_j x_j - ebar sum r_j x_j without that cancellation.
+// The block cache keeps FP64 (sum d, sum d^2), rebuilt from the shifted block sums.
 #pragma once
 
 #include "estimator.cuh"
@@ -175,6 +182,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     set_delta();
     double ell = 0.0, sig = 0.0;
     int buf = 0;
+    // shift of the row sums (identical in every warp): the cached subsample mean of d at this
+    // particle's current theta and u
+    CT Ksh = CT(0);
+    if (a.blk) {
+      const double *bc = a.blk + (int64_t)i * G * 2;
+      double s0 = 0.0;
+      for (int g = lane; g < G; g += 32) s0 += bc[2 * g];
+      Ksh = (CT)(warp_sum(s0) * inv_m);
+      if (!isfinite(Ksh)) Ksh = CT(0);
+    }
     // One estimator pass at the current delta (dr). Every warp ends with the gradient at its lanes
     // and l_hat, sigma2_hat; FINAL also fills the block sums blks.
     auto pass = [&](bool final, bool want_totals) {
@@ -193,11 +210,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
           CT d, r;
           row_incr<F, CT>(c, D, inv_s2, d, r);
           if (cv1) to_first_order(row_l2<F, CT>(c, inv_s2), D, d, r);
+          const CT e = d - Ksh;
           axpy_slots<CPL>(r, x, v);
-          axpy_slots<CPL>(d * r, x, v + CPL);
-          sd += d;
-          sd2 = fma(d, d, sd2);
-          if (final) dv[j] = d;
+          axpy_slots<CPL>(e * r, x, v + CPL);
+          sd += e;
+          sd2 = fma(e, e, sd2);
+          if (final) dv[j] = e;
         }
       };
       switch (fam) {
@@ -220,10 +238,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
         rd[2 * warp + 1] = s2;
       }
       __syncthreads();  // all warps' partial sums of this pass are in buffer buf
-      CT S1f = CT(0);   // sum of d over the subsample (the gradient needs only its mean)
+      CT S1f = CT(0);   // sum of e over the subsample (the gradient needs only its mean)
 #pragma unroll
       for (int w = 0; w < WARPS; ++w) S1f += rd[2 * w];
-      if (final) {  // block sums of d (floor partition of u into G blocks)
+      if (final) {  // shifted block sums of e (floor partition of u into G blocks)
         for (int g = warp; g < G; g += WARPS) {
           const int j0 = (int)(((int64_t)g * m) / G), j1 = (int)(((int64_t)(g + 1) * m) / G);
           CT bs = CT(0), bq = CT(0);
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
         __syncthreads();
       }
       // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at lane c (every warp, FP32)
-      const CT dbar = S1f * (CT)inv_m;
+      const CT dbar = S1f * (CT)inv_m;  // mean of e
       CT G1 = CT(0), G2 = CT(0);
       if (col) {
 #pragma unroll
@@ -272,9 +290,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
             S2 += (double)rd[2 * w + 1];
           }
         }
-        ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + (double)qlin + nm * S1;
-        sig = nm * nm * (S2 - S1 * S1 * inv_m);
+        ell = (a.A_dev ? __ldg(a.A_dev) : a.A) + (double)qlin + nm * fma((double)m, (double)Ksh, S1);
+        sig = nm * nm * fmax(0.0, S2 - S1 * S1 * inv_m);
       }
+      if (!final) Ksh += dbar;  // the next pass is shifted by this pass's mean of d
       buf ^= 1;
     };
 
@@ -306,8 +325,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       const bool acc = log(Uu) < H0 - H1;  // false when H1 is NaN
       if (acc) {
         if (col) thg[lane] = th;
+        // the cache holds FP64 (sum d, sum d^2) per block: rebuilt from the shifted sums
         double *blk = a.blk + (int64_t)i * G * 2;
-        for (int h = lane; h < 2 * G; h += 32) blk[h] = blks[h];
+        const double k = (double)Ksh;
+        for (int g = lane; g < G; g += 32) {
+          const double ng = (double)((int)(((int64_t)(g + 1) * m) / G) - (int)(((int64_t)g * m) / G));
+          const double se = blks[2 * g], qe = blks[2 * g + 1];
+          blk[2 * g] = fma(ng, k, se);
+          blk[2 * g + 1] = qe + k * fma(ng, k, 2.0 * se);
+        }
         if (lane == 0) {
           a.ell[i] = ell;
           a.sig2[i] = sig;
