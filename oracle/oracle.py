@@ -23,6 +23,7 @@ _SRC = os.path.join(_HERE, "smc_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
+_margin_lock = threading.Lock()  # one margin record at a time (the C side keeps one pointer)
 _lib = None
 
 FAMILIES = {"logistic": 0, "probit": 1, "poisson": 2, "gaussian": 3, "student_t": 4}
@@ -103,6 +104,8 @@ def lib():
                                             ctypes.POINTER(c_d), ctypes.POINTER(c_d)]
             L.orc_reweight_grid.restype = c_d
             L.orc_num_threads.restype = c_i
+            L.orc_set_margin_out.argtypes = [ctypes.c_void_p]
+            L.orc_set_margin_out.restype = None
             _lib = L
     return _lib
 
@@ -293,22 +296,57 @@ def init_particles(seed, N, p, m, n, prior_mean, prior_var):
     return th, us
 
 
-def upm_move(prob, m, G, seed, stage, move, a, thetas, us):
+class _Margins:
+    """Records the MH margins (log ratio - log U per particle) of one oracle move into `out`."""
+
+    def __init__(self, out):
+        self.out = out
+
+    def __enter__(self):
+        if self.out is not None:
+            L = lib()
+            _margin_lock.acquire()
+            L.orc_set_margin_out(self.out.ctypes.data)
+
+    def __exit__(self, *exc):
+        if self.out is not None:
+            lib().orc_set_margin_out(None)
+            _margin_lock.release()
+
+
+def _margin_buffer(margins, N):
+    if margins is None:
+        return None
+    if margins.dtype != np.float64 or margins.shape != (N,) or not margins.flags.c_contiguous:
+        raise ValueError("margins must be a contiguous float64 array of one value per particle")
+    return margins
+
+
+def upm_move(prob, m, G, seed, stage, move, a, thetas, us, margins=None):
+    """Block pseudo-marginal u update (Algorithm 1 step 1). margins: optional float64 [N] that
+    receives log r - log U per particle (the decision's distance from the MH threshold)."""
     N = thetas.shape[0]
     acc = np.zeros(N, dtype=np.int32)
-    lib().orc_upm_move(*prob.args(m, G), N, seed, stage_move(stage, move), a,
-                       np.ascontiguousarray(thetas, np.float64), us, acc)
+    args = prob.args(m, G)
+    with _Margins(_margin_buffer(margins, N)):
+        lib().orc_upm_move(*args, N, seed, stage_move(stage, move), a,
+                           np.ascontiguousarray(thetas, np.float64), us, acc)
     return acc
 
 
-def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us, jitter=0.3):
+def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us, jitter=0.3,
+             margins=None):
     """HMC move of theta given u (Algorithm 1 step 2); jitter > 0: each particle's step size is
-    uniform on eps [1 - jitter, 1 + jitter]."""
+    uniform on eps [1 - jitter, 1 + jitter]. margins: optional float64 [N] that receives
+    H0 - H1 - log U per particle."""
     N = thetas.shape[0]
     acc = np.zeros(N, dtype=np.int32)
-    lib().orc_hmc_move(*prob.args(m, G), N, seed, stage_move(stage, move), a, eps, jitter, L,
-                       np.ascontiguousarray(Sigma, np.float64), np.ascontiguousarray(Lc, np.float64),
-                       thetas, np.ascontiguousarray(us, np.int64), acc)
+    args = prob.args(m, G)
+    with _Margins(_margin_buffer(margins, N)):
+        lib().orc_hmc_move(*args, N, seed, stage_move(stage, move), a, eps, jitter, L,
+                           np.ascontiguousarray(Sigma, np.float64),
+                           np.ascontiguousarray(Lc, np.float64), thetas,
+                           np.ascontiguousarray(us, np.int64), acc)
     return acc
 
 

@@ -405,6 +405,14 @@ void orc_init(uint64_t seed, int N, int p, int m, int64_t n, const double *pm, c
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Optional record of every MH decision of the moves below: margin[i] = log ratio - log U of       */
+/* particle i (> 0: accepted). Test support only: a caller that computes the same ratio in lower  */
+/* precision may decide differently only where this margin is within its rounding. NULL = off.    */
+/* ------------------------------------------------------------------------------------------ */
+static double *g_margin = NULL;
+void orc_set_margin_out(double *buf) { g_margin = buf; }
+
+/* ------------------------------------------------------------------------------------------ */
 /* Block pseudo-marginal update of u (Algorithm 1 step 1, Eq. acc_prop_u): one block g of the G   */
 /* blocks is chosen uniformly, its indices are redrawn iid from p(u), and the proposal is          */
 /* accepted with probability min(1, r), r the ratio of annealed likelihood estimators at theta.     */
@@ -431,6 +439,7 @@ void orc_upm_move(int fam, int64_t n, int p, const double *X, const double *y, d
     double log_r = (a * ells - 0.5 * a * a * s2s) - (a * ell - 0.5 * a * a * s2);
     double U = orc_uniform(orc_r64(seed, TAG_MH_U, stage_move, (uint32_t)i, 0));
     int acc = log(U) < log_r;
+    if (g_margin) g_margin[i] = log_r - log(U);
     if (acc) memcpy(u, ustar, sizeof(int64_t) * m);
     accepted[i] = acc;
     free(ustar);
@@ -497,6 +506,7 @@ void orc_hmc_move(int fam, int64_t n, int p, const double *X, const double *y, d
     double H1 = -lt + kin1;
     double U = orc_uniform(orc_r64(seed, TAG_MH_THETA, stage_move, (uint32_t)i, 0));
     int acc = log(U) < H0 - H1;
+    if (g_margin) g_margin[i] = (H0 - H1) - log(U);
     if (acc) memcpy(theta0, th, sizeof(double) * p);
     accepted[i] = acc;
     free(z); free(rho); free(th); free(g); free(v);
@@ -531,6 +541,7 @@ void orc_rw_move(int fam, int64_t n, int p, const double *X, const double *y, do
     double lt1 = log_target(&P, u, th, a, NULL);
     double U = orc_uniform(orc_r64(seed, TAG_MH_THETA, stage_move, (uint32_t)i, 0));
     int acc = log(U) < lt1 - lt0;
+    if (g_margin) g_margin[i] = (lt1 - lt0) - log(U);
     if (acc) memcpy(theta0, th, sizeof(double) * p);
     accepted[i] = acc;
     free(z);

@@ -919,3 +919,35 @@ def test_hmc_at_zero_temperature_keeps_prior_draws_prior_distributed():
     z = (th - mu) / np.sqrt(var)
     assert np.all(np.abs(z.mean(axis=0)) < 5 / math.sqrt(N))
     assert np.all(np.abs(z.var(axis=0) - 1.0) < 5 * math.sqrt(2.0 / N))
+
+
+def test_move_margins_are_the_decisions_distance_from_the_threshold():
+    """The optional margin record of the oracle's moves (test support): for the u update the margin
+    equals a (l_hat* - l_hat) - a^2/2 (sigma2* - sigma2) - log U rebuilt here from the oracle's
+    estimator at the proposed indices (block and indices redrawn from the raw Philox streams);
+    for both moves the margin is positive exactly where the move was accepted."""
+    prob = tiny_problem("logistic", n=60, p=3, seed=5)
+    N, m, G, seed, stage, a = 40, 9, 3, 21, 4, 0.7
+    th, us = O.init_particles(seed, N, 3, m, prob.n, prob.prior_mean, prob.prior_var)
+    th = prob.theta_bar + 0.3 * (th - prob.prior_mean) / np.sqrt(prob.prior_var)
+    us0 = us.copy()
+    mu = np.zeros(N)
+    acc = O.upm_move(prob, m, G, seed, stage, 0, a, th, us, margins=mu)
+    assert np.array_equal(mu > 0, acc.astype(bool))
+    sm = O.stage_move(stage, 0)
+    ustar = us0.copy()
+    for i in range(N):
+        g = O.index(O.r64(seed, O.TAG_UPM_BLOCK, sm, i, 0), G)
+        j0, j1 = (g * m) // G, ((g + 1) * m) // G
+        for j in range(j0, j1):
+            ustar[i, j] = O.index(O.r64(seed, O.TAG_UPM_IDX, sm, i, j - j0), prob.n)
+    r0 = O.loglik_batch(prob, m, G, th, us0, grad=False)
+    r1 = O.loglik_batch(prob, m, G, th, ustar, grad=False)
+    logU = np.log([O.uniform(O.r64(seed, O.TAG_MH_U, sm, i, 0)) for i in range(N)])
+    want = a * (r1["ell"] - r0["ell"]) - 0.5 * a * a * (r1["sigma2"] - r0["sigma2"]) - logU
+    np.testing.assert_allclose(mu, want, rtol=1e-12, atol=1e-12)
+    S = np.diag([0.05, 0.02, 0.02])
+    mh = np.zeros(N)
+    acc = O.hmc_move(prob, m, G, seed, stage, 1, a, 2.5, 4, S, np.linalg.cholesky(S), th, us,
+                     margins=mh)
+    assert np.array_equal(mh > 0, acc.astype(bool)) and 0 < acc.sum() < N
