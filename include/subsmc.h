@@ -300,9 +300,10 @@ int smc_profile_read(smc_ctx *ctx, int32_t group, int64_t *launches, double *tot
  * allocate device memory when they need resampling: code that runs while a CUDA graph is being
  * captured (cudaMalloc is not allowed there), engines whose memory plan is fixed before they start,
  * and hosts that give the GPU a fixed arena and forbid further allocations.
- * It computes the same ancestors as smc_resample for the same normalised weights, seed and stage
- * (integer weights floor(W_i 2^40), uniform U from the stage's resampling stream), but needs no
- * context and calls no allocator: its scratch is one fixed device array inside this library
+ * It computes the same ancestors as smc_resample on a context configured for systematic
+ * resampling (smc_config.resampling = 0), for the same normalised weights, seed and stage (integer
+ * weights floor(W_i 2^40), one uniform U from the stage's resampling stream); it does not implement
+ * the multinomial scheme. It needs no context and calls no allocator: its scratch is one fixed device array inside this library
  * (SMC_NOALLOC_MAX_N + 2 eight-byte words, about 2 MiB), which every GPU that loads the library
  * holds until the process exits.
  *   N: 1 <= N <= SMC_NOALLOC_MAX_N, otherwise SMC_ERR_ARG (message in smc_last_error(NULL)).

@@ -239,11 +239,15 @@ class SubsampledLoglik(torch.autograd.Function):
 
 
 def smc_get_particles(ctx: Context, theta=None, u=None, W=None):
-    """Fill (or allocate on the context's device) theta [N,p], u [N,m] int32, W [N] float64."""
+    """Fill (or allocate on the context's device) theta [N,p], u [N,m] int32, W [N] float64.
+    u=False skips the indices (returned as None)."""
     dev = ctx.device
     theta = theta if theta is not None else torch.empty(ctx.N, ctx.p, dtype=ctx.state_dtype,
                                                         device=dev)
-    u = u if u is not None else torch.empty(ctx.N, ctx.m, dtype=torch.int32, device=dev)
+    if u is False:
+        u = None
+    elif u is None:
+        u = torch.empty(ctx.N, ctx.m, dtype=torch.int32, device=dev)
     W = W if W is not None else torch.empty(ctx.N, dtype=torch.float64, device=dev)
     check(_abi.load().smc_get_particles(ctx.handle, _ptr(theta), _ptr(u), _ptr(W)),
           "smc_get_particles", ctx.handle)
@@ -251,8 +255,10 @@ def smc_get_particles(ctx: Context, theta=None, u=None, W=None):
 
 
 def smc_set_particles(ctx: Context, theta, u, W=None) -> None:
-    theta = theta.to(ctx.state_dtype).contiguous()
-    u = u.to(torch.int32).contiguous()
+    """Replace theta [N, p], u [N, m] and W [N] (each may be None: kept, W = 1/N); the cached
+    estimates are recomputed."""
+    theta = None if theta is None else theta.to(ctx.state_dtype).contiguous()
+    u = None if u is None else u.to(torch.int32).contiguous()
     W = None if W is None else W.to(torch.float64).contiguous()
     check(_abi.load().smc_set_particles(ctx.handle, _ptr(theta), _ptr(u), _ptr(W)),
           "smc_set_particles", ctx.handle)
