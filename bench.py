@@ -1,10 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of likelihood-annealed subsampling SMC on one GB300 (or N replicas under torchrun).
 
-A step is one SMC stage (Algorithm 2): temperature search + reweighting, weighted moments + mass
-matrix, systematic resampling, and R Markov moves (Algorithm 1: block u update, then an HMC
-trajectory of L leapfrog steps). The metric is particle-row gradient evaluations per second:
-each stage evaluates the subsampled log-likelihood gradient N * m * R * (L + 1) times per row.
+A step is one complete SMC run of the workload (Algorithm 2 to completion): smc_init (packing X,
+the posterior-mode centre by Newton's method, the control-variate moments A, B, C, initial
+particles and their cached estimates), then stages of temperature search + reweighting, weighted
+moments + mass matrix, systematic resampling and R Markov moves (Algorithm 1: block u update, then
+an HMC trajectory of L leapfrog steps) until the temperature reaches 1, and the posterior (weighted
+mean, log Z) read back. The metric is particle-row gradient evaluations per second over whole
+runs: each stage evaluates the subsampled log-likelihood gradient N * m * R * (L + 1) times;
+ms_per_step is the SMC wall time from initialisation to a = 1.
 
 Default workload: logistic regression, n = 1,000,000 rows, p = 20 (intercept + 19 AR(1) N(0,1)
 covariates), N = 4096 particles, m = 1000, G = 10, L = 20, R = 5, X stored in BF16 with FP32
@@ -84,6 +88,22 @@ def peaks():
 def workload_name(wl, R):
     return (f"logistic n={wl.n} p={wl.p} N={wl.N} m={wl.m} G={wl.G} L={wl.L} R={R} "
             f"X={wl.x_dtype}")
+
+
+METRIC = "particle-row grad-evals/s (complete subsampling SMC runs, init to a = 1)"
+
+
+def bench_config(wl, R, world):
+    """The config object of both arms' JSON lines (the same workload and step definition)."""
+    return {"workload": workload_name(wl, R), "model": "logistic regression",
+            "global_batch": wl.N * world, "seq_len": wl.m, "parallelism": f"replicas{world}",
+            "stage_window": "complete runs: every stage from initialisation to a = 1",
+            "l2": "flushed between timed runs (256 MiB write)",
+            "accumulate": "FP32 per row, FP64 totals/weights/MH"}
+
+
+STEP = ("one complete SMC run: smc_init (packing, Newton centre, A/B/C, initial particles and "
+        "cache) + every stage to a = 1 + the posterior read back")
 
 
 def grad_evals_per_stage(wl, R):
@@ -177,41 +197,6 @@ def run_stage(S, ctx, R):
     return a
 
 
-def timed_stages(S, ctx, wl, R, steps, warmup, flush, dist, graph=False):
-    """Times `steps` stages after `warmup` untimed ones. graph: every stage is one smc_stage call
-    replaying a captured CUDA graph (captured during the warm-up), else the three calls
-    smc_reweight, smc_resample, smc_move with their host readbacks."""
-    import torch
-    stage = (lambda: S.smc_stage(ctx, R, use_graph=True)) if graph else (lambda: run_stage(S, ctx, R))
-    for _ in range(warmup):
-        stage()
-    torch.cuda.synchronize()
-    if dist:
-        torch.distributed.barrier()
-    S.smc_profile_enable(ctx, True)
-    for g in S.smc.PROFILE_GROUPS:
-        S.smc_profile_read(ctx, g)
-    launches0 = S.smc_launch_count(ctx)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(steps):
-        flush.add_(1)  # write a buffer larger than L2 between timed stages
-        starts[k].record()
-        stage()
-        ends[k].record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    launches = S.smc_launch_count(ctx) - launches0
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    prof = {g: S.smc_profile_read(ctx, g) for g in S.smc.PROFILE_GROUPS}
-    S.smc_profile_enable(ctx, False)
-    if dist:
-        ms = max_over_ranks(ms, "cuda")
-    return ms, wall, launches, prof
-
-
 def max_over_ranks(value: float, device) -> float:
     """The largest of every rank's value (the timing rule: the job's time is its slowest rank)."""
     import torch
@@ -224,6 +209,85 @@ def job_throughput(units_per_step: float, steps: int, world: int, ms: float) -> 
     """Whole-job throughput: every rank processes units_per_step per step (replicas, weak scaling);
     ms is the slowest rank's time for the steps."""
     return units_per_step * steps * world / (ms / 1e3)
+
+
+def complete_run(S, wl, Xd, yd, R, hints, seed, profile=False, max_stages=400, host_out=None):
+    """One benchmark step: a complete SMC run (init to a = 1) on the resident inputs Xd, yd, ending
+    with the posterior read back: the weighted mean of theta (device reduction, p values to the
+    host) and log Z; with host_out = (theta_h, W_h) pinned buffers, the whole weighted cloud is
+    copied to the host instead. hints: the (tile_hint, hmc_kernel) the autotuner chose. Returns
+    the context (still open: freed by the caller outside the timed region), stages, log Z and the
+    posterior mean."""
+    ctx = S.smc_init(Xd, yd, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
+                     L=wl.L, seed=seed, ess_frac=0.5, theta_bar=None, noise_sigma=wl.sigma,
+                     dof=wl.dof, tile_hint=hints[0], hmc_kernel=hints[1])
+    if profile:
+        S.smc_profile_enable(ctx, True)
+    stages, a = 0, 0.0
+    while a < 1.0 and stages < max_stages:
+        a = run_stage(S, ctx, R)
+        stages += 1
+    if host_out is None:
+        th, _, W = S.smc_get_particles(ctx, u=False)
+        mean = (th.double() * W[:, None]).sum(0).cpu().numpy()
+    else:
+        th_h, W_h = host_out
+        S.smc_get_particles(ctx, th_h, False, W_h)
+        mean = (th_h.double() * W_h[:, None]).sum(0).numpy()
+    lz = S.smc_get_status(ctx)["log_z"]
+    return ctx, stages, lz, mean
+
+
+def timed_runs(S, wl, Xd, yd, R, hints, steps, warmup, flush, dist, seed):
+    """`warmup` untimed complete runs, then `steps` timed ones (CUDA events on the library's
+    stream around each run; the L2 flush before each). Per-kernel-group device times come from the
+    library's tracing events over the timed runs."""
+    import torch
+    for _ in range(warmup):
+        ctx, _, _, _ = complete_run(S, wl, Xd, yd, R, hints, seed)
+        S.smc_free(ctx)
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    ms, stages, launches, lzs = [], [], 0, []
+    prof = {g: [0, 0.0] for g in S.smc.PROFILE_GROUPS}
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        flush.add_(1)  # write a buffer larger than L2 between timed runs
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx, k, lz, _ = complete_run(S, wl, Xd, yd, R, hints, seed, profile=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stages.append(k)
+        lzs.append(lz)
+        launches += S.smc_launch_count(ctx)
+        for g in S.smc.PROFILE_GROUPS:
+            n_g, t_g = S.smc_profile_read(ctx, g)
+            prof[g][0] += n_g
+            prof[g][1] += t_g
+        S.smc_free(ctx)
+    wall = time.perf_counter() - t0
+    tot = sum(ms)
+    if dist:
+        tot = max_over_ranks(tot, "cuda")
+    return tot, wall, launches, prof, stages, lzs
+
+
+def hmc_by_stage(S, ctx, R, max_stages=400):
+    """Device time of the HMC trajectory launch at every stage of one complete run (the kernel's
+    cost depends on how far the particles are from the centre), with the stage's temperature."""
+    S.smc_profile_enable(ctx, True)
+    S.smc_profile_read(ctx, "hmc")
+    out, a = [], 0.0
+    while a < 1.0 and len(out) < max_stages:
+        a = run_stage(S, ctx, R)
+        n_h, t_h = S.smc_profile_read(ctx, "hmc")
+        out.append([round(a, 8), round(t_h / max(n_h, 1), 4)])
+    S.smc_profile_enable(ctx, False)
+    return out
 
 
 def full_run(S, wl, dev, R, max_stages=400, adaptive=None, **kw):
@@ -502,29 +566,68 @@ def gam_leg(S, dev, hbm, tile_hint=0, n=10_000_000):
     return out
 
 
-def e2e_stages(S, ctx, wl, R, steps, warmup):
-    """The timed region's stages again, from a fresh context with the same seed (so the same
-    stage range as the device-timed value: warm-up stages untimed, then `steps` stages), through
-    the public API with the particle state resident on the host: each timed step copies theta, u,
-    W in from pinned host memory (smc_set_particles, which also re-estimates the cache) and the
-    new cloud back out."""
+def e2e_runs(S, wl, R, hints, steps, dev, seed):
+    """The same complete runs through the public API with the inputs in pinned host memory: each
+    step copies X and y to the device, runs init to a = 1, and copies the weighted cloud (theta,
+    W) back to pinned host memory with log Z."""
     import torch
-    for _ in range(warmup):
-        run_stage(S, ctx, R)
-    th, u, W = S.smc_get_particles(ctx)
-    th_h = th.cpu().pin_memory()
-    u_h = u.cpu().pin_memory()
-    W_h = W.cpu().pin_memory()
-    bytes_in = th_h.numel() * th_h.element_size() + u_h.numel() * 4 + W_h.numel() * 8
+    if wl.x_dtype == "bf16":
+        X_h = torch.from_numpy(wl.X_store.view(np.int16)).view(torch.bfloat16).pin_memory()
+    else:
+        X_h = torch.from_numpy(wl.X_store).pin_memory()
+    y_h = torch.from_numpy(wl.y_store).pin_memory()
+    th_h = torch.empty(wl.N, wl.p, dtype=torch.float32).pin_memory()
+    W_h = torch.empty(wl.N, dtype=torch.float64).pin_memory()
+    bytes_in = X_h.numel() * X_h.element_size() + y_h.numel() * y_h.element_size()
+    bytes_out = th_h.numel() * 4 + W_h.numel() * 8 + 8
+    units = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        S.smc_set_particles(ctx, th_h, u_h, W_h)
-        run_stage(S, ctx, R)
-        S.smc_get_particles(ctx, th_h, u_h, W_h)
+        Xd = X_h.to(dev, non_blocking=True)
+        yd = y_h.to(dev, non_blocking=True)
+        ctx, k, _, _ = complete_run(S, wl, Xd, yd, R, hints, seed, host_out=(th_h, W_h))
+        units += k * grad_evals_per_stage(wl, R)
+        S.smc_free(ctx)
+        del Xd, yd
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    return wall, bytes_in, bytes_in
+    return units / wall, bytes_in, bytes_out
+
+
+def graph_stage_leg(S, wl, dev, R, hints, seed):
+    """The stages of one complete run (after init) replayed as captured CUDA graphs (smc_stage,
+    no host synchronisation inside a stage) against the same stages launched one by one."""
+    import torch
+    out = {}
+    Xd, yd = device_workload(wl, dev)
+    for name, graph in (("launches", False), ("graph", True)):
+        ctx = S.smc_init(Xd, yd, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
+                         L=wl.L, seed=seed, ess_frac=0.5, theta_bar=None, tile_hint=hints[0],
+                         hmc_kernel=hints[1])
+        torch.cuda.synchronize()
+        l0 = S.smc_launch_count(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        k, a = 0, 0.0
+        while a < 1.0 and k < 400:
+            if graph:
+                S.smc_stage(ctx, R, use_graph=True)
+                a = S.smc_get_status(ctx)["a"]
+            else:
+                a = run_stage(S, ctx, R)
+            k += 1
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"stages": k, "ms_per_stage": ms / k,
+                     "grad_evals_per_s": k * grad_evals_per_stage(wl, R) / (ms / 1e3),
+                     "launches_per_stage": (S.smc_launch_count(ctx) - l0) / k}
+        S.smc_free(ctx)
+    out["note"] = ("stages of one run (init excluded); graph: one smc_stage graph launch per "
+                   "stage (the first two stages capture) and one status read")
+    return out
 
 
 def gpu_arm(args):
@@ -541,65 +644,70 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     R = R_MOVES
-
     wl = logistic_1e6("bf16", n=args.n)
-    ctx, tile = make_ctx(S, wl, dev, seed_offset=rank)
+    seed = wl.seed + rank  # replicas: each rank runs its own chain
+
+    # the estimator tile and trajectory kernel, chosen once by the library's autotuner on this
+    # workload (untimed) and passed to every timed run as hints; then the per-stage profile of
+    # one complete run
+    ctx0, hints = make_ctx(S, wl, dev, seed_offset=rank)
+    by_stage = hmc_by_stage(S, ctx0, R)
+    S.smc_free(ctx0)
+
+    Xd, yd = device_workload(wl, dev)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
     sampler = ClockSampler(local if not os.environ.get("CUDA_VISIBLE_DEVICES") else 0)
     sampler.start()
-    ms, wall, launches, prof = timed_stages(S, ctx, wl, R, args.steps, args.warmup, flush, dist)
+    ms, wall, launches, prof, stages, lzs = timed_runs(S, wl, Xd, yd, R, hints, args.steps,
+                                                       args.warmup, flush, dist, seed)
     clocks = sampler.stop()
-    per_stage = grad_evals_per_stage(wl, R)
-    value = job_throughput(per_stage, args.steps, world, ms)
+    del Xd, yd
+    units = sum(stages) * grad_evals_per_stage(wl, R)
+    value = units * world / (ms / 1e3)
 
     # roofline of the dominant kernel, the HMC trajectory with the subsample resident in shared
     # memory. It reads X once per trajectory and then runs L+1 estimator passes out of shared
     # memory, so it is bound by the FP32/integer issue rate, not by HBM: bound "alu" against the
     # FP32 peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz. Algorithmic FLOPs per particle-row
-    # evaluation: 2p (x'delta) + 4p (gradient partials) + 20 (increment terms d, r).
+    # evaluation: 8p (the survey's count: x'theta, x'theta_bar, sum r x, sum d r x; the second is
+    # cached per row here, the count is kept).
     hbm, peak_kind = peaks()
     n_h, ms_h = prof["hmc"]
-    units = (wl.L + 1) * wl.N * wl.m
-    flops_launch = units * (6 * wl.p + 20)
+    units_launch = (wl.L + 1) * wl.N * wl.m
+    flops_launch = units_launch * 8 * wl.p
     sec = ms_h / max(n_h, 1) / 1e3
     achieved = flops_launch / sec / 1e12 if n_h else None
     bytes_row = wl.p * 2 + 4 + 4
-    bytes_launch = units * bytes_row
+    bytes_launch = units_launch * bytes_row
     shares = {g: round(v[1] / ms, 4) for g, v in prof.items() if v[0]}
 
-    S.smc_free(ctx)
-    ctxe, _ = make_ctx(S, wl, dev, seed_offset=rank)
-    e2e_wall, bi, bo = e2e_stages(S, ctxe, wl, R, args.steps, args.warmup)
-    e2e_value = per_stage * args.steps * world / e2e_wall
-    S.smc_free(ctxe)
+    e2e_value, bi, bo = e2e_runs(S, wl, R, hints, args.steps, dev, seed)
 
-    # the same stages (fresh context, same seed) with every stage replayed as one CUDA graph
     graph = None
     if not args.no_graph:
-        ctxg, _ = make_ctx(S, wl, dev, seed_offset=rank)
-        msg, _, lg, _ = timed_stages(S, ctxg, wl, R, args.steps, args.warmup, flush, dist, graph=True)
-        S.smc_free(ctxg)
-        graph = {"value": per_stage * args.steps * world / (msg / 1e3),
-                 "ms_per_step": msg / args.steps, "gpu_launches": lg,
-                 "note": "smc_stage with use_graph: one graph launch per stage, no host sync"}
+        graph = graph_stage_leg(S, wl, dev, R, hints, seed)
 
     fp32 = None
     walls = {}
     if not args.no_compare and rank == 0:
         wl32 = logistic_1e6("f32", n=args.n)
-        ctx32, tile32 = make_ctx(S, wl32, dev, seed_offset=rank)
-        ms32, _, _, prof32 = timed_stages(S, ctx32, wl32, R, args.steps, args.warmup, flush, False)
-        S.smc_free(ctx32)
+        c32, hints32 = make_ctx(S, wl32, dev, seed_offset=rank)
+        S.smc_free(c32)
+        X32, y32 = device_workload(wl32, dev)
+        ms32, _, _, prof32, st32, lz32 = timed_runs(S, wl32, X32, y32, R, hints32, args.steps,
+                                                    args.warmup, flush, False, seed)
+        del X32, y32
         n32, t32 = prof32["hmc"]
-        fp32 = {"value": per_stage * args.steps / (ms32 / 1e3), "ms_per_step": ms32 / args.steps,
-                "hmc_ms_per_launch": t32 / max(n32, 1), "tile": tile32}
-        walls = {"bf16": full_run(S, wl, dev, R), "fp32": full_run(S, wl32, dev, R)}
+        fp32 = {"value": sum(st32) * grad_evals_per_stage(wl32, R) / (ms32 / 1e3),
+                "ms_per_step": ms32 / args.steps, "stages_per_run": sorted(set(st32)),
+                "log_z": lz32[0], "hmc_ms_per_launch": t32 / max(n32, 1), "tile": hints32,
+                "bf16_speedup_wall": (ms32 / args.steps) / (ms / args.steps)}
         del wl32
         # the paper's own stage settings (Algorithm 2 as printed): ESS target 0.8N by the grid
         # rule, multinomial resampling, control variates re-centred every stage, R tuned per stage
-        # R = 10 moves per stage: at p = 20 the five moves of the workload leave the cloud short of
-        # the tempered target each stage and log Z about 0.2 low (FP64 oracle: -0.18 mean over four
-        # seeds at R = 5, -0.05 at R = 10, n = 2e4, N = 4096)
+        # R = 10 moves per stage on the conjugate leg: at p = 20 the five moves of the workload
+        # leave the cloud short of the tempered target each stage and log Z about 0.2 low (FP64
+        # oracle: -0.18 mean over four seeds at R = 5, -0.05 at R = 10, n = 2e4, N = 4096)
         walls["conjugate_bf16_vs_fp32"] = precision_leg(S, dev, 10)
         walls["bf16_paper_settings"] = full_run(
             S, wl, dev, R, adaptive=(30, 0.1, 0.9), ess_frac=0.8, grid_points=1024,
@@ -609,7 +717,7 @@ def gpu_arm(args):
     tleg = None
     if not args.no_full and rank == 0:
         full = full_data_leg(S, wl, dev, R, bf16_peak())
-        full["subsampling_speedup_per_stage"] = full["ms_per_stage"] / (ms / args.steps)
+        full["subsampling_speedup_per_stage"] = full["ms_per_stage"] / (ms / sum(stages))
         tleg = student_t_leg(S, dev, R)
 
     batch = None
@@ -628,9 +736,9 @@ def gpu_arm(args):
         cpu = cpu_baseline(wl, R, args.cpu_seconds)
 
     traffic = committed_traffic(bytes_launch)
+    config = bench_config(wl, R, world)
     out = {
-        "metric": "particle-row grad-evals/s (subsampling SMC stage: reweight, resample, "
-                  "R moves)",
+        "metric": METRIC,
         "value": value,
         "unit": "grad-evals/s",
         "n_gpus": world,
@@ -642,23 +750,26 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": workload_name(wl, R), "model": "logistic regression",
-                   "global_batch": wl.N * world, "seq_len": wl.m,
-                   "parallelism": f"replicas{world}", "tile": tile,
-                   "l2": "flushed between timed stages (256 MiB write)",
-                   "accumulate": "FP32 per row, FP64 totals/weights/MH"},
+        "config": config,
+        "step": STEP,
+        "stages_per_run": sorted(set(stages)),
+        "tile": list(hints),
         "roofline": {"kernel": "k_hmc_res (HMC trajectory, rows resident in shared memory)",
                      "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
                      "traffic": traffic, "flops_per_launch": flops_launch,
+                     "flops_per_unit": 8 * wl.p,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "algorithmic_gbs": bytes_launch / sec / 1e9 if n_h else None,
                      "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind,
                      "launches": n_h, "ms_per_launch": ms_h / max(n_h, 1),
-                     "note": "traffic = DRAM bytes per launch (ncu); the rows of a particle are "
+                     "note": "averaged over every HMC launch of the timed runs (all stages); "
+                             "traffic = DRAM bytes per launch (ncu); the rows of a particle are "
                              "gathered once per trajectory, the L+1 passes read shared memory"},
+        "hmc_ms_by_stage": by_stage,
         "stage_shares": shares,
+        "log_z": lzs[0] if lzs else None,
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "grad-evals/s", "h2d_bytes_per_step": bi,
@@ -772,12 +883,11 @@ def reference_arm(args):
     value = evals / tot
     sample = (f"per step: one Algorithm-1 move (u block update + HMC, L={wl.L}) of {count} of the "
               f"{wl.N} particles; FP64 C oracle, OpenMP over particles")
-    out = {"impl": "reference", "metric": "particle-row grad-evals/s (subsampling SMC stage: "
-           "reweight, resample, R moves)", "value": value, "unit": "grad-evals/s",
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grad-evals/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(wl, R_MOVES), "model": "logistic regression"},
+           "config": bench_config(wl, R_MOVES, 1),
            "cpu_baseline": {"value": value, "unit": "grad-evals/s", "cores": cores,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
