@@ -65,6 +65,9 @@ def parse():
                     help="rows of the GAM workload (smaller for profiling captures)")
     ap.add_argument("--gam-only", action="store_true",
                     help="run only the GAM gather leg and print its JSON (for profiling)")
+    ap.add_argument("--profile-stages", type=int, default=0,
+                    help="run only the first K stages of one run of the default workload with the "
+                         "default kernels (no autotune), for ncu captures of a chosen stage")
     return ap.parse_args()
 
 
@@ -895,8 +898,30 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def profile_stages(args):
+    """The first K stages of one run of the default workload (BF16) with the library's default
+    kernel choice: k_hmc_res launches 5 (K - 1) .. 5 K - 1 are those of stage K."""
+    import torch
+    import paper_1805_03317_gb300 as S
+    from smc_workloads import logistic_1e6
+    torch.cuda.set_device(0)
+    wl = logistic_1e6("bf16", n=args.n)
+    X, y = device_workload(wl, torch.device("cuda", 0))
+    ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
+                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None)
+    a = 0.0
+    for _ in range(args.profile_stages):
+        a = run_stage(S, ctx, R_MOVES)
+    torch.cuda.synchronize()
+    print(json.dumps({"stages": args.profile_stages, "a": a}), flush=True)
+    S.smc_free(ctx)
+
+
 def main():
     args = parse()
+    if args.profile_stages:
+        profile_stages(args)
+        return
     if args.gather_only:
         import torch
         torch.cuda.set_device(0)

@@ -869,33 +869,19 @@ def test_singular_particle_covariance_gets_the_documented_jitter():
 def test_smc_log_marginal_on_the_plain_logistic_workload_against_importance_sampling():
     """The plain FP64 workload (logistic, n = 10,000, p = 5): a reference log marginal likelihood
     by importance sampling with a multivariate-t (5 degrees of freedom) proposal at the mode with
-    the Laplace covariance (numpy/scipy only: Bernoulli log-likelihood, normal prior, t density;
-    40,000 draws, relative standard error of the estimate of p(y) about 0.2%). The oracle's SMC at
-    N = 1024 recovers it: mean error over eight seeded runs within 0.15 (about 2.5 standard errors
-    of that mean)."""
+    the Laplace covariance (tests/logml_reference.py: numpy/scipy only; 40,000 draws, relative
+    standard error of the estimate of p(y) about 0.2%). The oracle's SMC at N = 1024 recovers it:
+    mean error over eight seeded runs within 0.15 (about 2.5 standard errors of that mean)."""
+    from logml_reference import importance_reference
     from smc_workloads import logistic_1e4
     wl = logistic_1e4()
-    X, y = wl.X, wl.y
-    prob = O.Problem("logistic", X, y, wl.prior_mean, wl.prior_var)
+    prob = O.Problem("logistic", wl.X, wl.y, wl.prior_mean, wl.prior_var)
     mode = O.newton_map(prob)
     prob.set_centre(mode)
-    Sig = np.linalg.inv(-(prob.C - np.diag(1.0 / wl.prior_var)))
-    rng = np.random.default_rng(0)
-    M, nu, p = 40000, 5.0, X.shape[1]
-    Lc = np.linalg.cholesky(Sig)
-    q = stats.multivariate_t(loc=mode, shape=Sig, df=nu)
-    logw = []
-    for _ in range(M // 2000):
-        z = rng.standard_normal((2000, p))
-        g = rng.chisquare(nu, 2000)
-        th = mode + (z @ Lc.T) / np.sqrt(g / nu)[:, None]
-        eta = X @ th.T
-        ll = (y[:, None] * eta - np.logaddexp(0.0, eta)).sum(axis=0)
-        lp = stats.norm.logpdf(th, 0.0, np.sqrt(wl.prior_var)).sum(axis=1)
-        logw.append(ll + lp - q.logpdf(th))
-    logw = np.concatenate(logw)
-    ref = float(special.logsumexp(logw) - math.log(M))
-    assert math.sqrt(np.var(np.exp(logw - ref)) / M) < 0.01
+    ref_d = importance_reference(wl.X, wl.y, wl.prior_var)
+    np.testing.assert_allclose(ref_d["mode"], mode, rtol=1e-9, atol=1e-10)
+    assert ref_d["rel_se"] < 0.01
+    ref = ref_d["log_ml"]
     errs = []
     for seed in range(1, 9):
         st = O.smc_run(prob, O.SMCConfig(N=1024, m=100, G=10, L=10, R=5, seed=seed, tau=0.5))
