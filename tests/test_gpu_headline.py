@@ -106,9 +106,9 @@ def test_resident_trajectory_at_the_headline_shape(x_dtype, regime):
     assert np.all(np.abs(ell_g[ok] - ref2["ell"][ok]) <= 1e-5 * scale[ok])
     s2o = ref2["sigma2"]
     assert np.all(np.abs(s2_g[ok] - s2o[ok]) <= 1e-4 * np.abs(s2o[ok]) + 1e-9 * scale[ok])
+    # block sums (sum d, sum d^2 per block of u) to 1e-4 of the largest, the bar the cache tests use
     bo = ref2["blocks"]
-    bscale = np.max(np.abs(bo), axis=(1, 2))
-    assert np.all(np.max(np.abs(blk_g - bo), axis=(1, 2))[ok] <= 1e-4 * bscale[ok])
+    assert np.max(np.abs(blk_g - bo)[ok]) <= 1e-4 * np.max(np.abs(bo[ok]))
     if regime == "prior":
         # far from the centre: the rows' increments share a large mean, so the one-pass variance
         # would cancel; sigma2_hat is still held to 1e-4 of itself
