@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--profile-stages", type=int, default=0,
                     help="run only the first K stages of one run of the default workload with the "
                          "default kernels (no autotune), for ncu captures of a chosen stage")
+    ap.add_argument("--hmc-kernel", type=int, default=0,
+                    help="with --profile-stages: the trajectory kernel (smc_config.hmc_kernel)")
     return ap.parse_args()
 
 
@@ -908,7 +910,8 @@ def profile_stages(args):
     wl = logistic_1e6("bf16", n=args.n)
     X, y = device_workload(wl, torch.device("cuda", 0))
     ctx = S.smc_init(X, y, wl.family, wl.prior_mean, wl.prior_var, N=wl.N, m=wl.m, G=wl.G,
-                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None)
+                     L=wl.L, seed=wl.seed, ess_frac=0.5, theta_bar=None,
+                     hmc_kernel=args.hmc_kernel)
     a = 0.0
     for _ in range(args.profile_stages):
         a = run_stage(S, ctx, R_MOVES)

@@ -240,6 +240,8 @@ int default_tile(const smc_ctx *c) {
 EstArgs base_args(const smc_ctx *c);
 
 // Smallest resident tile (4 warps) whose covariate slots cover p and whose plan fits on an SM.
+// The tensor-core trajectory kernel (a tile with T = 0) is left to smc_autotune: on the
+// workloads measured it is latency-bound and slower than the CUDA-core tiles.
 int default_res_tile(smc_ctx *c) {
   Tile t[32];
   const int nt = res_tiles(c, t, 32);
@@ -247,7 +249,7 @@ int default_res_tile(smc_ctx *c) {
   a.B = c->N;
   int best = -1;
   for (int i = 0; i < nt; ++i) {
-    if (t[i].warps != 4 || t[i].CPL < c->p) continue;
+    if (t[i].T == 0 || t[i].warps != 4 || t[i].CPL < c->p) continue;
     if (res_launch(c, i, a, true) != 0) continue;
     if (best < 0 || t[i].CPL < t[best].CPL) best = i;
   }

@@ -1,12 +1,14 @@
 // Resident-trajectory HMC kernels for bf16 storage of X: one instantiation per compiled tile.
 // A translation unit of its own so that the library's sources compile in parallel.
 #include "resident.cuh"
+#include "resident_tc.cuh"
 
 namespace subsmc {
 namespace {
 using XT = __nv_bfloat16;
+// T = 0 marks the tensor-core trajectory kernel (resident_tc.cuh: p <= 32, 8 warps).
 const Tile kResTiles[] = {{1, 8, 1, 4}, {1, 16, 1, 4}, {1, 24, 1, 4}, {1, 32, 1, 4}, {1, 16, 1, 8},
-                          {1, 24, 1, 8}, {1, 20, 1, 4}, {1, 12, 1, 4}};
+                          {1, 24, 1, 8}, {1, 20, 1, 4}, {1, 12, 1, 4}, {0, 32, 1, 8}};
 }  // namespace
 
 int res_tiles_bf16(Tile *out, int cap) {
@@ -25,6 +27,7 @@ int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dr
     case 5: return launch_res<XT, 24, 8>(a, s, sms, dry);
     case 6: return launch_res<XT, 20, 4>(a, s, sms, dry);
     case 7: return launch_res<XT, 12, 4>(a, s, sms, dry);
+    case 8: return launch_res_tc(a, s, sms, dry);
     default: return -1;
   }
 }

@@ -58,6 +58,10 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   return P;
 }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -127,12 +131,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     __syncthreads();  // the previous particle is finished with shared memory
     // 1. gather x_{u_j} and the row's constants at the centre (its tail) with 16-byte copies;
     // invalid indices are flagged and their rows zeroed. Vectors the tile reads beyond the row's
-    // covariates (a tile wider than p) are zero-filled.
+    // covariates (a tile wider than p) are zero-filled. The indices are staged in shared memory
+    // first (the block-sum buffer is free until the last pass), so no copy waits on a global load.
+    int32_t *us = reinterpret_cast<int32_t *>(dv);
+    for (int j = tid; j < m; j += blockDim.x) cp_async4(us + j, u + j);
+    cp_async_wait_all();
+    __syncthreads();
     constexpr int NTV = (int)sizeof(RowC<CT>) / 16;
     const int nvr = P.nvl + NTV;
     for (int t = tid; t < m * nvr; t += blockDim.x) {
       const int j = t / nvr, q = t - j * nvr;
-      const int k = u[j];
+      const int k = us[j];
       unsigned char *dst = q < P.nvl ? rows + (size_t)j * P.rb + 16 * q
                                      : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvl);
       const int qs = q < P.nvl ? q : P.nvec + (q - P.nvl);  // 16-byte vector of the packed row

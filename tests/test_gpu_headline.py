@@ -28,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 HMC_20_SLOT = 8  # hmc_kernel value of the resident 20-slot, 4-warp tile (both storage types)
+HMC_TC = 10      # the tensor-core trajectory kernel (BF16 storage)
 
 
 def S():
@@ -46,11 +47,14 @@ def _headline(x_dtype, N=256):
 REGIMES = {"prior": ("prior", 0.0, 0.4), "mid": (0.08, 0.002, 0.3), "late": (0.01, 0.6, 0.2)}
 
 
-@pytest.mark.parametrize("x_dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("kernel,x_dtype", [(HMC_20_SLOT, "bf16"), (HMC_20_SLOT, "f32"),
+                                            (HMC_TC, "bf16")])
 @pytest.mark.parametrize("regime", ["prior", "mid", "late"])
-def test_resident_trajectory_at_the_headline_shape(x_dtype, regime):
+def test_resident_trajectory_at_the_headline_shape(kernel, x_dtype, regime):
+    """One move of the resident trajectory kernels (the 20-slot CUDA-core tile and the tensor-core
+    kernel) against the oracle's move on the same cloud."""
     wl = _headline(x_dtype)
-    prob, ctx = make_pair(wl, hmc_kernel=HMC_20_SLOT)
+    prob, ctx = make_pair(wl, hmc_kernel=kernel)
     cloud, a0, eps = REGIMES[regime]
     rng = np.random.default_rng(17)
     if cloud == "prior":

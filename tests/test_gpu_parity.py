@@ -320,12 +320,13 @@ def test_full_smc_run_matches_oracle_fp64(hmc_kernel):
 
 @pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
-@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8])
+@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10])
 def test_moves_reduced_precision_match_oracle(x_dtype, family, hmc_kernel):
     """FP32 arithmetic on FP32/BF16-stored rows against the FP64 oracle on the same stored values:
     the MH decisions may differ only where the FP64 log ratio is within rounding of the uniform;
     accepted end points agree to FP32 leapfrog rounding. hmc_kernel 5 and 8 are resident tiles
-    wider than the rows (32 and 20 slots for p = 13), whose slots past p must read zeros."""
+    wider than the rows (32 and 20 slots for p = 13), whose slots past p must read zeros; 10 is
+    the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90)."""
     wl = _wl(family, x_dtype, p=13, N=256, m=90, G=6)
     try:
         prob, ctx = make_pair(wl, hmc_kernel=hmc_kernel)
