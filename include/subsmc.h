@@ -123,6 +123,11 @@ typedef struct {
                              /* [1 - j, 1 + j] (second word of its theta-MH Philox block); random   */
                              /* steps break near-periodic trajectories of a fixed eps L (Neal 2011, */
                              /* cited in Sec. 1). j < 0.9; 0 -> 0.3; negative -> a fixed step       */
+  int32_t shard_base;        /* Particle sharding (see "Particle shards" below). shard_count = 0:   */
+  int32_t shard_count;       /* off. Otherwise smc_move moves only particles [shard_base,           */
+                             /* shard_base + shard_count) of the N, with their global indices in   */
+                             /* every random stream, and leaves the step-size update to            */
+                             /* smc_finish_moves. Needs cv_centre = 0, full_data = 0               */
 } smc_config;
 
 /* ------------------------------------------------------------------------------------------- */
@@ -288,6 +293,57 @@ int64_t smc_launch_count(const smc_ctx *ctx);
  * summed device time in milliseconds for one group, and clears that group's record. */
 int smc_profile_enable(smc_ctx *ctx, int32_t on);
 int smc_profile_read(smc_ctx *ctx, int32_t group, int64_t *launches, double *total_ms);
+
+/* ------------------------------------------------------------------------------------------- */
+/* Particle shards (several processes, one posterior)                                           */
+/* ------------------------------------------------------------------------------------------- */
+
+/* The moves of different particles are independent (Sec. 2.1: the method parallelises over the M
+ * particles), so R processes (one per GPU) can share one posterior. Each creates a context with
+ * the same problem, seed and N, and its own slice [shard_base, shard_base + shard_count) of the
+ * particles. The stage's reweighting, moments, mass matrix and resampling then run redundantly on
+ * every process over the full arrays (identical inputs give identical temperatures, weights and
+ * integer ancestors), while smc_move moves only the slice. Between stages the caller:
+ *   1. sums the slices' accept counts (smc_move_accepts) over the processes and passes the totals
+ *      to smc_finish_moves (the step-size update of smc_move);
+ *   2. gathers every process's slice of theta and of the cached estimates (smc_shard_export) and
+ *      writes the full arrays back (smc_shard_import);
+ *   3. after smc_resample, hands the u rows of ancestors that lived on another process to the
+ *      process that now holds their offspring (smc_shard_gather_u with before_resample = 1 on the
+ *      owner, smc_shard_scatter_u on the receiver).
+ * u is kept current only inside a process's own slice. The results equal those of one context
+ * with all N particles: the same kernels see the same values, and the random streams are indexed
+ * by global particle number. */
+
+/* Copy this context's slice of theta [count, p] (state type), the cached l_hat and sigma2_hat
+ * [count] and block sums [count, G, 2] (double) to caller buffers ("any"; each may be NULL).
+ * Synchronises the stream. SMC_ERR_STATE when the context has no shard. */
+int smc_shard_export(smc_ctx *ctx, void *theta, double *ell, double *sigma2, double *blocks);
+
+/* Overwrite theta [N, p], l_hat, sigma2_hat [N] and the block sums [N, G, 2] of all N particles
+ * ("any"; each may be NULL) without recomputing the estimates. Synchronises the stream. */
+int smc_shard_import(smc_ctx *ctx, const void *theta, const double *ell, const double *sigma2,
+                     const double *blocks);
+
+/* rows[k, 0..m) = u of global particle idx[k], k < count; before_resample = 1 reads the indices
+ * as they were before the last smc_resample (the ancestors' rows), 0 the current ones.
+ * idx, rows: device. Indices outside [0, N) are skipped and reported as SMC_ERR_ARG by the next
+ * synchronising call. Stream-ordered. */
+int smc_shard_gather_u(smc_ctx *ctx, int32_t count, const int32_t *idx, int32_t *rows,
+                       int32_t before_resample);
+
+/* u of global particle idx[k] = rows[k, 0..m), k < count (the current buffer; the cached
+ * estimates are not recomputed). idx, rows: device. Stream-ordered. */
+int smc_shard_scatter_u(smc_ctx *ctx, int32_t count, const int32_t *idx, const int32_t *rows);
+
+/* Accepted u updates and theta moves since the last smc_move began (this context's particles).
+ * Host outputs; synchronises the stream. */
+int smc_move_accepts(smc_ctx *ctx, uint64_t *acc_u, uint64_t *acc_theta);
+
+/* The step-size update that smc_move performs for an unsharded context, from accept totals over
+ * all processes: eps *= clip(exp(acc_theta / (N R) - t), 0.5, 2) (t = 0.65 for HMC, 0.234 for the
+ * random walk). Stream-ordered. */
+int smc_finish_moves(smc_ctx *ctx, int32_t R, uint64_t acc_u, uint64_t acc_theta);
 
 /* ------------------------------------------------------------------------------------------- */
 /* Resampling without allocation                                                                */

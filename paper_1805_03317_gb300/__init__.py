@@ -11,7 +11,10 @@ from .smc import (Batch, Context, SubsampledLoglik, SubsampledSMC, loglik_bwd, l
                   smc_profile_read, smc_resample, smc_resample_noalloc,
                   smc_reweight, smc_set_particles, smc_set_scalars, smc_stage, smc_batch_init,
                   smc_batch_free, smc_batch_stage, smc_batch_autotune, smc_batch_tile,
-                  smc_batch_launch_count, smc_batch_context, smc_batch_last_error)
+                  smc_batch_launch_count, smc_batch_context, smc_batch_last_error,
+                  smc_shard_export, smc_shard_import, smc_shard_gather_u, smc_shard_scatter_u,
+                  smc_move_accepts, smc_finish_moves)
+from .sharded import ShardedSMC, shard_bounds
 
 __all__ = ["Batch", "smc_batch_init", "smc_batch_free", "smc_batch_stage", "smc_batch_autotune",
            "smc_batch_tile", "smc_batch_launch_count", "smc_batch_context", "smc_batch_last_error",
@@ -21,4 +24,6 @@ __all__ = ["Batch", "smc_batch_init", "smc_batch_free", "smc_batch_stage", "smc_
            "smc_get_particles", "smc_get_status", "smc_init", "smc_launch_count", "smc_move",
            "smc_move_adaptive",
            "smc_profile_enable", "smc_profile_read", "smc_resample_noalloc",
-           "smc_resample", "smc_reweight", "smc_set_particles", "smc_set_scalars", "smc_stage"]
+           "smc_resample", "smc_reweight", "smc_set_particles", "smc_set_scalars", "smc_stage",
+           "smc_shard_export", "smc_shard_import", "smc_shard_gather_u", "smc_shard_scatter_u",
+           "smc_move_accepts", "smc_finish_moves", "ShardedSMC", "shard_bounds"]

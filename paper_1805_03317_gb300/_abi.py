@@ -31,7 +31,8 @@ class SmcConfig(ctypes.Structure):
                 ("tile_hint", c_i32), ("hmc_kernel", c_i32), ("cv_kernel", c_i32),
                 ("cv_order", c_i32), ("cv_centre", c_i32), ("full_data", c_i32),
                 ("resampling", c_i32), ("grid_points", c_i32), ("grid_decades", c_d),
-                ("theta_move", c_i32), ("eps_jitter", c_d)]
+                ("theta_move", c_i32), ("eps_jitter", c_d), ("shard_base", c_i32),
+                ("shard_count", c_i32)]
 
 
 # name -> (restype, argtypes)
@@ -72,6 +73,12 @@ SIGNATURES = {
     "smc_profile_enable": (ctypes.c_int, [c_vp, c_i32]),
     "smc_profile_read": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_i64), c_dp]),
     "smc_resample_noalloc": (ctypes.c_int, [c_i32, c_vp, c_u64, c_i32, c_vp, c_vp]),
+    "smc_shard_export": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "smc_shard_import": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "smc_shard_gather_u": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp, c_i32]),
+    "smc_shard_scatter_u": (ctypes.c_int, [c_vp, c_i32, c_vp, c_vp]),
+    "smc_move_accepts": (ctypes.c_int, [c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
+    "smc_finish_moves": (ctypes.c_int, [c_vp, c_i32, c_u64, c_u64]),
 }
 NOALLOC_MAX_N = 262144
 

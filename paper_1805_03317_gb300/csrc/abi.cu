@@ -25,6 +25,7 @@ struct smc_ctx {
   double eps_jitter = 0.3;          // HMC step-size jitter (0: fixed step)
   int grid_points = 0;              // > 0: grid temperature rule with this many points
   double grid_decades = 16.0;
+  int shard_base = 0, shard_count = 0;  // shard_count > 0: smc_move moves only this slice
   int64_t n = 0;
   double noise_sigma = 1.0;  // Gaussian sd or Student-t scale (1 for the other families)
   double dof = 0.0;          // Student-t degrees of freedom
@@ -692,6 +693,16 @@ int smc_init(smc_ctx **out, const smc_problem *P, const smc_config *cfg, const d
   c->eps_jitter = cfg->eps_jitter == 0.0 ? 0.3 : (cfg->eps_jitter < 0.0 ? 0.0 : cfg->eps_jitter);
   c->grid_points = cfg->grid_points;
   c->grid_decades = cfg->grid_decades > 0.0 ? cfg->grid_decades : 16.0;
+  if (cfg->shard_count < 0 || cfg->shard_base < 0 ||
+      (cfg->shard_count > 0 && (int64_t)cfg->shard_base + cfg->shard_count > cfg->N) ||
+      (cfg->shard_count > 0 && (cfg->cv_centre != 0 || cfg->full_data))) {
+    g_init_error = "shard: need 0 <= shard_base, shard_base + shard_count <= N, cv_centre = 0 and "
+                   "full_data = 0";
+    delete c;
+    return SMC_ERR_ARG;
+  }
+  c->shard_base = cfg->shard_base;
+  c->shard_count = cfg->shard_count;
   c->full_data = cfg->full_data ? 1 : 0;
   if (c->full_data && (P->x_dtype != SMC_BF16 || P->p > 64)) {
     g_init_error = "full_data needs BF16 storage and p <= 64";
@@ -848,7 +859,8 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
   }
   for (int r = 0; r < (c->full_data ? 0 : R); ++r) {
     EstArgs a = base_args(c);
-    a.B = c->N;
+    a.B = c->shard_count > 0 ? c->shard_count : c->N;
+    a.i0 = c->shard_count > 0 ? c->shard_base : 0;
     a.theta = c->theta;
     a.theta_out = c->theta;
     a.u = c->u;
@@ -863,13 +875,15 @@ int smc_move(smc_ctx *c, int32_t R, double *acc_u, double *acc_theta) {
     LAUNCH(c, hmc_launch(c, a), 0);
   }
   c->moves_in_stage += R;
-  LAUNCH(c, eps_update(c->N, R, c->st, c->stream, c->rw ? 0.234 : 0.65), 1);
+  // a shard leaves the step size to smc_finish_moves (it needs every shard's accept counts)
+  if (c->shard_count == 0) LAUNCH(c, eps_update(c->N, R, c->st, c->stream, c->rw ? 0.234 : 0.65), 1);
   if (acc_u || acc_theta) {
     DevState h;
     int r = sync_state(c, &h);
     if (r) return r;
-    if (acc_u) *acc_u = (double)h.acc_u / ((double)c->N * R);
-    if (acc_theta) *acc_theta = (double)h.acc_theta / ((double)c->N * R);
+    const double moved = (double)(c->shard_count > 0 ? c->shard_count : c->N) * R;
+    if (acc_u) *acc_u = (double)h.acc_u / moved;
+    if (acc_theta) *acc_theta = (double)h.acc_theta / moved;
     return check_err_bits(c, h);
   }
   return SMC_OK;
@@ -889,6 +903,7 @@ int smc_move_adaptive(smc_ctx *c, int32_t R_max, double rho_max, double quantile
   if (!(rho_max >= -1.0 && rho_max <= 1.0) || !(quantile > 0.0 && quantile <= 1.0))
     return fail(c, SMC_ERR_ARG, "rho_max must be in [-1, 1] and quantile in (0, 1]");
   if (c->capturing) return fail(c, SMC_ERR_ARG, "adaptive moves cannot be graph-captured");
+  if (c->shard_count > 0) return fail(c, SMC_ERR_STATE, "adaptive moves are not sharded");
   const int N = c->N, p = c->p;
   const size_t tbytes = (size_t)N * p * (c->is_f64 ? sizeof(double) : sizeof(float));
   if (!c->theta0) {
@@ -1409,6 +1424,114 @@ int smc_profile_read(smc_ctx *c, int32_t group, int64_t *launches, double *total
   c->prof[group].clear();
   return SMC_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Particle shards: slices of one posterior's particles on several processes (see subsmc.h).
+// ------------------------------------------------------------------------------------------------
+namespace {
+// rows[k] = u[idx[k]] (dir 0) or u[idx[k]] = rows[k] (dir 1); one warp per listed particle.
+__global__ void k_shard_rows(int count, int N, int m, const int32_t *idx, int32_t *u,
+                             int32_t *rows, int dir, DevState *st) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= count) return;
+  const int i = idx[k];
+  if (i < 0 || i >= N) {
+    if (lane == 0) atomicOr(&st->err, kErrIndex);
+    return;
+  }
+  int32_t *ur = u + (int64_t)i * m, *rr = rows + (int64_t)k * m;
+  for (int j = lane; j < m; j += 32) {
+    if (dir == 0)
+      rr[j] = ur[j];
+    else
+      ur[j] = rr[j];
+  }
+}
+int shard_rows(smc_ctx *c, int32_t count, const int32_t *idx, int32_t *rows, int32_t *u, int dir) {
+  if (count < 0 || (count > 0 && (!idx || !rows)))
+    return fail(c, SMC_ERR_ARG, "shard rows: bad arguments");
+  if (count == 0) return SMC_OK;
+  const int wpb = 8;
+  k_shard_rows<<<(count + wpb - 1) / wpb, wpb * 32, 0, c->stream>>>(count, c->N, c->m, idx, u,
+                                                                    rows, dir, c->st);
+  c->launches += 1;
+  CUDA_OK(c, cudaGetLastError());
+  return SMC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int smc_shard_export(smc_ctx *c, void *theta, double *ell, double *sigma2, double *blocks) {
+  if (!c) return SMC_ERR_ARG;
+  if (c->shard_count == 0) return fail(c, SMC_ERR_STATE, "the context has no shard");
+  const size_t b = (size_t)c->shard_base, n = (size_t)c->shard_count, cts = ct_size(c);
+  const size_t G2 = (size_t)c->G * 2;
+  if (theta)
+    CUDA_OK(c, cudaMemcpyAsync(theta, (char *)c->theta + b * c->p * cts, n * c->p * cts,
+                               cudaMemcpyDefault, c->stream));
+  if (ell)
+    CUDA_OK(c, cudaMemcpyAsync(ell, c->ell + b, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  if (sigma2)
+    CUDA_OK(c, cudaMemcpyAsync(sigma2, c->sig2 + b, n * sizeof(double), cudaMemcpyDefault,
+                               c->stream));
+  if (blocks)
+    CUDA_OK(c, cudaMemcpyAsync(blocks, c->blk + b * G2, n * G2 * sizeof(double), cudaMemcpyDefault,
+                               c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_shard_import(smc_ctx *c, const void *theta, const double *ell, const double *sigma2,
+                     const double *blocks) {
+  if (!c) return SMC_ERR_ARG;
+  const size_t N = (size_t)c->N, G2 = (size_t)c->G * 2;
+  if (theta)
+    CUDA_OK(c, cudaMemcpyAsync(c->theta, theta, N * c->p * ct_size(c), cudaMemcpyDefault,
+                               c->stream));
+  if (ell) CUDA_OK(c, cudaMemcpyAsync(c->ell, ell, N * sizeof(double), cudaMemcpyDefault, c->stream));
+  if (sigma2)
+    CUDA_OK(c, cudaMemcpyAsync(c->sig2, sigma2, N * sizeof(double), cudaMemcpyDefault, c->stream));
+  if (blocks)
+    CUDA_OK(c, cudaMemcpyAsync(c->blk, blocks, N * G2 * sizeof(double), cudaMemcpyDefault,
+                               c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return SMC_OK;
+}
+
+int smc_shard_gather_u(smc_ctx *c, int32_t count, const int32_t *idx, int32_t *rows,
+                       int32_t before_resample) {
+  if (!c) return SMC_ERR_ARG;
+  return shard_rows(c, count, idx, rows, before_resample ? c->u_alt : c->u, 0);
+}
+
+int smc_shard_scatter_u(smc_ctx *c, int32_t count, const int32_t *idx, const int32_t *rows) {
+  if (!c) return SMC_ERR_ARG;
+  return shard_rows(c, count, idx, const_cast<int32_t *>(rows), c->u, 1);
+}
+
+int smc_move_accepts(smc_ctx *c, uint64_t *acc_u, uint64_t *acc_theta) {
+  if (!c) return SMC_ERR_ARG;
+  DevState h;
+  int r = sync_state(c, &h);
+  if (r) return r;
+  if (acc_u) *acc_u = h.acc_u;
+  if (acc_theta) *acc_theta = h.acc_theta;
+  return check_err_bits(c, h);
+}
+
+int smc_finish_moves(smc_ctx *c, int32_t R, uint64_t acc_u, uint64_t acc_theta) {
+  if (!c) return SMC_ERR_ARG;
+  if (R < 1) return fail(c, SMC_ERR_ARG, "R must be >= 1");
+  unsigned long long v[2] = {acc_u, acc_theta};
+  CUDA_OK(c, cudaMemcpyAsync(&c->st->acc_u, v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+  LAUNCH(c, eps_update(c->N, R, c->st, c->stream, c->rw ? 0.234 : 0.65), 1);
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));  // v lives on this stack frame
+  return SMC_OK;
+}
+
+}  // extern "C"
 
 // ------------------------------------------------------------------------------------------------
 // Batches of independent posteriors (many problems of uneven n and p stepped together): one context

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_upm(EstArgs a) {
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * WARPS + warp;
   if (i >= a.B) return;
-  upm_body<XT, T, CPL, U, WARPS, K>(a, i,
+  upm_body<XT, T, CPL, U, WARPS, K>(a, a.i0 + i,
                                   smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p));
 }
 // All particles of a batch of independent posteriors in one launch: the global warp index picks
@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc(EstArgs a) {
   const int warp = threadIdx.x >> 5;
   const int i = blockIdx.x * WARPS + warp;
   if (i >= a.B) return;
-  hmc_body<XT, T, CPL, U, WARPS, K>(a, i,
+  hmc_body<XT, T, CPL, U, WARPS, K>(a, a.i0 + i,
                                   smem_raw + (size_t)warp * warp_smem_bytes<XT, T, CPL, U>(a.p));
 }
 // All particles of a batch of independent posteriors in one launch: the global warp index picks

@@ -74,6 +74,8 @@ struct EstArgs {
   double eps_jitter;      // HMC: particle step sizes uniform on eps [1 - j, 1 + j] (0: fixed)
   int cv_order;           // 1: first-order control variates (row increments without the
                           //    second-order term; C is zero in the state-type copy), else 2
+  int i0;                 // moves: global index of the launch's first particle (its B particles
+                          //    are i0 .. i0 + B - 1 in every array and random stream)
   const double *g_ell, *g_sig2;
 };
 

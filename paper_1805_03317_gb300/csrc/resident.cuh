@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
     Sgs[e] = in ? ldg_ct<CT>(a.Sigma_ct, r * p + c) : CT(0);
   }
 
-  for (int i = blockIdx.x; i < a.B; i += gridDim.x) {
+  for (int il = blockIdx.x; il < a.B; il += gridDim.x) {
+    const int i = a.i0 + il;  // global particle index
     const int32_t *u = a.u + (int64_t)i * m;
     __syncthreads();  // the previous particle is finished with shared memory
     // 1. gather x_{u_j} and the row's constants at the centre (its tail) with 16-byte copies;

@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_hmc_tc(EstArgs a, TcPlan P) {
     __syncwarp();
   };
 
-  for (int i = blockIdx.x; i < a.B && ok; i += gridDim.x) {
+  for (int il = blockIdx.x; il < a.B && ok; il += gridDim.x) {
+    const int i = a.i0 + il;  // global particle index
     const int32_t *u = a.u + (int64_t)i * m;
     __syncthreads();  // the previous particle is finished with shared and tensor memory
     // 1. gather the rows (covariate chunks and tails) with 16-byte copies; bad indices flagged,

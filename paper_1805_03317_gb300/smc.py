@@ -62,7 +62,8 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
              tile_hint: int = 0, hmc_kernel: int = 0, cv_kernel: int = 0,
              cv_order: int = 2, cv_centre: int = 0, full_data: bool = False,
              resampling: str = "systematic", grid_points: int = 0, grid_decades: float = 0.0,
-             theta_move: str = "hmc", eps_jitter: float = 0.0, stream=None) -> Context:
+             theta_move: str = "hmc", eps_jitter: float = 0.0, shard_base: int = 0,
+             shard_count: int = 0, stream=None) -> Context:
     """Create a context (Algorithm 2 step 1) on X's device; the fields mirror smc_problem and
     smc_config in include/subsmc.h.
 
@@ -75,7 +76,8 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
     it), resampling ("systematic" or "multinomial"), grid_points / grid_decades (the grid
     temperature rule), theta_move ("hmc" or "rw"), eps_jitter (0: 0.3; negative: fixed step),
     full_data (the full-data comparison method). Tuning: search_k, search_rounds, eps0, tile_hint,
-    hmc_kernel, cv_kernel (0 = automatic)."""
+    hmc_kernel, cv_kernel (0 = automatic). shard_base / shard_count: this process moves only
+    particles [shard_base, shard_base + shard_count) of the N (sharded.py drives such contexts)."""
     lib = _abi.load()
     if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
@@ -91,7 +93,7 @@ def smc_init(X: torch.Tensor, y: torch.Tensor, family: str, prior_mean, prior_va
                     search_rounds, float(eps0), tile_hint, hmc_kernel, cv_kernel,
                     int(cv_order), int(cv_centre), 1 if full_data else 0,
                     RESAMPLING[resampling], int(grid_points), float(grid_decades),
-                    THETA_MOVE[theta_move], float(eps_jitter))
+                    THETA_MOVE[theta_move], float(eps_jitter), int(shard_base), int(shard_count))
     tb = None
     tb_ptr = None
     if theta_bar is not None:
@@ -392,6 +394,61 @@ class SubsampledSMC:
 
     def close(self):
         smc_free(self.ctx)
+
+
+# ------------------------------------------------------------------------------------------------
+# Particle shards (sharded.py combines them across processes)
+# ------------------------------------------------------------------------------------------------
+def smc_shard_export(ctx: Context, count: int):
+    """This context's slice: theta [count, p], l_hat, sigma2_hat [count], blocks [count, G, 2]."""
+    dev = ctx.device
+    th = torch.empty(count, ctx.p, dtype=ctx.state_dtype, device=dev)
+    ell = torch.empty(count, dtype=torch.float64, device=dev)
+    s2 = torch.empty_like(ell)
+    blk = torch.empty(count, ctx.G, 2, dtype=torch.float64, device=dev)
+    check(_abi.load().smc_shard_export(ctx.handle, _ptr(th), _ptr(ell), _ptr(s2), _ptr(blk)),
+          "smc_shard_export", ctx.handle)
+    return th, ell, s2, blk
+
+
+def smc_shard_import(ctx: Context, theta, ell, sigma2, blocks) -> None:
+    """Overwrite theta [N, p] and the cached estimates of all N particles (no recomputation)."""
+    th = theta.to(ctx.state_dtype).contiguous()
+    e = ell.to(torch.float64).contiguous()
+    s2 = sigma2.to(torch.float64).contiguous()
+    b = blocks.to(torch.float64).contiguous()
+    check(_abi.load().smc_shard_import(ctx.handle, _ptr(th), _ptr(e), _ptr(s2), _ptr(b)),
+          "smc_shard_import", ctx.handle)
+
+
+def smc_shard_gather_u(ctx: Context, idx: torch.Tensor, before_resample: bool) -> torch.Tensor:
+    """u rows [len(idx), m] of global particles idx (before the last resampling if asked)."""
+    idx = idx.to(device=ctx.device, dtype=torch.int32).contiguous()
+    rows = torch.empty(idx.numel(), ctx.m, dtype=torch.int32, device=ctx.device)
+    check(_abi.load().smc_shard_gather_u(ctx.handle, idx.numel(), _ptr(idx), _ptr(rows),
+                                         int(bool(before_resample))),
+          "smc_shard_gather_u", ctx.handle)
+    return rows
+
+
+def smc_shard_scatter_u(ctx: Context, idx: torch.Tensor, rows: torch.Tensor) -> None:
+    idx = idx.to(device=ctx.device, dtype=torch.int32).contiguous()
+    rows = rows.to(device=ctx.device, dtype=torch.int32).contiguous()
+    check(_abi.load().smc_shard_scatter_u(ctx.handle, idx.numel(), _ptr(idx), _ptr(rows)),
+          "smc_shard_scatter_u", ctx.handle)
+    torch.cuda.current_stream(ctx.device).synchronize()  # idx and rows may be freed after return
+
+
+def smc_move_accepts(ctx: Context) -> tuple[int, int]:
+    au, at = ctypes.c_uint64(), ctypes.c_uint64()
+    check(_abi.load().smc_move_accepts(ctx.handle, ctypes.byref(au), ctypes.byref(at)),
+          "smc_move_accepts", ctx.handle)
+    return au.value, at.value
+
+
+def smc_finish_moves(ctx: Context, R: int, acc_u: int, acc_theta: int) -> None:
+    check(_abi.load().smc_finish_moves(ctx.handle, int(R), int(acc_u), int(acc_theta)),
+          "smc_finish_moves", ctx.handle)
 
 
 def smc_resample_noalloc(W: torch.Tensor, seed: int, stage: int, ancestors: torch.Tensor,
