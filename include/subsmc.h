@@ -379,7 +379,10 @@ int smc_resample_noalloc(int32_t N, const double *W, uint64_t seed, int32_t stag
 
 /* Many independent problems (uneven n and p; BF16 storage) stepped together. One context per
  * problem, created as by smc_init with cfgs[q] (all on the same stream; the estimator tile is
- * the narrowest compiled tile that covers the widest row, the HMC kernel the streamed one). */
+ * the narrowest compiled tile that covers the widest row). The trajectories run in groups: each
+ * problem goes to the narrowest resident tile (subsample kept in shared memory, 4 warps) that
+ * takes its p, m and G, unless cfgs[q].hmc_kernel = 1 asks for the streamed kernel; problems no
+ * resident tile takes (p > 32) and random-walk problems form the streamed group. */
 typedef struct smc_batch smc_batch;
 int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const smc_config *cfgs,
                    void *stream);
@@ -390,12 +393,17 @@ const char *smc_batch_last_error(const smc_batch *b);
 int smc_batch_context(smc_batch *b, int32_t q, smc_ctx **ctx);
 /* The batch's estimator tile as a tile_hint value. */
 int smc_batch_tile(const smc_batch *b, int32_t *tile_hint);
+/* The trajectory kernel of problem q as an hmc_kernel value (1 = streamed, k >= 2 = resident
+ * tile k - 2): a context created with it (and the batch's tile) steps problem q identically. */
+int smc_batch_hmc_kernel(const smc_batch *b, int32_t q, int32_t *hmc_kernel);
 int64_t smc_batch_launch_count(const smc_batch *b);
-/* One stage of every problem (Algorithm 2 (a)-(f)): reweight and resample per problem, then per
- * move one u-update launch and one HMC trajectory launch over the particles of all problems
- * together, then the step sizes. use_graph = 1: the whole batch stage is captured once per buffer
- * parity and replayed as one CUDA graph (kernels read the stage index from device counters), with
- * results bit-identical to use_graph = 0 and to stepping each problem alone with the same tile. */
+/* One stage of every problem (Algorithm 2 (a)-(f)): reweight and resample per problem (the
+ * problems side by side on up to 16 side streams, forked from and joined back to the batch's
+ * stream), then per move one u-update launch over the particles of all problems and one
+ * trajectory launch per group, then the step sizes. use_graph = 1: the whole batch stage is
+ * captured once per buffer parity and replayed as one CUDA graph (kernels read the stage index
+ * from device counters), with results bit-identical to use_graph = 0 and to stepping each problem
+ * alone with the same tiles (smc_batch_tile, smc_batch_hmc_kernel). */
 int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph);
 /* Time the batched HMC launch for every compiled tile that covers the widest row (on scratch
  * copies; the state is unchanged) and keep the fastest; output: the tile as a tile_hint value. */

@@ -52,6 +52,7 @@ SIGNATURES = {
     "smc_batch_last_error": (ctypes.c_char_p, [c_vp]),
     "smc_batch_context": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
     "smc_batch_tile": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i32)]),
+    "smc_batch_hmc_kernel": (ctypes.c_int, [c_vp, c_i32, ctypes.POINTER(c_i32)]),
     "smc_batch_launch_count": (ctypes.c_int64, [c_vp]),
     "smc_batch_stage": (ctypes.c_int, [c_vp, c_i32, c_i32]),
     "smc_batch_autotune": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i32)]),

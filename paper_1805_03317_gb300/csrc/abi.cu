@@ -1538,18 +1538,35 @@ int smc_finish_moves(smc_ctx *c, int32_t R, uint64_t acc_u, uint64_t acc_theta) 
 // per problem, and per move one u-update launch and one HMC launch over all particles of all
 // problems (the kernels find each particle's problem from the prefix offsets).
 // ------------------------------------------------------------------------------------------------
+// A group of problems whose trajectories run in one launch: a resident tile (tile >= 0, the
+// subsample kept in shared memory; the plan sized by the group's largest p, m and G) or the
+// streamed kernel (tile = -1). The group's problems are order[start .. start + count).
+struct BatchGroup {
+  int tile, start, count, total, pmax, mmax, Gmax;
+};
+
 struct smc_batch {
   int P = 0, tile = 0, total = 0, wstride = 0, Rcap = 0;
   std::vector<smc_ctx *> ctx;
   cudaStream_t stream = nullptr;
-  int *offsets_d = nullptr;
-  EstArgs *args_d = nullptr;  // [Rcap] x [P] arguments of the batched launches
+  int *offsets_d = nullptr;   // [P] first particle of each problem (problem order)
+  int *goff_d = nullptr;      // [P] first particle of each problem within its group (sorted order)
+  std::vector<int> order;     // problems sorted by group
+  std::vector<int> group_of;  // per problem: its group
+  std::vector<BatchGroup> groups;
+  EstArgs *args_d = nullptr;  // [Rcap] x [2 P]: per move the problems' arguments in problem order,
+                              // then in the sorted order of the groups
   std::vector<EstArgs> args_h;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   EstArgs *gargs[2] = {nullptr, nullptr};  // the argument arrays each graph reads
   int gR[2] = {0, 0};
   int64_t glaunches[2] = {0, 0};  // kernel launches inside each graph
   int64_t launches = 0;
+  // side streams for the per-problem stage steps (reweighting, moments, resampling): problem q
+  // runs on side[q % side.size()], forked from and joined back to the batch stream by events
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev_side;
+  cudaEvent_t ev_fork = nullptr;
   std::string err;
 };
 
@@ -1575,51 +1592,89 @@ static EstArgs batch_move_args(smc_ctx *c, int move, bool swapped, int stage_dev
 }
 
 static int batch_upload(smc_batch *b, int R, bool swapped, int stage_dev) {
+  const size_t P2 = 2 * (size_t)b->P;
   if (R > b->Rcap) {
     if (b->args_d) cudaFree(b->args_d);
     b->args_d = nullptr;
-    if (cudaMalloc(&b->args_d, sizeof(EstArgs) * (size_t)R * b->P) != cudaSuccess)
+    if (cudaMalloc(&b->args_d, sizeof(EstArgs) * (size_t)R * P2) != cudaSuccess)
       return bfail(b, SMC_ERR_OOM, "batch argument array");
     b->Rcap = R;
   }
-  b->args_h.resize((size_t)R * b->P);
+  b->args_h.resize((size_t)R * P2);
   for (int r = 0; r < R; ++r)
     for (int q = 0; q < b->P; ++q)
-      b->args_h[(size_t)r * b->P + q] =
+      b->args_h[(size_t)r * P2 + q] =
           batch_move_args(b->ctx[q], swapped ? r : b->ctx[q]->moves_in_stage + r, swapped,
                           stage_dev);
+  for (int r = 0; r < R; ++r)
+    for (int k = 0; k < b->P; ++k)
+      b->args_h[(size_t)r * P2 + b->P + k] = b->args_h[(size_t)r * P2 + b->order[k]];
   // synchronous with respect to the host (pageable source), before any capture begins
-  if (cudaMemcpyAsync(b->args_d, b->args_h.data(), sizeof(EstArgs) * (size_t)R * b->P,
+  if (cudaMemcpyAsync(b->args_d, b->args_h.data(), sizeof(EstArgs) * (size_t)R * P2,
                       cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return bfail(b, SMC_ERR_CUDA, "batch argument upload");
   return SMC_OK;
 }
 
+// Per move: one u-update launch over all problems (streamed rows), then one trajectory launch
+// per group (resident tile, or the streamed kernel for problems no resident tile takes).
 static int batch_moves(smc_batch *b, int R) {
+  const size_t P2 = 2 * (size_t)b->P;
+  const int sms = b->ctx[0]->sms;
   for (int r = 0; r < R; ++r) {
     BatchArgs ba;
-    ba.probs = b->args_d + (size_t)r * b->P;
+    ba.probs = b->args_d + (size_t)r * P2;
     ba.offsets = b->offsets_d;
     ba.nprob = b->P;
     ba.total = b->total;
     ba.wstride = b->wstride;
     int e = est_launch_batch_bf16(1, b->tile, ba, b->stream);
-    if (!e) e = est_launch_batch_bf16(2, b->tile, ba, b->stream);
+    b->launches += 1;
+    for (size_t g = 0; g < b->groups.size() && !e; ++g) {
+      const BatchGroup &gr = b->groups[g];
+      BatchArgs bg;
+      bg.probs = b->args_d + (size_t)r * P2 + b->P + gr.start;
+      bg.offsets = b->goff_d + gr.start;
+      bg.nprob = gr.count;
+      bg.total = gr.total;
+      bg.wstride = b->wstride;
+      e = gr.tile >= 0 ? res_launch_batch_bf16(gr.tile, bg, gr.pmax, gr.mmax, gr.Gmax, b->stream,
+                                               sms, false)
+                       : est_launch_batch_bf16(2, b->tile, bg, b->stream);
+      b->launches += 1;
+    }
     if (e) return bfail(b, SMC_ERR_CUDA, std::string("batched move: ") +
                                              cudaGetErrorString((cudaError_t)e));
-    b->launches += 2;
   }
   return SMC_OK;
 }
 
 // The stage of every problem: reweight and resample per problem, R batched moves, step sizes.
 static int batch_stage_body(smc_batch *b, int R, bool args_ready) {
-  for (smc_ctx *c : b->ctx) {
+  // the problems' reweighting and resampling are independent: side streams run them side by
+  // side (inside a capture they become parallel branches of the graph)
+  const int ns = (int)b->side.size();
+  if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess)
+    return bfail(b, SMC_ERR_CUDA, "stage fork");
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamWaitEvent(b->side[k], b->ev_fork, 0) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "stage fork");
+  for (int q = 0; q < b->P; ++q) {
+    smc_ctx *c = b->ctx[q];
+    cudaStream_t own = c->stream;
+    c->stream = b->side[q % ns];
     int r = smc_reweight(c, nullptr, nullptr, nullptr);
     if (!r) r = smc_resample(c, nullptr);
+    if (!r && cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream) !=
+                  cudaSuccess)
+      r = fail(c, SMC_ERR_CUDA, "accept counters");
+    c->stream = own;
     if (r) return bfail(b, r, c->err);
-    if (cudaMemsetAsync(&c->st->acc_u, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
-      return bfail(b, SMC_ERR_CUDA, "accept counters");
+  }
+  for (int k = 0; k < ns; ++k) {
+    if (cudaEventRecord(b->ev_side[k], b->side[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev_side[k], 0) != cudaSuccess)
+      return bfail(b, SMC_ERR_CUDA, "stage join");
   }
   if (!args_ready) {
     int r = batch_upload(b, R, false, 0);
@@ -1669,8 +1724,9 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
   for (int q = 0; q < P; ++q) {
     smc_config cfg = cfgs[q];
     cfg.tile_hint = tile + 1;
-    cfg.hmc_kernel = 1;  // the batched HMC launch is the streamed trajectory kernel
+    cfg.hmc_kernel = 1;  // the context's own kernel; the batch chooses its trajectory launches
     cfg.full_data = 0;
+    cfg.shard_base = cfg.shard_count = 0;
     smc_ctx *c = nullptr;
     const int r = smc_init(&c, &probs[q], &cfg, nullptr, stream);
     if (r != SMC_OK) {
@@ -1691,6 +1747,69 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
     g_init_error = "batch offsets";
     return SMC_ERR_OOM;
   }
+  // groups: each problem goes to the narrowest resident tile (4 warps) that takes its p, m and
+  // G, unless its configuration asks for the streamed trajectory (hmc_kernel = 1)
+  {
+    static const int kCand[][2] = {{0, 8}, {7, 12}, {1, 16}, {6, 20}, {2, 24}, {3, 32}};
+    std::vector<int> gt(P, -1);
+    BatchArgs dry{};
+    for (int q = 0; q < P; ++q) {
+      // the random-walk move runs on the streamed kernel only
+      if (cfgs[q].hmc_kernel == 1 || cfgs[q].theta_move == 1) continue;
+      const smc_ctx *c = b->ctx[q];
+      for (const auto &t : kCand)
+        if (c->p <= t[1] &&
+            res_launch_batch_bf16(t[0], dry, c->p, c->m, c->G, b->stream, c->sms, true) == 0) {
+          gt[q] = t[0];
+          break;
+        }
+    }
+    std::vector<int> tiles;
+    for (int q = 0; q < P; ++q)
+      if (std::find(tiles.begin(), tiles.end(), gt[q]) == tiles.end()) tiles.push_back(gt[q]);
+    b->group_of.assign(P, 0);
+    std::vector<int> goff(P, 0);
+    for (int t : tiles) {
+      BatchGroup g{t, (int)b->order.size(), 0, 0, 0, 0, 0};
+      for (int q = 0; q < P; ++q) {
+        if (gt[q] != t) continue;
+        const smc_ctx *c = b->ctx[q];
+        b->group_of[q] = (int)b->groups.size();
+        goff[b->order.size()] = g.total;
+        b->order.push_back(q);
+        g.count += 1;
+        g.total += c->N;
+        g.pmax = std::max(g.pmax, c->p);
+        g.mmax = std::max(g.mmax, c->m);
+        g.Gmax = std::max(g.Gmax, c->G);
+      }
+      if (t >= 0 && res_launch_batch_bf16(t, dry, g.pmax, g.mmax, g.Gmax, b->stream,
+                                          b->ctx[0]->sms, true) != 0) {
+        smc_batch_free(b);
+        g_init_error = "batch: a resident group's plan does not fit";
+        return SMC_ERR_ARG;
+      }
+      b->groups.push_back(g);
+    }
+    if (cudaMalloc(&b->goff_d, sizeof(int) * P) != cudaSuccess ||
+        cudaMemcpy(b->goff_d, goff.data(), sizeof(int) * P, cudaMemcpyHostToDevice) != cudaSuccess) {
+      smc_batch_free(b);
+      g_init_error = "batch group offsets";
+      return SMC_ERR_OOM;
+    }
+  }
+  const int ns = P < 16 ? P : 16;
+  b->side.assign(ns, nullptr);
+  b->ev_side.assign(ns, nullptr);
+  bool ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < ns && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_side[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    smc_batch_free(b);
+    g_init_error = "batch side streams";
+    return SMC_ERR_CUDA;
+  }
   *out = b;
   return SMC_OK;
 }
@@ -1704,7 +1823,13 @@ int smc_batch_free(smc_batch *b) {
   }
   for (smc_ctx *c : b->ctx) smc_free(c);
   if (b->offsets_d) cudaFree(b->offsets_d);
+  if (b->goff_d) cudaFree(b->goff_d);
   if (b->args_d) cudaFree(b->args_d);
+  for (cudaStream_t st : b->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->ev_side)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
   return SMC_OK;
 }
@@ -1722,6 +1847,13 @@ int smc_batch_context(smc_batch *b, int32_t q, smc_ctx **ctx) {
 int smc_batch_tile(const smc_batch *b, int32_t *tile_hint) {
   if (!b || !tile_hint) return SMC_ERR_ARG;
   *tile_hint = b->tile + 1;
+  return SMC_OK;
+}
+
+int smc_batch_hmc_kernel(const smc_batch *b, int32_t q, int32_t *hmc_kernel) {
+  if (!b || !hmc_kernel || q < 0 || q >= b->P) return SMC_ERR_ARG;
+  const int t = b->groups[b->group_of[q]].tile;
+  *hmc_kernel = t >= 0 ? t + 2 : 1;
   return SMC_OK;
 }
 

@@ -119,6 +119,11 @@ int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dr
 int res_tiles_f64(Tile *out, int cap);
 int res_tiles_f32(Tile *out, int cap);
 int res_tiles_bf16(Tile *out, int cap);
+// The resident trajectory over the particles of a batch of problems that share one resident
+// tile (BF16 storage): the shared-memory plan is sized by the largest p, m and G among them.
+// Returns a cudaError_t, -1 for a tile without a batched form, -2 when the plan does not fit.
+int res_launch_batch_bf16(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
+                          cudaStream_t s, int sms, bool dry);
 
 // Stage kernels (stage.cu). All return cudaError_t.
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,

@@ -32,4 +32,17 @@ int res_launch_bf16(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dr
   }
 }
 
+int res_launch_batch_bf16(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
+                          cudaStream_t s, int sms, bool dry) {
+  switch (tile) {
+    case 0: return launch_res_batch<XT, 8, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    case 1: return launch_res_batch<XT, 16, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    case 2: return launch_res_batch<XT, 24, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    case 3: return launch_res_batch<XT, 32, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    case 6: return launch_res_batch<XT, 20, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    case 7: return launch_res_batch<XT, 12, 4>(b, p_max, m_max, G_max, s, sms, dry);
+    default: return -1;  // the 8-warp and tensor-core tiles have no batched form
+  }
+}
+
 }  // namespace subsmc

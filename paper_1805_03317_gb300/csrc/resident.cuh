@@ -87,8 +87,11 @@ __device__ __forceinline__ void load_res_row(const unsigned char *row,
   }
 }
 
+// One particle's trajectory: particle i of the problem described by a. reload: the CTA's previous
+// particle belonged to another problem (or there was none), so the C and Sigma tiles are loaded.
 template <typename XT, int CPL, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
+__device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reload,
+                                             const ResPlan &P) {
   using SD = Store<XT>;
   using CT = typename SD::CT;
   static_assert(CPL <= 32, "one column per lane");
@@ -118,18 +121,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   const CT muc = col ? ldg_ct<CT>(a.mu_ct, lane) : CT(0);
   const CT ivc = col ? ldg_ct<CT>(a.ivar_ct, lane) : CT(0);
   const CT tbc = col ? ldg_ct<CT>(a.tb_ct, lane) : CT(0);
+  const int nvec = round16(p * (int)sizeof(XT)) / 16;  // 16-byte vectors of this problem's rows
 
-  for (int e = tid; e < CPL * CPL; e += blockDim.x) {
-    const int r = e / CPL, c = e - r * CPL;
-    const bool in = r < p && c < p;
-    Cs[e] = in ? ldg_ct<CT>(a.C_ct, r * p + c) : CT(0);
-    Sgs[e] = in ? ldg_ct<CT>(a.Sigma_ct, r * p + c) : CT(0);
+  __syncthreads();  // the previous particle is finished with shared memory
+  if (reload) {
+    for (int e = tid; e < CPL * CPL; e += blockDim.x) {
+      const int r = e / CPL, c = e - r * CPL;
+      const bool in = r < p && c < p;
+      Cs[e] = in ? ldg_ct<CT>(a.C_ct, r * p + c) : CT(0);
+      Sgs[e] = in ? ldg_ct<CT>(a.Sigma_ct, r * p + c) : CT(0);
+    }
   }
-
-  for (int il = blockIdx.x; il < a.B; il += gridDim.x) {
-    const int i = a.i0 + il;  // global particle index
+  {
     const int32_t *u = a.u + (int64_t)i * m;
-    __syncthreads();  // the previous particle is finished with shared memory
     // 1. gather x_{u_j} and the row's constants at the centre (its tail) with 16-byte copies;
     // invalid indices are flagged and their rows zeroed. Vectors the tile reads beyond the row's
     // covariates (a tile wider than p) are zero-filled. The indices are staged in shared memory
@@ -145,8 +149,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
       const int k = us[j];
       unsigned char *dst = q < P.nvl ? rows + (size_t)j * P.rb + 16 * q
                                      : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvl);
-      const int qs = q < P.nvl ? q : P.nvec + (q - P.nvl);  // 16-byte vector of the packed row
-      if (k < 0 || (int64_t)k >= a.n || (q >= P.nvec && q < P.nvl)) {
+      const int qs = q < P.nvl ? q : nvec + (q - P.nvl);  // 16-byte vector of the packed row
+      if (k < 0 || (int64_t)k >= a.n || (q >= nvec && q < P.nvl)) {
         *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
         if (q == 0 && (k < 0 || (int64_t)k >= a.n)) set_err(a.st, kErrIndex);
         continue;
@@ -354,6 +358,25 @@ __global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
   }
 }
 
+template <typename XT, int CPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_hmc_res(EstArgs a, ResPlan P) {
+  for (int il = blockIdx.x; il < a.B; il += gridDim.x)
+    res_particle<XT, CPL, WARPS>(a, a.i0 + il, il == (int)blockIdx.x, P);
+}
+
+// All particles of a batch of independent posteriors (the problems of one resident tile): the
+// global particle index picks the problem from the prefix offsets; the shared-memory plan is the
+// largest over those problems.
+template <typename XT, int CPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_hmc_res_batch(BatchArgs b, ResPlan P) {
+  int qcur = -1;
+  for (int g = blockIdx.x; g < b.total; g += gridDim.x) {
+    const int q = batch_problem(b.offsets, b.nprob, g);
+    res_particle<XT, CPL, WARPS>(b.probs[q], g - b.offsets[q], q != qcur, P);
+    qcur = q;
+  }
+}
+
 // dry: only check that the plan fits (no launch).
 template <typename XT, int CPL, int WARPS>
 inline int launch_res(const EstArgs &a, cudaStream_t s, int sms, bool dry) {
@@ -376,6 +399,33 @@ inline int launch_res(const EstArgs &a, cudaStream_t s, int sms, bool dry) {
   if (dry || a.B <= 0) return 0;
   const int grid = a.B < per_sm * sms ? a.B : per_sm * sms;
   k_hmc_res<XT, CPL, WARPS><<<grid, WARPS * 32, P.total, s>>>(a, P);
+  return (int)cudaGetLastError();
+}
+
+// Batched launch over the problems in b (their largest p, m and G size the plan). dry: check the
+// fit only. Returns a cudaError_t or -2 when the plan does not fit.
+template <typename XT, int CPL, int WARPS>
+inline int launch_res_batch(const BatchArgs &b, int p_max, int m_max, int G_max, cudaStream_t s,
+                            int sms, bool dry) {
+  using CT = typename Store<XT>::CT;
+  if (p_max > CPL) return -2;
+  const ResPlan P = res_plan<CT>(p_max, m_max, G_max, (int)sizeof(XT), WARPS, CPL);
+  cudaError_t e = cudaFuncSetAttribute(k_hmc_res_batch<XT, CPL, WARPS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, P.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hmc_res_batch<XT, CPL, WARPS>,
+                                                    WARPS * 32, P.total);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return -2;
+  }
+  if (dry || b.total <= 0) return 0;
+  const int grid = b.total < per_sm * sms ? b.total : per_sm * sms;
+  k_hmc_res_batch<XT, CPL, WARPS><<<grid, WARPS * 32, P.total, s>>>(b, P);
   return (int)cudaGetLastError();
 }
 

@@ -493,7 +493,8 @@ def _bcheck(code: int, where: str, handle) -> None:
 def smc_batch_init(problems, stream=None) -> Batch:
     """problems: list of dicts with X, y, family, prior_mean, prior_var and the smc_init settings
     (N, m, G, L, seed; optional ess_frac, noise_sigma, dof, eps0, search_k, search_rounds,
-    cv_order, cv_centre, resampling, grid_points, grid_decades, theta_move)."""
+    cv_order, cv_centre, resampling, grid_points, grid_decades, theta_move, hmc_kernel: 1 keeps
+    the problem on the streamed trajectory kernel, 0 lets the batch pick a resident tile)."""
     lib = _abi.load()
     P = len(problems)
     probs = (SmcProblem * P)()
@@ -513,7 +514,8 @@ def smc_batch_init(problems, stream=None) -> Batch:
                               float(d.get("dof", 5.0)))
         cfgs[q] = SmcConfig(d["N"], d["m"], d["G"], d["L"], float(d.get("ess_frac", 0.5)),
                             int(d["seed"]) & ((1 << 64) - 1), d.get("search_k", 16),
-                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0, 1, 0,
+                            d.get("search_rounds", 10), float(d.get("eps0", 0.0)), 0,
+                            int(d.get("hmc_kernel", 0)), 0,
                             int(d.get("cv_order", 2)), int(d.get("cv_centre", 0)), 0,
                             RESAMPLING[d.get("resampling", "systematic")],
                             int(d.get("grid_points", 0)), float(d.get("grid_decades", 0.0)),
@@ -557,6 +559,14 @@ def smc_batch_autotune(b: Batch) -> int:
 def smc_batch_tile(b: Batch) -> int:
     t = ctypes.c_int32()
     _bcheck(_abi.load().smc_batch_tile(b.handle, ctypes.byref(t)), "smc_batch_tile", b.handle)
+    return t.value
+
+
+def smc_batch_hmc_kernel(b: Batch, q: int) -> int:
+    """Problem q's trajectory kernel as an hmc_kernel value (1 streamed, k >= 2 resident tile)."""
+    t = ctypes.c_int32()
+    _bcheck(_abi.load().smc_batch_hmc_kernel(b.handle, int(q), ctypes.byref(t)),
+            "smc_batch_hmc_kernel", b.handle)
     return t.value
 
 

@@ -450,7 +450,9 @@ def test_batch_with_mixed_options_matches_single_problems():
         # the same centre as the batch's problem (the device's Newton mode; an independently
         # found mode can round to another FP32 value)
         tb = S().smc_get_centre(S().smc_batch_context(b, q))[0]
-        singles.append(make_pair(w, tile_hint=tile, hmc_kernel=1, theta_bar=tb, **kw)[1])
+        hk = S().smc_batch_hmc_kernel(b, q)  # resident tile, or streamed (the random walk)
+        assert (hk == 1) == (o.get("theta_move") == "rw")
+        singles.append(make_pair(w, tile_hint=tile, hmc_kernel=hk, theta_bar=tb, **kw)[1])
     for use_graph in [False, True, True, False]:
         S().smc_batch_stage(b, 2, use_graph=use_graph)
         for c in singles:

@@ -644,16 +644,28 @@ def _batch_problem_dicts(wls):
     return out
 
 
-def test_batch_stages_match_single_problems():
-    """One batched u-update and one batched HMC launch per move over all problems' particles
-    (plain and graph-replayed stages) gives bit-identical results to stepping each problem alone
-    with the same tile and the streamed trajectory kernel."""
+@pytest.mark.parametrize("streamed", [False, True])
+def test_batch_stages_match_single_problems(streamed):
+    """One batched u-update launch and one trajectory launch per group per move (resident tiles
+    grouped by p, the streamed kernel for p > 32 or when asked; per-problem stage steps on side
+    streams; plain and graph-replayed stages) give bit-identical results to stepping each problem
+    alone with the same tiles."""
     from smc_workloads import batch_uneven
-    wls = batch_uneven(P=5, N=96, G=5, L=4, R=2, n_lo=2000, n_hi=20000)
-    b = S().smc_batch_init(_batch_problem_dicts(wls))
+    wls = batch_uneven(P=7, N=96, G=5, L=4, R=2, n_lo=2000, n_hi=20000)
+    dicts = _batch_problem_dicts(wls)
+    if streamed:
+        for d in dicts:
+            d["hmc_kernel"] = 1
+    b = S().smc_batch_init(dicts)
     tile = S().smc_batch_tile(b)
+    kernels = [S().smc_batch_hmc_kernel(b, q) for q in range(len(wls))]
+    if streamed:
+        assert kernels == [1] * len(wls)
+    else:
+        assert len(set(kernels)) >= 3 and all(
+            (k == 1) == (w.p > 32) for k, w in zip(kernels, wls))
     # the singles take the batch problems' centres (the device's Newton modes)
-    singles = [make_pair(w, tile_hint=tile, hmc_kernel=1,
+    singles = [make_pair(w, tile_hint=tile, hmc_kernel=kernels[q],
                          theta_bar=S().smc_get_centre(S().smc_batch_context(b, q))[0])[1]
                for q, w in enumerate(wls)]
     for use_graph in [False, True, True, False, True, True]:
