@@ -14,7 +14,7 @@ its own slice [lo, hi) (smc_config.shard_base / shard_count). A stage then runs 
 The reweighting and resampling see identical inputs on every process, so the temperatures,
 weights and integer ancestors agree exactly; the moves use the particles' global indices in the
 counter-based random streams, so a sharded run reproduces the single-process run bit for bit. The
-exchanged volumes per stage are 16N + 8NG + 4Np bytes in the all-gather (FP64 estimates, block
+exchanged volumes per stage are 16N + 16NG + 4Np bytes in the all-gather (FP64 estimates, block
 sums, FP32 theta) and 4m bytes per migrated particle.
 
 The collectives are torch.distributed's (NCCL between GPUs: device tensors; gloo: host tensors).
