@@ -89,6 +89,27 @@ __device__ __forceinline__ double stream_normal(const Stream &st, uint32_t j) {
   box_muller(ra, rb, z0, z1);
   return (j & 1) ? z1 : z0;
 }
+// The same normal evaluated in FP32 (for FP32 particle states): the same u1 = (k + 1) 2^-53 and
+// u2, with log u1 formed without losing the integer's bits: logf of the exactly scaled value when
+// u1 < 1/2, log1pf of the exact integer complement -(2^53 - 1 - k) 2^-53 otherwise. Agrees with
+// the FP64 value rounded to FP32 to a few units in the last place.
+__device__ __forceinline__ float stream_normal_f32(const Stream &st, uint32_t j) {
+  uint64_t ra, rb;
+  st.pair(j >> 1, ra, rb);
+  const uint64_t k = ra >> 11;
+  const float lu = k < (1ull << 52) ? logf((float)(k + 1) * 0x1.0p-53f)
+                                    : log1pf(-(float)((1ull << 53) - 1 - k) * 0x1.0p-53f);
+  const float r = sqrtf(-2.0f * lu);
+  float sn, cs;
+  sincospif(2.0f * ((float)(rb >> 11) * 0x1.0p-53f), &sn, &cs);
+  return (j & 1) ? r * sn : r * cs;
+}
+template <typename CT> __device__ __forceinline__ CT stream_normal_ct(const Stream &st, uint32_t j) {
+  if constexpr (sizeof(CT) == 4)
+    return stream_normal_f32(st, j);
+  else
+    return stream_normal(st, j);
+}
 
 // ------------------------------------------------------------------------------------------------
 // Packed row layout. Row k of the library's copy of the data holds
@@ -267,7 +288,15 @@ __device__ __forceinline__ void row_incr(const RowC<CT> &c, CT D, CT inv_s2, CT 
       r = -D2 * pr;
       return;
     }
-    if (fabs(D) <= kSmall) {
+    // FP32: one form per warp (a vote over the lanes evaluating a row here), so a warp whose rows
+    // straddle |D| = 1/2 does not run both forms; rows with small |D| in a warp that takes the
+    // exp/log form carry that form's absolute error (about 3e-7) instead of the series' relative one
+    bool series;
+    if constexpr (sizeof(CT) == 4)
+      series = !__any_sync(__activemask(), fabs(D) > kSmall);
+    else
+      series = fabs(D) <= kSmall;
+    if (series) {
       const CT q = CT(1) - CT(2) * sb;
       const CT k3 = w * q;
       const CT k4 = w * (CT(1) - CT(6) * w);

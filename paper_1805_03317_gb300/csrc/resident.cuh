@@ -163,7 +163,7 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
     const CT eps = (CT)jittered_eps(a.st->eps, a.eps_jitter, a.seed, smv, (uint32_t)i);
     if (warp == 0) {
       const Stream smom(a.seed, kMomentum, smv, (uint32_t)i);
-      CT z = col ? (CT)stream_normal(smom, (uint32_t)lane) : CT(0);
+      CT z = col ? stream_normal_ct<CT>(smom, (uint32_t)lane) : CT(0);
       CT acc = CT(0);
       for (int c = 0; c < p; ++c) {  // rho_r = sum_{c >= r} Linv[c, r] z_c
         const CT zc = __shfl_sync(0xffffffffu, z, c);

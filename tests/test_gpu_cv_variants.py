@@ -261,8 +261,22 @@ def test_grid_temperature_rule_matches_oracle(x_dtype, a0, grid):
     assert lz == pytest.approx(rlz, rel=rtol, abs=lz_abs)
     assert ess == pytest.approx(ress, rel=max(rtol, 1e-9))
     _, _, Wg = S().smc_get_particles(ctx)
-    np.testing.assert_allclose(Wg.cpu().numpy(), rW, rtol=1e-6 if x_dtype != "f64" else 1e-9,
-                               atol=1e-12)
+    Wg = Wg.cpu().numpy()
+    if x_dtype == "f64":
+        np.testing.assert_allclose(Wg, rW, rtol=1e-9, atol=1e-12)
+    else:
+        # FP32 estimates: the new weights are exactly the FP64 reweighting of the GPU's own
+        # cached estimates, and those are the oracle's within the estimator bars (an FP32 error
+        # e in l_hat moves a log weight by (a_new - a0) e, which no fixed weight bar can hold)
+        ell_g, s2_g, _ = (t.cpu().numpy() for t in S().smc_get_cache(ctx))
+        D = a_new - a0
+        h = 0.5 * ((a0 + D) ** 2 - a0 ** 2)
+        lw = np.log(W) + D * ell_g - h * s2_g
+        Wp = np.exp(lw - (lw.max() + np.log(np.exp(lw - lw.max()).sum())))
+        np.testing.assert_allclose(Wg, Wp, rtol=1e-9, atol=1e-15)
+        assert np.all(np.abs(ell_g - ref["ell"]) <= tol(x_dtype)["ell"] * np.abs(ref["ell"]))
+        bound = tol(x_dtype)["sig2"] * np.abs(ref["sigma2"]).max() + tol(x_dtype)["ell"] * np.abs(ref["ell"]).max()
+        assert np.max(np.abs(s2_g - ref["sigma2"])) <= bound
     S().smc_free(ctx)
 
 
