@@ -382,7 +382,7 @@ int smc_resample_noalloc(int32_t N, const double *W, uint64_t seed, int32_t stag
  * the narrowest compiled tile that covers the widest row). The trajectories run in groups: each
  * problem goes to the narrowest resident tile (subsample kept in shared memory, 4 warps) that
  * takes its p, m and G, unless cfgs[q].hmc_kernel = 1 asks for the streamed kernel; problems no
- * resident tile takes (p > 32) and random-walk problems form the streamed group. */
+ * resident tile takes (p > 40) and random-walk problems form the streamed group. */
 typedef struct smc_batch smc_batch;
 int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const smc_config *cfgs,
                    void *stream);

@@ -1750,7 +1750,7 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
   // groups: each problem goes to the narrowest resident tile (4 warps) that takes its p, m and
   // G, unless its configuration asks for the streamed trajectory (hmc_kernel = 1)
   {
-    static const int kCand[][2] = {{0, 8}, {7, 12}, {1, 16}, {6, 20}, {2, 24}, {3, 32}};
+    static const int kCand[][2] = {{0, 8}, {7, 12}, {1, 16}, {6, 20}, {2, 24}, {3, 32}, {9, 40}};
     std::vector<int> gt(P, -1);
     BatchArgs dry{};
     for (int q = 0; q < P; ++q) {

@@ -7,8 +7,9 @@
 // d_j, r_j (device.cuh), gradient partials in registers, a shuffle reduce-scatter per warp and one
 // CTA barrier per pass (partials double-buffered). Every warp then assembles the totals and the
 // gradient and runs the leapfrog update itself, with theta, rho and the gradient held one column
-// per lane, so no warp waits for another between passes. One CTA handles one particle at a time
-// and loops over particles (persistent grid).
+// per lane (lane l also holds column l + 32 in tiles wider than 32 slots), so no warp waits for
+// another between passes. One CTA handles one particle at a time and loops over particles
+// (persistent grid).
 //
 // Sums over rows are of e_j = d_j - K with a CTA-uniform shift K near the subsample mean of d: the
 // cached mean for the first pass, then the previous pass's mean (shifted data: Chan, Golub &
@@ -27,7 +28,15 @@ struct ResPlan {
   int rb;    // bytes per resident row (covariates only): an odd multiple of 16 (conflict-free LDS.128)
   int nvec;  // 16-byte vectors of covariates per row (copied from the packed row)
   int nvl;   // 16-byte vectors the tile's CPL slots read (>= nvec; the extra ones are zero-filled)
-  int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, total;
+  int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, off_k, total;
+};
+
+// Constants of one launch of a problem (temperature, n/m, stage counter), computed once per
+// problem by one thread instead of once per particle by every thread.
+template <typename CT> struct alignas(16) ResK {
+  double temp, nm, inv_m;
+  CT ta, ta2, tnm;
+  uint32_t smv;
 };
 
 inline __host__ __device__ int round16(int v) { return (v + 15) & ~15; }
@@ -54,6 +63,8 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   off = round16(off + G * 2 * (int)sizeof(double));
   P.off_mat = off;  // C and Sigma, zero-padded to [cpl, cpl], state type
   off = round16(off + 2 * cpl * cpl * (int)sizeof(CT));
+  P.off_k = off;
+  off = round16(off + (int)sizeof(ResK<CT>));
   P.total = off;
   return P;
 }
@@ -89,12 +100,14 @@ __device__ __forceinline__ void load_res_row(const unsigned char *row,
 
 // One particle's trajectory: particle i of the problem described by a. reload: the CTA's previous
 // particle belonged to another problem (or there was none), so the C and Sigma tiles are loaded.
+// Lane l of every warp holds columns l, l + 32, .. of theta, rho and the gradient (NC per lane).
 template <typename XT, int CPL, int WARPS>
 __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reload,
                                              const ResPlan &P) {
   using SD = Store<XT>;
   using CT = typename SD::CT;
-  static_assert(CPL <= 32, "one column per lane");
+  constexpr int NC = (CPL + 31) / 32;
+  static_assert(NC <= 2, "at most two columns per lane");
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = a.p, m = a.m, G = a.G, S = a.S;
@@ -108,23 +121,39 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
   double *blks = reinterpret_cast<double *>(smem + P.off_blk);   // [G][2]
   CT *Cs = reinterpret_cast<CT *>(smem + P.off_mat);  // [CPL, CPL] zero-padded
   CT *Sgs = Cs + CPL * CPL;                            // [CPL, CPL] zero-padded
-  const double temp = a.st->a;
+  ResK<CT> *ks = reinterpret_cast<ResK<CT> *>(smem + P.off_k);
   const CT inv_s2 = (CT)a.inv_s2;
-  const double nm = (double)a.n / (double)m, inv_m = 1.0 / (double)m;
-  const CT ta = (CT)temp, ta2 = (CT)(temp * temp * nm * nm), tnm = (CT)(temp * nm);
-  const uint32_t smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
   const int fam = a.fam;
   const int cv1 = a.cv_order == 1;
-  const bool col = lane < p;
-  // per-lane column constants (lane c holds column c)
-  const CT Bc = col ? ldg_ct<CT>(a.B_ct, lane) : CT(0);
-  const CT muc = col ? ldg_ct<CT>(a.mu_ct, lane) : CT(0);
-  const CT ivc = col ? ldg_ct<CT>(a.ivar_ct, lane) : CT(0);
-  const CT tbc = col ? ldg_ct<CT>(a.tb_ct, lane) : CT(0);
+  // per-lane column constants (slot h of lane l is column l + 32 h)
+  bool col[NC];
+  int cl[NC];  // the column's index into the [CPL, CPL] tiles (0 past CPL: a padded read)
+  CT Bc[NC], muc[NC], ivc[NC], tbc[NC];
+#pragma unroll
+  for (int h = 0; h < NC; ++h) {
+    const int c = lane + 32 * h;
+    col[h] = c < p;
+    cl[h] = c < CPL ? c : 0;
+    Bc[h] = col[h] ? ldg_ct<CT>(a.B_ct, c) : CT(0);
+    muc[h] = col[h] ? ldg_ct<CT>(a.mu_ct, c) : CT(0);
+    ivc[h] = col[h] ? ldg_ct<CT>(a.ivar_ct, c) : CT(0);
+    tbc[h] = col[h] ? ldg_ct<CT>(a.tb_ct, c) : CT(0);
+  }
   const int nvec = round16(p * (int)sizeof(XT)) / 16;  // 16-byte vectors of this problem's rows
 
   __syncthreads();  // the previous particle is finished with shared memory
   if (reload) {
+    if (tid == 0) {
+      ResK<CT> k;
+      k.temp = a.st->a;
+      k.nm = (double)a.n / (double)m;
+      k.inv_m = 1.0 / (double)m;
+      k.ta = (CT)k.temp;
+      k.ta2 = (CT)(k.temp * k.temp * k.nm * k.nm);
+      k.tnm = (CT)(k.temp * k.nm);
+      k.smv = stage_move(a.stage_dev ? a.st->stage : a.stage, a.move);
+      *ks = k;
+    }
     for (int e = tid; e < CPL * CPL; e += blockDim.x) {
       const int r = e / CPL, c = e - r * CPL;
       const bool in = r < p && c < p;
@@ -144,8 +173,10 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
     __syncthreads();
     constexpr int NTV = (int)sizeof(RowC<CT>) / 16;
     const int nvr = P.nvl + NTV;
-    for (int t = tid; t < m * nvr; t += blockDim.x) {
-      const int j = t / nvr, q = t - j * nvr;
+    // copy t = j nvr + q (vector q of row j); each thread steps by blockDim.x = dj nvr + dq
+    const int dj = (int)blockDim.x / nvr, dq = (int)blockDim.x - dj * nvr;
+    int j = tid / nvr, q = tid - (tid / nvr) * nvr;
+    while (j < m) {
       const int k = us[j];
       unsigned char *dst = q < P.nvl ? rows + (size_t)j * P.rb + 16 * q
                                      : reinterpret_cast<unsigned char *>(cst + j) + 16 * (q - P.nvl);
@@ -153,45 +184,91 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
       if (k < 0 || (int64_t)k >= a.n || (q >= nvec && q < P.nvl)) {
         *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
         if (q == 0 && (k < 0 || (int64_t)k >= a.n)) set_err(a.st, kErrIndex);
-        continue;
+      } else {
+        cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * qs);
       }
-      cp_async16(dst, reinterpret_cast<const unsigned char *>(Xp + (int64_t)k * S) + 16 * qs);
+      j += dj;
+      q += dq;
+      if (q >= nvr) {
+        q -= nvr;
+        ++j;
+      }
     }
     cp_async_wait_all();
+    const ResK<CT> kc = *ks;  // written before the index-staging barrier
+    const double temp = kc.temp, nm = kc.nm, inv_m = kc.inv_m;
+    const CT ta = kc.ta, ta2 = kc.ta2, tnm = kc.tnm;
+    const uint32_t smv = kc.smv;
     // 2. initial momentum rho = Linv' z (warp 0; shared with the other warps below)
     CT *thg = reinterpret_cast<CT *>(a.theta_out) + (int64_t)i * p;
     const CT eps = (CT)jittered_eps(a.st->eps, a.eps_jitter, a.seed, smv, (uint32_t)i);
     if (warp == 0) {
       const Stream smom(a.seed, kMomentum, smv, (uint32_t)i);
-      CT z = col ? stream_normal_ct<CT>(smom, (uint32_t)lane) : CT(0);
-      CT acc = CT(0);
-      for (int c = 0; c < p; ++c) {  // rho_r = sum_{c >= r} Linv[c, r] z_c
-        const CT zc = __shfl_sync(0xffffffffu, z, c);
-        if (col && c >= lane) acc = fma(ldg_ct<CT>(a.Linv_ct, c * p + lane), zc, acc);
+      CT z[NC], acc[NC];
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+        z[h] = col[h] ? stream_normal_ct<CT>(smom, (uint32_t)(lane + 32 * h)) : CT(0);
+        acc[h] = CT(0);
       }
-      if (lane < CPL) rho0[lane] = col ? acc : CT(0);
+#pragma unroll
+      for (int hz = 0; hz < NC; ++hz)  // rho_r = sum_{c >= r} Linv[c, r] z_c, c ascending
+        for (int cc = 0; cc < 32 && 32 * hz + cc < p; ++cc) {
+          const int c = 32 * hz + cc;
+          const CT zc = __shfl_sync(0xffffffffu, z[hz], cc);
+#pragma unroll
+          for (int h = 0; h < NC; ++h) {
+            const int r = lane + 32 * h;
+            if (col[h] && c >= r) acc[h] = fma(ldg_ct<CT>(a.Linv_ct, c * p + r), zc, acc[h]);
+          }
+        }
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+        if (lane + 32 * h < CPL) rho0[lane + 32 * h] = col[h] ? acc[h] : CT(0);
     }
     __syncthreads();
-    // every warp now carries the trajectory in its lanes: theta_c, rho_c, grad_c at lane c
-    CT th = col ? thg[lane] : CT(0);
-    CT rho = lane < CPL ? rho0[lane] : CT(0);
-    CT gr = CT(0);
+    // every warp now carries the trajectory in its lanes: theta_c, rho_c, grad_c at lane c mod 32
+    CT th[NC], rho[NC], gr[NC];
+#pragma unroll
+    for (int h = 0; h < NC; ++h) {
+      const int c = lane + 32 * h;
+      th[h] = col[h] ? thg[c] : CT(0);
+      rho[h] = c < CPL ? rho0[c] : CT(0);
+      gr[h] = CT(0);
+    }
     CT dr[CPL];
     auto set_delta = [&]() {
-      const CT dl = col ? th - tbc : CT(0);
+      CT dl[NC];
 #pragma unroll
-      for (int s = 0; s < CPL; ++s) dr[s] = __shfl_sync(0xffffffffu, dl, s);
+      for (int h = 0; h < NC; ++h) dl[h] = col[h] ? th[h] - tbc[h] : CT(0);
+#pragma unroll
+      for (int s = 0; s < CPL; ++s) dr[s] = __shfl_sync(0xffffffffu, dl[s / 32], s % 32);
+    };
+    auto sigma_rho = [&](CT *vs) {  // (Sigma rho)_c at the lane's columns
+#pragma unroll
+      for (int h = 0; h < NC; ++h) vs[h] = CT(0);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const CT rk = __shfl_sync(0xffffffffu, rho[k / 32], k % 32);
+#pragma unroll
+        for (int h = 0; h < NC; ++h) vs[h] = fma(Sgs[k * CPL + cl[h]], rk, vs[h]);
+      }
     };
     auto kinetic = [&]() -> double {  // rho' Sigma rho / 2 (every lane of the warp)
-      CT v = CT(0);
+      CT v[NC];
+      sigma_rho(v);
+      double t = 0.0;
 #pragma unroll
-      for (int k = 0; k < CPL; ++k) v = fma(Sgs[k * CPL + (lane < CPL ? lane : 0)],
-                                            __shfl_sync(0xffffffffu, rho, k), v);
-      return 0.5 * warp_sum(col ? (double)rho * (double)v : 0.0);
+      for (int h = 0; h < NC; ++h) t += col[h] ? (double)rho[h] * (double)v[h] : 0.0;
+      return 0.5 * warp_sum(t);
     };
     auto log_prior = [&]() -> double {
-      const double rr = (double)th - (double)muc;
-      return warp_sum(col ? -0.5 * rr * rr * (double)ivc : 0.0) + a.log_prior_const;
+      double t = 0.0;
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+        const double rr = (double)th[h] - (double)muc[h];
+        t += col[h] ? -0.5 * rr * rr * (double)ivc[h] : 0.0;
+      }
+      return warp_sum(t) + a.log_prior_const;
     };
     set_delta();
     double ell = 0.0, sig = 0.0;
@@ -273,24 +350,36 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
         }
         __syncthreads();
       }
-      // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at lane c (every warp, FP32)
+      // gradient of a l_hat - a^2/2 sigma2_hat + log p(theta) at the lane's columns (every warp)
       const CT dbar = S1f * (CT)inv_m;  // mean of e
-      CT G1 = CT(0), G2 = CT(0);
-      if (col) {
+      CT cd[NC];
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-          G1 += rb[w * 2 * CPL + lane];
-          G2 += rb[w * 2 * CPL + CPL + lane];
+      for (int h = 0; h < NC; ++h) cd[h] = CT(0);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k)
+#pragma unroll
+        for (int h = 0; h < NC; ++h) cd[h] = fma(Cs[k * CPL + cl[h]], dr[k], cd[h]);
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+        const int c = lane + 32 * h;
+        CT G1 = CT(0), G2 = CT(0);
+        if (col[h]) {
+#pragma unroll
+          for (int w = 0; w < WARPS; ++w) {
+            G1 += rb[w * 2 * CPL + c];
+            G2 += rb[w * 2 * CPL + CPL + c];
+          }
         }
+        gr[h] = col[h] ? ta * (Bc[h] + cd[h]) + tnm * G1 - ta2 * (G2 - dbar * G1) -
+                             (th[h] - muc[h]) * ivc[h]
+                       : CT(0);
       }
-      CT cd = CT(0);
-      const int cl = lane < CPL ? lane : 0;
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) cd = fma(Cs[k * CPL + cl], dr[k], cd);
-      gr = col ? ta * (Bc + cd) + tnm * G1 - ta2 * (G2 - dbar * G1) - (th - muc) * ivc : CT(0);
       if (want_totals && warp == 0) {  // l_hat and sigma2_hat in FP64 (first and last pass)
-        const CT dc = col ? th - tbc : CT(0);
-        const CT qlin = warp_sum(col ? dc * (Bc + CT(0.5) * cd) : CT(0));
+        CT ql = CT(0);
+#pragma unroll
+        for (int h = 0; h < NC; ++h)
+          if (col[h]) ql += (th[h] - tbc[h]) * (Bc[h] + CT(0.5) * cd[h]);
+        const CT qlin = warp_sum(ql);
         double S1 = 0.0, S2 = 0.0;
         if (final) {
           for (int g = 0; g < G; ++g) {
@@ -320,15 +409,17 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
     pass(false, true);
     const double H0 = -(temp * ell - 0.5 * temp * temp * sig + lp0) + kin0;
     for (int l = 0; l < a.L; ++l) {
-      rho += CT(0.5) * eps * gr;
-      CT vs = CT(0);  // (Sigma rho)_c
+      CT vs[NC];
 #pragma unroll
-      for (int k = 0; k < CPL; ++k) vs = fma(Sgs[k * CPL + (lane < CPL ? lane : 0)],
-                                             __shfl_sync(0xffffffffu, rho, k), vs);
-      if (col) th += eps * vs;
+      for (int h = 0; h < NC; ++h) rho[h] += CT(0.5) * eps * gr[h];
+      sigma_rho(vs);
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+        if (col[h]) th[h] += eps * vs[h];
       set_delta();
       pass(l == a.L - 1, l == a.L - 1);
-      rho += CT(0.5) * eps * gr;
+#pragma unroll
+      for (int h = 0; h < NC; ++h) rho[h] += CT(0.5) * eps * gr[h];
     }
     // 4. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
     if (warp == 0) {
@@ -338,7 +429,9 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
       const double Uu = draw_uniform(smh.draw(0));
       const bool acc = log(Uu) < H0 - H1;  // false when H1 is NaN
       if (acc) {
-        if (col) thg[lane] = th;
+#pragma unroll
+        for (int h = 0; h < NC; ++h)
+          if (col[h]) thg[lane + 32 * h] = th[h];
         // the cache holds FP64 (sum d, sum d^2) per block: rebuilt from the shifted sums
         double *blk = a.blk + (int64_t)i * G * 2;
         const double k = (double)Ksh;

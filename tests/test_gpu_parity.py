@@ -320,14 +320,27 @@ def test_full_smc_run_matches_oracle_fp64(hmc_kernel):
 
 @pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
-@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10])
+@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10, 11])
 def test_moves_reduced_precision_match_oracle(x_dtype, family, hmc_kernel):
     """FP32 arithmetic on FP32/BF16-stored rows against the FP64 oracle on the same stored values:
     the MH decisions may differ only where the FP64 log ratio is within rounding of the uniform;
-    accepted end points agree to FP32 leapfrog rounding. hmc_kernel 5 and 8 are resident tiles
-    wider than the rows (32 and 20 slots for p = 13), whose slots past p must read zeros; 10 is
+    accepted end points agree to FP32 leapfrog rounding. hmc_kernel 5, 8 and 11 are resident tiles
+    wider than the rows (32, 20 and 40 slots for p = 13), whose slots past p must read zeros; 10 is
     the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90)."""
-    wl = _wl(family, x_dtype, p=13, N=256, m=90, G=6)
+    _moves_reduced_precision(_wl(family, x_dtype, p=13, N=256, m=90, G=6), x_dtype, hmc_kernel)
+
+
+@pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
+@pytest.mark.parametrize("p", [33, 37, 40])
+@pytest.mark.parametrize("hmc_kernel", [1, 11])
+def test_moves_two_columns_per_lane_match_oracle(family, p, hmc_kernel):
+    """p past one warp's lanes: the 40-slot resident tile (hmc_kernel 11) holds columns l and
+    l + 32 in lane l (momentum draw, mass-matrix and C products, gradient, write-back), against
+    the FP64 oracle on the same BF16-stored values, beside the streamed kernel (hmc_kernel 1)."""
+    _moves_reduced_precision(_wl(family, "bf16", p=p, N=256, m=90, G=6), "bf16", hmc_kernel)
+
+
+def _moves_reduced_precision(wl, x_dtype, hmc_kernel):
     try:
         prob, ctx = make_pair(wl, hmc_kernel=hmc_kernel)
     except S()._abi.SmcError as e:
@@ -647,7 +660,7 @@ def _batch_problem_dicts(wls):
 @pytest.mark.parametrize("streamed", [False, True])
 def test_batch_stages_match_single_problems(streamed):
     """One batched u-update launch and one trajectory launch per group per move (resident tiles
-    grouped by p, the streamed kernel for p > 32 or when asked; per-problem stage steps on side
+    grouped by p, the streamed kernel when asked; per-problem stage steps on side
     streams; plain and graph-replayed stages) give bit-identical results to stepping each problem
     alone with the same tiles."""
     from smc_workloads import batch_uneven
@@ -662,8 +675,10 @@ def test_batch_stages_match_single_problems(streamed):
     if streamed:
         assert kernels == [1] * len(wls)
     else:
-        assert len(set(kernels)) >= 3 and all(
-            (k == 1) == (w.p > 32) for k, w in zip(kernels, wls))
+        # every p here (5..40) has a resident tile; p > 32 takes the 40-slot two-column tile
+        assert len(set(kernels)) >= 3 and all(k >= 2 for k in kernels)
+        assert any(w.p > 32 for w in wls)
+        assert all(k == 11 for k, w in zip(kernels, wls) if w.p > 32)
     # the singles take the batch problems' centres (the device's Newton modes)
     singles = [make_pair(w, tile_hint=tile, hmc_kernel=kernels[q],
                          theta_bar=S().smc_get_centre(S().smc_batch_context(b, q))[0])[1]
