@@ -486,12 +486,19 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 // ------------------------------------------------------------------------------------------------
 // Temperature search and reweighting (Sec. 2.2, Sec. 3.3, Algorithm 2 (b)-(c)).
 //   lw_i(D) = log W_i + D l_hat_i - ((a + D)^2 - a^2)/2 sigma2_hat_i,  ESS(D) = s1^2 / s2
-// with s1 = sum e^{lw - max}, s2 = sum e^{2(lw - max)}. Round -1 tests D = 1 - a; each later round
-// evaluates the K-1 interior points of the bracket and keeps the first sub-interval whose right end
-// has ESS < tau N. Partials of every block are merged in block order by the last block to finish.
+// with s1 = sum e^{lw - M}, s2 = sum e^{2(lw - M)}, M = max lw (the exact FP64 maximum: early in
+// the run |lw| reaches ~1e11, where a float maximum can miss the true one by ~1e4 and overflow
+// exp). Round 0 also tests D = 1 - a; each round evaluates the K-1 interior points of the bracket
+// and keeps the first sub-interval whose right end has ESS < tau N. Two launches per round (the
+// maxima, then the sums); in each, a thread covers one candidate over a stream of particles, the
+// block merges its streams, and the last block to finish merges the blocks' partials: thread
+// (q, k) a fixed subset q of the blocks for candidate k (loads in flight together), then the
+// subsets in order. Merges are maxima and FP64 sums only (an FP64 exponential costs about 1000
+// cycles of a warp's issue on GB300, so none is spent outside the per-particle terms).
 // ------------------------------------------------------------------------------------------------
-constexpr int kRwThreads = 32, kMaxK = 32, kRwMaxBlocks = 152;  // final kernels: one warp
-constexpr int kSwWarps = 4;  // search kernels: warps per block, lanes = candidates
+constexpr int kMaxK = 32, kRwMaxBlocks = 152;
+constexpr int kSwThreads = 128;   // search: threads per block; lanes = candidates x particle streams
+constexpr int kFinThreads = 128;  // final reweighting: threads per block
 
 // Candidates of a search round. Bracket search (S = 0): round 0 evaluates the K - 1 interior
 // points of [0, 1 - a] and the end point 1 - a itself (the test "ESS(1 - a) >= tau N" of the
@@ -528,116 +535,141 @@ __device__ __forceinline__ int load_candidates(const DevState *st, int K, int ro
     Dk[k] = D;
     hk[k] = 0.5 * ((a + D) * (a + D) - a * a);
   }
-  __syncwarp();
   return ncand;
 }
 
-// Phase 1 of a round: the maximum of lw_i(D_k) over all particles, per candidate. Each block
-// takes a contiguous chunk of particles; lane k handles candidate k over the whole chunk (the
-// particle loads are broadcasts), so the candidates' chains run side by side.
-__global__ void __launch_bounds__(kSwWarps * 32)
+// Lane layout of the search kernels: kslots = 16 lanes per candidate row when the round has at
+// most 16 candidates (so a warp carries two particle streams and no lane idles), else 32.
+struct SearchLanes {
+  int kslots, nstream, k, stream;
+  __device__ __forceinline__ explicit SearchLanes(int ncand) {
+    kslots = ncand <= 16 ? 16 : 32;
+    nstream = kSwThreads / kslots;
+    k = (int)threadIdx.x % kslots;
+    stream = (int)threadIdx.x / kslots;
+  }
+};
+
+// Signals the block that finishes last (ticket in the device state). Call after the block's
+// partials are written; every thread receives the answer.
+__device__ __forceinline__ bool last_block(DevState *st, bool *flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (*flag) __threadfence();
+  return *flag;
+}
+
+// Phase 1 of a round: max_i lw_i(D_k) per candidate.
+__global__ void __launch_bounds__(kSwThreads)
     k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
                  int round, int S, double E, DevState *st, double *pmax, double *gmax) {
   __shared__ double Dk[kMaxK], hk[kMaxK];
-  __shared__ double wmax[kSwWarps][kMaxK];
+  __shared__ double ws[kSwThreads];
   __shared__ bool is_last;
   if (st->search_done) return;  // uniform across the grid
   double lo, hi;
   const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
+  const SearchLanes L(ncand);
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane < ncand) {
-    // The maximum sets the shift M of the sums below. It must be the FP64 maximum: early in the
-    // run |lw| reaches ~1e11, where a float maximum can miss the true one by ~1e4 and overflow exp.
-    const double D = Dk[lane], h = hk[lane];
-    double mx = -INFINITY;
+  double mx = -INFINITY;
+  if (L.k < ncand) {
+    const double D = Dk[L.k], h = hk[L.k];
 #pragma unroll 4
-    for (int i = i0 + warp; i < i1; i += kSwWarps)
+    for (int i = i0 + L.stream; i < i1; i += L.nstream)
       mx = fmax(mx, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
-    wmax[warp][lane] = mx;
   }
+  ws[threadIdx.x] = mx;
   __syncthreads();
-  if (warp == 0 && lane < ncand) {
-    double mx = wmax[0][lane];
-#pragma unroll
-    for (int w = 1; w < kSwWarps; ++w) mx = fmax(mx, wmax[w][lane]);
-    pmax[blockIdx.x * kMaxK + lane] = mx;
+  if ((int)threadIdx.x < ncand) {
+    double m = ws[threadIdx.x];
+    for (int q = 1; q < L.nstream; ++q) m = fmax(m, ws[q * L.kslots + threadIdx.x]);
+    pmax[blockIdx.x * kMaxK + threadIdx.x] = m;
   }
-  __threadfence();
-  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!is_last || warp != 0) return;
-  __threadfence();
-  if (lane < ncand) {  // lane k: candidate k, loads over blocks in flight together
-    double M = -INFINITY;
+  if (!last_block(st, &is_last)) return;
+  double m = -INFINITY;
+  if (L.k < ncand) {
 #pragma unroll 8
-    for (int b = 0; b < (int)gridDim.x; ++b) M = fmax(M, pmax[b * kMaxK + lane]);
-    gmax[lane] = M;
+    for (int b = L.stream; b < (int)gridDim.x; b += L.nstream)
+      m = fmax(m, __ldcg(pmax + b * kMaxK + L.k));
   }
-  if (lane == 0) st->ticket = 0;
+  ws[threadIdx.x] = m;
+  __syncthreads();
+  if ((int)threadIdx.x < ncand) {
+    double g = ws[threadIdx.x];
+    for (int q = 1; q < L.nstream; ++q) g = fmax(g, ws[q * L.kslots + threadIdx.x]);
+    gmax[threadIdx.x] = g;
+  }
+  if (threadIdx.x == 0) st->ticket = 0;
 }
 
 // Phase 2: s1 = sum e^{lw - M}, s2 = sum e^{2(lw - M)} (one exponential per particle and
-// candidate), ESS = s1^2 / s2; the last block sums the block partials in block order (lanes over
-// blocks, fixed tree) and updates the bracket: the first sub-interval whose right end has
-// ESS < tau N.
-__global__ void __launch_bounds__(kSwWarps * 32)
+// candidate), ESS = s1^2 / s2; the last block sums the block partials and updates the bracket:
+// the first sub-interval whose right end has ESS < tau N.
+__global__ void __launch_bounds__(kSwThreads)
     k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
                  int K, int round, int last_round, int S, double E, DevState *st,
                  const double *gmax, double *psum) {
   __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK];
-  __shared__ double wsum[kSwWarps][kMaxK][2];
+  __shared__ double w1[kSwThreads], w2[kSwThreads];
   __shared__ bool is_last;
   if (st->search_done) return;
   double lo, hi;
   const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
+  const SearchLanes L(ncand);
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane < ncand) {  // lane k: candidate k over this warp's share of the block's particles
-    const double D = Dk[lane], h = hk[lane], M = gmax[lane];
-    double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0, s2 = 0.0;
+  if (L.k < ncand) {
+    const double D = Dk[L.k], h = hk[L.k], M = __ldcg(gmax + L.k);
     if (M > -INFINITY) {
 #pragma unroll 4
-      for (int i = i0 + warp; i < i1; i += kSwWarps) {
+      for (int i = i0 + L.stream; i < i1; i += L.nstream) {
         const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M);
         s1 += e;
         s2 = fma(e, e, s2);
       }
     }
-    wsum[warp][lane][0] = s1;
-    wsum[warp][lane][1] = s2;
   }
+  w1[threadIdx.x] = s1;
+  w2[threadIdx.x] = s2;
   __syncthreads();
-  if (warp == 0 && lane < ncand) {  // warps combined in a fixed order
-    double s1 = 0.0, s2 = 0.0;
-#pragma unroll
-    for (int w = 0; w < kSwWarps; ++w) {
-      s1 += wsum[w][lane][0];
-      s2 += wsum[w][lane][1];
+  if ((int)threadIdx.x < ncand) {  // the streams of candidate k in stream order
+    double t1 = w1[threadIdx.x], t2 = w2[threadIdx.x];
+    for (int q = 1; q < L.nstream; ++q) {
+      t1 += w1[q * L.kslots + threadIdx.x];
+      t2 += w2[q * L.kslots + threadIdx.x];
     }
-    psum[2 * (blockIdx.x * kMaxK + lane)] = s1;
-    psum[2 * (blockIdx.x * kMaxK + lane) + 1] = s2;
+    psum[2 * (blockIdx.x * kMaxK + threadIdx.x)] = t1;
+    psum[2 * (blockIdx.x * kMaxK + threadIdx.x) + 1] = t2;
   }
-  __threadfence();
-  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!is_last || warp != 0) return;
-  __threadfence();
-  if ((int)threadIdx.x < ncand) {  // lane k: candidate k, block partials summed in block order
-    const int k = threadIdx.x;
-    double s1 = 0.0, s2 = 0.0;
+  if (!last_block(st, &is_last)) return;
+  {
+    double t1 = 0.0, t2 = 0.0;
+    if (L.k < ncand) {
 #pragma unroll 8
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      s1 += psum[2 * (b * kMaxK + k)];
-      s2 += psum[2 * (b * kMaxK + k) + 1];
+      for (int b = L.stream; b < (int)gridDim.x; b += L.nstream) {
+        t1 += __ldcg(psum + 2 * (b * kMaxK + L.k));
+        t2 += __ldcg(psum + 2 * (b * kMaxK + L.k) + 1);
+      }
     }
-    ess_k[k] = s1 * s1 / s2;
+    w1[threadIdx.x] = t1;
+    w2[threadIdx.x] = t2;
   }
-  __syncwarp();
+  __syncthreads();
+  if ((int)threadIdx.x < ncand) {
+    double t1 = w1[threadIdx.x], t2 = w2[threadIdx.x];
+    for (int q = 1; q < L.nstream; ++q) {
+      t1 += w1[q * L.kslots + threadIdx.x];
+      t2 += w2[q * L.kslots + threadIdx.x];
+    }
+    ess_k[threadIdx.x] = t1 * t1 / t2;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   const double target = tau * (double)N;
   const int ninner = round == 0 ? K - 1 : ncand;  // interior points (round 0 adds the end point)
@@ -683,78 +715,108 @@ __global__ void __launch_bounds__(kSwWarps * 32)
 }
 
 // Final reweighting: log-sum-exps of the new (x = lw(D)) and old (x = log W) log weights, the
-// ESS at D and the log Z increment (Sec. 3.5). Same two phases; index 0 = new, 1 = old.
-__global__ void __launch_bounds__(kRwThreads)
-    k_final_max(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
-                double *pmax, double *gmax) {
-  __shared__ bool is_last;
-  const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
-  const int stride = gridDim.x * blockDim.x;
-  double m0 = -INFINITY, m1 = -INFINITY;  // FP64 shifts (see k_search_max)
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
-    m1 = fmax(m1, logW[i]);
+// ESS at D and the log Z increment (Sec. 3.5). Same two phases; index 0 = new, 1 = old. Within a
+// block the threads' values are combined by a fixed tree; the last block combines the blocks'
+// partials in the same way (thread t the blocks t, t + 128, ..).
+__device__ __forceinline__ void tree_max2(double *v0, double *v1) {
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    __syncthreads();
+    if ((int)threadIdx.x < w) {
+      v0[threadIdx.x] = fmax(v0[threadIdx.x], v0[threadIdx.x + w]);
+      v1[threadIdx.x] = fmax(v1[threadIdx.x], v1[threadIdx.x + w]);
+    }
   }
-  m0 = warp_max(m0);
-  m1 = warp_max(m1);
-  if (threadIdx.x == 0) {
-    pmax[2 * blockIdx.x] = m0;
-    pmax[2 * blockIdx.x + 1] = m1;
+  __syncthreads();
+}
+__device__ __forceinline__ void tree_sum3(double *v0, double *v1, double *v2) {
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    __syncthreads();
+    if ((int)threadIdx.x < w) {
+      v0[threadIdx.x] += v0[threadIdx.x + w];
+      v1[threadIdx.x] += v1[threadIdx.x + w];
+      v2[threadIdx.x] += v2[threadIdx.x + w];
+    }
   }
-  __threadfence();
-  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncwarp();
-  if (!is_last) return;
-  __threadfence();
-  if (threadIdx.x < 2) {
-    double M = -INFINITY;
-#pragma unroll 8
-    for (int b = 0; b < (int)gridDim.x; ++b) M = fmax(M, pmax[2 * b + threadIdx.x]);
-    gmax[threadIdx.x] = M;
-  }
-  if (threadIdx.x == 0) st->ticket = 0;
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(kRwThreads)
-    k_final_sum(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
-                const double *gmax, double *psum) {
+__global__ void __launch_bounds__(kFinThreads)
+    k_final_max(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                double *pmax, double *gmax) {
+  __shared__ double v0[kFinThreads], v1[kFinThreads];
   __shared__ bool is_last;
   const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
-  const double M0 = gmax[0], M1 = gmax[1];
-  const int stride = gridDim.x * blockDim.x;
+  const int tid = threadIdx.x, stride = gridDim.x * blockDim.x;
+  double m0 = -INFINITY, m1 = -INFINITY;
+  for (int i = blockIdx.x * blockDim.x + tid; i < N; i += stride) {
+    const double lw = logW[i];
+    m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], lw)));
+    m1 = fmax(m1, lw);
+  }
+  v0[tid] = m0;
+  v1[tid] = m1;
+  tree_max2(v0, v1);
+  if (tid == 0) {
+    pmax[2 * blockIdx.x] = v0[0];
+    pmax[2 * blockIdx.x + 1] = v1[0];
+  }
+  if (!last_block(st, &is_last)) return;
+  m0 = m1 = -INFINITY;
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    m0 = fmax(m0, __ldcg(pmax + 2 * b));
+    m1 = fmax(m1, __ldcg(pmax + 2 * b + 1));
+  }
+  v0[tid] = m0;
+  v1[tid] = m1;
+  tree_max2(v0, v1);
+  if (tid == 0) {
+    gmax[0] = v0[0];
+    gmax[1] = v1[0];
+    st->ticket = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+    k_final_sum(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                const double *gmax, double *psum) {
+  __shared__ double v0[kFinThreads], v1[kFinThreads], v2[kFinThreads];
+  __shared__ bool is_last;
+  const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
+  const double M0 = __ldcg(gmax), M1 = __ldcg(gmax + 1);
+  const int tid = threadIdx.x, stride = gridDim.x * blockDim.x;
   double s1 = 0.0, s2 = 0.0, so = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M0);
+  for (int i = blockIdx.x * blockDim.x + tid; i < N; i += stride) {
+    const double lw = logW[i];
+    const double e = exp(fma(-h, sig2[i], fma(D, ell[i], lw)) - M0);
     s1 += e;
     s2 = fma(e, e, s2);
-    so += exp(logW[i] - M1);
+    so += exp(lw - M1);
   }
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  so = warp_sum(so);
-  if (threadIdx.x == 0) {
-    psum[3 * blockIdx.x] = s1;
-    psum[3 * blockIdx.x + 1] = s2;
-    psum[3 * blockIdx.x + 2] = so;
+  v0[tid] = s1;
+  v1[tid] = s2;
+  v2[tid] = so;
+  tree_sum3(v0, v1, v2);
+  if (tid == 0) {
+    psum[3 * blockIdx.x] = v0[0];
+    psum[3 * blockIdx.x + 1] = v1[0];
+    psum[3 * blockIdx.x + 2] = v2[0];
   }
-  __threadfence();
-  if (threadIdx.x == 0) is_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
-  __syncwarp();
-  if (!is_last) return;
-  __threadfence();
-  __shared__ double tot[3];
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-#pragma unroll 8
-    for (int b = 0; b < (int)gridDim.x; ++b) t += psum[3 * b + threadIdx.x];
-    tot[threadIdx.x] = t;
+  if (!last_block(st, &is_last)) return;
+  s1 = s2 = so = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    s1 += __ldcg(psum + 3 * b);
+    s2 += __ldcg(psum + 3 * b + 1);
+    so += __ldcg(psum + 3 * b + 2);
   }
-  __syncwarp();
-  if (threadIdx.x != 0) return;
-  const double lse_new = M0 + log(tot[0]), lse_old = M1 + log(tot[2]);
+  v0[tid] = s1;
+  v1[tid] = s2;
+  v2[tid] = so;
+  tree_sum3(v0, v1, v2);
+  if (tid != 0) return;
+  const double lse_new = M0 + log(v0[0]), lse_old = M1 + log(v2[0]);
   st->lse_new = lse_new;
   st->lse_old = lse_old;
-  st->ess = tot[0] * tot[0] / tot[1];
+  st->ess = v0[0] * v0[0] / v1[0];
   st->log_z_inc = lse_new - lse_old;
   st->log_z += st->log_z_inc;
   st->a_prev = a;
@@ -794,26 +856,26 @@ int reweight(int N, const double *ell, const double *sig2, double *logW, double 
     rounds = (grid_points + kMaxK - 1) / kMaxK;
   }
   if (K < 2 || K > kMaxK) return (int)cudaErrorInvalidValue;
-  int nb = (N + kRwThreads - 1) / kRwThreads;
+  int nb = (N + kFinThreads - 1) / kFinThreads;
   if (nb > kRwMaxBlocks) nb = kRwMaxBlocks;
-  int nbs = (N + 4 * kSwWarps - 1) / (4 * kSwWarps);  // search: at least 4 particles per warp
+  int nbs = (N + 15) / 16;  // search: at least two particles per stream of 16 lanes
   if (nbs > kRwMaxBlocks) nbs = kRwMaxBlocks;
-  double *gmax = partials;                  // [kMaxK]
-  double *pmax = gmax + kMaxK;              // [nb][kMaxK]
-  double *psum = pmax + kRwMaxBlocks * kMaxK;  // [nb][kMaxK][2]
+  double *gmax = partials;                     // [kMaxK]
+  double *pmax = gmax + kMaxK;                 // [nbs][kMaxK]
+  double *psum = pmax + kRwMaxBlocks * kMaxK;  // [nbs][kMaxK][2]
   int count = 0;
   k_search_begin<<<1, 1, 0, s>>>(st);
   ++count;
   for (int r = 0; r < rounds; ++r) {
-    k_search_max<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, K, r, grid_points,
-                                               grid_decades, st, pmax, gmax);
-    k_search_sum<<<nbs, kSwWarps * 32, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1,
-                                               grid_points, grid_decades, st, gmax, psum);
+    k_search_max<<<nbs, kSwThreads, 0, s>>>(N, ell, sig2, logW, K, r, grid_points, grid_decades,
+                                            st, pmax, gmax);
+    k_search_sum<<<nbs, kSwThreads, 0, s>>>(N, ell, sig2, logW, tau, K, r, rounds - 1,
+                                            grid_points, grid_decades, st, gmax, psum);
     count += 2;
   }
-  k_final_max<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, pmax, gmax);
-  k_final_sum<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, st, gmax, psum);
-  k_normalise<<<nb, kRwThreads, 0, s>>>(N, ell, sig2, logW, W, st);
+  k_final_max<<<nb, kFinThreads, 0, s>>>(N, ell, sig2, logW, st, pmax, gmax);
+  k_final_sum<<<nb, kFinThreads, 0, s>>>(N, ell, sig2, logW, st, gmax, psum);
+  k_normalise<<<nb, kFinThreads, 0, s>>>(N, ell, sig2, logW, W, st);
   count += 3;
   if (launches) *launches += count;
   return (int)cudaGetLastError();
