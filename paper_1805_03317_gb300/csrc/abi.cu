@@ -248,13 +248,18 @@ int default_res_tile(smc_ctx *c) {
   const int nt = res_tiles(c, t, 32);
   EstArgs a = base_args(c);
   a.B = c->N;
-  int best = -1;
-  for (int i = 0; i < nt; ++i) {
-    if (t[i].T == 0 || t[i].warps != 4 || t[i].CPL < c->p) continue;
-    if (res_launch(c, i, a, true) != 0) continue;
-    if (best < 0 || t[i].CPL < t[best].CPL) best = i;
-  }
-  return best;
+  auto narrowest = [&](int warps) {  // the narrowest resident tile with `warps` warps that fits
+    int best = -1;
+    for (int i = 0; i < nt; ++i) {
+      if (t[i].T == 0 || t[i].warps != warps || t[i].CPL < c->p) continue;
+      if (res_launch(c, i, a, true) != 0) continue;
+      if (best < 0 || t[i].CPL < t[best].CPL) best = i;
+    }
+    return best;
+  };
+  // two warps per CTA for small subsamples (where such a tile is compiled and fits), else four
+  const int best = c->m <= kTwoWarpRows ? narrowest(2) : -1;
+  return best >= 0 ? best : narrowest(4);
 }
 
 EstArgs base_args(const smc_ctx *c) {
@@ -329,15 +334,37 @@ __global__ void k_log_post(int p, const double *theta, const double *mu, const d
   }
 }
 
-// Posterior mode by Newton's method with step halving (FP64, on the device).
-int newton_map(smc_ctx *c, double *theta_d) {
+__global__ void k_scale(int count, double f, double *v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    v[e] *= f;
+}
+
+// A, B, C of the strided subsample of rows 0, stride, 2 stride, .. (the packed rows read with
+// stride x their row pitch), scaled by n / n_sub to stand in for the full-data sums.
+int moments_strided(smc_ctx *c, const double *theta_d, double *A, int64_t stride) {
+  if (stride <= 1) return moments_at(c, theta_d, A, A + 1, A + 1 + c->p);
+  const int p = c->p;
+  const int64_t ns = (c->n + stride - 1) / stride;
+  LAUNCH(c,
+         cv_moments(c->Xp, c->x_dtype, ns, p, (int)(c->S * stride), c->Yo, c->fam,
+                    c->noise_sigma * c->noise_sigma, c->dof, theta_d, c->part,
+                    cv_moments_blocks(p), A, A + 1, A + 1 + p, c->cv_kernel, c->stream),
+         2);
+  k_scale<<<8, 256, 0, c->stream>>>(1 + p + p * p, (double)c->n / (double)ns, A);
+  c->launches += 1;
+  CUDA_OK(c, cudaGetLastError());
+  return SMC_OK;
+}
+
+// Newton's method with step halving on the log posterior whose likelihood sums come from
+// moments_strided(stride), from theta_d (updated in place) until the accepted step is below tol
+// in every coordinate.
+int newton_iterate(smc_ctx *c, double *theta_d, int64_t stride, double tol) {
   const int p = c->p;
   double *A0 = c->scratch_d, *B0 = A0 + 1, *C0 = B0 + p;
-  double *A1 = C0 + p * p, *B1 = A1 + 1, *C1 = B1 + p;
-  double *step = C1 + p * p, *cand = step + p, *f_d = cand + p;
-  CUDA_OK(c, cudaMemcpyAsync(theta_d, c->mu_d, sizeof(double) * p, cudaMemcpyDeviceToDevice,
-                             c->stream));
-  int r = moments_at(c, theta_d, A0, B0, C0);
+  double *A1 = C0 + p * p;
+  double *step = A1 + 1 + p + p * p, *cand = step + p, *f_d = cand + p;
+  int r = moments_strided(c, theta_d, A0, stride);
   if (r) return r;
   double f, fc;
   std::vector<double> sh(p);
@@ -363,7 +390,7 @@ int newton_map(smc_ctx *c, double *theta_d) {
     double t = 1.0;
     while (true) {
       LAUNCH(c, axpy_vec(p, theta_d, t, step, cand, c->stream), 1);
-      if ((r = moments_at(c, cand, A1, B1, C1))) return r;
+      if ((r = moments_strided(c, cand, A1, stride))) return r;
       if ((r = objective(cand, A1, &fc))) return r;
       if (fc >= f || t < 1e-8) break;
       t *= 0.5;
@@ -375,9 +402,25 @@ int newton_map(smc_ctx *c, double *theta_d) {
     f = fc;
     double mx = 0.0;
     for (int k = 0; k < p; ++k) mx = fmax(mx, fabs(t * sh[k]));
-    if (mx < 1e-10) break;
+    if (mx < tol) break;
   }
   return SMC_OK;
+}
+
+// Posterior mode by Newton's method with step halving (FP64, on the device). With many rows the
+// iterations first run on a strided subsample of about kWarmRows rows (its sums scaled by
+// n / n_sub), whose mode lies close to the full-data mode, so the full-data iterations (each a
+// pass over all n rows) start near it and converge in two or three steps.
+constexpr int64_t kWarmRows = 65536;
+int newton_map(smc_ctx *c, double *theta_d) {
+  CUDA_OK(c, cudaMemcpyAsync(theta_d, c->mu_d, sizeof(double) * c->p, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  const int64_t stride = c->n / kWarmRows;
+  if (stride >= 4 && (int64_t)c->S * stride < (int64_t)1 << 30) {
+    const int r = newton_iterate(c, theta_d, stride, 1e-6);
+    if (r) return r;
+  }
+  return newton_iterate(c, theta_d, 1, 1e-10);
 }
 
 // Centre theta_bar (device FP64, already in c->tb_d): round to the state type, moments, CT copies
@@ -1370,12 +1413,18 @@ int smc_autotune(smc_ctx *c, int32_t *tile, int32_t *hmc_kernel) {
   a.blk = c->blk_alt;
   a.blk_prop = c->blk_prop;
   a.move = 255;
+  // The default kernel is timed first and stays unless another is faster by more than 3%: the
+  // candidates are timed on the initial particles only, where near-equal tiles trade places by
+  // noise, while the default is the one chosen for the whole run's range of stages.
   const int keep_res = c->res_tile;
-  int best_res = -1;
+  const int def_res = c->rw ? -1 : default_res_tile(c);
+  int best_res = def_res;
   float best_hmc = 1e30f;
   Tile tr[32];
   const int nr = res_tiles(c, tr, 32);
-  for (int t = -1; t < nr; ++t) {
+  for (int k = -2; k < nr; ++k) {
+    const int t = k == -2 ? def_res : k;  // the default first, then every candidate
+    if (k >= -1 && t == def_res) continue;
     if (t >= 0 && res_launch(c, t, a, true) != 0) continue;
     c->res_tile = t;
     float ms = 0.f;
@@ -1384,7 +1433,7 @@ int smc_autotune(smc_ctx *c, int32_t *tile, int32_t *hmc_kernel) {
       c->res_tile = keep_res;
       return r;
     }
-    if (ms < best_hmc) {
+    if (k == -2 ? true : ms < 0.97f * best_hmc) {
       best_hmc = ms;
       best_res = t;
     }
@@ -1617,10 +1666,14 @@ static int batch_upload(smc_batch *b, int R, bool swapped, int stage_dev) {
 }
 
 // Per move: one u-update launch over all problems (streamed rows), then one trajectory launch
-// per group (resident tile, or the streamed kernel for problems no resident tile takes).
+// per group (resident tile, or the streamed kernel for problems no resident tile takes). The
+// groups touch disjoint problems, so their launches run side by side on the side streams (forked
+// from and joined back to the batch stream: one group's tail overlaps the others' work).
 static int batch_moves(smc_batch *b, int R) {
   const size_t P2 = 2 * (size_t)b->P;
   const int sms = b->ctx[0]->sms;
+  const int ng = (int)b->groups.size();
+  const int nfork = ng > 1 ? std::min(ng, (int)b->side.size()) : 0;
   for (int r = 0; r < R; ++r) {
     BatchArgs ba;
     ba.probs = b->args_d + (size_t)r * P2;
@@ -1630,18 +1683,27 @@ static int batch_moves(smc_batch *b, int R) {
     ba.wstride = b->wstride;
     int e = est_launch_batch_bf16(1, b->tile, ba, b->stream);
     b->launches += 1;
-    for (size_t g = 0; g < b->groups.size() && !e; ++g) {
+    if (!e && nfork > 0) {
+      e = (int)cudaEventRecord(b->ev_fork, b->stream);
+      for (int k = 0; k < nfork && !e; ++k) e = (int)cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+    }
+    for (int g = 0; g < ng && !e; ++g) {
       const BatchGroup &gr = b->groups[g];
+      cudaStream_t st = nfork > 0 ? b->side[g % nfork] : b->stream;
       BatchArgs bg;
       bg.probs = b->args_d + (size_t)r * P2 + b->P + gr.start;
       bg.offsets = b->goff_d + gr.start;
       bg.nprob = gr.count;
       bg.total = gr.total;
       bg.wstride = b->wstride;
-      e = gr.tile >= 0 ? res_launch_batch_bf16(gr.tile, bg, gr.pmax, gr.mmax, gr.Gmax, b->stream,
-                                               sms, false)
-                       : est_launch_batch_bf16(2, b->tile, bg, b->stream);
+      e = gr.tile >= 0 ? res_launch_batch_bf16(gr.tile, bg, gr.pmax, gr.mmax, gr.Gmax, st, sms,
+                                               false)
+                       : est_launch_batch_bf16(2, b->tile, bg, st);
       b->launches += 1;
+    }
+    for (int k = 0; k < nfork && !e; ++k) {
+      e = (int)cudaEventRecord(b->ev_side[k], b->side[k]);
+      if (!e) e = (int)cudaStreamWaitEvent(b->stream, b->ev_side[k], 0);
     }
     if (e) return bfail(b, SMC_ERR_CUDA, std::string("batched move: ") +
                                              cudaGetErrorString((cudaError_t)e));
@@ -1747,22 +1809,29 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
     g_init_error = "batch offsets";
     return SMC_ERR_OOM;
   }
-  // groups: each problem goes to the narrowest resident tile (4 warps) that takes its p, m and
-  // G, unless its configuration asks for the streamed trajectory (hmc_kernel = 1)
+  // groups: each problem goes to the narrowest resident tile that takes its p, m and G (two
+  // warps per CTA up to kTwoWarpRows subsample rows when one fits, else four), unless its
+  // configuration asks for the streamed trajectory (hmc_kernel = 1)
   {
-    static const int kCand[][2] = {{0, 8}, {7, 12}, {1, 16}, {6, 20}, {2, 24}, {3, 32}, {9, 40}};
+    static const int kCand4[][2] = {{0, 8},  {7, 12},  {1, 16},  {6, 20},
+                                    {2, 24}, {3, 32},  {9, 40}};
+    static const int kCand2[][2] = {{10, 8}, {11, 12}, {12, 16}, {13, 20},
+                                    {14, 24}, {15, 32}, {16, 40}};
     std::vector<int> gt(P, -1);
     BatchArgs dry{};
     for (int q = 0; q < P; ++q) {
       // the random-walk move runs on the streamed kernel only
       if (cfgs[q].hmc_kernel == 1 || cfgs[q].theta_move == 1) continue;
       const smc_ctx *c = b->ctx[q];
-      for (const auto &t : kCand)
-        if (c->p <= t[1] &&
-            res_launch_batch_bf16(t[0], dry, c->p, c->m, c->G, b->stream, c->sms, true) == 0) {
-          gt[q] = t[0];
-          break;
-        }
+      for (int pass = c->m <= kTwoWarpRows ? 0 : 1; pass < 2 && gt[q] < 0; ++pass) {
+        const int(*cand)[2] = pass == 0 ? kCand2 : kCand4;
+        for (int t = 0; t < 7; ++t)
+          if (c->p <= cand[t][1] && res_launch_batch_bf16(cand[t][0], dry, c->p, c->m, c->G,
+                                                          b->stream, c->sms, true) == 0) {
+            gt[q] = cand[t][0];
+            break;
+          }
+      }
     }
     std::vector<int> tiles;
     for (int q = 0; q < P; ++q)

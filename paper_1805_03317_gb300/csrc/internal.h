@@ -124,6 +124,13 @@ int res_tiles_bf16(Tile *out, int cap);
 // Returns a cudaError_t, -1 for a tile without a batched form, -2 when the plan does not fit.
 int res_launch_batch_bf16(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
                           cudaStream_t s, int sms, bool dry);
+// Subsample sizes up to which the trajectories run in two-warp CTAs by default (measured on
+// GB300: at m <= 512 the per-pass work that every warp repeats outweighs the rows of a warp).
+constexpr int kTwoWarpRows = 512;
+// The two-warp tiles (10..16) of the BF16 table, single problem and batched.
+int res_launch_bf16_w2(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
+int res_launch_batch_bf16_w2(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
+                             cudaStream_t s, int sms, bool dry);
 
 // Stage kernels (stage.cu). All return cudaError_t.
 int pack_rows(const void *X, int x_dtype, int64_t n, int p, int64_t ld, const void *y, void *Xp,

@@ -28,7 +28,7 @@ struct ResPlan {
   int rb;    // bytes per resident row (covariates only): an odd multiple of 16 (conflict-free LDS.128)
   int nvec;  // 16-byte vectors of covariates per row (copied from the packed row)
   int nvl;   // 16-byte vectors the tile's CPL slots read (>= nvec; the extra ones are zero-filled)
-  int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, off_k, total;
+  int off_consts, off_d, off_vec, off_red, off_redd, off_blk, off_mat, off_k, off_h, total;
 };
 
 // Constants of one launch of a problem (temperature, n/m, stage counter), computed once per
@@ -65,6 +65,8 @@ inline ResPlan res_plan(int p, int m, int G, int esz, int warps, int cpl) {
   off = round16(off + 2 * cpl * cpl * (int)sizeof(CT));
   P.off_k = off;
   off = round16(off + (int)sizeof(ResK<CT>));
+  P.off_h = off;  // [3] log p(theta_0), log p(theta_L), log U of the MH test
+  off = round16(off + 3 * (int)sizeof(double));
   P.total = off;
   return P;
 }
@@ -108,6 +110,8 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
   using CT = typename SD::CT;
   constexpr int NC = (CPL + 31) / 32;
   static_assert(NC <= 2, "at most two columns per lane");
+  static_assert(WARPS >= 2, "the FP64 Hamiltonian terms are split over the warps");
+  constexpr int kWarpU = WARPS > 2 ? 2 : 1;  // the warp that takes the log of the MH uniform
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = a.p, m = a.m, G = a.G, S = a.S;
@@ -400,14 +404,25 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
       buf ^= 1;
     };
 
-    // 3. trajectory (the Hamiltonian is needed by warp 0 only)
-    double kin0 = 0.0, lp0 = 0.0;
+    // 3. trajectory. The Hamiltonian's FP64 terms (slow on this part: a warp-wide FP64
+    // instruction holds the sub-partition's FP64 pipe for tens of cycles) are split over warps
+    // that run on different sub-partitions: warp 0 the kinetic energy (it also assembles H and
+    // runs the MH test), warp 1 the log prior, warp 2 (warp 1 in two-warp tiles) the log of the
+    // MH uniform; every warp carries the same theta and rho.
+    double *hs = reinterpret_cast<double *>(smem + P.off_h);
+    double kin0 = 0.0;
     if (warp == 0) {
       kin0 = kinetic();
-      lp0 = log_prior();
+    } else if (warp == 1) {
+      const double lp = log_prior();
+      if (lane == 0) hs[0] = lp;
     }
-    pass(false, true);
-    const double H0 = -(temp * ell - 0.5 * temp * temp * sig + lp0) + kin0;
+    if (warp == kWarpU && lane == 0) {
+      const Stream smh(a.seed, kMhTheta, smv, (uint32_t)i);
+      hs[2] = log(draw_uniform(smh.draw(0)));
+    }
+    pass(false, true);  // its barrier publishes hs[0] and hs[2]
+    const double H0 = warp == 0 ? -(temp * ell - 0.5 * temp * temp * sig + hs[0]) + kin0 : 0.0;
     for (int l = 0; l < a.L; ++l) {
       CT vs[NC];
 #pragma unroll
@@ -422,12 +437,17 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
       for (int h = 0; h < NC; ++h) rho[h] += CT(0.5) * eps * gr[h];
     }
     // 4. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
+    double kin1 = 0.0;
     if (warp == 0) {
-      const double kin1 = kinetic(), lp1 = log_prior();
-      const double H1 = -(temp * ell - 0.5 * temp * temp * sig + lp1) + kin1;
-      const Stream smh(a.seed, kMhTheta, smv, (uint32_t)i);
-      const double Uu = draw_uniform(smh.draw(0));
-      const bool acc = log(Uu) < H0 - H1;  // false when H1 is NaN
+      kin1 = kinetic();
+    } else if (warp == 1) {
+      const double lp = log_prior();
+      if (lane == 0) hs[1] = lp;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const double H1 = -(temp * ell - 0.5 * temp * temp * sig + hs[1]) + kin1;
+      const bool acc = hs[2] < H0 - H1;  // log U < H0 - H1; false when H1 is NaN
       if (acc) {
 #pragma unroll
         for (int h = 0; h < NC; ++h)

@@ -162,6 +162,23 @@ def test_device_newton_centre_matches_oracle(family):
     S().smc_free(ctx)
 
 
+@pytest.mark.parametrize("family,x_dtype", [("logistic", "bf16"), ("poisson", "f32"),
+                                            ("probit", "f64")])
+def test_device_newton_centre_with_subsample_start_matches_oracle(family, x_dtype):
+    """n = 300000: the device Newton first converges on a strided subsample of 75000 rows (sums
+    scaled by n / n_sub), then iterates on all rows; the centre is still the full-data posterior
+    mode of the stored values."""
+    wl = _wl(family, x_dtype, n=300000)
+    from gpu_common import device_arrays
+    prob = oracle_problem(wl)
+    X, y = device_arrays(wl)
+    ctx = S().smc_init(X, y, family, wl.prior_mean, wl.prior_var, N=8, m=10, G=2, L=2, seed=1,
+                       noise_sigma=wl.sigma, theta_bar=None)
+    tb = S().smc_get_centre(ctx)[0]
+    np.testing.assert_allclose(tb, state_round(prob.theta_bar, x_dtype), rtol=1e-6, atol=1e-7)
+    S().smc_free(ctx)
+
+
 @pytest.mark.parametrize("x_dtype", ["f64", "f32"])
 def test_initial_particles_and_cache_match_oracle(x_dtype):
     wl = _wl("logistic", x_dtype, N=50, m=31, G=4)
@@ -320,23 +337,25 @@ def test_full_smc_run_matches_oracle_fp64(hmc_kernel):
 
 @pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
-@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10, 11])
+@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10, 11, 14])
 def test_moves_reduced_precision_match_oracle(x_dtype, family, hmc_kernel):
     """FP32 arithmetic on FP32/BF16-stored rows against the FP64 oracle on the same stored values:
     the MH decisions may differ only where the FP64 log ratio is within rounding of the uniform;
     accepted end points agree to FP32 leapfrog rounding. hmc_kernel 5, 8 and 11 are resident tiles
     wider than the rows (32, 20 and 40 slots for p = 13), whose slots past p must read zeros; 10 is
-    the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90)."""
+    the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90); 14 is the
+    16-slot tile with two warps per CTA (BF16 only)."""
     _moves_reduced_precision(_wl(family, x_dtype, p=13, N=256, m=90, G=6), x_dtype, hmc_kernel)
 
 
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
 @pytest.mark.parametrize("p", [33, 37, 40])
-@pytest.mark.parametrize("hmc_kernel", [1, 11])
+@pytest.mark.parametrize("hmc_kernel", [1, 11, 18])
 def test_moves_two_columns_per_lane_match_oracle(family, p, hmc_kernel):
-    """p past one warp's lanes: the 40-slot resident tile (hmc_kernel 11) holds columns l and
-    l + 32 in lane l (momentum draw, mass-matrix and C products, gradient, write-back), against
-    the FP64 oracle on the same BF16-stored values, beside the streamed kernel (hmc_kernel 1)."""
+    """p past one warp's lanes: the 40-slot resident tiles (hmc_kernel 11: four warps, 18: two)
+    hold columns l and l + 32 in lane l (momentum draw, mass-matrix and C products, gradient,
+    write-back), against the FP64 oracle on the same BF16-stored values, beside the streamed
+    kernel (hmc_kernel 1)."""
     _moves_reduced_precision(_wl(family, "bf16", p=p, N=256, m=90, G=6), "bf16", hmc_kernel)
 
 
@@ -657,14 +676,17 @@ def _batch_problem_dicts(wls):
     return out
 
 
-@pytest.mark.parametrize("streamed", [False, True])
-def test_batch_stages_match_single_problems(streamed):
-    """One batched u-update launch and one trajectory launch per group per move (resident tiles
-    grouped by p, the streamed kernel when asked; per-problem stage steps on side
+@pytest.mark.parametrize("streamed,n_lo,n_hi",
+                         [(False, 2000, 20000), (False, 300000, 1000000), (True, 2000, 20000)])
+def test_batch_stages_match_single_problems(streamed, n_lo, n_hi):
+    """One batched u-update launch per move and one trajectory launch per group, the groups side
+    by side on side streams (resident tiles grouped by p and by warps per CTA: two up to 512
+    subsample rows, four above; the streamed kernel when asked; per-problem stage steps on side
     streams; plain and graph-replayed stages) give bit-identical results to stepping each problem
-    alone with the same tiles."""
+    alone with the same tiles. n in [2000, 20000] gives m = 100 everywhere, [3e5, 1e6] a mix of
+    m = 337 .. 725."""
     from smc_workloads import batch_uneven
-    wls = batch_uneven(P=7, N=96, G=5, L=4, R=2, n_lo=2000, n_hi=20000)
+    wls = batch_uneven(P=7, N=96, G=5, L=4, R=2, n_lo=n_lo, n_hi=n_hi)
     dicts = _batch_problem_dicts(wls)
     if streamed:
         for d in dicts:
@@ -675,10 +697,13 @@ def test_batch_stages_match_single_problems(streamed):
     if streamed:
         assert kernels == [1] * len(wls)
     else:
-        # every p here (5..40) has a resident tile; p > 32 takes the 40-slot two-column tile
+        # every p here (5..40) has a resident tile; p > 32 takes a 40-slot two-column tile, with
+        # two warps per CTA up to m = 512 (hmc_kernel 18) and four above (11)
         assert len(set(kernels)) >= 3 and all(k >= 2 for k in kernels)
         assert any(w.p > 32 for w in wls)
-        assert all(k == 11 for k, w in zip(kernels, wls) if w.p > 32)
+        assert all(k == (18 if w.m <= 512 else 11) for k, w in zip(kernels, wls) if w.p > 32)
+        if n_hi > 100000:
+            assert any(w.m > 512 for w in wls) and any(w.m <= 512 for w in wls)
     # the singles take the batch problems' centres (the device's Newton modes)
     singles = [make_pair(w, tile_hint=tile, hmc_kernel=kernels[q],
                          theta_bar=S().smc_get_centre(S().smc_batch_context(b, q))[0])[1]
