@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsubsmc.so")
 SOURCES = ["abi.cu", "stage.cu", "est_f64.cu", "est_f32.cu", "est_bf16.cu", "est_bf16_batch.cu",
-           "res_bf16.cu", "res_bf16_w2.cu", "noalloc.cu", "cv_mma.cu", "full_mma.cu"]
+           "res_bf16.cu", "res_bf16_w2.cu", "res_bf16_w1.cu", "noalloc.cu", "cv_mma.cu", "full_mma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -257,9 +257,10 @@ int default_res_tile(smc_ctx *c) {
     }
     return best;
   };
-  // two warps per CTA for small subsamples (where such a tile is compiled and fits), else four
-  const int best = c->m <= kTwoWarpRows ? narrowest(2) : -1;
-  return best >= 0 ? best : narrowest(4);
+  // fewer warps per CTA for small subsamples (where such a tile is compiled and fits), else four
+  int best = -1;
+  for (int w = res_default_warps(c->p, c->m); w <= 4 && best < 0; w *= 2) best = narrowest(w);
+  return best;
 }
 
 EstArgs base_args(const smc_ctx *c) {
@@ -1616,6 +1617,12 @@ struct smc_batch {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_side;
   cudaEvent_t ev_fork = nullptr;
+  // batched stage steps (every problem with a fixed centre): the problems' stage arguments per
+  // buffer parity and the block offsets of each launch kind
+  bool stage_kernels = false;
+  StageArgs *sargs_d[2] = {nullptr, nullptr};
+  int *soff_d = nullptr;
+  StageBatch sb{};
   std::string err;
 };
 
@@ -1711,8 +1718,54 @@ static int batch_moves(smc_batch *b, int R) {
   return SMC_OK;
 }
 
+// True when this stage can run the batched stage kernels: every problem has a fixed centre (set
+// at init) and all are at the same buffer parity.
+static bool batch_stage_kernels(const smc_batch *b) {
+  if (!b->stage_kernels) return false;
+  for (const smc_ctx *c : b->ctx)
+    if (c->parity != b->ctx[0]->parity) return false;
+  return true;
+}
+
+// The stage of every problem with the batched stage kernels: the temperature search, reweighting,
+// moments, mass matrices and resampling of all problems in about 2 rounds + 12 launches, then R
+// batched moves and the step sizes. The device stage counters are advanced by the first launch.
+static int batch_stage_batched(smc_batch *b, int R, bool args_ready) {
+  for (smc_ctx *c : b->ctx) {
+    if (!c->dev_stage_synced) {  // outside a capture: a per-problem call left the counter stale
+      if (stage_set(c->st, c->stage, b->stream)) return bfail(b, SMC_ERR_CUDA, "stage counter");
+      c->dev_stage_synced = true;
+    }
+  }
+  StageBatch sb = b->sb;
+  sb.args = b->sargs_d[b->ctx[0]->parity];
+  if (stage_batch(sb, b->stream, &b->launches))
+    return bfail(b, SMC_ERR_CUDA, "batched stage steps");
+  for (smc_ctx *c : b->ctx) {  // the host side of smc_reweight and smc_resample
+    c->stage += 1;
+    c->moves_in_stage = 0;
+    std::swap(c->theta, c->theta_alt);
+    std::swap(c->u, c->u_alt);
+    std::swap(c->ell, c->ell_alt);
+    std::swap(c->sig2, c->sig2_alt);
+    std::swap(c->blk, c->blk_alt);
+    c->parity ^= 1;
+  }
+  if (!args_ready) {
+    int r = batch_upload(b, R, false, 0);
+    if (r) return r;
+  }
+  int r = batch_moves(b, R);
+  if (r) return r;
+  for (smc_ctx *c : b->ctx) c->moves_in_stage += R;
+  if (eps_update_batch(sb, R, b->stream)) return bfail(b, SMC_ERR_CUDA, "step size");
+  b->launches += 1;
+  return SMC_OK;
+}
+
 // The stage of every problem: reweight and resample per problem, R batched moves, step sizes.
 static int batch_stage_body(smc_batch *b, int R, bool args_ready) {
+  if (batch_stage_kernels(b)) return batch_stage_batched(b, R, args_ready);
   // the problems' reweighting and resampling are independent: side streams run them side by
   // side (inside a capture they become parallel branches of the graph)
   const int ns = (int)b->side.size();
@@ -1809,22 +1862,24 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
     g_init_error = "batch offsets";
     return SMC_ERR_OOM;
   }
-  // groups: each problem goes to the narrowest resident tile that takes its p, m and G (two
-  // warps per CTA up to kTwoWarpRows subsample rows when one fits, else four), unless its
+  // groups: each problem goes to the narrowest resident tile that takes its p, m and G, with the
+  // default warps per CTA for its p and m (res_default_warps; more when none fits), unless its
   // configuration asks for the streamed trajectory (hmc_kernel = 1)
   {
     static const int kCand4[][2] = {{0, 8},  {7, 12},  {1, 16},  {6, 20},
                                     {2, 24}, {3, 32},  {9, 40}};
     static const int kCand2[][2] = {{10, 8}, {11, 12}, {12, 16}, {13, 20},
                                     {14, 24}, {15, 32}, {16, 40}};
+    static const int kCand1[][2] = {{17, 8}, {18, 12}, {19, 16}, {20, 20},
+                                    {21, 24}, {22, 32}, {23, 40}};
     std::vector<int> gt(P, -1);
     BatchArgs dry{};
     for (int q = 0; q < P; ++q) {
       // the random-walk move runs on the streamed kernel only
       if (cfgs[q].hmc_kernel == 1 || cfgs[q].theta_move == 1) continue;
       const smc_ctx *c = b->ctx[q];
-      for (int pass = c->m <= kTwoWarpRows ? 0 : 1; pass < 2 && gt[q] < 0; ++pass) {
-        const int(*cand)[2] = pass == 0 ? kCand2 : kCand4;
+      for (int w = res_default_warps(c->p, c->m); w <= 4 && gt[q] < 0; w *= 2) {
+        const int(*cand)[2] = w == 1 ? kCand1 : w == 2 ? kCand2 : kCand4;
         for (int t = 0; t < 7; ++t)
           if (c->p <= cand[t][1] && res_launch_batch_bf16(cand[t][0], dry, c->p, c->m, c->G,
                                                           b->stream, c->sms, true) == 0) {
@@ -1867,6 +1922,85 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
       return SMC_ERR_OOM;
     }
   }
+  // batched stage steps: every problem with a fixed centre (cv_centre = 0) and p <= 128
+  b->stage_kernels = true;
+  for (const smc_ctx *c : b->ctx)
+    if (c->cv_centre != 0 || c->full_data || c->is_f64 || c->p > 128 || c->parity != 0)
+      b->stage_kernels = false;
+  if (b->stage_kernels) {
+    std::vector<StageArgs> sa[2];
+    std::vector<int> off((size_t)kSkKinds * (P + 1), 0);
+    b->sb = StageBatch{};
+    b->sb.P = P;
+    for (int q = 0; q < P; ++q) {
+      const smc_ctx *c = b->ctx[q];
+      const bool grid = c->grid_points > 0;
+      const int rounds = grid ? (c->grid_points + kSearchMaxK - 1) / kSearchMaxK : c->rounds;
+      StageArgs a{};
+      a.N = c->N;
+      a.p = c->p;
+      a.m = c->m;
+      a.G = c->G;
+      a.K = grid ? kSearchMaxK : c->K;
+      a.last_round = rounds - 1;
+      a.S = c->grid_points;
+      a.multinomial = c->multinomial;
+      a.tau = c->tau;
+      a.E = c->grid_decades;
+      a.eps_target = c->rw ? 0.234 : 0.65;
+      a.seed = c->seed;
+      a.st = c->st;
+      a.part = c->part;
+      a.logW = c->logW;
+      a.W = c->W;
+      a.mean = c->mean_d;
+      a.Sigma_raw = c->Sigma_raw;
+      a.Sigma = c->Sigma_d;
+      a.chol = c->chol_d;
+      a.work = c->mass_work;
+      a.Sigma_ct = static_cast<float *>(c->Sigma_ct);
+      a.Linv_ct = static_cast<float *>(c->Linv_ct);
+      a.cum = c->cum;
+      a.anc = c->anc;
+      for (int par = 0; par < 2; ++par) {  // parity 0: the buffers current at init
+        StageArgs t = a;
+        float *th[2] = {static_cast<float *>(c->theta), static_cast<float *>(c->theta_alt)};
+        int32_t *uu[2] = {c->u, c->u_alt};
+        double *el[2] = {c->ell, c->ell_alt}, *sg[2] = {c->sig2, c->sig2_alt};
+        double *bk[2] = {c->blk, c->blk_alt};
+        t.theta = th[par];
+        t.theta_out = th[par ^ 1];
+        t.u = uu[par];
+        t.u_out = uu[par ^ 1];
+        t.ell = el[par];
+        t.ell_out = el[par ^ 1];
+        t.sig2 = sg[par];
+        t.sig2_out = sg[par ^ 1];
+        t.blk = bk[par];
+        t.blk_out = bk[par ^ 1];
+        sa[par].push_back(t);
+      }
+      for (int k = 0; k < kSkKinds; ++k)
+        off[(size_t)k * (P + 1) + q + 1] =
+            off[(size_t)k * (P + 1) + q] + stage_kind_blocks(k, c->N, c->p);
+      b->sb.max_rounds = std::max(b->sb.max_rounds, rounds);
+      b->sb.max_p = std::max(b->sb.max_p, c->p);
+    }
+    for (int k = 0; k < kSkKinds; ++k) b->sb.total[k] = off[(size_t)k * (P + 1) + P];
+    bool ok = cudaMalloc(&b->soff_d, sizeof(int) * off.size()) == cudaSuccess &&
+              cudaMemcpy(b->soff_d, off.data(), sizeof(int) * off.size(),
+                         cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int par = 0; par < 2 && ok; ++par)
+      ok = cudaMalloc(&b->sargs_d[par], sizeof(StageArgs) * P) == cudaSuccess &&
+           cudaMemcpy(b->sargs_d[par], sa[par].data(), sizeof(StageArgs) * P,
+                      cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+      smc_batch_free(b);
+      g_init_error = "batch stage arguments";
+      return SMC_ERR_OOM;
+    }
+    b->sb.off = b->soff_d;
+  }
   const int ns = P < 16 ? P : 16;
   b->side.assign(ns, nullptr);
   b->ev_side.assign(ns, nullptr);
@@ -1893,6 +2027,9 @@ int smc_batch_free(smc_batch *b) {
   for (smc_ctx *c : b->ctx) smc_free(c);
   if (b->offsets_d) cudaFree(b->offsets_d);
   if (b->goff_d) cudaFree(b->goff_d);
+  if (b->soff_d) cudaFree(b->soff_d);
+  for (StageArgs *a : b->sargs_d)
+    if (a) cudaFree(a);
   if (b->args_d) cudaFree(b->args_d);
   for (cudaStream_t st : b->side)
     if (st) cudaStreamDestroy(st);
@@ -1978,8 +2115,9 @@ int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph) {
     b->args_d = keep;
     b->Rcap = R;
     r = 0;
-    for (smc_ctx *c : b->ctx)
-      if (!r && stage_advance(c->st, cap)) r = SMC_ERR_CUDA;
+    if (!batch_stage_kernels(b))  // the batched stage steps advance the counters themselves
+      for (smc_ctx *c : b->ctx)
+        if (!r && stage_advance(c->st, cap)) r = SMC_ERR_CUDA;
     if (!r) r = batch_stage_body(b, R, true);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cap, &g);

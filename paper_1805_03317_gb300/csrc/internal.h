@@ -127,9 +127,20 @@ int res_launch_batch_bf16(int tile, const BatchArgs &b, int p_max, int m_max, in
 // Subsample sizes up to which the trajectories run in two-warp CTAs by default (measured on
 // GB300: at m <= 512 the per-pass work that every warp repeats outweighs the rows of a warp).
 constexpr int kTwoWarpRows = 512;
-// The two-warp tiles (10..16) of the BF16 table, single problem and batched.
+// Warps per CTA of the default resident tile for p covariates and m subsample rows (measured on
+// GB300, 1024 particles per problem): one warp while a warp's rows outweigh the per-pass work
+// that every warp repeats (p 9..24 up to m = 400, p > 24 up to m = 160; at p <= 8 two warps
+// always do better), two up to m = 512, else four.
+inline int res_default_warps(int p, int m) {
+  if (p > 8 && m <= (p <= 24 ? 400 : 160)) return 1;
+  return m <= kTwoWarpRows ? 2 : 4;
+}
+// The two-warp (10..16) and one-warp (17..23) tiles of the BF16 table, single problem and batched.
 int res_launch_bf16_w2(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
 int res_launch_batch_bf16_w2(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
+                             cudaStream_t s, int sms, bool dry);
+int res_launch_bf16_w1(int tile, const EstArgs &a, cudaStream_t s, int sms, bool dry);
+int res_launch_batch_bf16_w1(int tile, const BatchArgs &b, int p_max, int m_max, int G_max,
                              cudaStream_t s, int sms, bool dry);
 
 // Stage kernels (stage.cu). All return cudaError_t.
@@ -178,6 +189,47 @@ int stage_advance(DevState *st, cudaStream_t s);
 int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_t s);
 // eps *= clip(exp(acceptance - target), 0.5, 2) over the last R moves.
 int eps_update(int N, int R, DevState *st, cudaStream_t s, double target = 0.65);
+
+// Candidates per temperature-search round at most (the grid rule evaluates this many per round).
+constexpr int kSearchMaxK = 32;
+// The stage steps of many problems at once (batches of BF16-stored problems: FP32 states; fixed
+// centre). Problem q's arguments for the buffers that are current before the stage's resampling:
+struct StageArgs {
+  int N, p, m, G, K, last_round, S, multinomial;
+  double tau, E, eps_target;
+  uint64_t seed;
+  DevState *st;
+  double *part;                  // the problem's search / moment partials
+  const double *ell, *sig2;      // the cached estimates
+  double *logW, *W;
+  const float *theta;            // the particles
+  double *mean, *Sigma_raw, *Sigma, *chol, *work;
+  float *Sigma_ct, *Linv_ct;
+  uint64_t *cum;
+  int32_t *anc;
+  float *theta_out;              // resampling writes the other buffer of each pair
+  const int32_t *u;
+  int32_t *u_out;
+  double *ell_out, *sig2_out;
+  const double *blk;
+  double *blk_out;
+};
+// Batched launch kinds: each gives problem q the block count of its single-problem launch (so
+// every reduction runs in the same order) at blocks off[kind][q] .. off[kind][q + 1] - 1.
+enum StageKind { kSkSearch, kSkFinal, kSkMom, kSkSumMean, kSkSumCov, kSkAnc, kSkGather, kSkKinds };
+int stage_kind_blocks(int kind, int N, int p);
+struct StageBatch {
+  int P, max_rounds, max_p;
+  const StageArgs *args;  // device [P]
+  const int *off;         // device [kSkKinds][P + 1]
+  int total[kSkKinds];    // off[kind][P]
+};
+// Algorithm 2 (a)-(e) for every problem of the batch: the device stage counter advanced, the
+// temperature search and reweighting, the weighted moments and mass matrix, resampling into the
+// other buffers and the accept counters cleared; launches are counted into *launches.
+int stage_batch(const StageBatch &sb, cudaStream_t s, int64_t *launches);
+// The step-size update of every problem after R moves.
+int eps_update_batch(const StageBatch &sb, int R, cudaStream_t s);
 // rho[c] = correlation across the N particles of component c of clouds a and b (state type).
 int autocorr(int is_f64, int N, int p, const void *a, const void *b, double *rho, cudaStream_t s);
 int to_state_type(int is_f64, int count, const double *src, void *dst, cudaStream_t s);

@@ -110,8 +110,8 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
   using CT = typename SD::CT;
   constexpr int NC = (CPL + 31) / 32;
   static_assert(NC <= 2, "at most two columns per lane");
-  static_assert(WARPS >= 2, "the FP64 Hamiltonian terms are split over the warps");
-  constexpr int kWarpU = WARPS > 2 ? 2 : 1;  // the warp that takes the log of the MH uniform
+  // the warps that take the log prior and the log of the MH uniform (warp 0: the kinetic energy)
+  constexpr int kWarpP = WARPS > 1 ? 1 : 0, kWarpU = WARPS > 2 ? 2 : kWarpP;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = a.p, m = a.m, G = a.G, S = a.S;
@@ -407,13 +407,12 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
     // 3. trajectory. The Hamiltonian's FP64 terms (slow on this part: a warp-wide FP64
     // instruction holds the sub-partition's FP64 pipe for tens of cycles) are split over warps
     // that run on different sub-partitions: warp 0 the kinetic energy (it also assembles H and
-    // runs the MH test), warp 1 the log prior, warp 2 (warp 1 in two-warp tiles) the log of the
-    // MH uniform; every warp carries the same theta and rho.
+    // runs the MH test), warp 1 the log prior, warp 2 the log of the MH uniform (fewer warps take
+    // more of them); every warp carries the same theta and rho.
     double *hs = reinterpret_cast<double *>(smem + P.off_h);
     double kin0 = 0.0;
-    if (warp == 0) {
-      kin0 = kinetic();
-    } else if (warp == 1) {
+    if (warp == 0) kin0 = kinetic();
+    if (warp == kWarpP) {
       const double lp = log_prior();
       if (lane == 0) hs[0] = lp;
     }
@@ -438,9 +437,8 @@ __device__ __forceinline__ void res_particle(const EstArgs &a, int i, bool reloa
     }
     // 4. Metropolis-Hastings in FP64, write-back on acceptance (warp 0)
     double kin1 = 0.0;
-    if (warp == 0) {
-      kin1 = kinetic();
-    } else if (warp == 1) {
+    if (warp == 0) kin1 = kinetic();
+    if (warp == kWarpP) {
       const double lp = log_prior();
       if (lane == 0) hs[1] = lp;
     }

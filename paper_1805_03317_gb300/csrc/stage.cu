@@ -496,8 +496,8 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 // subsets in order. Merges are maxima and FP64 sums only (an FP64 exponential costs about 1000
 // cycles of a warp's issue on GB300, so none is spent outside the per-particle terms).
 // ------------------------------------------------------------------------------------------------
-constexpr int kMaxK = 32, kRwMaxBlocks = 152;
-constexpr int kSwThreads = 128;   // search: threads per block; lanes = candidates x particle streams
+constexpr int kMaxK = kSearchMaxK, kRwMaxBlocks = 152;
+constexpr int kSwThreads = 128;   // search: threads per block (candidates x particle streams)
 constexpr int kFinThreads = 128;  // final reweighting: threads per block
 
 // Candidates of a search round. Bracket search (S = 0): round 0 evaluates the K - 1 interior
@@ -551,20 +551,20 @@ struct SearchLanes {
 };
 
 // Signals the block that finishes last (ticket in the device state). Call after the block's
-// partials are written; every thread receives the answer.
-__device__ __forceinline__ bool last_block(DevState *st, bool *flag) {
+// partials are written; every thread receives the answer. nblk: the problem's blocks.
+__device__ __forceinline__ bool last_block(DevState *st, bool *flag, int nblk) {
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) *flag = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) *flag = atomicAdd(&st->ticket, 1u) == (unsigned)nblk - 1;
   __syncthreads();
   if (*flag) __threadfence();
   return *flag;
 }
 
 // Phase 1 of a round: max_i lw_i(D_k) per candidate.
-__global__ void __launch_bounds__(kSwThreads)
-    k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
-                 int round, int S, double E, DevState *st, double *pmax, double *gmax) {
+__device__ __forceinline__ void k_search_max_body(int N, const double *ell, const double *sig2,
+    const double *logW, int K, int round, int S, double E, DevState *st, double *pmax, double *gmax,
+    int bid_, int nblk_) {
   __shared__ double Dk[kMaxK], hk[kMaxK];
   __shared__ double ws[kSwThreads];
   __shared__ bool is_last;
@@ -573,8 +573,8 @@ __global__ void __launch_bounds__(kSwThreads)
   const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
   const SearchLanes L(ncand);
-  const int chunk = (N + gridDim.x - 1) / gridDim.x;
-  const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+  const int chunk = (N + nblk_ - 1) / nblk_;
+  const int i0 = bid_ * chunk, i1 = min(N, i0 + chunk);
   double mx = -INFINITY;
   if (L.k < ncand) {
     const double D = Dk[L.k], h = hk[L.k];
@@ -587,13 +587,13 @@ __global__ void __launch_bounds__(kSwThreads)
   if ((int)threadIdx.x < ncand) {
     double m = ws[threadIdx.x];
     for (int q = 1; q < L.nstream; ++q) m = fmax(m, ws[q * L.kslots + threadIdx.x]);
-    pmax[blockIdx.x * kMaxK + threadIdx.x] = m;
+    pmax[bid_ * kMaxK + threadIdx.x] = m;
   }
-  if (!last_block(st, &is_last)) return;
+  if (!last_block(st, &is_last, nblk_)) return;
   double m = -INFINITY;
   if (L.k < ncand) {
 #pragma unroll 8
-    for (int b = L.stream; b < (int)gridDim.x; b += L.nstream)
+    for (int b = L.stream; b < (int)nblk_; b += L.nstream)
       m = fmax(m, __ldcg(pmax + b * kMaxK + L.k));
   }
   ws[threadIdx.x] = m;
@@ -605,14 +605,18 @@ __global__ void __launch_bounds__(kSwThreads)
   }
   if (threadIdx.x == 0) st->ticket = 0;
 }
+__global__ void __launch_bounds__(kSwThreads)
+    k_search_max(int N, const double *ell, const double *sig2, const double *logW, int K,
+                 int round, int S, double E, DevState *st, double *pmax, double *gmax) {
+  k_search_max_body(N, ell, sig2, logW, K, round, S, E, st, pmax, gmax, blockIdx.x, gridDim.x);
+}
 
 // Phase 2: s1 = sum e^{lw - M}, s2 = sum e^{2(lw - M)} (one exponential per particle and
 // candidate), ESS = s1^2 / s2; the last block sums the block partials and updates the bracket:
 // the first sub-interval whose right end has ESS < tau N.
-__global__ void __launch_bounds__(kSwThreads)
-    k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
-                 int K, int round, int last_round, int S, double E, DevState *st,
-                 const double *gmax, double *psum) {
+__device__ __forceinline__ void k_search_sum_body(int N, const double *ell, const double *sig2,
+    const double *logW, double tau, int K, int round, int last_round, int S, double E, DevState *st,
+    const double *gmax, double *psum, int bid_, int nblk_) {
   __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK];
   __shared__ double w1[kSwThreads], w2[kSwThreads];
   __shared__ bool is_last;
@@ -621,8 +625,8 @@ __global__ void __launch_bounds__(kSwThreads)
   const int ncand = load_candidates(st, K, round, S, E, Dk, hk, lo, hi);
   __syncthreads();
   const SearchLanes L(ncand);
-  const int chunk = (N + gridDim.x - 1) / gridDim.x;
-  const int i0 = blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+  const int chunk = (N + nblk_ - 1) / nblk_;
+  const int i0 = bid_ * chunk, i1 = min(N, i0 + chunk);
   double s1 = 0.0, s2 = 0.0;
   if (L.k < ncand) {
     const double D = Dk[L.k], h = hk[L.k], M = __ldcg(gmax + L.k);
@@ -644,15 +648,15 @@ __global__ void __launch_bounds__(kSwThreads)
       t1 += w1[q * L.kslots + threadIdx.x];
       t2 += w2[q * L.kslots + threadIdx.x];
     }
-    psum[2 * (blockIdx.x * kMaxK + threadIdx.x)] = t1;
-    psum[2 * (blockIdx.x * kMaxK + threadIdx.x) + 1] = t2;
+    psum[2 * (bid_ * kMaxK + threadIdx.x)] = t1;
+    psum[2 * (bid_ * kMaxK + threadIdx.x) + 1] = t2;
   }
-  if (!last_block(st, &is_last)) return;
+  if (!last_block(st, &is_last, nblk_)) return;
   {
     double t1 = 0.0, t2 = 0.0;
     if (L.k < ncand) {
 #pragma unroll 8
-      for (int b = L.stream; b < (int)gridDim.x; b += L.nstream) {
+      for (int b = L.stream; b < (int)nblk_; b += L.nstream) {
         t1 += __ldcg(psum + 2 * (b * kMaxK + L.k));
         t2 += __ldcg(psum + 2 * (b * kMaxK + L.k) + 1);
       }
@@ -713,6 +717,13 @@ __global__ void __launch_bounds__(kSwThreads)
   }
   st->ticket = 0;
 }
+__global__ void __launch_bounds__(kSwThreads)
+    k_search_sum(int N, const double *ell, const double *sig2, const double *logW, double tau,
+                 int K, int round, int last_round, int S, double E, DevState *st,
+                 const double *gmax, double *psum) {
+  k_search_sum_body(N, ell, sig2, logW, tau, K, round, last_round, S, E, st, gmax, psum, blockIdx.x,
+      gridDim.x);
+}
 
 // Final reweighting: log-sum-exps of the new (x = lw(D)) and old (x = log W) log weights, the
 // ESS at D and the log Z increment (Sec. 3.5). Same two phases; index 0 = new, 1 = old. Within a
@@ -740,15 +751,14 @@ __device__ __forceinline__ void tree_sum3(double *v0, double *v1, double *v2) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kFinThreads)
-    k_final_max(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
-                double *pmax, double *gmax) {
+__device__ __forceinline__ void k_final_max_body(int N, const double *ell, const double *sig2,
+    const double *logW, DevState *st, double *pmax, double *gmax, int bid_, int nblk_) {
   __shared__ double v0[kFinThreads], v1[kFinThreads];
   __shared__ bool is_last;
   const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
-  const int tid = threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int tid = threadIdx.x, stride = nblk_ * blockDim.x;
   double m0 = -INFINITY, m1 = -INFINITY;
-  for (int i = blockIdx.x * blockDim.x + tid; i < N; i += stride) {
+  for (int i = bid_ * blockDim.x + tid; i < N; i += stride) {
     const double lw = logW[i];
     m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], lw)));
     m1 = fmax(m1, lw);
@@ -757,12 +767,12 @@ __global__ void __launch_bounds__(kFinThreads)
   v1[tid] = m1;
   tree_max2(v0, v1);
   if (tid == 0) {
-    pmax[2 * blockIdx.x] = v0[0];
-    pmax[2 * blockIdx.x + 1] = v1[0];
+    pmax[2 * bid_] = v0[0];
+    pmax[2 * bid_ + 1] = v1[0];
   }
-  if (!last_block(st, &is_last)) return;
+  if (!last_block(st, &is_last, nblk_)) return;
   m0 = m1 = -INFINITY;
-  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = tid; b < (int)nblk_; b += blockDim.x) {
     m0 = fmax(m0, __ldcg(pmax + 2 * b));
     m1 = fmax(m1, __ldcg(pmax + 2 * b + 1));
   }
@@ -775,17 +785,21 @@ __global__ void __launch_bounds__(kFinThreads)
     st->ticket = 0;
   }
 }
-
 __global__ void __launch_bounds__(kFinThreads)
-    k_final_sum(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
-                const double *gmax, double *psum) {
+    k_final_max(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                double *pmax, double *gmax) {
+  k_final_max_body(N, ell, sig2, logW, st, pmax, gmax, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void k_final_sum_body(int N, const double *ell, const double *sig2,
+    const double *logW, DevState *st, const double *gmax, double *psum, int bid_, int nblk_) {
   __shared__ double v0[kFinThreads], v1[kFinThreads], v2[kFinThreads];
   __shared__ bool is_last;
   const double a = st->a, D = st->D, h = 0.5 * ((a + D) * (a + D) - a * a);
   const double M0 = __ldcg(gmax), M1 = __ldcg(gmax + 1);
-  const int tid = threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int tid = threadIdx.x, stride = nblk_ * blockDim.x;
   double s1 = 0.0, s2 = 0.0, so = 0.0;
-  for (int i = blockIdx.x * blockDim.x + tid; i < N; i += stride) {
+  for (int i = bid_ * blockDim.x + tid; i < N; i += stride) {
     const double lw = logW[i];
     const double e = exp(fma(-h, sig2[i], fma(D, ell[i], lw)) - M0);
     s1 += e;
@@ -797,13 +811,13 @@ __global__ void __launch_bounds__(kFinThreads)
   v2[tid] = so;
   tree_sum3(v0, v1, v2);
   if (tid == 0) {
-    psum[3 * blockIdx.x] = v0[0];
-    psum[3 * blockIdx.x + 1] = v1[0];
-    psum[3 * blockIdx.x + 2] = v2[0];
+    psum[3 * bid_] = v0[0];
+    psum[3 * bid_ + 1] = v1[0];
+    psum[3 * bid_ + 2] = v2[0];
   }
-  if (!last_block(st, &is_last)) return;
+  if (!last_block(st, &is_last, nblk_)) return;
   s1 = s2 = so = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = tid; b < (int)nblk_; b += blockDim.x) {
     s1 += __ldcg(psum + 3 * b);
     s2 += __ldcg(psum + 3 * b + 1);
     so += __ldcg(psum + 3 * b + 2);
@@ -824,19 +838,28 @@ __global__ void __launch_bounds__(kFinThreads)
   if (!isfinite(lse_new) || !isfinite(lse_old)) atomicOr(&st->err, kErrNonFinite);
   st->ticket = 0;
 }
+__global__ void __launch_bounds__(kFinThreads)
+    k_final_sum(int N, const double *ell, const double *sig2, const double *logW, DevState *st,
+                const double *gmax, double *psum) {
+  k_final_sum_body(N, ell, sig2, logW, st, gmax, psum, blockIdx.x, gridDim.x);
+}
 
-__global__ void k_normalise(int N, const double *ell, const double *sig2, double *logW, double *W,
-                            const DevState *st) {
+__device__ __forceinline__ void k_normalise_body(int N, const double *ell, const double *sig2,
+    double *logW, double *W, const DevState *st, int bid_, int nblk_) {
   const double a = st->a_prev, D = st->D, lse = st->lse_new;
   const double h = 0.5 * ((a + D) * (a + D) - a * a);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+  for (int i = bid_ * blockDim.x + threadIdx.x; i < N; i += nblk_ * blockDim.x) {
     const double l = fma(-h, sig2[i], fma(D, ell[i], logW[i])) - lse;
     logW[i] = l;
     W[i] = exp(l);
   }
 }
+__global__ void k_normalise(int N, const double *ell, const double *sig2, double *logW, double *W,
+                            const DevState *st) {
+  k_normalise_body(N, ell, sig2, logW, W, st, blockIdx.x, gridDim.x);
+}
 
-__global__ void k_search_begin(DevState *st) {
+__device__ __forceinline__ void k_search_begin_body(DevState *st, int bid_, int nblk_) {
   st->dmax = 1.0 - st->a;
   st->lo = 0.0;
   st->hi = st->dmax;
@@ -845,6 +868,9 @@ __global__ void k_search_begin(DevState *st) {
   st->best_D = st->dmax;
   st->search_done = 0;
   st->ticket = 0;
+}
+__global__ void k_search_begin(DevState *st) {
+  k_search_begin_body(st, blockIdx.x, gridDim.x);
 }
 
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
@@ -891,18 +917,23 @@ int reweight_scratch_doubles() { return kMaxK + kRwMaxBlocks * kMaxK * 3; }
 constexpr int kMomThreads = 256, kMomBlocks = 152;
 
 template <typename CT>
-__global__ void k_mean_partials(int N, int p, const double *W, const CT *theta, double *part) {
+__device__ __forceinline__ void k_mean_partials_body(int N, int p, const double *W, const CT *theta,
+    double *part, int bid_, int nblk_) {
   for (int c = threadIdx.x; c < p; c += blockDim.x) {
     double s = 0.0;
-    for (int i = blockIdx.x; i < N; i += gridDim.x) s += W[i] * (double)theta[(int64_t)i * p + c];
-    part[(int64_t)blockIdx.x * p + c] = s;
+    for (int i = bid_; i < N; i += nblk_) s += W[i] * (double)theta[(int64_t)i * p + c];
+    part[(int64_t)bid_ * p + c] = s;
   }
 }
-__global__ void k_sum_partials(const double *part, int nblk, int width, double *out,
-                               int symmetric_p) {
+template <typename CT>
+__global__ void k_mean_partials(int N, int p, const double *W, const CT *theta, double *part) {
+  k_mean_partials_body<CT>(N, p, W, theta, part, blockIdx.x, gridDim.x);
+}
+__device__ __forceinline__ void k_sum_partials_body(const double *part, int nblk, int width,
+    double *out, int symmetric_p, int bid_, int nblk_) {
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < width; e += warps) {
+  const int warps = (nblk_ * blockDim.x) >> 5;
+  for (int e = (bid_ * blockDim.x + threadIdx.x) >> 5; e < width; e += warps) {
     if (symmetric_p && e % symmetric_p < e / symmetric_p) continue;  // lower triangle: mirrored
     double s = 0.0;
     for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * width + e];
@@ -917,20 +948,29 @@ __global__ void k_sum_partials(const double *part, int nblk, int width, double *
     }
   }
 }
+__global__ void k_sum_partials(const double *part, int nblk, int width, double *out,
+                               int symmetric_p) {
+  k_sum_partials_body(part, nblk, width, out, symmetric_p, blockIdx.x, gridDim.x);
+}
 template <typename CT>
-__global__ void k_cov_partials(int N, int p, const double *W, const CT *theta, const double *mean,
-                               double *part) {
+__device__ __forceinline__ void k_cov_partials_body(int N, int p, const double *W, const CT *theta,
+    const double *mean, double *part, int bid_, int nblk_) {
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int r = e / p, c = e % p;
     if (c < r) continue;
     double s = 0.0;
-    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    for (int i = bid_; i < N; i += nblk_) {
       const double dr = (double)theta[(int64_t)i * p + r] - mean[r];
       const double dc = (double)theta[(int64_t)i * p + c] - mean[c];
       s += W[i] * dr * dc;
     }
-    part[(int64_t)blockIdx.x * p * p + e] = s;
+    part[(int64_t)bid_ * p * p + e] = s;
   }
+}
+template <typename CT>
+__global__ void k_cov_partials(int N, int p, const double *W, const CT *theta, const double *mean,
+                               double *part) {
+  k_cov_partials_body<CT>(N, p, W, theta, mean, part, blockIdx.x, gridDim.x);
 }
 
 int weighted_moments(int is_f64, int N, int p, const double *W, const void *theta,
@@ -955,8 +995,8 @@ int weighted_moments(int is_f64, int N, int p, const double *W, const void *thet
 // cumulatively, at most 12 retries); then Linv = chol^{-1} for drawing rho = Linv' z. When no
 // retry succeeds (e.g. a single particle: Sigma = 0) the previous mass matrix is kept.
 template <typename CT>
-__global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *chol, CT *Sigma_ct,
-                       CT *Linv_ct, double *work, DevState *st) {
+__device__ __forceinline__ void k_mass_body(int p, const double *Sigma_in, double *Sigma,
+    double *chol, CT *Sigma_ct, CT *Linv_ct, double *work, DevState *st, int bid_, int nblk_) {
   extern __shared__ double M[];
   __shared__ int flag;
   __shared__ double jit;
@@ -1003,6 +1043,11 @@ __global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *cho
   __syncthreads();
   for (int e = tid; e < p * p; e += blockDim.x) Linv_ct[e] = (CT)work[e];
 }
+template <typename CT>
+__global__ void k_mass(int p, const double *Sigma_in, double *Sigma, double *chol, CT *Sigma_ct,
+                       CT *Linv_ct, double *work, DevState *st) {
+  k_mass_body<CT>(p, Sigma_in, Sigma, chol, Sigma_ct, Linv_ct, work, st, blockIdx.x, gridDim.x);
+}
 
 int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double *chol,
                 void *Sigma_ct, void *Linv_ct, double *work, DevState *st, cudaStream_t s) {
@@ -1033,9 +1078,8 @@ int mass_matrix(int is_f64, int p, const double *Sigma_in, double *Sigma, double
 // ------------------------------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads)
-    k_res_scan(int N, const double *W, uint64_t *cum, uint64_t seed, int stage, int stage_dev,
-               DevState *st) {
+__device__ __forceinline__ void k_res_scan_body(int N, const double *W, uint64_t *cum,
+    uint64_t seed, int stage, int stage_dev, DevState *st, int bid_, int nblk_) {
   __shared__ unsigned long long tot[kScanThreads];
   const int tid = threadIdx.x;
   const int per = (N + kScanThreads - 1) / kScanThreads;
@@ -1063,12 +1107,18 @@ __global__ void __launch_bounds__(kScanThreads)
     st->res_off = (unsigned long long)floor(U * (double)T);
   }
 }
+__global__ void __launch_bounds__(kScanThreads)
+    k_res_scan(int N, const double *W, uint64_t *cum, uint64_t seed, int stage, int stage_dev,
+               DevState *st) {
+  k_res_scan_body(N, W, cum, seed, stage, stage_dev, st, blockIdx.x, gridDim.x);
+}
 
-__global__ void k_res_ancestors(int N, const uint64_t *cum, int32_t *anc, const DevState *st,
-                                uint64_t seed, int stage, int stage_dev, int multinomial) {
+__device__ __forceinline__ void k_res_ancestors_body(int N, const uint64_t *cum, int32_t *anc,
+    const DevState *st, uint64_t seed, int stage, int stage_dev, int multinomial, int bid_,
+    int nblk_) {
   const unsigned long long T = st->res_T, off = st->res_off;
   const uint32_t sm = stage_move(stage_dev ? st->stage : stage, 0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+  for (int i = bid_ * blockDim.x + threadIdx.x; i < N; i += nblk_ * blockDim.x) {
     if (T == 0) {
       anc[i] = i;
       continue;
@@ -1092,14 +1142,18 @@ __global__ void k_res_ancestors(int N, const uint64_t *cum, int32_t *anc, const 
     anc[i] = lo;
   }
 }
+__global__ void k_res_ancestors(int N, const uint64_t *cum, int32_t *anc, const DevState *st,
+                                uint64_t seed, int stage, int stage_dev, int multinomial) {
+  k_res_ancestors_body(N, cum, anc, st, seed, stage, stage_dev, multinomial, blockIdx.x, gridDim.x);
+}
 
 template <typename CT>
-__global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, const CT *theta,
-                             CT *theta_out, const int32_t *u, int32_t *u_out, const double *ell,
-                             double *ell_out, const double *sig2, double *sig2_out,
-                             const double *blk, double *blk_out, double *logW, double *W) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+__device__ __forceinline__ void k_res_gather_body(int N, int p, int m, int G, const int32_t *anc,
+    const CT *theta, CT *theta_out, const int32_t *u, int32_t *u_out, const double *ell,
+    double *ell_out, const double *sig2, double *sig2_out, const double *blk, double *blk_out,
+    double *logW, double *W, int bid_, int nblk_) {
+  const int warp = (bid_ * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (nblk_ * blockDim.x) >> 5;
   for (int i = warp; i < N; i += nwarps) {
     const int a = anc[i];
     for (int c = lane; c < p; c += 32) theta_out[(int64_t)i * p + c] = theta[(int64_t)a * p + c];
@@ -1112,7 +1166,8 @@ __global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, con
     } else {
       for (int j = lane; j < m; j += 32) ud[j] = us[j];
     }
-    for (int h = lane; h < 2 * G; h += 32) blk_out[(int64_t)i * 2 * G + h] = blk[(int64_t)a * 2 * G + h];
+    for (int h = lane; h < 2 * G; h += 32)
+      blk_out[(int64_t)i * 2 * G + h] = blk[(int64_t)a * 2 * G + h];
     if (lane == 0) {
       ell_out[i] = ell[a];
       sig2_out[i] = sig2[a];
@@ -1120,6 +1175,14 @@ __global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, con
       W[i] = 1.0 / (double)N;
     }
   }
+}
+template <typename CT>
+__global__ void k_res_gather(int N, int p, int m, int G, const int32_t *anc, const CT *theta,
+                             CT *theta_out, const int32_t *u, int32_t *u_out, const double *ell,
+                             double *ell_out, const double *sig2, double *sig2_out,
+                             const double *blk, double *blk_out, double *logW, double *W) {
+  k_res_gather_body<CT>(N, p, m, G, anc, theta, theta_out, u, u_out, ell, ell_out, sig2, sig2_out,
+                        blk, blk_out, logW, W, blockIdx.x, gridDim.x);
 }
 
 int resample(int is_f64, int N, int p, int m, int G, uint64_t seed, int stage, int stage_dev,
@@ -1158,10 +1221,14 @@ int weights_from(int N, const double *W_in, double *logW, double *W, cudaStream_
   return (int)cudaGetLastError();
 }
 
-__global__ void k_eps_update(int N, int R, double target, DevState *st) {
+__device__ __forceinline__ void k_eps_update_body(int N, int R, double target, DevState *st,
+    int bid_, int nblk_) {
   const double rate = (double)st->acc_theta / ((double)N * (double)R);
   const double f = exp(rate - target);
   st->eps *= f < 0.5 ? 0.5 : (f > 2.0 ? 2.0 : f);
+}
+__global__ void k_eps_update(int N, int R, double target, DevState *st) {
+  k_eps_update_body(N, R, target, st, blockIdx.x, gridDim.x);
 }
 int eps_update(int N, int R, DevState *st, cudaStream_t s, double target) {
   k_eps_update<<<1, 1, 0, s>>>(N, R, target, st);
@@ -1253,6 +1320,198 @@ int stage_set(DevState *st, int stage, cudaStream_t s) {
 
 int stage_advance(DevState *st, cudaStream_t s) {
   k_stage_advance<<<1, 1, 0, s>>>(st);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace subsmc
+
+// ------------------------------------------------------------------------------------------------
+// The stage steps of a batch of problems in a few launches: every kernel body above runs for
+// problem q on blocks off[kind][q] .. off[kind][q + 1] - 1 of one launch, with q's own block count
+// (that of its single-problem launch), so each problem's reductions run in the same order as when
+// it is stepped alone.
+// ------------------------------------------------------------------------------------------------
+namespace subsmc {
+
+int stage_kind_blocks(int kind, int N, int p) {
+  switch (kind) {
+    case kSkSearch: return N + 15 < 16 * kRwMaxBlocks ? (N + 15) / 16 : kRwMaxBlocks;
+    case kSkFinal: {
+      const int nb = (N + kFinThreads - 1) / kFinThreads;
+      return nb < kRwMaxBlocks ? nb : kRwMaxBlocks;
+    }
+    case kSkMom: return N < kMomBlocks ? N : kMomBlocks;
+    case kSkSumMean: return (p + 7) / 8;
+    case kSkSumCov: return (p * p + 7) / 8;
+    case kSkAnc: return (N + 255) / 256;
+    case kSkGather: {
+      const int gw = (N * 32 + 255) / 256;
+      return gw < 152 * 16 ? gw : 152 * 16;
+    }
+    default: return 0;
+  }
+}
+
+namespace {
+
+__device__ __forceinline__ int stage_kind_blocks_dev(int kind, int N) {
+  return kind == kSkMom ? (N < kMomBlocks ? N : kMomBlocks) : 0;
+}
+
+// the problem that owns block g: the last q with off[q] <= g
+__device__ __forceinline__ int problem_of(const int *off, int P, int g) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+struct Slot {
+  const StageArgs *a;
+  int bid, nblk;
+};
+__device__ __forceinline__ Slot slot_of(const StageArgs *A, const int *off, int P) {
+  const int q = problem_of(off, P, (int)blockIdx.x);
+  return Slot{A + q, (int)blockIdx.x - off[q], off[q + 1] - off[q]};
+}
+
+// partial scratch of a problem: [kMaxK] maxima | [kRwMaxBlocks][kMaxK] | [kRwMaxBlocks][kMaxK][2]
+__device__ __forceinline__ double *gmax_of(const StageArgs &a) { return a.part; }
+__device__ __forceinline__ double *pmax_of(const StageArgs &a) { return a.part + kMaxK; }
+__device__ __forceinline__ double *psum_of(const StageArgs &a) {
+  return a.part + kMaxK + kRwMaxBlocks * kMaxK;
+}
+
+// one thread per problem: stage counter, accept counters, search bracket
+__global__ void kb_begin(const StageArgs *A, int P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  DevState *st = A[q].st;
+  st->stage += 1;
+  st->acc_u = 0ull;
+  st->acc_theta = 0ull;
+  k_search_begin_body(st, 0, 1);
+}
+
+__global__ void __launch_bounds__(kSwThreads)
+    kb_search_max(const StageArgs *A, const int *off, int P, int round) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_search_max_body(a.N, a.ell, a.sig2, a.logW, a.K, round, a.S, a.E, a.st, pmax_of(a), gmax_of(a),
+                    s.bid, s.nblk);
+}
+__global__ void __launch_bounds__(kSwThreads)
+    kb_search_sum(const StageArgs *A, const int *off, int P, int round) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_search_sum_body(a.N, a.ell, a.sig2, a.logW, a.tau, a.K, round, a.last_round, a.S, a.E, a.st,
+                    gmax_of(a), psum_of(a), s.bid, s.nblk);
+}
+__global__ void __launch_bounds__(kFinThreads)
+    kb_final_max(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_final_max_body(a.N, a.ell, a.sig2, a.logW, a.st, pmax_of(a), gmax_of(a), s.bid, s.nblk);
+}
+__global__ void __launch_bounds__(kFinThreads)
+    kb_final_sum(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_final_sum_body(a.N, a.ell, a.sig2, a.logW, a.st, gmax_of(a), psum_of(a), s.bid, s.nblk);
+}
+__global__ void kb_normalise(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_normalise_body(a.N, a.ell, a.sig2, a.logW, a.W, a.st, s.bid, s.nblk);
+}
+__global__ void kb_mean_partials(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_mean_partials_body<float>(a.N, a.p, a.W, a.theta, a.part, s.bid, s.nblk);
+}
+__global__ void kb_sum_mean(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_sum_partials_body(a.part, stage_kind_blocks_dev(kSkMom, a.N), a.p, a.mean, 0, s.bid, s.nblk);
+}
+__global__ void kb_cov_partials(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_cov_partials_body<float>(a.N, a.p, a.W, a.theta, a.mean, a.part, s.bid, s.nblk);
+}
+__global__ void kb_sum_cov(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_sum_partials_body(a.part, stage_kind_blocks_dev(kSkMom, a.N), a.p * a.p, a.Sigma_raw, a.p,
+                      s.bid, s.nblk);
+}
+__global__ void kb_mass(const StageArgs *A) {
+  const StageArgs &a = A[blockIdx.x];
+  k_mass_body<float>(a.p, a.Sigma_raw, a.Sigma, a.chol, a.Sigma_ct, a.Linv_ct, a.work, a.st, 0, 1);
+}
+__global__ void __launch_bounds__(kScanThreads) kb_res_scan(const StageArgs *A) {
+  const StageArgs &a = A[blockIdx.x];
+  k_res_scan_body(a.N, a.W, a.cum, a.seed, 0, 1, a.st, 0, 1);
+}
+__global__ void kb_res_ancestors(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_res_ancestors_body(a.N, a.cum, a.anc, a.st, a.seed, 0, 1, a.multinomial, s.bid, s.nblk);
+}
+__global__ void kb_res_gather(const StageArgs *A, const int *off, int P) {
+  const Slot s = slot_of(A, off, P);
+  const StageArgs &a = *s.a;
+  k_res_gather_body<float>(a.N, a.p, a.m, a.G, a.anc, a.theta, a.theta_out, a.u, a.u_out, a.ell,
+                           a.ell_out, a.sig2, a.sig2_out, a.blk, a.blk_out, a.logW, a.W, s.bid,
+                           s.nblk);
+}
+__global__ void kb_eps_update(const StageArgs *A, int P, int R) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  const StageArgs &a = A[q];
+  k_eps_update_body(a.N, R, a.eps_target, a.st, 0, 1);
+}
+
+}  // namespace
+
+int stage_batch(const StageBatch &sb, cudaStream_t s, int64_t *launches) {
+  const int P = sb.P;
+  auto off = [&](int kind) { return sb.off + (size_t)kind * (P + 1); };
+  int64_t nl = 0;
+  kb_begin<<<(P + 127) / 128, 128, 0, s>>>(sb.args, P);
+  ++nl;
+  for (int r = 0; r < sb.max_rounds; ++r) {
+    kb_search_max<<<sb.total[kSkSearch], kSwThreads, 0, s>>>(sb.args, off(kSkSearch), P, r);
+    kb_search_sum<<<sb.total[kSkSearch], kSwThreads, 0, s>>>(sb.args, off(kSkSearch), P, r);
+    nl += 2;
+  }
+  kb_final_max<<<sb.total[kSkFinal], kFinThreads, 0, s>>>(sb.args, off(kSkFinal), P);
+  kb_final_sum<<<sb.total[kSkFinal], kFinThreads, 0, s>>>(sb.args, off(kSkFinal), P);
+  kb_normalise<<<sb.total[kSkFinal], kFinThreads, 0, s>>>(sb.args, off(kSkFinal), P);
+  kb_mean_partials<<<sb.total[kSkMom], 128, 0, s>>>(sb.args, off(kSkMom), P);
+  kb_sum_mean<<<sb.total[kSkSumMean], 256, 0, s>>>(sb.args, off(kSkSumMean), P);
+  kb_cov_partials<<<sb.total[kSkMom], kMomThreads, 0, s>>>(sb.args, off(kSkMom), P);
+  kb_sum_cov<<<sb.total[kSkSumCov], 256, 0, s>>>(sb.args, off(kSkSumCov), P);
+  const size_t smem = (size_t)sb.max_p * sb.max_p * sizeof(double);
+  cudaError_t e =
+      cudaFuncSetAttribute(kb_mass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  kb_mass<<<P, 256, smem, s>>>(sb.args);
+  kb_res_scan<<<P, kScanThreads, 0, s>>>(sb.args);
+  kb_res_ancestors<<<sb.total[kSkAnc], 256, 0, s>>>(sb.args, off(kSkAnc), P);
+  kb_res_gather<<<sb.total[kSkGather], 256, 0, s>>>(sb.args, off(kSkGather), P);
+  nl += 11;
+  if (launches) *launches += nl;
+  return (int)cudaGetLastError();
+}
+
+int eps_update_batch(const StageBatch &sb, int R, cudaStream_t s) {
+  kb_eps_update<<<(sb.P + 127) / 128, 128, 0, s>>>(sb.args, sb.P, R);
   return (int)cudaGetLastError();
 }
 

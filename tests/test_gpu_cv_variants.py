@@ -436,15 +436,30 @@ def test_rw_smc_run_matches_oracle_fp64(hmc_kernel):
     S().smc_free(ctx)
 
 
-def test_batch_with_mixed_options_matches_single_problems():
+MIXED_OPTIONS = {
+    # re-centred problems: the stage steps run per problem on side streams
+    "recentred": [dict(family="student_t", cv_order=1),
+                  dict(family="logistic", cv_centre=1),
+                  dict(family="poisson", resampling="multinomial", grid_points=256, ess_frac=0.8),
+                  dict(family="probit", theta_move="rw", cv_centre=2)],
+    # fixed centres: the batched stage kernels (every problem's search, moments, mass matrix and
+    # resampling in shared launches), with per-problem search sizes, grid rule, resampling scheme
+    # and step-size target
+    "fixed_centre": [dict(family="student_t", cv_order=1, search_k=4, search_rounds=13),
+                     dict(family="logistic"),
+                     dict(family="poisson", resampling="multinomial", grid_points=256,
+                          ess_frac=0.8),
+                     dict(family="probit", theta_move="rw")],
+}
+
+
+@pytest.mark.parametrize("kind", sorted(MIXED_OPTIONS))
+def test_batch_with_mixed_options_matches_single_problems(kind):
     """A batch whose problems mix the options (Student-t and logistic families, first-order and
-    re-centred control variates, multinomial resampling with the grid rule, random-walk moves):
-    batched stages give bit-identical results to stepping each problem alone."""
+    re-centred control variates, multinomial resampling with the grid rule, random-walk moves,
+    search sizes): batched stages give bit-identical results to stepping each problem alone."""
     from gpu_common import device_arrays
-    opts = [dict(family="student_t", cv_order=1),
-            dict(family="logistic", cv_centre=1),
-            dict(family="poisson", resampling="multinomial", grid_points=256, ess_frac=0.8),
-            dict(family="probit", theta_move="rw", cv_centre=2)]
+    opts = MIXED_OPTIONS[kind]
     wls, dicts = [], []
     for q, o in enumerate(opts):
         kw = dict(x_scale=0.3) if o["family"] == "poisson" else {}

@@ -337,22 +337,23 @@ def test_full_smc_run_matches_oracle_fp64(hmc_kernel):
 
 @pytest.mark.parametrize("x_dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
-@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10, 11, 14])
+@pytest.mark.parametrize("hmc_kernel", [1, 3, 5, 6, 8, 10, 11, 14, 21])
 def test_moves_reduced_precision_match_oracle(x_dtype, family, hmc_kernel):
     """FP32 arithmetic on FP32/BF16-stored rows against the FP64 oracle on the same stored values:
     the MH decisions may differ only where the FP64 log ratio is within rounding of the uniform;
     accepted end points agree to FP32 leapfrog rounding. hmc_kernel 5, 8 and 11 are resident tiles
     wider than the rows (32, 20 and 40 slots for p = 13), whose slots past p must read zeros; 10 is
-    the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90); 14 is the
-    16-slot tile with two warps per CTA (BF16 only)."""
+    the tensor-core trajectory kernel (BF16 only), here with one 128-row tile (m = 90); 14 and 21
+    are the 16-slot tiles with two warps and one warp per CTA (BF16 only)."""
     _moves_reduced_precision(_wl(family, x_dtype, p=13, N=256, m=90, G=6), x_dtype, hmc_kernel)
 
 
 @pytest.mark.parametrize("family", ["logistic", "poisson", "probit"])
 @pytest.mark.parametrize("p", [33, 37, 40])
-@pytest.mark.parametrize("hmc_kernel", [1, 11, 18])
+@pytest.mark.parametrize("hmc_kernel", [1, 11, 18, 25])
 def test_moves_two_columns_per_lane_match_oracle(family, p, hmc_kernel):
-    """p past one warp's lanes: the 40-slot resident tiles (hmc_kernel 11: four warps, 18: two)
+    """p past one warp's lanes: the 40-slot resident tiles (hmc_kernel 11: four warps, 18: two,
+    25: one)
     hold columns l and l + 32 in lane l (momentum draw, mass-matrix and C products, gradient,
     write-back), against the FP64 oracle on the same BF16-stored values, beside the streamed
     kernel (hmc_kernel 1)."""
@@ -680,10 +681,10 @@ def _batch_problem_dicts(wls):
                          [(False, 2000, 20000), (False, 300000, 1000000), (True, 2000, 20000)])
 def test_batch_stages_match_single_problems(streamed, n_lo, n_hi):
     """One batched u-update launch per move and one trajectory launch per group, the groups side
-    by side on side streams (resident tiles grouped by p and by warps per CTA: two up to 512
-    subsample rows, four above; the streamed kernel when asked; per-problem stage steps on side
-    streams; plain and graph-replayed stages) give bit-identical results to stepping each problem
-    alone with the same tiles. n in [2000, 20000] gives m = 100 everywhere, [3e5, 1e6] a mix of
+    by side on side streams (resident tiles grouped by p and by warps per CTA: one or two for
+    small subsamples, four above 512 rows; the streamed kernel when asked; the stage steps of all
+    problems in shared launches; plain and graph-replayed stages) give bit-identical results to
+    stepping each problem alone with the same tiles. n in [2000, 20000] gives m = 100 everywhere, [3e5, 1e6] a mix of
     m = 337 .. 725."""
     from smc_workloads import batch_uneven
     wls = batch_uneven(P=7, N=96, G=5, L=4, R=2, n_lo=n_lo, n_hi=n_hi)
@@ -698,10 +699,11 @@ def test_batch_stages_match_single_problems(streamed, n_lo, n_hi):
         assert kernels == [1] * len(wls)
     else:
         # every p here (5..40) has a resident tile; p > 32 takes a 40-slot two-column tile, with
-        # two warps per CTA up to m = 512 (hmc_kernel 18) and four above (11)
+        # one warp per CTA up to m = 160 (hmc_kernel 25), two up to m = 512 (18), four above (11)
         assert len(set(kernels)) >= 3 and all(k >= 2 for k in kernels)
         assert any(w.p > 32 for w in wls)
-        assert all(k == (18 if w.m <= 512 else 11) for k, w in zip(kernels, wls) if w.p > 32)
+        assert all(k == (25 if w.m <= 160 else 18 if w.m <= 512 else 11)
+                   for k, w in zip(kernels, wls) if w.p > 32)
         if n_hi > 100000:
             assert any(w.m > 512 for w in wls) and any(w.m <= 512 for w in wls)
     # the singles take the batch problems' centres (the device's Newton modes)
