@@ -397,13 +397,16 @@ int smc_batch_tile(const smc_batch *b, int32_t *tile_hint);
  * tile k - 2): a context created with it (and the batch's tile) steps problem q identically. */
 int smc_batch_hmc_kernel(const smc_batch *b, int32_t q, int32_t *hmc_kernel);
 int64_t smc_batch_launch_count(const smc_batch *b);
-/* One stage of every problem (Algorithm 2 (a)-(f)): reweight and resample per problem (the
- * problems side by side on up to 16 side streams, forked from and joined back to the batch's
- * stream), then per move one u-update launch over the particles of all problems and one
- * trajectory launch per group, then the step sizes. use_graph = 1: the whole batch stage is
- * captured once per buffer parity and replayed as one CUDA graph (kernels read the stage index
- * from device counters), with results bit-identical to use_graph = 0 and to stepping each problem
- * alone with the same tiles (smc_batch_tile, smc_batch_hmc_kernel). */
+/* One stage of every problem (Algorithm 2 (a)-(f)): the temperature search, reweighting,
+ * moments, mass matrix and resampling of every problem; when every problem has a fixed centre
+ * (cv_centre = 0) they run in shared launches over all problems (each problem with its own
+ * block count, so its reductions follow the same order as alone), else per problem side by side
+ * on up to 16 side streams forked from and joined back to the batch's stream. Then per move one
+ * u-update launch over the particles of all problems and one trajectory launch per group (the
+ * groups side by side on the side streams), then the step sizes. use_graph = 1: the whole batch
+ * stage is captured once per buffer parity and replayed as one CUDA graph (kernels read the
+ * stage index from device counters), with results bit-identical to use_graph = 0 and to stepping
+ * each problem alone with the same tiles (smc_batch_tile, smc_batch_hmc_kernel). */
 int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph);
 /* Time the batched HMC launch for every compiled tile that covers the widest row (on scratch
  * copies; the state is unchanged) and keep the fastest; output: the tile as a tile_hint value. */
