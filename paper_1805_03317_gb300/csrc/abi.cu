@@ -74,6 +74,7 @@ struct smc_ctx {
   int64_t g_launches[2] = {0, 0};
   int parity = 0;             // 0: theta/u/ell/sig2/blk are the buffers allocated first
   bool capturing = false;     // inside a stream capture: no tracing events
+  bool batch_member = false;  // stepped by a batch: its stage kernels may run beside others
   int stage_dev = 0;          // kernels read the stage index from the device counter
   bool dev_stage_synced = false;  // the device counter equals stage
   // full-data comparison (loglik_full): FP64 per-particle accumulators, timeout flag, constant
@@ -309,7 +310,10 @@ int check_err_bits(smc_ctx *c, const DevState &h) {
   CUDA_OK(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
   if (bits & kErrIndex) return fail(c, SMC_ERR_ARG, "subsample index outside [0, n)");
   if (bits & kErrChol) return fail(c, SMC_ERR_NONFINITE, "particle covariance not positive definite");
-  if (bits & kErrCap) return fail(c, SMC_ERR_TIMEOUT, "device iteration cap reached");
+  if (bits & kErrCap) {  // a bounded wait gave up: clear the arrival counters it may have left
+    CUDA_OK(c, cudaMemsetAsync(&c->st->ticket, 0, 2 * sizeof(unsigned int), c->stream));
+    return fail(c, SMC_ERR_TIMEOUT, "device iteration cap reached");
+  }
   return fail(c, SMC_ERR_NONFINITE, "non-finite estimate or weight");
 }
 
@@ -838,8 +842,7 @@ int smc_reweight(smc_ctx *c, double *a_next, double *log_z_inc, double *ess) {
   {
     ProfScope ps(c, 3);
     e = reweight(c->N, c->ell, c->sig2, c->logW, c->W, c->tau, c->K, c->rounds, c->grid_points,
-                 c->grid_decades, c->st, c->part,
-                 &nl, c->stream);
+                 c->grid_decades, c->st, c->part, &nl, c->stream, !c->batch_member);
   }
   c->launches += nl;
   if (e) return fail(c, SMC_ERR_CUDA, std::string("reweight: ") + cudaGetErrorString((cudaError_t)e));
@@ -1850,6 +1853,7 @@ int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const s
       g_init_error = m;
       return r;
     }
+    c->batch_member = true;
     b->ctx.push_back(c);
     off[q] = b->total;
     b->total += c->N;

@@ -167,9 +167,12 @@ int init_particles(int is_f64, int N, int p, int m, int64_t n, uint64_t seed, co
 // grid_points > 0: the paper's grid rule (Sec. 2.3): the increment is the point of a geometric grid
 // of grid_points values over [(1 - a) 10^-grid_decades, 1 - a] whose ESS is closest to tau N;
 // otherwise the K-ary bracket search of `rounds` rounds.
+// one_launch: the whole reweighting as one launch with grid barriers between its phases (its
+// blocks must be able to be resident together: not while other such launches may run beside it);
+// else one launch per phase.
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
              int K, int rounds, int grid_points, double grid_decades, DevState *st,
-             double *partials, int *launches, cudaStream_t s);
+             double *partials, int *launches, cudaStream_t s, bool one_launch = true);
 int reweight_scratch_doubles();
 int weighted_moments(int is_f64, int N, int p, const double *W, const void *theta,
                      double *partials, double *mean, double *Sigma, cudaStream_t s);

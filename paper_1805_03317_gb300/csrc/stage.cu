@@ -873,9 +873,323 @@ __global__ void k_search_begin(DevState *st) {
   k_search_begin_body(st, blockIdx.x, gridDim.x);
 }
 
+// ------------------------------------------------------------------------------------------------
+// The whole reweighting of one problem in one launch: the search rounds and the final log-sum-exps
+// above, separated by grid barriers instead of kernel boundaries. Every phase keeps the block count
+// and the per-block work of its separate launch, and every block repeats the merge that the last
+// block does there (same loads, same order), so the results are those of the separate launches bit
+// for bit; block 0 alone writes the device state.
+// ------------------------------------------------------------------------------------------------
+constexpr long long kBarrierCycles = 4000000000ll;  // about 2 s at the maximum SM clock
+
+// Grid-wide barrier of a launch whose blocks are all resident at once (at most one small block per
+// SM, launched alone in its stream): arrivals counted in st->ticket, release by advancing
+// st->ticket2. Bounded: a block that waits about 2 s, or that finds another block has given up,
+// sets kErrCap and returns false on every thread (the kernel then leaves).
+__device__ __forceinline__ bool grid_barrier(DevState *st, int nblk, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = &st->ticket2;
+    volatile int *err = &st->err;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&st->ticket, 1u) == (unsigned)nblk - 1) {
+      atomicExch(&st->ticket, 0u);
+      __threadfence();
+      atomicAdd(&st->ticket2, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if ((*err & kErrCap) || clock64() - t0 > kBarrierCycles) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (!ok) atomicOr(&st->err, kErrCap);
+    __threadfence();
+    *flag = ok;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// The search bracket of one stage, kept by every block of the one-launch reweighting.
+struct SearchState {
+  double a, dmax, lo, hi, D, best_dist, best_D;
+  int done;
+};
+
+__device__ __forceinline__ int state_candidates(const SearchState &ss, int K, int round, int S,
+                                                double E, double *Dk, double *hk, double &lo,
+                                                double &hi) {
+  int ncand;
+  if (S > 0) {
+    lo = hi = ss.dmax;
+    ncand = min(K, S - round * K);
+  } else {
+    lo = round == 0 ? 0.0 : ss.lo;
+    hi = round == 0 ? ss.dmax : ss.hi;
+    ncand = round == 0 ? K : K - 1;
+  }
+  const double a = ss.a;
+  for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+    const double D = S > 0 ? grid_point(ss.dmax, S, E, round * K + k) : candidate(lo, hi, K, k);
+    Dk[k] = D;
+    hk[k] = 0.5 * ((a + D) * (a + D) - a * a);
+  }
+  return ncand;
+}
+
+// nbs: the blocks of a search round, nb: the blocks of the final reweighting (gridDim.x is the
+// larger); part: the same scratch as the separate launches.
+__global__ void __launch_bounds__(kSwThreads)
+    k_reweight_one(int N, const double *ell, const double *sig2, double *logW, double *W,
+                   double tau, int K, int rounds, int S, double E, DevState *st, double *part,
+                   int nbs, int nb) {
+  __shared__ double Dk[kMaxK], hk[kMaxK], ess_k[kMaxK], gm[kMaxK];
+  __shared__ double w1[kSwThreads], w2[kSwThreads], w3[kSwThreads];
+  __shared__ SearchState ss;
+  __shared__ int flag;
+  const int bid = blockIdx.x, tid = threadIdx.x, nblk = gridDim.x;
+  double *pmax = part + kMaxK, *psum = pmax + kRwMaxBlocks * kMaxK;
+  if (tid == 0) {
+    ss.a = st->a;
+    ss.dmax = 1.0 - ss.a;
+    ss.lo = 0.0;
+    ss.hi = ss.dmax;
+    ss.D = 0.0;
+    ss.best_dist = INFINITY;
+    ss.best_D = ss.dmax;
+    ss.done = 0;
+  }
+  __syncthreads();
+  const double target = tau * (double)N;
+  for (int r = 0; r < rounds && !ss.done; ++r) {
+    double lo, hi;
+    const int ncand = state_candidates(ss, K, r, S, E, Dk, hk, lo, hi);
+    __syncthreads();
+    const SearchLanes L(ncand);
+    const int chunk = (N + nbs - 1) / nbs;
+    const int i0 = bid * chunk, i1 = min(N, i0 + chunk);
+    if (bid < nbs) {  // the maxima of this block's particles (k_search_max)
+      double mx = -INFINITY;
+      if (L.k < ncand) {
+        const double D = Dk[L.k], h = hk[L.k];
+#pragma unroll 4
+        for (int i = i0 + L.stream; i < i1; i += L.nstream)
+          mx = fmax(mx, fma(-h, sig2[i], fma(D, ell[i], logW[i])));
+      }
+      w1[tid] = mx;
+      __syncthreads();
+      if (tid < ncand) {
+        double m = w1[tid];
+        for (int q = 1; q < L.nstream; ++q) m = fmax(m, w1[q * L.kslots + tid]);
+        pmax[bid * kMaxK + tid] = m;
+      }
+    }
+    if (!grid_barrier(st, nblk, &flag)) return;
+    {  // every block: the maxima over blocks, merged as the last block of k_search_max does
+      double m = -INFINITY;
+      if (L.k < ncand) {
+#pragma unroll 8
+        for (int b = L.stream; b < nbs; b += L.nstream) m = fmax(m, __ldcg(pmax + b * kMaxK + L.k));
+      }
+      w1[tid] = m;
+      __syncthreads();
+      if (tid < ncand) {
+        double g = w1[tid];
+        for (int q = 1; q < L.nstream; ++q) g = fmax(g, w1[q * L.kslots + tid]);
+        gm[tid] = g;
+      }
+      __syncthreads();
+    }
+    if (bid < nbs) {  // the sums of this block's particles (k_search_sum)
+      double s1 = 0.0, s2 = 0.0;
+      if (L.k < ncand) {
+        const double D = Dk[L.k], h = hk[L.k], M = gm[L.k];
+        if (M > -INFINITY) {
+#pragma unroll 4
+          for (int i = i0 + L.stream; i < i1; i += L.nstream) {
+            const double e = exp(fma(-h, sig2[i], fma(D, ell[i], logW[i])) - M);
+            s1 += e;
+            s2 = fma(e, e, s2);
+          }
+        }
+      }
+      w1[tid] = s1;
+      w2[tid] = s2;
+      __syncthreads();
+      if (tid < ncand) {
+        double t1 = w1[tid], t2 = w2[tid];
+        for (int q = 1; q < L.nstream; ++q) {
+          t1 += w1[q * L.kslots + tid];
+          t2 += w2[q * L.kslots + tid];
+        }
+        psum[2 * (bid * kMaxK + tid)] = t1;
+        psum[2 * (bid * kMaxK + tid) + 1] = t2;
+      }
+    }
+    if (!grid_barrier(st, nblk, &flag)) return;
+    {  // every block: the ESS of each candidate, merged as the last block of k_search_sum does
+      double t1 = 0.0, t2 = 0.0;
+      if (L.k < ncand) {
+#pragma unroll 8
+        for (int b = L.stream; b < nbs; b += L.nstream) {
+          t1 += __ldcg(psum + 2 * (b * kMaxK + L.k));
+          t2 += __ldcg(psum + 2 * (b * kMaxK + L.k) + 1);
+        }
+      }
+      w1[tid] = t1;
+      w2[tid] = t2;
+      __syncthreads();
+      if (tid < ncand) {
+        t1 = w1[tid];
+        t2 = w2[tid];
+        for (int q = 1; q < L.nstream; ++q) {
+          t1 += w1[q * L.kslots + tid];
+          t2 += w2[q * L.kslots + tid];
+        }
+        ess_k[tid] = t1 * t1 / t2;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {  // the bracket (the same arithmetic in every block)
+      const int ninner = r == 0 ? K - 1 : ncand;
+      if (bid == 0)
+        for (int k = 0; k < ncand; ++k)
+          if (!(ess_k[k] == ess_k[k])) atomicOr(&st->err, kErrNonFinite);
+      if (S > 0) {  // grid rule: the closest ESS so far wins; ties keep the smaller increment
+        for (int k = 0; k < ncand; ++k) {
+          const double dist = fabs(ess_k[k] - target);
+          if (dist < ss.best_dist) {
+            ss.best_dist = dist;
+            ss.best_D = Dk[k];
+          }
+        }
+        if (r == rounds - 1) {
+          ss.D = ss.best_D;
+          ss.done = 1;
+        }
+      } else if (r == 0 && ess_k[K - 1] >= target) {  // go straight to a = 1
+        ss.D = ss.dmax;
+        ss.done = 1;
+      } else {
+        int first = ninner + 1;
+        for (int k = 0; k < ninner; ++k) {
+          if (ess_k[k] < target) {
+            first = k + 1;
+            break;
+          }
+        }
+        const double nlo = lo + (hi - lo) * (first - 1) / K;
+        const double nhi = first <= ninner ? lo + (hi - lo) * first / K : hi;
+        ss.lo = nlo;
+        ss.hi = nhi;
+        if (r == rounds - 1) {
+          ss.D = nlo > 0.0 ? nlo : nhi;
+          ss.done = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // the final reweighting at D (k_final_max, k_final_sum, k_normalise: nb blocks)
+  const double a = ss.a, D = ss.D, h = 0.5 * ((a + D) * (a + D) - a * a);
+  const int fstride = nb * blockDim.x;
+  if (bid < nb) {
+    double m0 = -INFINITY, m1 = -INFINITY;
+    for (int i = bid * blockDim.x + tid; i < N; i += fstride) {
+      const double lw = logW[i];
+      m0 = fmax(m0, fma(-h, sig2[i], fma(D, ell[i], lw)));
+      m1 = fmax(m1, lw);
+    }
+    w1[tid] = m0;
+    w2[tid] = m1;
+    tree_max2(w1, w2);
+    if (tid == 0) {
+      pmax[2 * bid] = w1[0];
+      pmax[2 * bid + 1] = w2[0];
+    }
+  }
+  if (!grid_barrier(st, nblk, &flag)) return;
+  double M0, M1;
+  {
+    double m0 = -INFINITY, m1 = -INFINITY;
+    for (int b = tid; b < nb; b += blockDim.x) {
+      m0 = fmax(m0, __ldcg(pmax + 2 * b));
+      m1 = fmax(m1, __ldcg(pmax + 2 * b + 1));
+    }
+    w1[tid] = m0;
+    w2[tid] = m1;
+    tree_max2(w1, w2);
+    M0 = w1[0];
+    M1 = w2[0];
+    __syncthreads();
+  }
+  if (bid < nb) {
+    double s1 = 0.0, s2 = 0.0, so = 0.0;
+    for (int i = bid * blockDim.x + tid; i < N; i += fstride) {
+      const double lw = logW[i];
+      const double e = exp(fma(-h, sig2[i], fma(D, ell[i], lw)) - M0);
+      s1 += e;
+      s2 = fma(e, e, s2);
+      so += exp(lw - M1);
+    }
+    w1[tid] = s1;
+    w2[tid] = s2;
+    w3[tid] = so;
+    tree_sum3(w1, w2, w3);
+    if (tid == 0) {
+      psum[3 * bid] = w1[0];
+      psum[3 * bid + 1] = w2[0];
+      psum[3 * bid + 2] = w3[0];
+    }
+  }
+  if (!grid_barrier(st, nblk, &flag)) return;
+  {
+    double s1 = 0.0, s2 = 0.0, so = 0.0;
+    for (int b = tid; b < nb; b += blockDim.x) {
+      s1 += __ldcg(psum + 3 * b);
+      s2 += __ldcg(psum + 3 * b + 1);
+      so += __ldcg(psum + 3 * b + 2);
+    }
+    w1[tid] = s1;
+    w2[tid] = s2;
+    w3[tid] = so;
+    tree_sum3(w1, w2, w3);
+  }
+  const double t1 = w1[0], t2 = w2[0], to = w3[0];
+  const double lse_new = M0 + log(t1), lse_old = M1 + log(to);
+  if (bid == 0 && tid == 0) {  // the device state, as the separate launches leave it
+    st->dmax = ss.dmax;
+    st->lo = ss.lo;
+    st->hi = ss.hi;
+    st->best_dist = ss.best_dist;
+    st->best_D = ss.best_D;
+    st->D = D;
+    st->search_done = 1;
+    st->lse_new = lse_new;
+    st->lse_old = lse_old;
+    st->ess = t1 * t1 / t2;
+    st->log_z_inc = lse_new - lse_old;
+    st->log_z += st->log_z_inc;
+    st->a_prev = a;
+    st->a = (D == ss.dmax) ? 1.0 : a + D;
+    if (!isfinite(lse_new) || !isfinite(lse_old)) atomicOr(&st->err, kErrNonFinite);
+  }
+  // normalised weights (every block; the reads of log W above are finished everywhere)
+  for (int i = bid * blockDim.x + tid; i < N; i += nblk * blockDim.x) {
+    const double l = fma(-h, sig2[i], fma(D, ell[i], logW[i])) - lse_new;
+    logW[i] = l;
+    W[i] = exp(l);
+  }
+}
+
 int reweight(int N, const double *ell, const double *sig2, double *logW, double *W, double tau,
              int K, int rounds, int grid_points, double grid_decades, DevState *st,
-             double *partials, int *launches, cudaStream_t s) {
+             double *partials, int *launches, cudaStream_t s, bool one_launch) {
   if (grid_points > 0) {  // the grid in rounds of kMaxK points
     if (grid_points < 2 || !(grid_decades > 0.0)) return (int)cudaErrorInvalidValue;
     K = kMaxK;
@@ -889,6 +1203,13 @@ int reweight(int N, const double *ell, const double *sig2, double *logW, double 
   double *gmax = partials;                     // [kMaxK]
   double *pmax = gmax + kMaxK;                 // [nbs][kMaxK]
   double *psum = pmax + kRwMaxBlocks * kMaxK;  // [nbs][kMaxK][2]
+  if (one_launch) {  // every block resident at once: at most 152 blocks of 128 threads
+    const int grid = nbs > nb ? nbs : nb;
+    k_reweight_one<<<grid, kSwThreads, 0, s>>>(N, ell, sig2, logW, W, tau, K, rounds,
+                                               grid_points, grid_decades, st, partials, nbs, nb);
+    if (launches) *launches += 1;
+    return (int)cudaGetLastError();
+  }
   int count = 0;
   k_search_begin<<<1, 1, 0, s>>>(st);
   ++count;
