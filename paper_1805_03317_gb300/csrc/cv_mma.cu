@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
   const uint32_t a_base = smem_u32(At), b_base = smem_u32(Bt);
 
   double Aacc = 0.0, Bacc = 0.0;
+  const int bgroups = kRows / p, bgrp = tid / p, bcol = tid - (tid / p) * p;
   uint32_t phase = 0;
   int since_drain = 0;
   bool timed_out = false;
@@ -247,16 +248,18 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
       }
       mma_commit(bar);
     }
-    if (tid < p) {
-      const int c = tid >> 3, e = tid & 7;
-      double b4[4] = {0.0, 0.0, 0.0, 0.0};  // independent FP64 chains
+    // B: thread (g, c) of the bgroups groups of p threads takes column c of rows g, g + bgroups,
+    // .. (the FP64 work of a tile spread over all warps; the groups are merged once at the end)
+    if (bgrp < bgroups) {
+      const int c = bcol >> 3, e = bcol & 7;
+      double b2[2] = {0.0, 0.0};  // independent FP64 chains
 #pragma unroll 4
-      for (int k = 0; k < kRows; ++k) {
+      for (int k = bgrp, t = 0; k < kRows; k += bgroups, ++t) {
         const float x = __bfloat162float(
             *reinterpret_cast<const __nv_bfloat16 *>(At + unit_off(k, c) + 2 * e));
-        b4[k & 3] = fma(lps[k], (double)x, b4[k & 3]);
+        b2[t & 1] = fma(lps[k], (double)x, b2[t & 1]);
       }
-      Bacc += (b4[0] + b4[1]) + (b4[2] + b4[3]);
+      Bacc += b2[0] + b2[1];
     }
     // 4. wait for the MMAs (bounded in time; a timeout is reported as a NaN A partial)
     {
@@ -301,7 +304,13 @@ __global__ void __launch_bounds__(kRows) k_cv_mma(const __nv_bfloat16 *Xp, int64
     for (int w = 0; w < kRows / 32; ++w) t += red[w];
     out[0] = timed_out ? __longlong_as_double(0x7FF8000000000000ll) : t;
   }
-  if (tid < p) out[1 + tid] = Bacc;
+  lps[tid] = Bacc;  // the tiles are done with lps: it collects the groups' B partials
+  __syncthreads();
+  if (tid < p) {
+    double b = 0.0;
+    for (int g = 0; g < bgroups; ++g) b += lps[g * p + tid];
+    out[1 + tid] = b;
+  }
   for (int q = tid; q < np; q += kRows) out[1 + p + q] = Cacc[q];
   tc_fence_before();
   __syncthreads();
