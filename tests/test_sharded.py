@@ -1,5 +1,5 @@
 """Particle sharding of one posterior over processes (paper_1805_03317_gb300/sharded.py), host
-logic on CPU: two gloo ranks drive the sharded stage with a host stand-in for the library's
+logic on CPU: two or three gloo ranks drive the sharded stage with a host stand-in for the library's
 per-process calls (tests/shard_fake.py: the oracle's reweighting, moments and resampling, a toy
 move that reads each particle's own u and global index, u kept only inside each slice). The
 sharded run must equal the one-process run of the same driver exactly: temperatures, log Z,
@@ -69,17 +69,19 @@ def F_status(c):
     return (c.a, c.log_z, c.eps, c.stage)
 
 
-def test_two_gloo_ranks_reproduce_the_single_process_run():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_reproduce_the_single_process_run(world):
+    """world = 3: slices of 32, 32 and 33 particles, rows migrating between every pair of ranks."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(timeout=180)
         assert p.exitcode == 0
-    got = sorted((q.get(timeout=10) for _ in range(2)), key=lambda d: d["rank"])
+    got = sorted((q.get(timeout=10) for _ in range(world)), key=lambda d: d["rank"])
     for d in got:
         assert d["same_history"] and d["same_status"], d
         assert d["same_theta"] and d["same_cache"] and d["same_u_slice"], d
