@@ -65,6 +65,8 @@ def parse():
                     help="rows of the GAM workload (smaller for profiling captures)")
     ap.add_argument("--gam-only", action="store_true",
                     help="run only the GAM gather leg and print its JSON (for profiling)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-posteriors leg and print its JSON (for profiling)")
     ap.add_argument("--profile-stages", type=int, default=0,
                     help="run only the first K stages of one run of the default workload with the "
                          "default kernels (no autotune), for ncu captures of a chosen stage")
@@ -518,9 +520,10 @@ def student_t_leg(S, dev, R=5, max_stages=200, N=280, seeds=3):
 
 def batch_leg(S, dev, P=64, stages=5, warmup=3):
     """Batched uneven posteriors: 64 logistic/probit problems (n log-uniform in [1e4, 1e6], p in
-    5..40, N = 1024 each, m = clamp(ceil(n/1000), 100, 1000), G = 10, L = 20, R = 5), all
-    particles of all problems in one u-update and one HMC launch per move, the whole batch stage
-    replayed as one CUDA graph; tile from the batch autotuner."""
+    5..40, N = 1024 each, m = clamp(ceil(n/1000), 100, 1000), G = 10, L = 20, R = 5): the stage
+    steps of all problems in shared launches, per move one u-update launch over all particles and
+    one trajectory launch per tile group; timed as graph-replayed stages and launch by launch;
+    estimator tile from the batch autotuner."""
     import torch
     from smc_workloads import batch_uneven
     t0 = time.perf_counter()
@@ -930,6 +933,12 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps(gather_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0),
                                     peaks()[0], tile_hint=args.gather_tile)), flush=True)
+        return
+    if args.batch_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(batch_leg(__import__("paper_1805_03317_gb300"), torch.device("cuda", 0))),
+              flush=True)
         return
     if args.gam_only:
         import torch
