@@ -14,8 +14,6 @@ namespace subsmc {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum_d(double v) { return warp_sum(v); }
-
 // Block-wide sum of one double (blockDim.x <= 1024). Result valid on every thread.
 __device__ double block_sum(double v, double *red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
