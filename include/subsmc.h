@@ -163,8 +163,13 @@ const char *smc_last_error(const smc_ctx *ctx);
  * With smc_config.cv_centre = 1 the control variates then move to the reweighted particle mean
  * (Algorithm 2 (d)); with cv_centre = 2 they move to the current weighted mean before the
  * reweighting. Either way A, B, C, the row constants and every particle's cached l_hat and
- * sigma2_hat are recomputed, stream-ordered (no host synchronisation).
- * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS. */
+ * sigma2_hat are recomputed, stream-ordered (no host synchronisation). The temperature search and
+ * the reweighting run as one launch whose blocks wait for each other between phases (at most 152
+ * blocks, all resident at once); a wait that does not end within about 2 s is reported as
+ * SMC_ERR_TIMEOUT, and the context stays usable. Contexts that belong to a batch use one launch
+ * per phase instead.
+ * Host outputs (any may be NULL): the new temperature, the log-evidence increment and the ESS;
+ * with all three NULL nothing synchronises with the host and errors surface at the next read. */
 int smc_reweight(smc_ctx *ctx, double *a_next, double *log_z_inc, double *ess);
 
 /* Step (e): resampling with the current weights, carrying theta, u and the cached estimates; then
