@@ -677,8 +677,8 @@ def gpu_arm(args):
     # memory. It reads X once per trajectory and then runs L+1 estimator passes out of shared
     # memory, so it is bound by the FP32/integer issue rate, not by HBM: bound "alu" against the
     # FP32 peak 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz. Algorithmic FLOPs per particle-row
-    # evaluation: 8p (the survey's count: x'theta, x'theta_bar, sum r x, sum d r x; the second is
-    # cached per row here, the count is kept).
+    # evaluation: 8p, the four length-p products of a row (x'theta, x'theta_bar, sum r x,
+    # sum d r x); the second is cached per row here, but the count keeps it.
     hbm, peak_kind = peaks()
     n_h, ms_h = prof["hmc"]
     units_launch = (wl.L + 1) * wl.N * wl.m
