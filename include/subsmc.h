@@ -283,7 +283,9 @@ int smc_set_scalars(smc_ctx *ctx, int32_t stage, double a, double eps, double lo
 
 /* Time the estimator's compiled tile shapes on this context's own particles and keep the fastest;
  * then time the HMC trajectory kernels (streamed, and every resident tile that fits) on scratch
- * copies of the particles and keep the fastest. The particle state is not changed.
+ * copies of the particles. The default trajectory kernel (the narrowest resident tile, with the
+ * warps per CTA chosen by p and m) is kept unless another one is more than 3% faster, since
+ * near-equal kernels trade places by timing noise. The particle state is not changed.
  * Host outputs (may be NULL): the estimator tile as a tile_hint value (>= 1) and the HMC kernel as
  * an hmc_kernel value (1 = streamed, >= 2 = resident tile). */
 int smc_autotune(smc_ctx *ctx, int32_t *tile, int32_t *hmc_kernel);
@@ -385,9 +387,11 @@ int smc_resample_noalloc(int32_t N, const double *W, uint64_t seed, int32_t stag
 /* Many independent problems (uneven n and p; BF16 storage) stepped together. One context per
  * problem, created as by smc_init with cfgs[q] (all on the same stream; the estimator tile is
  * the narrowest compiled tile that covers the widest row). The trajectories run in groups: each
- * problem goes to the narrowest resident tile (subsample kept in shared memory, 4 warps) that
- * takes its p, m and G, unless cfgs[q].hmc_kernel = 1 asks for the streamed kernel; problems no
- * resident tile takes (p > 40) and random-walk problems form the streamed group. */
+ * problem goes to the narrowest resident tile (subsample kept in shared memory) that takes its
+ * p, m and G, with one, two or four warps per CTA chosen by p and m (one warp for small
+ * subsamples, four for large ones), unless cfgs[q].hmc_kernel = 1 asks for the streamed kernel;
+ * problems no resident tile takes (p > 40) and random-walk problems form the streamed group.
+ * Problems that share a tile and a warp count share one trajectory launch per move. */
 typedef struct smc_batch smc_batch;
 int smc_batch_init(smc_batch **out, int32_t P, const smc_problem *probs, const smc_config *cfgs,
                    void *stream);
@@ -413,8 +417,10 @@ int64_t smc_batch_launch_count(const smc_batch *b);
  * stage index from device counters), with results bit-identical to use_graph = 0 and to stepping
  * each problem alone with the same tiles (smc_batch_tile, smc_batch_hmc_kernel). */
 int smc_batch_stage(smc_batch *b, int32_t R, int32_t use_graph);
-/* Time the batched HMC launch for every compiled tile that covers the widest row (on scratch
- * copies; the state is unchanged) and keep the fastest; output: the tile as a tile_hint value. */
+/* Choose the batch's estimator tile: time the streamed batched trajectory launch over all problems
+ * for every compiled tile that covers the widest row (on scratch copies; the state is unchanged)
+ * and keep the fastest. The tile serves the u-update launch and the streamed group; the resident
+ * groups keep their tiles. Output: the tile as a tile_hint value. */
 int smc_batch_autotune(smc_batch *b, int32_t *tile_hint);
 
 #ifdef __cplusplus
