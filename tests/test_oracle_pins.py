@@ -937,3 +937,33 @@ def test_move_margins_are_the_decisions_distance_from_the_threshold():
     acc = O.hmc_move(prob, m, G, seed, stage, 1, a, 2.5, 4, S, np.linalg.cholesky(S), th, us,
                      margins=mh)
     assert np.array_equal(mh > 0, acc.astype(bool)) and 0 < acc.sum() < N
+
+
+@pytest.mark.parametrize("fam", ["logistic", "probit", "poisson", "gaussian", "student_t"])
+def test_hmc_energy_error_is_second_order_in_the_step(fam):
+    """Leapfrog is a second-order integrator, so over a fixed trajectory time the change of the
+    Hamiltonian H = -log target + rho' Sigma rho / 2 shrinks by 4 each time the step is halved,
+    provided the force is the exact gradient of the log target that H uses (here a l_hat -
+    a^2 sigma2_hat / 2 + log p, at a = 0.8 so that the sigma2_hat term counts). A force that
+    missed a term, a wrong sign, the inverse mass matrix in place of Sigma, or a first-order
+    update would leave a ratio near 1 or 2. H1 - H0 is read from the move's MH margin
+    (H0 - H1 - log U) with log U rebuilt from the raw Philox stream; the step is fixed (no
+    jitter) and the same momentum is drawn at every step size."""
+    prob = tiny_problem(fam, n=200, p=3, seed=7)
+    N, m, G, seed, stage, a = 48, 40, 4, 13, 3, 0.8
+    th, us = O.init_particles(seed, N, 3, m, prob.n, prob.prior_mean, prob.prior_var)
+    th = prob.theta_bar + 0.15 * (th - prob.prior_mean) / np.sqrt(prob.prior_var)
+    S = np.diag([0.05, 0.03, 0.03])
+    Lc = np.linalg.cholesky(S)
+    sm = O.stage_move(stage, 0)
+    logU = np.log([O.uniform(O.r64(seed, O.TAG_MH_THETA, sm, i, 0)) for i in range(N)])
+    dH = []
+    for eps, L in [(0.04, 16), (0.02, 32), (0.01, 64)]:  # trajectory time 0.64 each
+        margin = np.zeros(N)
+        O.hmc_move(prob, m, G, seed, stage, 0, a, eps, L, S, Lc, th.copy(), us, jitter=-1.0,
+                   margins=margin)
+        dH.append(-(margin + logU))
+    assert np.abs(dH[-1]).max() > 1e-6  # far above rounding: the ratios below measure the method
+    for big, small in zip(dH[:-1], dH[1:]):
+        assert 3.9 < np.abs(big).sum() / np.abs(small).sum() < 4.1
+        assert 3.9 < np.median(big / small) < 4.1
