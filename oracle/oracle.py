@@ -89,6 +89,8 @@ def lib():
                                               _dp, _i64p, _i32p]
             L.orc_rw_move.argtypes = prob + [c_i, c_u64, c_u32, c_d, c_d, _dp, _dp, _i64p,
                                              _i32p]
+            L.orc_leapfrog.argtypes = prob + [_i64p, c_d, c_d, c_i, _dp, _dp, _dp]
+            L.orc_leapfrog.restype = c_d
             L.orc_ess_at.argtypes = [c_i, _dp, _dp, _dp, c_d, c_d]
             L.orc_ess_at.restype = c_d
             L.orc_reweight.argtypes = [c_i, _dp, _dp, _dp, _dp, c_d, c_d, c_i, c_i,
@@ -348,6 +350,16 @@ def hmc_move(prob, m, G, seed, stage, move, a, eps, L, Sigma, Lc, thetas, us, ji
                            np.ascontiguousarray(Lc, np.float64), thetas,
                            np.ascontiguousarray(us, np.int64), acc)
     return acc
+
+
+def leapfrog(prob, m, G, u, a, eps, L, Sigma, theta, rho):
+    """One leapfrog trajectory of the HMC move (the same routine the move runs) from (theta, rho)
+    at fixed u: returns (theta_L, rho_L, log target at theta_L). Test support."""
+    th = np.array(theta, dtype=np.float64)
+    r = np.array(rho, dtype=np.float64)
+    lt = lib().orc_leapfrog(*prob.args(m, G), np.ascontiguousarray(u, np.int64), a, eps, L,
+                            np.ascontiguousarray(Sigma, np.float64), th, r)
+    return th, r, lt
 
 
 def rw_move(prob, m, G, seed, stage, move, a, eps, Lc, thetas, us):

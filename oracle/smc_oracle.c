@@ -447,6 +447,45 @@ void orc_upm_move(int fam, int64_t n, int p, const double *X, const double *y, d
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Lsteps leapfrog steps of size eps for the Hamiltonian -log target(theta) + rho' Sigma rho / 2  */
+/* at fixed u (Algorithm 1 step 2): half kick with the gradient, drift by eps Sigma rho, gradient */
+/* at the new point, half kick. On entry g holds the gradient at th and lt the log target there; */
+/* th, rho and g are updated in place, v is scratch [p]. Returns the log target at the end.       */
+/* ------------------------------------------------------------------------------------------ */
+static double leapfrog(const orc_prob *P, const int64_t *u, double a, double eps, int Lsteps,
+                       const double *Sigma, double *th, double *rho, double *g, double *v,
+                       double lt) {
+  const int p = P->p;
+  for (int l = 0; l < Lsteps; ++l) {
+    for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps * g[c];
+    for (int r = 0; r < p; ++r) {
+      v[r] = 0.0;
+      for (int c = 0; c < p; ++c) v[r] += Sigma[r * p + c] * rho[c];
+    }
+    for (int c = 0; c < p; ++c) th[c] += eps * v[c];
+    lt = log_target(P, u, th, a, g);
+    for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps * g[c];
+  }
+  return lt;
+}
+
+/* Test support: one trajectory of the leapfrog above from (theta, rho), both updated in place;
+ * returns the log target at the end point. */
+double orc_leapfrog(int fam, int64_t n, int p, const double *X, const double *y, double sigma,
+                    const double *tb, double A, const double *B, const double *C, const double *pm,
+                    const double *pv, int m, int G, const int64_t *u, double a, double eps,
+                    int Lsteps, const double *Sigma, double *theta, double *rho) {
+  orc_prob P = make_prob(fam, n, p, X, y, sigma, tb, A, B, C, pm, pv, m, G);
+  double *g = (double *)malloc(sizeof(double) * p);
+  double *v = (double *)malloc(sizeof(double) * p);
+  double lt = log_target(&P, u, theta, a, g);
+  lt = leapfrog(&P, u, a, eps, Lsteps, Sigma, theta, rho, g, v, lt);
+  free(g);
+  free(v);
+  return lt;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* HMC move of theta given u (Algorithm 1 step 2): momentum rho ~ N(0, H) with mass matrix         */
 /* H = Sigma^{-1} (Algorithm 2 step (d)), drawn as rho = L^{-T} z with Sigma = L L'; L leapfrog     */
 /* steps of size eps on the annealed log target; MH accept with the Hamiltonian difference.       */
@@ -490,16 +529,7 @@ void orc_hmc_move(int fam, int64_t n, int p, const double *X, const double *y, d
       double Uj = orc_uniform(orc_r64(seed, TAG_MH_THETA, stage_move, (uint32_t)i, 1));
       eps_i = eps * (1.0 - jitter + 2.0 * jitter * Uj);
     }
-    for (int l = 0; l < Lsteps; ++l) {
-      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps_i * g[c];
-      for (int r = 0; r < p; ++r) {
-        v[r] = 0.0;
-        for (int c = 0; c < p; ++c) v[r] += Sigma[r * p + c] * rho[c];
-      }
-      for (int c = 0; c < p; ++c) th[c] += eps_i * v[c];
-      lt = log_target(&P, u, th, a, g);
-      for (int c = 0; c < p; ++c) rho[c] += 0.5 * eps_i * g[c];
-    }
+    lt = leapfrog(&P, u, a, eps_i, Lsteps, Sigma, th, rho, g, v, lt);
     double kin1 = 0.0;
     for (int r = 0; r < p; ++r)
       for (int c = 0; c < p; ++c) kin1 += 0.5 * rho[r] * Sigma[r * p + c] * rho[c];

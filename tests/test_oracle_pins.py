@@ -967,3 +967,34 @@ def test_hmc_energy_error_is_second_order_in_the_step(fam):
     for big, small in zip(dH[:-1], dH[1:]):
         assert 3.9 < np.abs(big).sum() / np.abs(small).sum() < 4.1
         assert 3.9 < np.median(big / small) < 4.1
+
+
+@pytest.mark.parametrize("fam", ["logistic", "probit", "poisson", "gaussian", "student_t"])
+def test_leapfrog_is_reversible_and_volume_preserving(fam):
+    """The two properties that make the HMC move's acceptance ratio (Algorithm 1 step 2) the
+    Hamiltonian difference alone, checked on the move's own leapfrog routine: L steps from
+    (theta, rho), then L steps from the end point with the momentum negated, return to
+    (theta, -rho) up to rounding (time reversibility); and the Jacobian of the map
+    (theta, rho) -> (theta_L, rho_L), by central differences, has determinant 1 (volume
+    preservation). A non-symmetric step (a full first kick, a missing last half kick) fails the
+    first."""
+    prob = tiny_problem(fam, n=200, p=3, seed=7)
+    m, G, a, eps, L = 40, 4, 0.8, 0.05, 12
+    _, us = O.init_particles(17, 1, 3, m, prob.n, prob.prior_mean, prob.prior_var)
+    rng = np.random.default_rng(5)
+    theta = prob.theta_bar + 0.1 * rng.standard_normal(3)
+    S = np.array([[0.05, 0.01, 0.0], [0.01, 0.03, 0.005], [0.0, 0.005, 0.03]])
+    rho = np.linalg.solve(np.linalg.cholesky(S).T, rng.standard_normal(3))  # N(0, S^-1)
+    th1, r1, _ = O.leapfrog(prob, m, G, us[0], a, eps, L, S, theta, rho)
+    assert np.linalg.norm(th1 - theta) > 0.02  # the trajectory went somewhere
+    th2, r2, _ = O.leapfrog(prob, m, G, us[0], a, eps, L, S, th1, -r1)
+    np.testing.assert_allclose(th2, theta, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(-r2, rho, rtol=0, atol=1e-10 * np.abs(rho).max())
+
+    def flow(z):
+        t, r, _ = O.leapfrog(prob, m, G, us[0], a, eps, L, S, z[:3], z[3:])
+        return np.concatenate([t, r])
+
+    z0, h = np.concatenate([theta, rho]), 1e-6
+    J = np.column_stack([(flow(z0 + h * e) - flow(z0 - h * e)) / (2 * h) for e in np.eye(6)])
+    assert abs(np.linalg.det(J) - 1.0) < 1e-6
