@@ -504,22 +504,44 @@ def test_hmc_leaves_exact_posterior_invariant():
     assert np.all(np.abs(z.var(axis=0) - 1.0) < 5 * math.sqrt(2.0 / N))
 
 
+def _conjugate_tempered_log_z(prob, a):
+    """log of the integral of p(y | theta)^a p(theta) for the conjugate Gaussian model (prior
+    N(0, tau2 I)), in closed form: with Lam = a X'X / s^2 + I / tau2 and b = a X'y / s^2,
+    -(a n / 2) log 2 pi s^2 - log det(tau2 Lam) / 2 + b' Lam^-1 b / 2 - a y'y / (2 s^2)."""
+    X, y, s2, tau2 = prob.X, prob.y, prob.sigma ** 2, prob.prior_var[0]
+    n, p = X.shape
+    lam = a * X.T @ X / s2 + np.eye(p) / tau2
+    b = a * X.T @ y / s2
+    return (-0.5 * a * n * math.log(2 * math.pi * s2) - 0.5 * np.linalg.slogdet(tau2 * lam)[1]
+            + 0.5 * b @ np.linalg.solve(lam, b) - a * (y @ y) / (2 * s2))
+
+
 def test_smc_recovers_conjugate_posterior_and_log_marginal():
     """Averaged over 8 seeded runs (the paper repeats each run 10 times for its standard errors):
-    single-run log-ML sd is about 0.13 at N=1024, so the mean is held to 0.15."""
+    single-run log-ML sd is about 0.13 at N=1024, so the mean is held to 0.15. The running sum of
+    the stage increments (Sec. 3.5) is also held, stage by stage, to the closed-form log evidence
+    of the tempered posterior at that stage's temperature."""
     prob, mu, S, logml = _conjugate()
     prob.set_centre(mu)
-    errs, means = [], []
+    assert _conjugate_tempered_log_z(prob, 1.0) == pytest.approx(logml, abs=1e-9)
+    assert _conjugate_tempered_log_z(prob, 0.0) == pytest.approx(0.0, abs=1e-12)
+    errs, means, path_errs = [], [], []
     for seed in range(1, 9):
         cfg = O.SMCConfig(N=1024, m=8, G=2, L=8, R=3, seed=seed, tau=0.5)
         st = O.smc_run(prob, cfg)
         assert st.a == 1.0 and st.stage >= 2
         errs.append(st.log_z - logml)
         means.append(st.thetas.mean(axis=0))
+        running = np.cumsum([h["log_z_inc"] for h in st.history])
+        path_errs.append([z - _conjugate_tempered_log_z(prob, h["a"])
+                          for z, h in zip(running, st.history)])
     sd = np.sqrt(np.diag(S))
     assert np.all(np.abs(np.mean(means, axis=0) - mu) < 0.05 * sd)
     assert abs(np.mean(errs)) < 0.15
     assert np.max(np.abs(errs)) < 0.6
+    k = min(len(e) for e in path_errs)
+    assert np.all(np.abs(np.mean([e[:k] for e in path_errs], axis=0)) < 0.1)
+    assert max(np.max(np.abs(e)) for e in path_errs) < 0.5
 
 
 @pytest.mark.parametrize("fam", ["logistic", "poisson", "probit"])
